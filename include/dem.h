@@ -1,0 +1,241 @@
+/*
+ * dem.h -- C ABI of the GB300 clump-of-spheres DEM library (libdem.so).
+ *
+ * The library runs the hot path of the discrete element method of
+ * arXiv 2307.03445 on one GPU: contact detection with an enlarged geometry
+ * (section 2.2), the Hertz-Mindlin contact law with persistent tangential
+ * history (section 2.1, Eq. (1)-(4)), the reduction of sphere forces to their
+ * clump and the explicit integration of the clumps (Eq. (5)).
+ *
+ * Conventions for every entry point:
+ *   - the return value is DEM_OK (0) or a negative DEM_ERR_* code; nothing
+ *     throws across this boundary; dem_last_error() describes the last failure;
+ *   - input arrays are plain host pointers (unless a call says otherwise),
+ *     are read during the call only and stay owned by the caller;
+ *   - output arrays are caller-owned buffers of the stated size;
+ *   - a context is bound to one CUDA device and one stream, and is used by one
+ *     host thread at a time;
+ *   - units are SI; quaternions are (w, x, y, z) and unit length; angular
+ *     velocities are in the world frame.
+ * Equation numbers refer to the paper's section 2.1 in reading order:
+ * Eq. (1a)-(1e) contact forces, (2a)-(2c) contact kinematics, (3) tangential
+ * micro-displacement update, (4) its cap, (5a)-(5b) equations of motion.
+ */
+#ifndef DEM_H
+#define DEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define DEM_OK 0
+#define DEM_ERR_INVALID_ARG (-1) /* bad pointer, size, enum or value          */
+#define DEM_ERR_OOM (-2)         /* device allocation failed                  */
+#define DEM_ERR_CAPACITY (-3)    /* a list outgrew max_contacts               */
+#define DEM_ERR_NONFINITE (-4)   /* a NaN/Inf appeared in the state           */
+#define DEM_ERR_TIMEOUT (-5)     /* a bounded device wait ran out             */
+#define DEM_ERR_CUDA (-6)        /* any other CUDA runtime error              */
+#define DEM_ERR_STATE (-7)       /* call out of order (e.g. no templates)     */
+#define DEM_ERR_GUARD (-8)       /* a list failed its validity check and no   */
+                                 /* recovery was configured                   */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum { DEM_FP64 = 0, DEM_FP32_VOXEL = 1 };
+enum { DEM_WALL_PLANE = 0, DEM_WALL_CYLINDER = 1, DEM_WALL_CONE = 2 };
+enum { DEM_MIX_MEAN = 0, DEM_MIX_MIN = 1, DEM_MIX_MAX = 2 };
+enum { DEM_MARGIN_FIXED = 0, DEM_MARGIN_LEARNED = 1 };
+enum { DEM_GUARD_OFF = 0, DEM_GUARD_COUNT = 1, DEM_GUARD_ROLLBACK = 2 };
+
+/* An analytic boundary with a prescribed translation (section 4 uses meshes
+ * for funnels, cones and wheels; the library offers analytic stand-ins).
+ *   PLANE:    p = a point, n = unit normal pointing towards the grains.
+ *   CYLINDER: p = a point on the axis, n = unit axis, radius; grains inside.
+ *   CONE:     p = tip, n = unit axis from the tip towards the base,
+ *             half_angle [rad], height (tip to base); grains outside the solid.
+ * The surface moves with velocity vel: its reference point at time t is
+ * p + vel * t.  material indexes the material table.  scene = -1 applies the
+ * wall to every scene, otherwise to one scene. */
+typedef struct {
+    int type;
+    int material;
+    double p[3];
+    double n[3];
+    double radius;
+    double half_angle;
+    double height;
+    double vel[3];
+    int scene;
+} dem_wall;
+
+/* Creation parameters.  Arrays are copied by dem_create. */
+typedef struct {
+    double dt;                /* time step h [s] (> 0)                               */
+    double g[3];              /* gravity [m/s^2]                                      */
+    double domain_lo[3];      /* detection domain of scene 0 [m]; spheres outside it  */
+    double domain_hi[3];      /*   are binned into the boundary bins (still detected)  */
+    int precision;            /* DEM_FP64 or DEM_FP32_VOXEL                           */
+    double bin_size;          /* bin edge [m]; 0 = twice the largest enlarged radius  */
+    int margin_policy;        /* DEM_MARGIN_FIXED | DEM_MARGIN_LEARNED                */
+    int rebuild_interval;     /* K: list rebuilt every K steps (>= 1)                 */
+    double v_bound;           /* speed bound [m/s]; margin = v_bound * dt * K ...      */
+    double margin;            /* ... unless margin > 0, which sets it directly [m]    */
+    int mix_rule;             /* how mu and CoR of two spheres combine: DEM_MIX_*     */
+    int n_materials;          /* >= 1                                                  */
+    const double* E;          /* Young's modulus per material [Pa]                    */
+    const double* nu;         /* Poisson ratio                                         */
+    const double* mu;         /* friction coefficient                                  */
+    const double* cor;        /* coefficient of restitution in [0, 1]                  */
+    int n_walls;
+    const dem_wall* walls;
+    long long max_contacts;   /* cap on listed pairs; 0 = no cap (grows on demand)    */
+    int guard;                /* DEM_GUARD_*: what a failed validity check does        */
+    void* cuda_stream;        /* cudaStream_t to run on; NULL = the library's own     */
+    int device;               /* CUDA device ordinal                                   */
+    /* Optional device allocator (e.g. a framework's caching allocator); both
+     * NULL = cudaMallocAsync / cudaFreeAsync on the context stream. */
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* alloc_user;
+} dem_params;
+
+/* Counters and timings since creation (or the last dem_reset_stats). */
+typedef struct {
+    long long steps;            /* force steps taken                               */
+    long long rebuilds;         /* contact-list rebuilds                           */
+    long long n_clumps, n_spheres;
+    long long n_pairs;          /* listed sphere-sphere pairs (current list)       */
+    long long n_wall_contacts;  /* listed sphere-wall contacts (current list)      */
+    long long bin_entries;      /* (bin, sphere) registrations of the last rebuild */
+    long long pair_steps;       /* sum over steps of listed pairs + wall contacts  */
+    long long active_last;      /* contacts with delta_n > 0 in the last step      */
+    long long guard_violations; /* steps whose list failed the validity check      */
+    long long rollbacks;        /* rollbacks to the last snapshot                   */
+    long long missed_contacts;  /* touching contacts found missing by audits        */
+    double margin;              /* current margin [m] (fixed policy)               */
+    double time;                /* simulated time [s]                               */
+    /* device time per phase [ms], accumulated while timing is on: list
+     * rebuilds, sphere-sphere force kernel, sphere-wall force kernel, clump
+     * update kernel; timed_steps counts the steps these cover. */
+    double ms_detect, ms_pairs, ms_walls, ms_update;
+    long long timed_steps;
+    long long launches;         /* kernels this library launched                    */
+} dem_stats;
+
+typedef struct dem_ctx dem_ctx;
+
+/* Creates a context.  Validates the parameters (DEM_ERR_INVALID_ARG), selects
+ * params->device, copies the material table and walls, precomputes the pair
+ * material table (section 2.1: pair stiffness and damping from each sphere's
+ * E, nu, mu, CoR).  *out receives the context, or NULL on failure. */
+int dem_create(const dem_params* params, dem_ctx** out);
+
+/* Frees every device and host resource of the context.  NULL is accepted. */
+void dem_destroy(dem_ctx* ctx);
+
+/* Text of the last error on this context (or of the last failed dem_create
+ * when ctx is NULL).  Valid until the next call on the context. */
+const char* dem_last_error(const dem_ctx* ctx);
+
+/* Loads the clump templates (section 2.1: a clump is a rigid union of
+ * possibly overlapping spheres, each with its own material).
+ *   n_tpl           number of templates (>= 1)
+ *   sphere_offsets  n_tpl + 1 ints; template t owns spheres [off[t], off[t+1])
+ *   local_pos       3 * S doubles: sphere centres in the template's principal
+ *                   frame, centre of mass at the origin (S = off[n_tpl])
+ *   radius          S doubles (> 0)
+ *   material        S ints in [0, n_materials)
+ *   mass            n_tpl doubles (> 0)
+ *   inertia         3 * n_tpl doubles: principal moments (> 0)
+ * Must precede dem_add_clumps; may be called once. */
+int dem_load_clump_templates(dem_ctx* ctx, int n_tpl, const int* sphere_offsets,
+                             const double* local_pos, const double* radius,
+                             const int* material, const double* mass,
+                             const double* inertia);
+
+/* Adds a scene (an independent system sharing the templates, materials, dt
+ * and g) with its own detection domain and bin size; scene 0 exists from
+ * dem_create.  *scene_id receives the new id.  Bodies of different scenes
+ * never interact.  Must precede the first dem_add_clumps into that scene. */
+int dem_add_scene(dem_ctx* ctx, const double lo[3], const double hi[3], double bin_size,
+                  int* scene_id);
+
+/* Appends n clumps to a scene.
+ *   tpl    n ints, template ids
+ *   pos    3n doubles, centre of mass [m]
+ *   quat   4n doubles, unit quaternions (w, x, y, z)
+ *   vel    3n doubles [m/s]; angvel 3n doubles [rad/s], world frame
+ * Clump i receives id (number of clumps before the call) + i; its spheres are
+ * numbered consecutively in template order.  Rejects non-finite values. */
+int dem_add_clumps(dem_ctx* ctx, int n, const int* tpl, const double* pos,
+                   const double* quat, const double* vel, const double* angvel, int scene);
+
+/* Advances n_steps time steps: every step evaluates every listed contact
+ * (section 2.2: deferred list, false positives give zero force), reduces the
+ * forces and torques to the clumps and integrates Eq. (5); the list is
+ * rebuilt when the rebuild rule says so.  Synchronises the stream before
+ * returning and reports device-side failures (NONFINITE, CAPACITY, GUARD). */
+int dem_step(dem_ctx* ctx, int n_steps);
+
+/* Copies the clump state out.  on_device = 1: the four pointers are device
+ * pointers on the context's device; 0: host pointers.  Sizes as in
+ * dem_add_clumps, for all clumps in id order.  Any pointer may be NULL. */
+int dem_get_state(dem_ctx* ctx, double* pos, double* quat, double* vel, double* angvel,
+                  int on_device);
+
+/* Overwrites the state of all clumps (host pointers, same layout as
+ * dem_get_state).  The next step rebuilds the list; tangential history is kept
+ * for pairs that stay listed. */
+int dem_set_state(dem_ctx* ctx, const double* pos, const double* quat, const double* vel,
+                  const double* angvel);
+
+int dem_get_stats(dem_ctx* ctx, dem_stats* out);
+int dem_reset_stats(dem_ctx* ctx);
+/* timing = 1 records CUDA events around each phase of every step on the
+ * context stream; they are read once at the end of each dem_step call, so
+ * the steps themselves are not serialised. */
+int dem_set_timing(dem_ctx* ctx, int timing);
+
+/* ---- inspection (tests, tools) ----------------------------------------- */
+
+/* Rebuilds the contact list now from the current state (section 2.2), keeping
+ * the tangential history of pairs present before and after. */
+int dem_rebuild(dem_ctx* ctx);
+
+/* Evaluates the contact forces of the current state with the current list
+ * (rebuilding first if none exists) without integrating or advancing time;
+ * updates the tangential history exactly as a step would.  The per-clump
+ * totals are then readable with dem_get_forces. */
+int dem_eval_forces(dem_ctx* ctx);
+
+/* Net contact force and torque per clump from the last dem_eval_forces
+ * (3 * n_clumps doubles each, host buffers).  Torque about the clump CoM. */
+int dem_get_forces(dem_ctx* ctx, double* force, double* torque);
+
+/* Net force on each wall from the last force evaluation (3 * n_walls). */
+int dem_get_wall_forces(dem_ctx* ctx, double* force);
+
+/* Sizes of the current lists. */
+int dem_num_contacts(dem_ctx* ctx, long long* n_pairs, long long* n_wall);
+
+/* Copies the current lists (host buffers sized by dem_num_contacts): pairs
+ * (a < b, sphere ids, sorted by (a, b)) with their tangential history u
+ * (3 doubles each), and sphere-wall contacts (sphere, wall) with history. */
+int dem_get_contacts(dem_ctx* ctx, int* a, int* b, double* u, int* wall_sphere, int* wall_id,
+                     double* wall_u);
+
+/* Bin registrations of the last rebuild sorted by (bin key, sphere id):
+ * keys/ids hold up to cap entries; *n receives the total. */
+int dem_get_bins(dem_ctx* ctx, long long cap, unsigned int* keys, int* ids, long long* n);
+
+/* The exact missed-contact check: a fresh zero-margin detection of the
+ * current state compared with the current list.  *missed receives the number
+ * of touching sphere pairs and sphere-wall contacts that are not listed. */
+int dem_audit(dem_ctx* ctx, long long* missed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

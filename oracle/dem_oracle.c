@@ -443,7 +443,7 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
                      const double* quat, const double* vel, const double* angvel,
                      double t, long long np, const int* pa, const int* pb, double* up,
                      long long nw, const int* ws, const int* ww, double* uw, double* F,
-                     double* T, double* Fw) {
+                     double* T, double* Fw, double* mag) {
     const long long ns = orc_num_spheres(m, n, tpl);
     double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)(ns + 1));
     int* owner = (int*)malloc(sizeof(int) * (size_t)(ns + 1));
@@ -451,6 +451,7 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
     orc_sphere_centres(m, n, tpl, pos, quat, xs, owner, tsph);
     for (long long i = 0; i < 3LL * n; ++i) { F[i] = 0.0; T[i] = 0.0; }
     if (Fw) for (int i = 0; i < 3 * m->n_walls; ++i) Fw[i] = 0.0;
+    if (mag) for (long long i = 0; i < 2LL * n; ++i) mag[i] = 0.0;
     long long active = 0;
     for (long long c = 0; c < np; ++c) {
         const int a = pa[c], b = pb[c];
@@ -464,10 +465,13 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
                               0.0, up + 3 * c, f, ca, cb);
         double tq[3], mf[3] = {-f[0], -f[1], -f[2]};
         for (int k = 0; k < 3; ++k) { F[3 * B + k] += f[k]; F[3 * A + k] -= f[k]; }
+        const double fl = sqrt(dot3(f, f));
         cross3(cb, f, tq);
         for (int k = 0; k < 3; ++k) T[3 * B + k] += tq[k];
+        if (mag) { mag[2 * B] += fl; mag[2 * B + 1] += sqrt(dot3(cb, cb)) * fl; }
         cross3(ca, mf, tq);
         for (int k = 0; k < 3; ++k) T[3 * A + k] += tq[k];
+        if (mag) { mag[2 * A] += fl; mag[2 * A + 1] += sqrt(dot3(ca, ca)) * fl; }
     }
     for (long long c = 0; c < nw; ++c) {
         const int s = ws[c], k0 = ww[c];
@@ -485,6 +489,10 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
         for (int k = 0; k < 3; ++k) F[3 * A + k] -= f[k];
         cross3(ca, mf, tq);
         for (int k = 0; k < 3; ++k) T[3 * A + k] += tq[k];
+        if (mag) {
+            mag[2 * A] += sqrt(dot3(f, f));
+            mag[2 * A + 1] += sqrt(dot3(ca, ca)) * sqrt(dot3(f, f));
+        }
         if (Fw) for (int k = 0; k < 3; ++k) Fw[3 * k0 + k] += f[k];
     }
     free(xs);
@@ -671,7 +679,7 @@ long long orc_sim_step(orc_sim* s, int nsteps, int audit) {
         const double t = (double)s->step * s->m.h;
         s->active = orc_forces(&s->m, s->n, s->tpl, s->pos, s->quat, s->vel, s->angvel, t,
                                s->np, s->pa, s->pb, s->up, s->nw, s->ws, s->ww, s->uw, s->F,
-                               s->T, NULL);
+                               s->T, NULL, NULL);
         orc_integrate(&s->m, s->n, s->tpl, s->pos, s->quat, s->vel, s->angvel, s->F, s->T);
         s->step += 1;
         s->since += 1;

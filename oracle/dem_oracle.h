@@ -102,12 +102,15 @@ int orc_contact(const orc_model* m, int mat_a, int mat_b, const double xa[3],
 
 /* Forces and torques on every clump for one step (contacts given).  The
  * history arrays are updated in place.  F, T: 3 * n.  Fw: 3 * n_walls or NULL.
+ * mag: 2 * n or NULL; receives, per clump, the sums over its contacts of |F|
+ * and of |lever arm| * |F| (the scales that bound the rounding of the force
+ * and torque totals, including the cancellation inside each cross product).
  * Returns the number of active contacts. */
 long long orc_forces(const orc_model* m, int n, const int* tpl, const double* pos,
                      const double* quat, const double* vel, const double* angvel,
                      double t, long long np, const int* pa, const int* pb, double* up,
                      long long nw, const int* ws, const int* ww, double* uw, double* F,
-                     double* T, double* Fw);
+                     double* T, double* Fw, double* mag);
 
 /* Explicit integration of Eq. (5) for every clump, in place. */
 void orc_integrate(const orc_model* m, int n, const int* tpl, double* pos, double* quat,

@@ -1,0 +1,226 @@
+"""GB300 clump-of-spheres DEM (arXiv 2307.03445 hot path) -- Python binding.
+
+The binding marshals numpy arrays and torch device pointers into the C ABI of
+libdem.so (include/dem.h); every step of the method runs in the CUDA kernels.
+
+    from paper_2307_03445_gb300 import Simulation, scenes
+    sc = scenes.config1()
+    sim = Simulation(sc, margin=5e-5, rebuild_interval=10)
+    sim.step(1000)
+    pos, quat, vel, angvel = sim.state()
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import capi
+from .capi import (DEM_FP32_VOXEL, DEM_FP64, DEM_GUARD_COUNT, DEM_GUARD_OFF,
+                   DEM_GUARD_ROLLBACK, DemError)
+
+__all__ = ["Simulation", "DemError", "DEM_FP64", "DEM_FP32_VOXEL", "DEM_GUARD_OFF",
+           "DEM_GUARD_COUNT", "DEM_GUARD_ROLLBACK", "load_library"]
+
+
+def load_library():
+    return capi.load()
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _pd(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _pi(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def walls_to_c(walls, scene_of=None):
+    arr = (capi.DemWall * max(1, len(walls)))()
+    for i, w in enumerate(walls):
+        arr[i].type = int(w["type"])
+        arr[i].material = int(w.get("material", 0))
+        for k in range(3):
+            arr[i].p[k] = float(w["p"][k])
+            arr[i].n[k] = float(w["n"][k])
+            arr[i].vel[k] = float(w.get("vel", (0.0, 0.0, 0.0))[k])
+        arr[i].radius = float(w.get("radius", 0.0))
+        arr[i].half_angle = float(w.get("half_angle", 0.0))
+        arr[i].height = float(w.get("height", 0.0))
+        arr[i].scene = int(w.get("scene", -1)) if scene_of is None else int(scene_of[i])
+    return arr
+
+
+class Simulation:
+    """One context of libdem.so holding one or more scenes.
+
+    scene: a ``scenes.Scene`` (templates, materials, walls, world, clumps).
+    margin: enlargement of every sphere for the contact list [m]; if None,
+        v_bound * dt * rebuild_interval.
+    extra_scenes: further Scene objects sharing templates/materials/dt/g with
+        the first one (batched independent systems).
+    """
+
+    def __init__(self, scene, margin=None, rebuild_interval=10, v_bound=0.5, precision=None,
+                 guard=DEM_GUARD_COUNT, device=0, stream=None, bin_size=None, max_contacts=0,
+                 extra_scenes=(), extra_walls=()):
+        self.lib = capi.load()
+        self.scene = scene
+        prec = scene.precision if precision is None else precision
+        self._keep = []
+        p = capi.DemParams()
+        p.dt = float(scene.h)
+        for k in range(3):
+            p.g[k] = float(scene.g[k])
+            p.domain_lo[k] = float(scene.lo[k])
+            p.domain_hi[k] = float(scene.hi[k])
+        p.precision = int(prec)
+        p.bin_size = float(bin_size if bin_size is not None else (scene.bin_size or 0.0))
+        p.margin_policy = 0
+        p.rebuild_interval = int(rebuild_interval)
+        p.v_bound = float(v_bound)
+        p.margin = float(margin) if margin is not None else 0.0
+        p.mix_rule = int(getattr(scene, "mix_rule", 0))
+        mats = [_f64(getattr(scene, k)) for k in ("E", "nu", "mu", "cor")]
+        self._keep += mats
+        p.n_materials = len(mats[0])
+        p.E, p.nu, p.mu, p.cor = (_pd(m) for m in mats)
+        walls = [dict(w, scene=0) for w in scene.walls]
+        for si, sc2 in enumerate(extra_scenes, start=1):
+            walls += [dict(w, scene=si) for w in sc2.walls]
+        walls += list(extra_walls)
+        warr = walls_to_c(walls)
+        self._keep.append(warr)
+        p.n_walls = len(walls)
+        p.walls = C.cast(warr, C.POINTER(capi.DemWall))
+        p.max_contacts = int(max_contacts)
+        p.guard = int(guard)
+        p.cuda_stream = stream
+        p.device = int(device)
+        ctx = C.c_void_p()
+        rc = self.lib.dem_create(C.byref(p), C.byref(ctx))
+        if rc != 0:
+            raise DemError(rc, self.lib.dem_last_error(None).decode())
+        self.ctx = ctx
+        self._check(self.lib.dem_load_clump_templates(
+            ctx, len(scene.tpl_mass), _pi(_i32(scene.tpl_off)), _pd(_f64(scene.tpl_pos).reshape(-1)),
+            _pd(_f64(scene.tpl_rad)), _pi(_i32(scene.tpl_mat)), _pd(_f64(scene.tpl_mass)),
+            _pd(_f64(scene.tpl_inertia).reshape(-1))))
+        self.n_walls = len(walls)
+        self.scene_ids = [0]
+        for sc2 in extra_scenes:
+            sid = C.c_int()
+            lo, hi = _f64(sc2.lo), _f64(sc2.hi)
+            self._check(self.lib.dem_add_scene(ctx, _pd(lo), _pd(hi),
+                                               float(sc2.bin_size or p.bin_size), C.byref(sid)))
+            self.scene_ids.append(sid.value)
+        self.n = 0
+        if scene.tpl is not None and len(scene.tpl):
+            self.add_clumps(scene.tpl, scene.pos, scene.quat, scene.vel, scene.angvel, 0)
+        for sid, sc2 in zip(self.scene_ids[1:], extra_scenes):
+            self.add_clumps(sc2.tpl, sc2.pos, sc2.quat, sc2.vel, sc2.angvel, sid)
+
+    # ------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise DemError(rc, self.lib.dem_last_error(self.ctx).decode())
+
+    def add_clumps(self, tpl, pos, quat, vel, angvel, scene=0):
+        tpl = _i32(tpl)
+        arr = [_f64(a) for a in (pos, quat, vel, angvel)]
+        self._check(self.lib.dem_add_clumps(self.ctx, len(tpl), _pi(tpl), *(_pd(a) for a in arr),
+                                            int(scene)))
+        self.n += len(tpl)
+
+    def step(self, n=1):
+        self._check(self.lib.dem_step(self.ctx, int(n)))
+
+    def state(self):
+        n = self.n
+        out = [np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 3)), np.zeros((n, 3))]
+        self._check(self.lib.dem_get_state(self.ctx, *(o.ctypes.data for o in out), 0))
+        return tuple(out)
+
+    def state_device(self, pos, quat, vel, angvel):
+        """Writes the state into device buffers (e.g. torch CUDA tensors, float64)."""
+        ptrs = [t.data_ptr() if t is not None else None for t in (pos, quat, vel, angvel)]
+        self._check(self.lib.dem_get_state(self.ctx, *ptrs, 1))
+
+    def set_state(self, pos, quat, vel, angvel):
+        arr = [_f64(a) for a in (pos, quat, vel, angvel)]
+        self._check(self.lib.dem_set_state(self.ctx, *(_pd(a) for a in arr)))
+
+    def rebuild(self):
+        self._check(self.lib.dem_rebuild(self.ctx))
+
+    def eval_forces(self):
+        self._check(self.lib.dem_eval_forces(self.ctx))
+        F, T = np.zeros((self.n, 3)), np.zeros((self.n, 3))
+        self._check(self.lib.dem_get_forces(self.ctx, _pd(F), _pd(T)))
+        return F, T
+
+    def wall_forces(self):
+        F = np.zeros((max(1, self.n_walls), 3))
+        self._check(self.lib.dem_get_wall_forces(self.ctx, _pd(F)))
+        return F[: self.n_walls]
+
+    def contacts(self):
+        npair, nw = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.dem_num_contacts(self.ctx, C.byref(npair), C.byref(nw)))
+        a, b = np.zeros(npair.value, np.int32), np.zeros(npair.value, np.int32)
+        u = np.zeros((npair.value, 3))
+        ws, ww = np.zeros(nw.value, np.int32), np.zeros(nw.value, np.int32)
+        uw = np.zeros((nw.value, 3))
+        self._check(self.lib.dem_get_contacts(self.ctx, _pi(a), _pi(b), _pd(u), _pi(ws), _pi(ww),
+                                              _pd(uw)))
+        return a, b, u, ws, ww, uw
+
+    def bins(self):
+        n = C.c_longlong()
+        self._check(self.lib.dem_get_bins(self.ctx, 0, None, None, C.byref(n)))
+        keys, ids = np.zeros(n.value, np.uint32), np.zeros(n.value, np.int32)
+        self._check(self.lib.dem_get_bins(self.ctx, n.value,
+                                          keys.ctypes.data_as(C.POINTER(C.c_uint)), _pi(ids),
+                                          C.byref(n)))
+        return keys, ids
+
+    def audit(self):
+        m = C.c_longlong()
+        self._check(self.lib.dem_audit(self.ctx, C.byref(m)))
+        return m.value
+
+    def stats(self):
+        s = capi.DemStats()
+        self._check(self.lib.dem_get_stats(self.ctx, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in capi.DemStats._fields_}
+
+    def reset_stats(self):
+        self._check(self.lib.dem_reset_stats(self.ctx))
+
+    def set_timing(self, on=True):
+        self._check(self.lib.dem_set_timing(self.ctx, 1 if on else 0))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.dem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,1040 @@
+// dem_api.cu -- host runtime and the C ABI declared in include/dem.h.
+//
+// One context owns every device buffer of one simulation (one or more
+// scenes) on one device and one stream.  A step is a fixed sequence of
+// launches on that stream: [rebuild] -> sphere-sphere forces -> sphere-wall
+// forces -> clump update (integration + sphere poses + certificate).  The
+// rebuild synchronises twice (to size the bin registrations and the pair
+// list); steps without a rebuild never synchronise.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dem.h"
+#include "dem_dev.cuh"
+#include "dem_prims.cuh"
+
+using namespace dem;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct SceneH {
+  double lo[3], hi[3], bin;
+};
+
+}  // namespace
+
+struct dem_ctx {
+  dem_params P{};
+  std::vector<double> E, nu, mu, cor;
+  std::vector<dem_wall> user_walls;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // templates
+  int n_tpl = 0;
+  std::vector<int> tpl_off, tpl_mat;
+  std::vector<double> tpl_pos, tpl_rad, tpl_mass, tpl_inert;
+  double r_max = 0.0;
+  // scenes and walls
+  std::vector<SceneH> scenes;
+  std::vector<WallDev> walls;
+  std::vector<int> wall_user, wall_scene;
+  std::vector<SceneGrid> grids;
+  uint32_t nbins = 0;
+  // clumps (host bookkeeping)
+  std::vector<int> h_ctpl, h_cscene;
+  long long ncl = 0, ns = 0;
+  // all device buffers
+  std::vector<Buf*> owned;
+  Buf b_tpl_off, b_tp64, b_tp32, b_tmat, b_tmass, b_tinert, b_tpbound;
+  Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cv, b_cw, b_mv64, b_mw64, b_mv32, b_mw32;
+  Buf b_acc64, b_acc32, b_ref_pos, b_ref_vox, b_ref_off, b_ref_q;
+  Buf b_sinfo, b_sa64, b_sb64, b_sa32, b_sb32;
+  Buf b_grids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
+  Buf b_flags, b_counters, b_totals;
+  // detection scratch
+  Buf b_det, b_bin_cnt, b_bin_off, b_wall_mask, b_wall_cnt, b_keys, b_ids, b_keys2, b_ids2;
+  Buf b_bin_start, b_bin_end, b_pair_cnt, b_scan_scr, b_sort_scr, b_tmp;
+  uint32_t* sorted_keys = nullptr;
+  uint32_t* sorted_ids = nullptr;
+  long long n_entries = 0;
+  // contact lists (current, next) and an audit list
+  struct ListBufs {
+    Buf pa, pb, u, row, ws, ww, uw, wrow;
+    ContactList L{};
+  } lists[3];
+  int cur = 0;
+  long long list_ns = 0;  // spheres when the current list was built
+  // state
+  bool finalized = false, need_rebuild = true, have_list = false, acc_dirty = true;
+  long long step = 0;
+  int since = 0;
+  double margin = 0.0;
+  int timing = 0;
+  dem_stats stats{};
+  DevState D{};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> evpool;  // 4 per timed step, read at the end of dem_step
+};
+
+namespace {
+
+int fail(dem_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+void* dalloc(dem_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->P.alloc) {
+    p = c->P.alloc(bytes, c->P.alloc_user);
+  } else if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+void dfree(dem_ctx* c, void* p) {
+  if (!p) return;
+  if (c->P.free) c->P.free(p, c->P.alloc_user);
+  else cudaFreeAsync(p, c->st);
+}
+
+// Grows b to at least `bytes`, preserving the first `keep` bytes.
+bool grow(dem_ctx* c, Buf& b, size_t bytes, size_t keep = 0) {
+  if (b.bytes >= bytes && b.p) return true;
+  size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
+  nb = (nb + 255) & ~(size_t)255;
+  void* p = dalloc(c, nb);
+  if (!p) return false;
+  if (keep && b.p) cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->st);
+  dfree(c, b.p);
+  b.p = p;
+  b.bytes = nb;
+  return true;
+}
+
+template <typename T>
+T* ptr(const Buf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+int cuda_check(dem_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, DEM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return DEM_OK;
+}
+
+void split_ff(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+// Rotation by a unit quaternion (host, double).
+void qrot(const double* q, const double* p, double* o, bool transpose) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  double r[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                 2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                 2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+  for (int i = 0; i < 3; ++i) {
+    o[i] = 0;
+    for (int k = 0; k < 3; ++k) o[i] += (transpose ? r[3 * k + i] : r[3 * i + k]) * p[k];
+  }
+}
+
+void refresh_devstate(dem_ctx* c) {
+  DevState& d = c->D;
+  d.prec = c->P.precision;
+  d.ncl = c->ncl;
+  d.ns = c->ns;
+  d.nmat = c->P.n_materials;
+  d.nwalls = (int)c->walls.size();
+  d.h = c->P.dt;
+  for (int k = 0; k < 3; ++k) d.g[k] = c->P.g[k];
+  d.tpl_off = ptr<int>(c->b_tpl_off);
+  d.tp64 = ptr<double4_32a>(c->b_tp64);
+  d.tp32 = ptr<float4>(c->b_tp32);
+  d.tmat = ptr<int>(c->b_tmat);
+  d.tmass = ptr<double>(c->b_tmass);
+  d.tinert = ptr<double>(c->b_tinert);
+  d.tpbound = ptr<float>(c->b_tpbound);
+  d.cinfo = ptr<int2>(c->b_cinfo);
+  d.csph = ptr<int>(c->b_csph);
+  d.cpos = ptr<double4_32a>(c->b_cpos);
+  d.cvox = ptr<int4>(c->b_cvox);
+  d.coff = ptr<float4>(c->b_coff);
+  d.cq = ptr<double4_32a>(c->b_cq);
+  d.cv = ptr<double4_32a>(c->b_cv);
+  d.cw = ptr<double4_32a>(c->b_cw);
+  d.mv64 = ptr<double4_32a>(c->b_mv64);
+  d.mw64 = ptr<double4_32a>(c->b_mw64);
+  d.mv32 = ptr<float4>(c->b_mv32);
+  d.mw32 = ptr<float4>(c->b_mw32);
+  d.acc64 = ptr<double>(c->b_acc64);
+  d.acc32 = ptr<float>(c->b_acc32);
+  d.ref_pos = ptr<double4_32a>(c->b_ref_pos);
+  d.ref_vox = ptr<int4>(c->b_ref_vox);
+  d.ref_off = ptr<float4>(c->b_ref_off);
+  d.ref_q = ptr<float4>(c->b_ref_q);
+  d.cmargin = nullptr;
+  d.sinfo = ptr<int2>(c->b_sinfo);
+  d.sa64 = ptr<SphA64>(c->b_sa64);
+  d.sb64 = ptr<double4_32a>(c->b_sb64);
+  d.sa32 = ptr<SphA32>(c->b_sa32);
+  d.sb32 = ptr<float4>(c->b_sb32);
+  d.grids = ptr<SceneGrid>(c->b_grids);
+  d.walls = ptr<WallDev>(c->b_walls);
+  d.wall_idx = ptr<int>(c->b_wall_idx);
+  d.wall_scene = ptr<int>(c->b_wall_scene);
+  d.wfix = ptr<long long>(c->b_wfix);
+  d.wpos = ptr<double>(c->b_wpos);
+  d.wforce = ptr<double>(c->b_wforce);
+  d.pm64 = ptr<PairMat<double>>(c->b_pm64);
+  d.pm32 = ptr<PairMat<float>>(c->b_pm32);
+  d.flags = ptr<int>(c->b_flags);
+  d.counters = ptr<unsigned long long>(c->b_counters);
+}
+
+ContactList& curL(dem_ctx* c) { return c->lists[c->cur].L; }
+
+// Pair material table (section 2.1: stiffness and damping of a contact from
+// the E, nu, mu, CoR of its two spheres).
+int build_pair_materials(dem_ctx* c) {
+  const int M = c->P.n_materials;
+  std::vector<PairMat<double>> pm64((size_t)M * M);
+  std::vector<PairMat<float>> pm32((size_t)M * M);
+  const double kPi = 3.14159265358979323846;
+  for (int a = 0; a < M; ++a)
+    for (int b = 0; b < M; ++b) {
+      const double Ea = c->E[a], Eb = c->E[b], na = c->nu[a], nb = c->nu[b];
+      const double Es = 1.0 / ((1.0 - na * na) / Ea + (1.0 - nb * nb) / Eb);
+      const double Gs = 1.0 / (2.0 * (2.0 - na) * (1.0 + na) / Ea + 2.0 * (2.0 - nb) * (1.0 + nb) / Eb);
+      double mu, e;
+      const double ma = c->mu[a], mb = c->mu[b], ca = c->cor[a], cb = c->cor[b];
+      switch (c->P.mix_rule) {
+        case DEM_MIX_MIN: mu = std::min(ma, mb); e = std::min(ca, cb); break;
+        case DEM_MIX_MAX: mu = std::max(ma, mb); e = std::max(ca, cb); break;
+        default: mu = 0.5 * (ma + mb); e = 0.5 * (ca + cb); break;
+      }
+      double beta;
+      if (e >= 1.0) beta = 0.0;
+      else if (e <= 0.0) beta = -1.0;
+      else beta = std::log(e) / std::sqrt(std::log(e) * std::log(e) + kPi * kPi);
+      PairMat<double> p{};
+      p.kn = 4.0 / 3.0 * Es;
+      p.kt = 8.0 * Gs;
+      p.mu = mu;
+      p.cn = -2.0 * std::sqrt(5.0 / 6.0) * beta * std::sqrt(2.0 * Es);
+      p.ct = -2.0 * std::sqrt(5.0 / 6.0) * beta * std::sqrt(8.0 * Gs);
+      pm64[(size_t)a * M + b] = p;
+      PairMat<float> q{};
+      q.kn = (float)p.kn; q.kt = (float)p.kt; q.mu = (float)p.mu; q.cn = (float)p.cn; q.ct = (float)p.ct;
+      pm32[(size_t)a * M + b] = q;
+    }
+  if (!grow(c, c->b_pm64, sizeof(PairMat<double>) * pm64.size()) ||
+      !grow(c, c->b_pm32, sizeof(PairMat<float>) * pm32.size()))
+    return fail(c, DEM_ERR_OOM, "pair material table");
+  cudaMemcpyAsync(c->b_pm64.p, pm64.data(), sizeof(PairMat<double>) * pm64.size(), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_pm32.p, pm32.data(), sizeof(PairMat<float>) * pm32.size(), cudaMemcpyHostToDevice, c->st);
+  cudaStreamSynchronize(c->st);
+  return DEM_OK;
+}
+
+double current_margin(const dem_ctx* c) {
+  if (c->P.margin > 0.0) return c->P.margin;
+  return c->P.v_bound * c->P.dt * (double)std::max(1, c->P.rebuild_interval);
+}
+
+// Grids, walls and zeroed accumulators; called before the first step.
+int finalize(dem_ctx* c) {
+  if (c->finalized) return DEM_OK;
+  if (c->n_tpl == 0) return fail(c, DEM_ERR_STATE, "no clump templates loaded");
+  c->margin = current_margin(c);
+  // detection grids
+  c->grids.clear();
+  uint64_t base = 0;
+  for (size_t s = 0; s < c->scenes.size(); ++s) {
+    const SceneH& sh = c->scenes[s];
+    SceneGrid g{};
+    double bin = sh.bin > 0.0 ? sh.bin : 2.0 * (c->r_max + c->margin);
+    long long L = (long long)std::ceil(bin * kDetScale);
+    if (L < 1) L = 1;
+    for (int k = 0; k < 3; ++k) {
+      g.lo[k] = sh.lo[k];
+      long long ext = std::llrint((sh.hi[k] - sh.lo[k]) * kDetScale);
+      long long dd = (ext + L - 1) / L;
+      if (dd < 1) dd = 1;
+      if (dd > (1ll << 30)) return fail(c, DEM_ERR_INVALID_ARG, "detection grid too fine");
+      g.dims[k] = (int)dd;
+    }
+    g.L = L;
+    g.key_base = (uint32_t)base;
+    base += (uint64_t)g.dims[0] * g.dims[1] * g.dims[2];
+    if (base >= (1ull << 32) - 1) return fail(c, DEM_ERR_INVALID_ARG, "too many bins (> 2^32)");
+    c->grids.push_back(g);
+  }
+  c->nbins = (uint32_t)base;
+  // internal walls: one copy per scene they apply to
+  c->walls.clear();
+  c->wall_user.clear();
+  c->wall_scene.clear();
+  std::vector<int> idx;
+  for (size_t s = 0; s < c->scenes.size(); ++s) {
+    c->grids[s].wall_start = (int)idx.size();
+    int cnt = 0;
+    for (size_t w = 0; w < c->user_walls.size(); ++w) {
+      const dem_wall& uw = c->user_walls[w];
+      if (uw.scene != -1 && uw.scene != (int)s) continue;
+      WallDev d{};
+      d.type = uw.type;
+      d.material = uw.material;
+      for (int k = 0; k < 3; ++k) {
+        d.p[k] = uw.p[k];
+        d.n[k] = uw.n[k];
+        d.vel[k] = uw.vel[k];
+        split_ff(uw.n[k], d.nh[k], d.nl[k]);
+      }
+      d.radius = uw.radius;
+      d.half_angle = uw.half_angle;
+      d.height = uw.height;
+      d.rb = uw.height * std::tan(uw.half_angle);
+      split_ff(uw.radius, d.rh, d.rl);
+      split_ff(std::cos(uw.half_angle), d.ch, d.cl);
+      split_ff(std::sin(uw.half_angle), d.sh, d.sl);
+      split_ff(uw.height, d.hh, d.hl);
+      split_ff(d.rb, d.rbh, d.rbl);
+      d.speed = (float)std::sqrt(uw.vel[0] * uw.vel[0] + uw.vel[1] * uw.vel[1] + uw.vel[2] * uw.vel[2]);
+      idx.push_back((int)c->walls.size());
+      c->wall_user.push_back((int)w);
+      c->wall_scene.push_back((int)s);
+      c->walls.push_back(d);
+      ++cnt;
+    }
+    if (cnt > 32) return fail(c, DEM_ERR_INVALID_ARG, "more than 32 walls in one scene");
+    c->grids[s].wall_count = cnt;
+  }
+  const size_t nw = std::max<size_t>(1, c->walls.size());
+  if (!grow(c, c->b_grids, sizeof(SceneGrid) * c->grids.size()) ||
+      !grow(c, c->b_walls, sizeof(WallDev) * nw) || !grow(c, c->b_wall_idx, sizeof(int) * std::max<size_t>(1, idx.size())) ||
+      !grow(c, c->b_wall_scene, sizeof(int) * nw) || !grow(c, c->b_wfix, 3 * sizeof(long long) * nw) ||
+      !grow(c, c->b_wpos, 3 * sizeof(double) * nw) || !grow(c, c->b_wforce, 3 * sizeof(double) * nw) ||
+      !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->b_totals, 64))
+    return fail(c, DEM_ERR_OOM, "scene tables");
+  cudaMemcpyAsync(c->b_grids.p, c->grids.data(), sizeof(SceneGrid) * c->grids.size(), cudaMemcpyHostToDevice, c->st);
+  if (!c->walls.empty()) {
+    cudaMemcpyAsync(c->b_walls.p, c->walls.data(), sizeof(WallDev) * c->walls.size(), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->b_wall_idx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->b_wall_scene.p, c->wall_scene.data(), sizeof(int) * c->wall_scene.size(), cudaMemcpyHostToDevice, c->st);
+  }
+  cudaMemsetAsync(c->b_wforce.p, 0, c->b_wforce.bytes, c->st);
+  cudaMemsetAsync(c->b_flags.p, 0, 64, c->st);
+  cudaMemsetAsync(c->b_counters.p, 0, 64, c->st);
+  c->stats.margin = c->margin;
+  c->finalized = true;
+  refresh_devstate(c);
+  // sphere poses and mirrors of the initial state, walls at the current time
+  launch_update(c->D, false, (double)c->step * c->P.dt, c->margin, false, c->st);
+  cudaStreamSynchronize(c->st);
+  return cuda_check(c, "finalize");
+}
+
+// Detection into lists[li] with margin m (rebuild) -- also used by the audit.
+int detect_into(dem_ctx* c, int li, double m) {
+  const long long ns = c->ns;
+  const double t = (double)c->step * c->P.dt;
+  const double travel = c->P.dt * (double)std::max(1, c->P.rebuild_interval);
+  auto& LB = c->lists[li];
+  if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_bin_cnt, 4 * (ns + 1)) ||
+      !grow(c, c->b_bin_off, 4 * (ns + 1)) || !grow(c, c->b_wall_mask, 4 * (ns + 1)) ||
+      !grow(c, c->b_wall_cnt, 4 * (ns + 1)) || !grow(c, c->b_pair_cnt, 4 * (ns + 1)) ||
+      !grow(c, LB.row, 4 * (ns + 1)) || !grow(c, LB.wrow, 4 * (ns + 1)) ||
+      !grow(c, c->b_scan_scr, scan_scratch_bytes(ns + 1) + 256))
+    return fail(c, DEM_ERR_OOM, "detection buffers");
+  DetectOut o{};
+  o.det = ptr<int4>(c->b_det);
+  o.bin_cnt = ptr<uint32_t>(c->b_bin_cnt);
+  o.bin_off = ptr<uint32_t>(c->b_bin_off);
+  o.wall_mask = ptr<uint32_t>(c->b_wall_mask);
+  o.wall_cnt = ptr<uint32_t>(c->b_wall_cnt);
+  o.wall_off = ptr<uint32_t>(LB.wrow);
+  o.pair_cnt = ptr<uint32_t>(c->b_pair_cnt);
+  o.pair_off = ptr<uint32_t>(LB.row);
+  unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
+  launch_detect(c->D, o, m, nullptr, t, travel, c->st);
+  exclusive_scan_u32(o.bin_cnt, o.bin_off, ns, c->b_scan_scr.p, tot + 0, c->st);
+  exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 1, c->st);
+  unsigned long long h_tot[4] = {0, 0, 0, 0};
+  cudaMemcpyAsync(h_tot, tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "detect");
+  const unsigned long long B = h_tot[0], NW = h_tot[1];
+  if (B >= (1ull << 32) || NW >= (1ull << 31))
+    return fail(c, DEM_ERR_CAPACITY, "bin registrations exceed 2^32");
+  c->n_entries = (long long)B;
+  if (!grow(c, c->b_keys, 4 * (B + 1)) || !grow(c, c->b_ids, 4 * (B + 1)) ||
+      !grow(c, c->b_keys2, 4 * (B + 1)) || !grow(c, c->b_ids2, 4 * (B + 1)) ||
+      !grow(c, c->b_sort_scr, radix_scratch_bytes((long long)B + 1) + 256) ||
+      !grow(c, c->b_bin_start, 4 * ((size_t)c->nbins + 1)) || !grow(c, c->b_bin_end, 4 * ((size_t)c->nbins + 1)))
+    return fail(c, DEM_ERR_OOM, "bin buffers");
+  o.keys = ptr<uint32_t>(c->b_keys);
+  o.ids = ptr<uint32_t>(c->b_ids);
+  launch_emit_bins(c->D, o, c->st);
+  int bits = 1;
+  while (bits < 32 && (1ull << bits) < (unsigned long long)c->nbins) ++bits;
+  const int alt = radix_sort_pairs(o.keys, o.ids, ptr<uint32_t>(c->b_keys2), ptr<uint32_t>(c->b_ids2),
+                                   (long long)B, bits, c->b_sort_scr.p, tot + 2, c->st);
+  if (alt) {
+    o.keys = ptr<uint32_t>(c->b_keys2);
+    o.ids = ptr<uint32_t>(c->b_ids2);
+  }
+  c->sorted_keys = o.keys;
+  c->sorted_ids = o.ids;
+  o.bin_start = ptr<uint32_t>(c->b_bin_start);
+  o.bin_end = ptr<uint32_t>(c->b_bin_end);
+  cudaMemsetAsync(o.bin_start, 0, 4 * (size_t)c->nbins, c->st);
+  cudaMemsetAsync(o.bin_end, 0, 4 * (size_t)c->nbins, c->st);
+  launch_bin_bounds(o.keys, (long long)B, o.bin_start, o.bin_end, c->st);
+  launch_narrow(c->D, o, false, nullptr, nullptr, c->st);
+  exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
+  cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "narrow phase");
+  const unsigned long long NP = h_tot[3];
+  if (NP >= (1ull << 31)) return fail(c, DEM_ERR_CAPACITY, "pair list exceeds 2^31 entries");
+  if (c->P.max_contacts > 0 && (long long)NP > c->P.max_contacts)
+    return fail(c, DEM_ERR_CAPACITY, "pair list exceeds max_contacts");
+  ContactList& L = LB.L;
+  if ((long long)NP > L.cap || !LB.pa.p) {
+    const long long cap = std::max<long long>((long long)(NP + NP / 4), 1024);
+    dfree(c, LB.pa.p); dfree(c, LB.pb.p); dfree(c, LB.u.p);
+    LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf();
+    if (!grow(c, LB.pa, 4 * cap) || !grow(c, LB.pb, 4 * cap) || !grow(c, LB.u, 24 * cap))
+      return fail(c, DEM_ERR_OOM, "pair list");
+    L.cap = cap;
+  }
+  if ((long long)NW > L.capw || !LB.ws.p) {
+    const long long cap = std::max<long long>((long long)(NW + NW / 4), 1024);
+    dfree(c, LB.ws.p); dfree(c, LB.ww.p); dfree(c, LB.uw.p);
+    LB.ws = Buf(); LB.ww = Buf(); LB.uw = Buf();
+    if (!grow(c, LB.ws, 4 * cap) || !grow(c, LB.ww, 4 * cap) || !grow(c, LB.uw, 24 * cap))
+      return fail(c, DEM_ERR_OOM, "wall list");
+    L.capw = cap;
+  }
+  L.pa = ptr<int>(LB.pa);
+  L.pb = ptr<uint32_t>(LB.pb);
+  L.u = ptr<double>(LB.u);
+  L.row = ptr<uint32_t>(LB.row);
+  L.ws = ptr<int>(LB.ws);
+  L.ww = ptr<uint32_t>(LB.ww);
+  L.uw = ptr<double>(LB.uw);
+  L.wrow = ptr<uint32_t>(LB.wrow);
+  L.n = (long long)NP;
+  L.nw = (long long)NW;
+  const uint32_t np32 = (uint32_t)NP, nw32 = (uint32_t)NW;
+  cudaMemcpyAsync(L.row + ns, &np32, 4, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(L.wrow + ns, &nw32, 4, cudaMemcpyHostToDevice, c->st);
+  launch_narrow(c->D, o, true, L.pa, L.pb, c->st);
+  launch_wall_emit(c->D, o, L.ws, L.ww, c->st);
+  cudaStreamSynchronize(c->st);  // the two host scalars above must outlive their copies
+  return cuda_check(c, "detect_into");
+}
+
+int rebuild(dem_ctx* c) {
+  const int nxt = c->cur == 0 ? 1 : 0;
+  if (c->timing) cudaEventRecord(c->ev[0], c->st);
+  int rc = detect_into(c, nxt, c->margin);
+  if (rc) return rc;
+  ContactList& N = c->lists[nxt].L;
+  if (c->have_list) launch_hist_map(curL(c), N, c->list_ns, c->st);
+  c->cur = nxt;
+  c->list_ns = c->ns;
+  c->have_list = true;
+  c->need_rebuild = false;
+  c->since = 0;
+  launch_set_cert_ref(c->D, c->st);
+  c->stats.rebuilds++;
+  c->stats.bin_entries = c->n_entries;
+  c->stats.n_pairs = N.n;
+  c->stats.n_wall_contacts = N.nw;
+  if (c->timing) {
+    cudaEventRecord(c->ev[1], c->st);
+    cudaEventSynchronize(c->ev[1]);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+    c->stats.ms_detect += ms;
+  }
+  return cuda_check(c, "rebuild");
+}
+
+// Sphere-sphere then sphere-wall contact forces; `mid` (optional) is recorded
+// between the two kernels.
+int force_pass(dem_ctx* c, bool count_active, cudaEvent_t mid = nullptr) {
+  if (c->acc_dirty) {
+    if (c->P.precision == DEM_FP64) cudaMemsetAsync(c->b_acc64.p, 0, 64 * (size_t)c->ncl, c->st);
+    else cudaMemsetAsync(c->b_acc32.p, 0, 32 * (size_t)c->ncl, c->st);
+    c->acc_dirty = false;
+  }
+  if (!c->walls.empty()) cudaMemsetAsync(c->b_wforce.p, 0, 24 * c->walls.size(), c->st);
+  const double t = (double)c->step * c->P.dt;
+  ContactList& L = curL(c);
+  launch_force_pairs(c->D, L, count_active, c->st);
+  if (mid) cudaEventRecord(mid, c->st);
+  launch_force_walls(c->D, L, t, count_active, c->st);
+  return DEM_OK;
+}
+
+int read_flags(dem_ctx* c) {
+  int flags = 0;
+  unsigned long long ctr[2] = {0, 0};
+  cudaMemcpyAsync(&flags, c->b_flags.p, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(ctr, c->b_counters.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "step");
+  cudaMemsetAsync(c->b_flags.p, 0, sizeof(int), c->st);
+  cudaMemsetAsync(c->b_counters.p, 0, 2 * sizeof(unsigned long long), c->st);
+  c->stats.active_last = (long long)ctr[0];
+  c->stats.guard_violations += (long long)ctr[1];
+  if (flags & kFlagNonFinite) return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
+  if ((flags & kFlagGuard) && c->P.guard == DEM_GUARD_ROLLBACK)
+    return fail(c, DEM_ERR_GUARD, "a clump moved further than the margin since the last rebuild");
+  return cuda_check(c, "step");
+}
+
+int upload_clumps(dem_ctx* c, long long first, int n, const int* tpl, const double* pos,
+                  const double* quat, const double* vel, const double* angvel) {
+  const bool f64 = c->P.precision == DEM_FP64;
+  std::vector<double4_32a> vq(n), vv(n), vw(n), vp;
+  std::vector<int4> vx;
+  std::vector<float4> vo;
+  if (f64) vp.resize(n); else { vx.resize(n); vo.resize(n); }
+  for (int i = 0; i < n; ++i) {
+    const double* q = quat + 4 * i;
+    vq[i] = make_double4_32a(q[0], q[1], q[2], q[3]);
+    vv[i] = make_double4_32a(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0);
+    double wb[3];
+    qrot(q, angvel + 3 * i, wb, true);
+    vw[i] = make_double4_32a(wb[0], wb[1], wb[2], 0.0);
+    if (f64) {
+      vp[i] = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], 0.0);
+    } else {
+      const SceneH& s = c->scenes[c->h_cscene[first + i]];
+      int vox[3];
+      float off[3];
+      for (int k = 0; k < 3; ++k) {
+        const double rel = pos[3 * i + k] - s.lo[k];
+        const double m = std::rint(rel / kVoxel);
+        if (std::fabs(m) > 2.0e9) return fail(c, DEM_ERR_INVALID_ARG, "clump too far from its scene corner");
+        vox[k] = (int)m;
+        off[k] = (float)(rel - m * kVoxel);
+      }
+      vx[i] = make_int4(vox[0], vox[1], vox[2], 0);
+      vo[i] = make_float4(off[0], off[1], off[2], 0.f);
+    }
+  }
+  cudaMemcpyAsync(ptr<double4_32a>(c->b_cq) + first, vq.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(ptr<double4_32a>(c->b_cv) + first, vv.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(ptr<double4_32a>(c->b_cw) + first, vw.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+  if (f64) {
+    cudaMemcpyAsync(ptr<double4_32a>(c->b_cpos) + first, vp.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+  } else {
+    cudaMemcpyAsync(ptr<int4>(c->b_cvox) + first, vx.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(ptr<float4>(c->b_coff) + first, vo.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+  }
+  cudaStreamSynchronize(c->st);
+  return cuda_check(c, "upload clumps");
+}
+
+bool finite_all(const double* p, long long n) {
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int dem_create(const dem_params* params, dem_ctx** out) {
+  if (out) *out = nullptr;
+  if (!params || !out) { g_create_error = "null argument"; return DEM_ERR_INVALID_ARG; }
+  const dem_params& p = *params;
+  auto bad = [&](const char* m) { g_create_error = m; return DEM_ERR_INVALID_ARG; };
+  if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return bad("dt must be > 0");
+  if (p.precision != DEM_FP64 && p.precision != DEM_FP32_VOXEL) return bad("unknown precision");
+  if (p.n_materials < 1 || !p.E || !p.nu || !p.mu || !p.cor) return bad("material table missing");
+  if (p.rebuild_interval < 1) return bad("rebuild_interval must be >= 1");
+  if (p.margin < 0.0 || p.v_bound < 0.0 || p.bin_size < 0.0) return bad("negative margin / v_bound / bin_size");
+  if (p.mix_rule < 0 || p.mix_rule > 2) return bad("unknown mix_rule");
+  if (p.n_walls < 0 || (p.n_walls > 0 && !p.walls)) return bad("walls missing");
+  if (p.guard < 0 || p.guard > 2) return bad("unknown guard mode");
+  if (p.margin_policy != DEM_MARGIN_FIXED && p.margin_policy != DEM_MARGIN_LEARNED) return bad("unknown margin policy");
+  if ((p.alloc == nullptr) != (p.free == nullptr)) return bad("alloc and free must be given together");
+  for (int k = 0; k < 3; ++k)
+    if (!(p.domain_hi[k] > p.domain_lo[k])) return bad("empty domain");
+  for (int i = 0; i < p.n_materials; ++i)
+    if (!(p.E[i] > 0) || !(p.nu[i] > -1 && p.nu[i] < 0.5) || !(p.mu[i] >= 0) || !(p.cor[i] >= 0 && p.cor[i] <= 1))
+      return bad("material out of range");
+  for (int w = 0; w < p.n_walls; ++w) {
+    const dem_wall& wl = p.walls[w];
+    if (wl.type < 0 || wl.type > 2) return bad("unknown wall type");
+    if (wl.material < 0 || wl.material >= p.n_materials) return bad("wall material out of range");
+    const double nn = wl.n[0] * wl.n[0] + wl.n[1] * wl.n[1] + wl.n[2] * wl.n[2];
+    if (!(std::fabs(nn - 1.0) < 1e-9)) return bad("wall normal / axis must be a unit vector");
+    if (wl.type == DEM_WALL_CYLINDER && !(wl.radius > 0)) return bad("cylinder radius must be > 0");
+    if (wl.type == DEM_WALL_CONE && !(wl.height > 0 && wl.half_angle > 0 && wl.half_angle < 1.5707963)) return bad("bad cone");
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    g_create_error = "no CUDA device";
+    return DEM_ERR_CUDA;
+  }
+  if (p.device < 0 || p.device >= ndev) return bad("device ordinal out of range");
+  if (cudaSetDevice(p.device) != cudaSuccess) { g_create_error = "cudaSetDevice failed"; return DEM_ERR_CUDA; }
+  dem_ctx* c = new dem_ctx();
+  c->P = p;
+  c->E.assign(p.E, p.E + p.n_materials);
+  c->nu.assign(p.nu, p.nu + p.n_materials);
+  c->mu.assign(p.mu, p.mu + p.n_materials);
+  c->cor.assign(p.cor, p.cor + p.n_materials);
+  c->P.E = c->E.data(); c->P.nu = c->nu.data(); c->P.mu = c->mu.data(); c->P.cor = c->cor.data();
+  c->user_walls.assign(p.walls, p.walls + p.n_walls);
+  c->P.walls = c->user_walls.data();
+  if (p.cuda_stream) {
+    c->st = (cudaStream_t)p.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      g_create_error = "cudaStreamCreate failed";
+      return DEM_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  for (auto& e : c->ev) cudaEventCreate(&e);
+  SceneH s0{};
+  for (int k = 0; k < 3; ++k) { s0.lo[k] = p.domain_lo[k]; s0.hi[k] = p.domain_hi[k]; }
+  s0.bin = p.bin_size;
+  c->scenes.push_back(s0);
+  int rc = build_pair_materials(c);
+  if (rc) {
+    g_create_error = c->err;
+    dem_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DEM_OK;
+}
+
+void dem_destroy(dem_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->P.device);
+  Buf* all[] = {&c->b_tpl_off, &c->b_tp64, &c->b_tp32, &c->b_tmat, &c->b_tmass, &c->b_tinert, &c->b_tpbound,
+                &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cv, &c->b_cw,
+                &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
+                &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_sa32,
+                &c->b_sb32, &c->b_grids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
+                &c->b_wpos, &c->b_wforce, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
+                &c->b_totals, &c->b_det, &c->b_bin_cnt, &c->b_bin_off, &c->b_wall_mask, &c->b_wall_cnt,
+                &c->b_keys, &c->b_ids, &c->b_keys2, &c->b_ids2, &c->b_bin_start, &c->b_bin_end,
+                &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp};
+  for (Buf* b : all) dfree(c, b->p);
+  for (auto& lb : c->lists) {
+    Buf* lbs[] = {&lb.pa, &lb.pb, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow};
+    for (Buf* b : lbs) dfree(c, b->p);
+  }
+  cudaStreamSynchronize(c->st);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+const char* dem_last_error(const dem_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double* local_pos,
+                             const double* radius, const int* material, const double* mass,
+                             const double* inertia) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  if (c->n_tpl > 0) return fail(c, DEM_ERR_STATE, "templates already loaded");
+  if (n_tpl < 1 || !off || !local_pos || !radius || !material || !mass || !inertia)
+    return fail(c, DEM_ERR_INVALID_ARG, "template arrays missing");
+  if (off[0] != 0) return fail(c, DEM_ERR_INVALID_ARG, "sphere_offsets[0] must be 0");
+  for (int t = 0; t < n_tpl; ++t) {
+    if (off[t + 1] <= off[t]) return fail(c, DEM_ERR_INVALID_ARG, "each template needs >= 1 sphere");
+    if (!(mass[t] > 0) || !(inertia[3 * t] > 0) || !(inertia[3 * t + 1] > 0) || !(inertia[3 * t + 2] > 0))
+      return fail(c, DEM_ERR_INVALID_ARG, "mass and inertia must be > 0");
+  }
+  const int S = off[n_tpl];
+  if (!finite_all(local_pos, 3ll * S)) return fail(c, DEM_ERR_INVALID_ARG, "non-finite sphere position");
+  for (int s = 0; s < S; ++s) {
+    if (!(radius[s] > 0) || !std::isfinite(radius[s])) return fail(c, DEM_ERR_INVALID_ARG, "radius must be > 0");
+    if (material[s] < 0 || material[s] >= c->P.n_materials) return fail(c, DEM_ERR_INVALID_ARG, "material out of range");
+  }
+  c->n_tpl = n_tpl;
+  c->tpl_off.assign(off, off + n_tpl + 1);
+  c->tpl_pos.assign(local_pos, local_pos + 3 * S);
+  c->tpl_rad.assign(radius, radius + S);
+  c->tpl_mat.assign(material, material + S);
+  c->tpl_mass.assign(mass, mass + n_tpl);
+  c->tpl_inert.assign(inertia, inertia + 3 * n_tpl);
+  c->r_max = *std::max_element(radius, radius + S);
+  std::vector<double4_32a> tp64(S);
+  std::vector<float4> tp32(S);
+  std::vector<float> pb(n_tpl, 0.f);
+  for (int t = 0; t < n_tpl; ++t)
+    for (int s = off[t]; s < off[t + 1]; ++s) {
+      const double* p = local_pos + 3 * s;
+      tp64[s] = make_double4_32a(p[0], p[1], p[2], radius[s]);
+      tp32[s] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)radius[s]);
+      pb[t] = std::max(pb[t], (float)std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) * 1.000001f);
+    }
+  if (!grow(c, c->b_tpl_off, 4 * (n_tpl + 1)) || !grow(c, c->b_tp64, 32 * S) || !grow(c, c->b_tp32, 16 * S) ||
+      !grow(c, c->b_tmat, 4 * S) || !grow(c, c->b_tmass, 8 * n_tpl) || !grow(c, c->b_tinert, 24 * n_tpl) ||
+      !grow(c, c->b_tpbound, 4 * n_tpl))
+    return fail(c, DEM_ERR_OOM, "template tables");
+  cudaMemcpyAsync(c->b_tpl_off.p, off, 4 * (n_tpl + 1), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tp64.p, tp64.data(), 32 * (size_t)S, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tp32.p, tp32.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tmat.p, material, 4 * (size_t)S, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tmass.p, mass, 8 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tinert.p, inertia, 24 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tpbound.p, pb.data(), 4 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
+  cudaStreamSynchronize(c->st);
+  return cuda_check(c, "load templates");
+}
+
+int dem_add_scene(dem_ctx* c, const double lo[3], const double hi[3], double bin_size, int* scene_id) {
+  if (!c || !lo || !hi) return DEM_ERR_INVALID_ARG;
+  if (c->finalized) return fail(c, DEM_ERR_STATE, "scenes must be added before the first step");
+  for (int k = 0; k < 3; ++k)
+    if (!(hi[k] > lo[k])) return fail(c, DEM_ERR_INVALID_ARG, "empty scene domain");
+  if (!(bin_size >= 0)) return fail(c, DEM_ERR_INVALID_ARG, "negative bin size");
+  SceneH s{};
+  for (int k = 0; k < 3; ++k) { s.lo[k] = lo[k]; s.hi[k] = hi[k]; }
+  s.bin = bin_size;
+  c->scenes.push_back(s);
+  if (scene_id) *scene_id = (int)c->scenes.size() - 1;
+  return DEM_OK;
+}
+
+int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const double* quat,
+                   const double* vel, const double* angvel, int scene) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  if (c->n_tpl == 0) return fail(c, DEM_ERR_STATE, "load templates first");
+  if (n < 0 || (n > 0 && (!tpl || !pos || !quat || !vel || !angvel)))
+    return fail(c, DEM_ERR_INVALID_ARG, "clump arrays missing");
+  if (scene < 0 || scene >= (int)c->scenes.size()) return fail(c, DEM_ERR_INVALID_ARG, "unknown scene");
+  if (n == 0) return DEM_OK;
+  for (int i = 0; i < n; ++i)
+    if (tpl[i] < 0 || tpl[i] >= c->n_tpl) return fail(c, DEM_ERR_INVALID_ARG, "template id out of range");
+  if (!finite_all(pos, 3ll * n) || !finite_all(quat, 4ll * n) || !finite_all(vel, 3ll * n) ||
+      !finite_all(angvel, 3ll * n))
+    return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
+  long long add_s = 0;
+  for (int i = 0; i < n; ++i) add_s += c->tpl_off[tpl[i] + 1] - c->tpl_off[tpl[i]];
+  const long long ncl = c->ncl + n, ns = c->ns + add_s;
+  if (ns >= (1ll << 31) - 1) return fail(c, DEM_ERR_INVALID_ARG, "more than 2^31 spheres");
+  const size_t k0 = (size_t)c->ncl, s0 = (size_t)c->ns;
+  bool ok = grow(c, c->b_cinfo, 8 * ncl, 8 * k0) && grow(c, c->b_csph, 4 * (ncl + 1), 4 * k0) &&
+            grow(c, c->b_cq, 32 * ncl, 32 * k0) && grow(c, c->b_cv, 32 * ncl, 32 * k0) &&
+            grow(c, c->b_cw, 32 * ncl, 32 * k0) && grow(c, c->b_ref_q, 16 * ncl) &&
+            grow(c, c->b_sinfo, 8 * ns, 8 * s0);
+  if (c->P.precision == DEM_FP64) {
+    ok = ok && grow(c, c->b_cpos, 32 * ncl, 32 * k0) && grow(c, c->b_mv64, 32 * ncl) &&
+         grow(c, c->b_mw64, 32 * ncl) && grow(c, c->b_acc64, 64 * ncl) && grow(c, c->b_ref_pos, 32 * ncl) &&
+         grow(c, c->b_sa64, sizeof(SphA64) * ns) && grow(c, c->b_sb64, 32 * ns);
+  } else {
+    ok = ok && grow(c, c->b_cvox, 16 * ncl, 16 * k0) && grow(c, c->b_coff, 16 * ncl, 16 * k0) &&
+         grow(c, c->b_mv32, 16 * ncl) && grow(c, c->b_mw32, 16 * ncl) && grow(c, c->b_acc32, 32 * ncl) &&
+         grow(c, c->b_ref_vox, 16 * ncl) && grow(c, c->b_ref_off, 16 * ncl) &&
+         grow(c, c->b_sa32, sizeof(SphA32) * ns) && grow(c, c->b_sb32, 16 * ns);
+  }
+  if (!ok) return fail(c, DEM_ERR_OOM, "clump buffers");
+  std::vector<int2> ci(n), si(add_s);
+  std::vector<int> cs(n + 1);
+  long long s = c->ns;
+  for (int i = 0; i < n; ++i) {
+    ci[i] = make_int2(tpl[i], scene);
+    cs[i] = (int)s;
+    for (int j = c->tpl_off[tpl[i]]; j < c->tpl_off[tpl[i] + 1]; ++j, ++s)
+      si[s - c->ns] = make_int2((int)(c->ncl + i), j);
+  }
+  cs[n] = (int)s;
+  cudaMemcpyAsync(ptr<int2>(c->b_cinfo) + k0, ci.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(ptr<int>(c->b_csph) + k0, cs.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(ptr<int2>(c->b_sinfo) + s0, si.data(), 8 * (size_t)add_s, cudaMemcpyHostToDevice, c->st);
+  for (int i = 0; i < n; ++i) {
+    c->h_ctpl.push_back(tpl[i]);
+    c->h_cscene.push_back(scene);
+  }
+  const long long first = c->ncl;
+  c->ncl = ncl;
+  c->ns = ns;
+  int rc = upload_clumps(c, first, n, tpl, pos, quat, vel, angvel);
+  if (rc) return rc;
+  c->stats.n_clumps = ncl;
+  c->stats.n_spheres = ns;
+  c->need_rebuild = true;
+  c->acc_dirty = true;
+  if (c->finalized) {
+    refresh_devstate(c);
+    launch_update(c->D, false, (double)c->step * c->P.dt, c->margin, false, c->st);
+    cudaStreamSynchronize(c->st);
+  }
+  return cuda_check(c, "add clumps");
+}
+
+int dem_step(dem_ctx* c, int n_steps) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  if (n_steps < 0) return fail(c, DEM_ERR_INVALID_ARG, "negative step count");
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  refresh_devstate(c);
+  const int K = std::max(1, c->P.rebuild_interval);
+  const bool cert = c->P.guard != DEM_GUARD_OFF;
+  const long long launches0 = g_kernel_launches;
+  const int n_timed = c->timing ? std::min(n_steps, 8192) : 0;
+  while ((int)c->evpool.size() < 4 * n_timed) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return cuda_check(c, "event pool");
+    c->evpool.push_back(e);
+  }
+  for (int it = 0; it < n_steps; ++it) {
+    if (c->need_rebuild || !c->have_list || c->since >= K) {
+      rc = rebuild(c);
+      if (rc) return rc;
+    }
+    const bool tm = it < n_timed;
+    cudaEvent_t* ev = tm ? &c->evpool[4 * (size_t)it] : nullptr;
+    if (tm) cudaEventRecord(ev[0], c->st);
+    force_pass(c, it == n_steps - 1, tm ? ev[1] : nullptr);
+    if (tm) cudaEventRecord(ev[2], c->st);
+    launch_update(c->D, true, (double)(c->step + 1) * c->P.dt, c->margin, cert, c->st);
+    if (tm) cudaEventRecord(ev[3], c->st);
+    c->step++;
+    c->since++;
+    c->stats.steps++;
+    c->stats.pair_steps += curL(c).n + curL(c).nw;
+  }
+  c->stats.time = (double)c->step * c->P.dt;
+  rc = read_flags(c);
+  for (int it = 0; it < n_timed; ++it) {
+    const cudaEvent_t* ev = &c->evpool[4 * (size_t)it];
+    float a = 0.f, b = 0.f, u = 0.f;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    cudaEventElapsedTime(&u, ev[2], ev[3]);
+    c->stats.ms_pairs += a;
+    c->stats.ms_walls += b;
+    c->stats.ms_update += u;
+    c->stats.timed_steps++;
+  }
+  c->stats.launches += g_kernel_launches - launches0;
+  return rc;
+}
+
+int dem_get_state(dem_ctx* c, double* pos, double* quat, double* vel, double* angvel, int on_device) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  refresh_devstate(c);
+  if (c->ncl == 0) return DEM_OK;
+  if (on_device) {
+    launch_get_state(c->D, pos, quat, vel, angvel, c->st);
+    cudaStreamSynchronize(c->st);
+    return cuda_check(c, "get_state");
+  }
+  const size_t n = (size_t)c->ncl;
+  if (!grow(c, c->b_tmp, 8 * 13 * n)) return fail(c, DEM_ERR_OOM, "staging");
+  double* t = ptr<double>(c->b_tmp);
+  launch_get_state(c->D, t, t + 3 * n, t + 7 * n, t + 10 * n, c->st);
+  if (pos) cudaMemcpyAsync(pos, t, 24 * n, cudaMemcpyDeviceToHost, c->st);
+  if (quat) cudaMemcpyAsync(quat, t + 3 * n, 32 * n, cudaMemcpyDeviceToHost, c->st);
+  if (vel) cudaMemcpyAsync(vel, t + 7 * n, 24 * n, cudaMemcpyDeviceToHost, c->st);
+  if (angvel) cudaMemcpyAsync(angvel, t + 10 * n, 24 * n, cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  return cuda_check(c, "get_state");
+}
+
+int dem_set_state(dem_ctx* c, const double* pos, const double* quat, const double* vel, const double* angvel) {
+  if (!c || !pos || !quat || !vel || !angvel) return DEM_ERR_INVALID_ARG;
+  cudaSetDevice(c->P.device);
+  const long long n = c->ncl;
+  if (!finite_all(pos, 3 * n) || !finite_all(quat, 4 * n) || !finite_all(vel, 3 * n) || !finite_all(angvel, 3 * n))
+    return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
+  int rc = upload_clumps(c, 0, (int)n, c->h_ctpl.data(), pos, quat, vel, angvel);
+  if (rc) return rc;
+  c->need_rebuild = true;
+  c->acc_dirty = true;
+  if (c->finalized) {
+    refresh_devstate(c);
+    launch_update(c->D, false, (double)c->step * c->P.dt, c->margin, false, c->st);
+    cudaStreamSynchronize(c->st);
+  }
+  return cuda_check(c, "set_state");
+}
+
+int dem_get_stats(dem_ctx* c, dem_stats* out) {
+  if (!c || !out) return DEM_ERR_INVALID_ARG;
+  *out = c->stats;
+  out->n_clumps = c->ncl;
+  out->n_spheres = c->ns;
+  if (c->have_list) {
+    out->n_pairs = curL(c).n;
+    out->n_wall_contacts = curL(c).nw;
+  }
+  out->margin = c->finalized ? c->margin : current_margin(c);
+  out->time = (double)c->step * c->P.dt;
+  return DEM_OK;
+}
+
+int dem_reset_stats(dem_ctx* c) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  c->stats = dem_stats{};
+  return DEM_OK;
+}
+
+int dem_set_timing(dem_ctx* c, int timing) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  c->timing = timing ? 1 : 0;
+  return DEM_OK;
+}
+
+int dem_rebuild(dem_ctx* c) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  refresh_devstate(c);
+  rc = rebuild(c);
+  if (rc) return rc;
+  cudaStreamSynchronize(c->st);
+  return cuda_check(c, "rebuild");
+}
+
+int dem_eval_forces(dem_ctx* c) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  refresh_devstate(c);
+  if (c->need_rebuild || !c->have_list) {
+    rc = rebuild(c);
+    if (rc) return rc;
+  }
+  force_pass(c, true);
+  c->acc_dirty = true;
+  return read_flags(c);
+}
+
+int dem_get_forces(dem_ctx* c, double* F, double* T) {
+  if (!c || !F || !T) return DEM_ERR_INVALID_ARG;
+  const size_t n = (size_t)c->ncl;
+  if (n == 0) return DEM_OK;
+  if (!grow(c, c->b_tmp, 48 * n)) return fail(c, DEM_ERR_OOM, "staging");
+  double* t = ptr<double>(c->b_tmp);
+  launch_get_forces(c->D, t, t + 3 * n, c->st);
+  cudaMemcpyAsync(F, t, 24 * n, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(T, t + 3 * n, 24 * n, cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  return cuda_check(c, "get_forces");
+}
+
+int dem_get_wall_forces(dem_ctx* c, double* F) {
+  if (!c || !F) return DEM_ERR_INVALID_ARG;
+  const size_t nu = c->user_walls.size();
+  std::fill(F, F + 3 * nu, 0.0);
+  if (c->walls.empty()) return DEM_OK;
+  std::vector<double> h(3 * c->walls.size());
+  cudaMemcpyAsync(h.data(), c->b_wforce.p, 24 * c->walls.size(), cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  for (size_t w = 0; w < c->walls.size(); ++w)
+    for (int k = 0; k < 3; ++k) F[3 * c->wall_user[w] + k] += h[3 * w + k];
+  return cuda_check(c, "get_wall_forces");
+}
+
+int dem_num_contacts(dem_ctx* c, long long* n_pairs, long long* n_wall) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  if (n_pairs) *n_pairs = c->have_list ? curL(c).n : 0;
+  if (n_wall) *n_wall = c->have_list ? curL(c).nw : 0;
+  return DEM_OK;
+}
+
+int dem_get_contacts(dem_ctx* c, int* a, int* b, double* u, int* wall_sphere, int* wall_id, double* wall_u) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  if (!c->have_list) return DEM_OK;
+  ContactList& L = curL(c);
+  std::vector<uint32_t> pb(L.n), ww(L.nw);
+  std::vector<double> uu(3 * L.cap), uw(3 * L.capw);
+  if (a && L.n) cudaMemcpyAsync(a, L.pa, 4 * L.n, cudaMemcpyDeviceToHost, c->st);
+  if (L.n) cudaMemcpyAsync(pb.data(), L.pb, 4 * L.n, cudaMemcpyDeviceToHost, c->st);
+  if (u && L.n) cudaMemcpyAsync(uu.data(), L.u, 24 * L.cap, cudaMemcpyDeviceToHost, c->st);
+  if (wall_sphere && L.nw) cudaMemcpyAsync(wall_sphere, L.ws, 4 * L.nw, cudaMemcpyDeviceToHost, c->st);
+  if (L.nw) cudaMemcpyAsync(ww.data(), L.ww, 4 * L.nw, cudaMemcpyDeviceToHost, c->st);
+  if (wall_u && L.nw) cudaMemcpyAsync(uw.data(), L.uw, 24 * L.capw, cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  for (long long i = 0; i < L.n; ++i) {
+    if (b) b[i] = (int)(pb[i] & ~kHistFlag);
+    if (u)
+      for (int k = 0; k < 3; ++k) u[3 * i + k] = (pb[i] & kHistFlag) ? uu[k * L.cap + i] : 0.0;
+  }
+  for (long long i = 0; i < L.nw; ++i) {
+    if (wall_id) wall_id[i] = c->wall_user[ww[i] & ~kHistFlag];
+    if (wall_u)
+      for (int k = 0; k < 3; ++k) wall_u[3 * i + k] = (ww[i] & kHistFlag) ? uw[k * L.capw + i] : 0.0;
+  }
+  return cuda_check(c, "get_contacts");
+}
+
+int dem_get_bins(dem_ctx* c, long long cap, unsigned int* keys, int* ids, long long* n) {
+  if (!c || !n) return DEM_ERR_INVALID_ARG;
+  *n = c->n_entries;
+  const long long m = std::min(cap, c->n_entries);
+  if (m > 0 && keys && ids && c->sorted_keys) {
+    cudaMemcpyAsync(keys, c->sorted_keys, 4 * m, cudaMemcpyDeviceToHost, c->st);
+    cudaMemcpyAsync(ids, c->sorted_ids, 4 * m, cudaMemcpyDeviceToHost, c->st);
+    cudaStreamSynchronize(c->st);
+  }
+  return cuda_check(c, "get_bins");
+}
+
+int dem_audit(dem_ctx* c, long long* missed) {
+  if (!c || !missed) return DEM_ERR_INVALID_ARG;
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  refresh_devstate(c);
+  if (!c->have_list) {
+    rc = rebuild(c);
+    if (rc) return rc;
+  }
+  rc = detect_into(c, 2, 0.0);
+  if (rc) return rc;
+  const ContactList& F = c->lists[2].L;
+  unsigned long long* d_m = ptr<unsigned long long>(c->b_totals) + 4;
+  cudaMemsetAsync(d_m, 0, 8, c->st);
+  DetectOut o{};
+  launch_audit(c->D, o, curL(c), F.n, F.pa, F.pb, F.nw, F.ws, F.ww, (double)c->step * c->P.dt, d_m, c->st);
+  unsigned long long h = 0;
+  cudaMemcpyAsync(&h, d_m, 8, cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  *missed = (long long)h;
+  c->stats.missed_contacts += (long long)h;
+  return cuda_check(c, "audit");
+}
+
+}  // extern "C"

@@ -1,0 +1,395 @@
+// dem_detect.cu -- contact detection with an enlarged geometry (section 2.2).
+//
+// Every sphere, enlarged by the safety margin, is quantised onto the 2^-24 m
+// detection lattice and registered in every bin its enlarged box touches
+// (multi-bin registration).  The registrations are sorted by bin key with the
+// radix sort; each sphere then walks its own bins and tests the members with a
+// larger id from another clump with the exact int64 predicate
+// |qa - qb|^2 <= (rho_a + rho_b)^2, keeping a pair only in the bin that holds
+// the per-axis maximum of the two boxes' lower corners, so each pair is found
+// once.  The output is a canonical list sorted by (a, b), one row per sphere,
+// onto which the tangential history of the previous list is carried.
+#include <cfloat>
+
+#include "dem_dev.cuh"
+#include "dem_prims.cuh"
+#include "dem_walls.cuh"
+
+namespace dem {
+
+namespace {
+
+__device__ __forceinline__ void clump_com(const DevState& d, int c, const SceneGrid& g,
+                                          double X[3]) {
+  if (d.prec == 0) {
+    const double4_32a p = d.cpos[c];
+    X[0] = p.x; X[1] = p.y; X[2] = p.z;
+  } else {
+    const int4 v = d.cvox[c];
+    const float4 o = d.coff[c];
+    // exact for positions on the 2^-44 m grid (see dem_set_state)
+    X[0] = __dadd_rn(g.lo[0], __dadd_rn(__dmul_rn((double)v.x, kVoxel), (double)o.x));
+    X[1] = __dadd_rn(g.lo[1], __dadd_rn(__dmul_rn((double)v.y, kVoxel), (double)o.y));
+    X[2] = __dadd_rn(g.lo[2], __dadd_rn(__dmul_rn((double)v.z, kVoxel), (double)o.z));
+  }
+}
+
+// Float estimate of the same distance; |error| is far below wall_slack().
+__device__ float wall_distance_est(const WallDev& w, double t, const double x[3]) {
+  float dd[3], n[3];
+  for (int k = 0; k < 3; ++k) {
+    dd[k] = (float)x[k] - ((float)w.p[k] + (float)w.vel[k] * (float)t);
+    n[k] = (float)w.n[k];
+  }
+  const float ax = dd[0] * n[0] + dd[1] * n[1] + dd[2] * n[2];
+  if (w.type == 0) return ax;
+  float rv[3] = {dd[0] - ax * n[0], dd[1] - ax * n[1], dd[2] - ax * n[2]};
+  const float rho = sqrtf(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+  if (w.type == 1) return (float)w.radius - rho;
+  const float H = (float)w.height, Rb = (float)w.rb;
+  float tl = (rho * Rb + ax * H) / (Rb * Rb + H * H);
+  tl = fminf(fmaxf(tl, 0.f), 1.f);
+  const float dl = sqrtf((rho - tl * Rb) * (rho - tl * Rb) + (ax - tl * H) * (ax - tl * H));
+  float tb = fminf(fmaxf(rho / Rb, 0.f), 1.f);
+  const float db = sqrtf((rho - tb * Rb) * (rho - tb * Rb) + (ax - H) * (ax - H));
+  const bool inside = (ax >= 0.f && ax <= H && rho * H <= ax * Rb);
+  const float dm = fminf(dl, db);
+  return inside ? -dm : dm;
+}
+
+__device__ __forceinline__ float wall_slack(const WallDev& w, const double x[3]) {
+  float m = fabsf((float)w.p[0]) + fabsf((float)w.p[1]) + fabsf((float)w.p[2]) +
+            fabsf((float)x[0]) + fabsf((float)x[1]) + fabsf((float)x[2]) + 1.f;
+  return 4e-6f * m;
+}
+
+__global__ void k_detect(DevState d, DetectOut o, double margin, const double* __restrict__ smargin,
+                         double t, double travel_time) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns) return;
+  const int2 si = d.sinfo[s];
+  const int2 ci = d.cinfo[si.x];
+  const SceneGrid g = d.grids[ci.y];
+  double X[3];
+  clump_com(d, si.x, g, X);
+  const double4_32a q4 = d.cq[si.x];
+  const double q[4] = {q4.x, q4.y, q4.z, q4.w};
+  const double4_32a tp = d.tp64[si.y];
+  const double p[3] = {tp.x, tp.y, tp.z};
+  double x[3];
+  det_centre(q, p, X, x);
+  const double m = smargin ? smargin[s] : margin;
+  long long qc[3];
+  for (int k = 0; k < 3; ++k) {
+    long long v = __double2ll_rn(__dmul_rn(__dsub_rn(x[k], g.lo[k]), kDetScale));
+    // a sphere more than 64 m outside its domain is clamped (it only meets
+    // the boundary bins, where it can still be found)
+    v = v < -(1ll << 30) ? -(1ll << 30) : (v > (1ll << 30) ? (1ll << 30) : v);
+    qc[k] = v;
+  }
+  const long long rho = (long long)ceil(__dmul_rn(__dadd_rn(tp.w, m), kDetScale)) + 1;
+  o.det[s] = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
+  long long cnt = 1;
+  for (int k = 0; k < 3; ++k) {
+    const int lo = clampi(floordiv_ll(qc[k] - rho, g.L), g.dims[k] - 1);
+    const int hi = clampi(floordiv_ll(qc[k] + rho, g.L), g.dims[k] - 1);
+    cnt *= (hi - lo + 1);
+  }
+  o.bin_cnt[s] = (uint32_t)cnt;
+  // sphere-wall candidates: distance within radius + margin + wall travel
+  uint32_t mask = 0;
+  for (int i = 0; i < g.wall_count; ++i) {
+    const WallDev& w = d.walls[d.wall_idx[g.wall_start + i]];
+    const double travel = __dmul_rn(__dsqrt_rn(dot3d(w.vel, w.vel)), travel_time);
+    const double thr = __dadd_rn(__dadd_rn(tp.w, m), travel);
+    const float est = wall_distance_est(w, t, x);
+    const float slack = wall_slack(w, x);
+    bool in;
+    if (est > (float)thr + slack) {
+      in = false;
+    } else if (est < (float)thr - slack) {
+      in = true;
+    } else {
+      double nw[3];
+      in = wall_distance64(w, t, x, nw) <= thr;
+    }
+    if (in) mask |= 1u << i;
+  }
+  o.wall_mask[s] = mask;
+  o.wall_cnt[s] = __popc(mask);
+}
+
+__global__ void k_emit_bins(DevState d, DetectOut o) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns) return;
+  const int4 q = o.det[s];
+  const SceneGrid g = d.grids[d.cinfo[d.sinfo[s].x].y];
+  int lo[3], hi[3];
+  const int qq[3] = {q.x, q.y, q.z};
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = clampi(floordiv_ll((long long)qq[k] - q.w, g.L), g.dims[k] - 1);
+    hi[k] = clampi(floordiv_ll((long long)qq[k] + q.w, g.L), g.dims[k] - 1);
+  }
+  uint32_t off = o.bin_off[s];
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        o.keys[off] = g.key_base + (uint32_t)((z * g.dims[1] + y) * g.dims[0] + x);
+        o.ids[off] = (uint32_t)s;
+        ++off;
+      }
+}
+
+__global__ void k_bin_bounds(const uint32_t* __restrict__ keys, long long n,
+                             uint32_t* __restrict__ start, uint32_t* __restrict__ end) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys[i];
+  if (i == 0 || keys[i - 1] != k) start[k] = (uint32_t)i;
+  if (i == n - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
+}
+
+// Narrow phase for sphere a over its own bins; count or write its row.
+template <bool WRITE>
+__global__ void k_narrow(DevState d, DetectOut o, int* __restrict__ pa, uint32_t* __restrict__ pb) {
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.ns) return;
+  const int4 qa = o.det[a];
+  const int owner_a = d.sinfo[a].x;
+  const SceneGrid g = d.grids[d.cinfo[owner_a].y];
+  const long long qaa[3] = {qa.x, qa.y, qa.z};
+  int lo[3], hi[3];
+  long long la[3];
+  for (int k = 0; k < 3; ++k) {
+    la[k] = qaa[k] - qa.w;
+    lo[k] = clampi(floordiv_ll(la[k], g.L), g.dims[k] - 1);
+    hi[k] = clampi(floordiv_ll(qaa[k] + qa.w, g.L), g.dims[k] - 1);
+  }
+  uint32_t n = 0;
+  const uint32_t row0 = WRITE ? o.pair_off[a] : 0u;
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        const uint32_t key = g.key_base + (uint32_t)((z * g.dims[1] + y) * g.dims[0] + x);
+        uint32_t i0 = o.bin_start[key], i1 = o.bin_end[key];
+        if (i1 <= i0) continue;
+        // members are sorted by id: skip to the first id > a
+        uint32_t lo_i = i0, hi_i = i1;
+        while (lo_i < hi_i) {
+          const uint32_t mid = (lo_i + hi_i) >> 1;
+          if (o.ids[mid] <= (uint32_t)a) lo_i = mid + 1; else hi_i = mid;
+        }
+        for (uint32_t j = lo_i; j < i1; ++j) {
+          const uint32_t b = o.ids[j];
+          if (d.sinfo[b].x == owner_a) continue;
+          const int4 qb = o.det[b];
+          const long long dx = (long long)qb.x - qa.x, dy = (long long)qb.y - qa.y,
+                          dz = (long long)qb.z - qa.z;
+          const long long rr = (long long)qa.w + qb.w;
+          if (dx * dx + dy * dy + dz * dz > rr * rr) continue;
+          // owning bin: the one holding the per-axis max of the lower corners
+          const long long lb0 = (long long)qb.x - qb.w, lb1 = (long long)qb.y - qb.w,
+                          lb2 = (long long)qb.z - qb.w;
+          if (clampi(floordiv_ll(la[0] > lb0 ? la[0] : lb0, g.L), g.dims[0] - 1) != x) continue;
+          if (clampi(floordiv_ll(la[1] > lb1 ? la[1] : lb1, g.L), g.dims[1] - 1) != y) continue;
+          if (clampi(floordiv_ll(la[2] > lb2 ? la[2] : lb2, g.L), g.dims[2] - 1) != z) continue;
+          if (WRITE) pb[row0 + n] = b;
+          ++n;
+        }
+      }
+  if (!WRITE) {
+    o.pair_cnt[a] = n;
+    return;
+  }
+  // canonical order inside the row: ascending b (rows are short)
+  for (uint32_t i = 1; i < n; ++i) {
+    const uint32_t v = pb[row0 + i];
+    uint32_t j = i;
+    while (j > 0 && pb[row0 + j - 1] > v) {
+      pb[row0 + j] = pb[row0 + j - 1];
+      --j;
+    }
+    pb[row0 + j] = v;
+  }
+  for (uint32_t i = 0; i < n; ++i) pa[row0 + i] = (int)a;
+}
+
+__global__ void k_wall_emit(DevState d, DetectOut o, int* __restrict__ ws, uint32_t* __restrict__ ww) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns) return;
+  uint32_t mask = o.wall_mask[s];
+  if (!mask) return;
+  const SceneGrid g = d.grids[d.cinfo[d.sinfo[s].x].y];
+  uint32_t off = o.wall_off[s];
+  while (mask) {
+    const int i = __ffs(mask) - 1;
+    mask &= mask - 1;
+    ws[off] = (int)s;
+    ww[off] = (uint32_t)d.wall_idx[g.wall_start + i];
+    ++off;
+  }
+}
+
+// Carry the tangential history of every (a, b) present in the old list.
+__global__ void k_hist_pairs(ContactList oldl, ContactList newl, long long old_ns) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= newl.n) return;
+  const int a = newl.pa[i];
+  const uint32_t b = newl.pb[i] & ~kHistFlag;
+  if (a >= old_ns || oldl.n == 0) return;
+  uint32_t lo = oldl.row[a], hi = oldl.row[a + 1];
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((oldl.pb[mid] & ~kHistFlag) < b) lo = mid + 1; else hi = mid;
+  }
+  if (lo < oldl.row[a + 1]) {
+    const uint32_t ob = oldl.pb[lo];
+    if ((ob & ~kHistFlag) == b && (ob & kHistFlag)) {
+      newl.u[i] = oldl.u[lo];
+      newl.u[newl.cap + i] = oldl.u[oldl.cap + lo];
+      newl.u[2 * newl.cap + i] = oldl.u[2 * oldl.cap + lo];
+      newl.pb[i] = b | kHistFlag;
+    }
+  }
+}
+
+__global__ void k_hist_walls(ContactList oldl, ContactList newl, long long old_ns) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= newl.nw) return;
+  const int s = newl.ws[i];
+  const uint32_t w = newl.ww[i] & ~kHistFlag;
+  if (s >= old_ns || oldl.nw == 0) return;
+  for (uint32_t j = oldl.wrow[s]; j < oldl.wrow[s + 1]; ++j) {
+    const uint32_t ow = oldl.ww[j];
+    if ((ow & ~kHistFlag) == w) {
+      if (ow & kHistFlag) {
+        newl.uw[i] = oldl.uw[j];
+        newl.uw[newl.capw + i] = oldl.uw[oldl.capw + j];
+        newl.uw[2 * newl.capw + i] = oldl.uw[2 * oldl.capw + j];
+        newl.ww[i] = w | kHistFlag;
+      }
+      break;
+    }
+  }
+}
+
+// Row pointers of the wall list from the per-sphere offsets.
+__global__ void k_copy_row(const uint32_t* __restrict__ off, long long n, uint32_t total,
+                           uint32_t* __restrict__ row) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) row[i] = off[i];
+  if (i == n) row[n] = total;
+}
+
+// Exact missed-contact check: each touching pair of a fresh zero-margin list
+// must be present in the current list.
+__global__ void k_audit_pairs(DevState d, ContactList cur, long long nf, const int* __restrict__ fa,
+                              const uint32_t* __restrict__ fb, unsigned long long* missed) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const int a = fa[i];
+  const uint32_t b = fb[i] & ~kHistFlag;
+  double xa[3], xb[3];
+  for (int side = 0; side < 2; ++side) {
+    const long long s = side ? (long long)b : (long long)a;
+    const int2 si = d.sinfo[s];
+    const SceneGrid g = d.grids[d.cinfo[si.x].y];
+    double X[3];
+    clump_com(d, si.x, g, X);
+    const double4_32a q4 = d.cq[si.x];
+    const double q[4] = {q4.x, q4.y, q4.z, q4.w};
+    const double4_32a tp = d.tp64[si.y];
+    const double p[3] = {tp.x, tp.y, tp.z};
+    det_centre(q, p, X, side ? xb : xa);
+  }
+  const double ra = d.tp64[d.sinfo[a].y].w, rb = d.tp64[d.sinfo[b].y].w;
+  double dd[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+  const double gap = __dsub_rn(__dsqrt_rn(dot3d(dd, dd)), __dadd_rn(ra, rb));
+  if (!(gap < 0.0)) return;
+  uint32_t lo = cur.row[a], hi = cur.row[a + 1];
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((cur.pb[mid] & ~kHistFlag) < b) lo = mid + 1; else hi = mid;
+  }
+  if (!(lo < cur.row[a + 1] && (cur.pb[lo] & ~kHistFlag) == b)) atomicAdd(missed, 1ull);
+}
+
+__global__ void k_audit_walls(DevState d, ContactList cur, long long nf, const int* __restrict__ fs,
+                              const uint32_t* __restrict__ fw, double t,
+                              unsigned long long* missed) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const int s = fs[i];
+  const uint32_t w = fw[i] & ~kHistFlag;
+  const int2 si = d.sinfo[s];
+  const SceneGrid g = d.grids[d.cinfo[si.x].y];
+  double X[3], x[3], nw[3];
+  clump_com(d, si.x, g, X);
+  const double4_32a q4 = d.cq[si.x];
+  const double q[4] = {q4.x, q4.y, q4.z, q4.w};
+  const double4_32a tp = d.tp64[si.y];
+  const double p[3] = {tp.x, tp.y, tp.z};
+  det_centre(q, p, X, x);
+  if (!(wall_distance64(d.walls[w], t, x, nw) < tp.w)) return;
+  for (uint32_t j = cur.wrow[s]; j < cur.wrow[s + 1]; ++j)
+    if ((cur.ww[j] & ~kHistFlag) == w) return;
+  atomicAdd(missed, 1ull);
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_detect(const DevState& d, const DetectOut& o, double margin, const double* smargin,
+                   double t, double travel_time, cudaStream_t st) {
+  if (d.ns == 0) return;
+  { k_detect<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, margin, smargin, t, travel_time); count_launch(); }
+}
+
+void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st) {
+  if (d.ns == 0) return;
+  { k_emit_bins<<<nblk(d.ns, 128), 128, 0, st>>>(d, o); count_launch(); }
+}
+
+void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint32_t* end,
+                       cudaStream_t st) {
+  if (n == 0) return;
+  { k_bin_bounds<<<nblk(n, 256), 256, 0, st>>>(keys, n, start, end); count_launch(); }
+}
+
+void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
+                   cudaStream_t st) {
+  if (d.ns == 0) return;
+  if (write)
+    { k_narrow<true><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, pa, pb); count_launch(); }
+  else
+    { k_narrow<false><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, pa, pb); count_launch(); }
+}
+
+void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,
+                      cudaStream_t st) {
+  if (d.ns == 0) return;
+  { k_wall_emit<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, ws, ww); count_launch(); }
+}
+
+void launch_hist_map(const ContactList& oldl, ContactList& newl, long long old_ns,
+                     cudaStream_t st) {
+  if (newl.n > 0) { k_hist_pairs<<<nblk(newl.n, 256), 256, 0, st>>>(oldl, newl, old_ns); count_launch(); }
+  if (newl.nw > 0) { k_hist_walls<<<nblk(newl.nw, 256), 256, 0, st>>>(oldl, newl, old_ns); count_launch(); }
+}
+
+void launch_copy_row(const uint32_t* off, long long n, uint32_t total, uint32_t* row,
+                     cudaStream_t st) {
+  { k_copy_row<<<nblk(n + 1, 256), 256, 0, st>>>(off, n, total, row); count_launch(); }
+}
+
+void launch_audit(const DevState& d, const DetectOut& o, const ContactList& cur, long long n_fresh,
+                  const int* fa, const uint32_t* fb, long long nw_fresh, const int* fws,
+                  const uint32_t* fww, double t, unsigned long long* d_missed, cudaStream_t st) {
+  (void)o;
+  if (n_fresh > 0) { k_audit_pairs<<<nblk(n_fresh, 128), 128, 0, st>>>(d, cur, n_fresh, fa, fb, d_missed); count_launch(); }
+  if (nw_fresh > 0)
+    { k_audit_walls<<<nblk(nw_fresh, 128), 128, 0, st>>>(d, cur, nw_fresh, fws, fww, t, d_missed); count_launch(); }
+}
+
+}  // namespace dem

@@ -1,0 +1,120 @@
+// dem_dev.cuh -- device view of a context and the kernel launchers.
+#pragma once
+#include "dem_internal.cuh"
+
+namespace dem {
+
+// Pointers into the context's device buffers, passed by value to kernels.
+struct DevState {
+  int prec;                 // 0 FP64, 1 FP32_VOXEL
+  long long ncl, ns;
+  int nmat, nwalls;
+  double h, g[3];
+  // templates
+  const int* tpl_off;
+  const double4_32a* tp64;      // per template sphere: p (FP64), r
+  const float4* tp32;       // per template sphere: p, r (float)
+  const int* tmat;          // per template sphere: material
+  const double* tmass;      // per template
+  const double* tinert;     // per template, 3 principal moments
+  const float* tpbound;     // per template: max |p| over its spheres
+  // clumps
+  const int2* cinfo;        // {template, scene}
+  const int* csph;          // first sphere of each clump (ncl + 1)
+  double4_32a* cpos;            // FP64: centre of mass
+  int4* cvox;               // FP32_VOXEL: voxel index (w unused)
+  float4* coff;             // FP32_VOXEL: offset in the voxel (w unused)
+  double4_32a* cq;              // orientation (both modes)
+  double4_32a* cv;              // velocity (both modes)
+  double4_32a* cw;              // angular velocity, body frame (both modes)
+  double4_32a* mv64;            // FP64 mirrors for contacts: {v, mass}
+  double4_32a* mw64;            //                            {omega world, 0}
+  float4* mv32;             // FP32 mirrors: {v, mass}
+  float4* mw32;             //               {omega world, 0}
+  double* acc64;            // 8 per clump: F, T (FP64)
+  float* acc32;             // 8 per clump: F, T (FP32)
+  // certificate reference (state at the last rebuild)
+  double4_32a* ref_pos;         // FP64: CoM at the last rebuild
+  int4* ref_vox;            // FP32_VOXEL: voxel / offset at the last rebuild
+  float4* ref_off;
+  float4* ref_q;            // orientation at the last rebuild (float)
+  const float* cmargin;     // per clump margin for the certificate (or NULL)
+  // spheres
+  const int2* sinfo;        // {owner, template sphere}
+  SphA64* sa64;
+  double4_32a* sb64;            // {rel = R p, bits(owner | mat << 32)}
+  SphA32* sa32;
+  float4* sb32;             // {rel = R p, int bits(mat)}
+  // scenes, walls, materials
+  const SceneGrid* grids;
+  const WallDev* walls;
+  const int* wall_idx;      // per scene wall lists (global wall ids)
+  const int* wall_scene;    // scene of each (internal) wall
+  long long* wfix;          // FP32_VOXEL: wall reference point at the current time, fixed point
+                            //   relative to its scene corner (3 per wall)
+  double* wpos;             // wall reference point in world coordinates at the current time (3 per wall)
+  double* wforce;           // 3 per wall (FP64 accumulation)
+  const PairMat<double>* pm64;
+  const PairMat<float>* pm32;
+  int* flags;
+  unsigned long long* counters;  // [0] active contacts, [1] guard violations
+};
+
+struct DetectOut {
+  int4* det;                // per sphere {qx, qy, qz, rho}
+  uint32_t* bin_cnt;        // per sphere
+  uint32_t* bin_off;        // per sphere (scan)
+  uint32_t* wall_mask;      // per sphere
+  uint32_t* wall_cnt;       // per sphere
+  uint32_t* wall_off;       // per sphere (scan)
+  uint32_t* keys;           // per entry
+  uint32_t* ids;            // per entry
+  uint32_t* bin_start;      // per bin
+  uint32_t* bin_end;        // per bin
+  uint32_t* pair_cnt;       // per sphere
+  uint32_t* pair_off;       // per sphere (scan) -> row pointer (ns + 1 entries)
+};
+
+struct ContactList {
+  int* pa;                  // sphere a (pairs)
+  uint32_t* pb;             // sphere b | kHistFlag
+  double* u;                // 3 * capacity (SoA: ux | uy | uz)
+  uint32_t* row;            // ns + 1 row pointer by sphere a
+  long long n, cap;
+  int* ws;                  // wall contacts: sphere
+  uint32_t* ww;             // wall id | kHistFlag
+  double* uw;               // 3 * capacity (SoA)
+  uint32_t* wrow;           // ns + 1
+  long long nw, capw;
+};
+
+// detection
+void launch_detect(const DevState& d, const DetectOut& o, double margin, const double* smargin,
+                   double t, double travel_time, cudaStream_t st);
+void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st);
+void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint32_t* end,
+                       cudaStream_t st);
+void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
+                   cudaStream_t st);
+void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,
+                      cudaStream_t st);
+void launch_hist_map(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
+void launch_copy_row(const uint32_t* off, long long n, uint32_t total, uint32_t* row,
+                     cudaStream_t st);
+void launch_audit(const DevState& d, const DetectOut& o, const ContactList& cur, long long n_fresh,
+                  const int* fa, const uint32_t* fb, long long nw_fresh, const int* fws,
+                  const uint32_t* fww, double t, unsigned long long* d_missed, cudaStream_t st);
+
+// per step
+void launch_force_pairs(const DevState& d, ContactList& l, bool count_active, cudaStream_t st);
+void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_active,
+                        cudaStream_t st);
+void launch_update(const DevState& d, bool integrate, double t_next, double margin,
+                   bool check_cert, cudaStream_t st);
+void launch_walls_at(const DevState& d, double t, cudaStream_t st);
+void launch_set_cert_ref(const DevState& d, cudaStream_t st);
+void launch_get_state(const DevState& d, double* pos, double* quat, double* vel, double* angvel,
+                      cudaStream_t st);
+void launch_get_forces(const DevState& d, double* F, double* T, cudaStream_t st);
+
+}  // namespace dem

@@ -1,0 +1,230 @@
+// dem_internal.cuh -- device layouts and helpers shared by the DEM kernels.
+//
+// Two precision modes (the C ABI's DEM_FP64 and DEM_FP32_VOXEL):
+//   FP64        every quantity in double; used for small reference runs.
+//   FP32_VOXEL  clump position = int voxel index (voxel edge 2^-20 m) + float
+//               offset; forces, torques and contact kinematics in float;
+//               double only for the velocity / angular velocity / orientation
+//               state of the integrator and the tangential-history sums.
+//               Where a float difference would cancel catastrophically (the
+//               overlap delta_n = r_a + r_b - |x_b - x_a| of Eq. (1)), sphere
+//               centres are carried as int64 fixed point (2^-44 m) and the
+//               overlap is formed with float-float error-free transforms
+//               (Knuth's TwoSum, FMA-based TwoProduct), not with double.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dem {
+
+constexpr int kDetBits = 24;   // detection lattice: 2^-24 m
+constexpr int kFixBits = 44;   // fixed-point sphere centres: 2^-44 m
+constexpr int kVoxLog2 = 20;   // voxel edge 2^-20 m (FP32_VOXEL positions)
+constexpr double kDetScale = 16777216.0;          // 2^24
+constexpr double kVoxel = 1.0 / 1048576.0;        // 2^-20
+constexpr float kFixToM = 5.684341886080802e-14f; // 2^-44
+constexpr float kMToFix = 17592186044416.0f;      // 2^44
+constexpr uint32_t kHistFlag = 0x80000000u;       // in pb / ww: history is non-zero
+
+// Pair material coefficients (section 2.1: derived from E, nu, CoR and mu).
+// kn = 4/3 E*, kt = 8 G*, mu; the damping terms of Eq. (1a), (1b) are
+//   f gamma_n m = cn sqrt(f m),  f gamma_t m = ct sqrt(f m)
+// with cn = -2 sqrt(5/6) beta sqrt(2 E*), ct = -2 sqrt(5/6) beta sqrt(8 G*).
+template <typename T>
+struct PairMat {
+  T kn, kt, mu, cn, ct, pad0, pad1, pad2;
+};
+
+// Per-scene detection grid.
+struct SceneGrid {
+  double lo[3];      // domain corner (also the voxel origin in FP32_VOXEL)
+  long long L;       // bin edge in lattice units (2^-24 m)
+  int dims[3];       // bins per axis
+  uint32_t key_base; // first bin key of this scene
+  int wall_start;    // this scene's walls: wall_idx[wall_start .. wall_start+wall_count)
+  int wall_count;
+};
+
+// Wall description on the device (both precisions).  For FP32_VOXEL the
+// geometric constants are also kept as float-float pairs.
+struct WallDev {
+  int type, material;
+  double p[3], n[3], vel[3];
+  double radius, half_angle, height;
+  double rb;          // cone base radius = height * tan(half_angle)
+  float nh[3], nl[3]; // unit normal / axis as float-float
+  float rh, rl;       // cylinder radius as float-float
+  float ch, cl, sh, sl; // cone cos / sin of the half angle as float-float
+  float hh, hl;       // cone height as float-float
+  float rbh, rbl;     // cone base radius as float-float
+  float speed;        // |vel|
+};
+
+// Sphere pose record used by the contact kernels (written every step).
+struct alignas(32) SphA32 {  // FP32_VOXEL
+  long long x, y, z;          // centre, fixed point 2^-44 m, relative to the scene corner
+  float r;                    // radius
+  int owner;                  // clump id
+};
+struct alignas(32) SphA64 {  // FP64
+  double x, y, z, r;
+};
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic (error-free transforms)
+// ---------------------------------------------------------------------------
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.h, b.h);
+  float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+  return fast_two_sum(s.h, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
+  return fast_two_sum(p.h, e);
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+  ff p = two_prod(a.h, b);
+  float e = __fmaf_rn(a.l, b, p.l);
+  return fast_two_sum(p.h, e);
+}
+__device__ __forceinline__ ff ff_scale2(ff a, float pow2) { return {a.h * pow2, a.l * pow2}; }
+__device__ __forceinline__ ff ff_from_double(double d) {
+  float h = __double2float_rn(d);
+  float l = __double2float_rn(d - (double)h);
+  return {h, l};
+}
+__device__ __forceinline__ float ff_to_float(ff a) { return __fadd_rn(a.h, a.l); }
+// sqrt of a non-negative float-float to float-float accuracy (one Newton step)
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  if (!(a.h > 0.f)) return {0.f, 0.f};
+  float s = sqrtf(a.h);
+  ff s2 = two_prod(s, s);
+  float corr = __fdiv_rn(__fadd_rn(__fsub_rn(a.h, s2.h), __fsub_rn(a.l, s2.l)), 2.f * s);
+  return fast_two_sum(s, corr);
+}
+// int64 fixed-point value -> float-float metres (exact residual)
+__device__ __forceinline__ ff fix_to_ff(long long v) {
+  float h = __ll2float_rn(v);
+  long long rem = v - __float2ll_rn(h);
+  float l = __ll2float_rn(rem);
+  return {h * kFixToM, l * kFixToM};
+}
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ V3<T> v3(T x, T y, T z) { return {x, y, z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename T>
+__device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+template <typename T>
+__device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Rotation matrix of a unit quaternion (w, x, y, z), rows r[0..8].
+template <typename T>
+__device__ __forceinline__ void quat_to_mat(T w, T x, T y, T z, T r[9]) {
+  T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  T wx = w * x, wy = w * y, wz = w * z;
+  r[0] = T(1) - T(2) * (yy + zz); r[1] = T(2) * (xy - wz); r[2] = T(2) * (xz + wy);
+  r[3] = T(2) * (xy + wz); r[4] = T(1) - T(2) * (xx + zz); r[5] = T(2) * (yz - wx);
+  r[6] = T(2) * (xz - wy); r[7] = T(2) * (yz + wx); r[8] = T(1) - T(2) * (xx + yy);
+}
+template <typename T>
+__device__ __forceinline__ V3<T> mat_mul(const T r[9], V3<T> p) {
+  return {(r[0] * p.x + r[1] * p.y) + r[2] * p.z, (r[3] * p.x + r[4] * p.y) + r[5] * p.z,
+          (r[6] * p.x + r[7] * p.y) + r[8] * p.z};
+}
+template <typename T>
+__device__ __forceinline__ V3<T> mat_tmul(const T r[9], V3<T> p) {
+  return {(r[0] * p.x + r[3] * p.y) + r[6] * p.z, (r[1] * p.x + r[4] * p.y) + r[7] * p.z,
+          (r[2] * p.x + r[5] * p.y) + r[8] * p.z};
+}
+
+// The detection centre x = X + R(q) p evaluated with exactly one IEEE double
+// rounding per operation in a fixed order (no contraction into FMA): the
+// detection lattice coordinates are integers decided by this value, and the
+// definition is the same wherever it is evaluated.
+__device__ __forceinline__ void det_centre(const double q[4], const double p[3], const double X[3],
+                                           double x[3]) {
+  const double w = q[0], qx = q[1], qy = q[2], qz = q[3];
+  const double xx = __dmul_rn(qx, qx), yy = __dmul_rn(qy, qy), zz = __dmul_rn(qz, qz);
+  const double xy = __dmul_rn(qx, qy), xz = __dmul_rn(qx, qz), yz = __dmul_rn(qy, qz);
+  const double wx = __dmul_rn(w, qx), wy = __dmul_rn(w, qy), wz = __dmul_rn(w, qz);
+  double r[9];
+  r[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(yy, zz)));
+  r[1] = __dmul_rn(2.0, __dsub_rn(xy, wz));
+  r[2] = __dmul_rn(2.0, __dadd_rn(xz, wy));
+  r[3] = __dmul_rn(2.0, __dadd_rn(xy, wz));
+  r[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, zz)));
+  r[5] = __dmul_rn(2.0, __dsub_rn(yz, wx));
+  r[6] = __dmul_rn(2.0, __dsub_rn(xz, wy));
+  r[7] = __dmul_rn(2.0, __dadd_rn(yz, wx));
+  r[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, yy)));
+  for (int k = 0; k < 3; ++k) {
+    const double rp = __dadd_rn(__dadd_rn(__dmul_rn(r[3 * k], p[0]), __dmul_rn(r[3 * k + 1], p[1])),
+                                __dmul_rn(r[3 * k + 2], p[2]));
+    x[k] = __dadd_rn(X[k], rp);
+  }
+}
+
+__device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
+  return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+__device__ __forceinline__ int clampi(long long v, int hi) {
+  return v < 0 ? 0 : (v > hi ? hi : (int)v);
+}
+
+// Vector reductions into global float memory (sm_90+).
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+// Error flags written by kernels, read by the host after each call.
+enum : int {
+  kFlagNonFinite = 1,
+  kFlagCapacity = 2,
+  kFlagGuard = 4,
+  kFlagTimeout = 8,
+  kFlagBounds = 16,
+};
+
+}  // namespace dem

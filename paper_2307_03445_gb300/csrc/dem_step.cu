@@ -1,0 +1,696 @@
+// dem_step.cu -- per-step kernels: contact forces and clump update.
+//
+// Force kernels run one thread per listed contact (grid-stride, persistent
+// grid).  A listed contact whose overlap is not positive is a false positive
+// of the enlarged list and contributes nothing (section 2.2); its history is
+// dropped by clearing a flag bit instead of rewriting it.  Active contacts
+// evaluate Eq. (2) (kinematics), Eq. (3) (history update), Eq. (1) (forces)
+// and Eq. (4) (cap), and add +F to body b and -F to body a together with the
+// moments of F about each centre of mass (vector reductions into float
+// accumulators in FP32_VOXEL, double atomics in FP64).
+//
+// The update kernel integrates Eq. (5) for a block of clumps, then, with the
+// new orientation held as a float-float rotation matrix in shared memory,
+// recomputes the pose records of all spheres of those clumps.
+#include "dem_dev.cuh"
+#include "dem_prims.cuh"
+#include "dem_walls.cuh"
+
+namespace dem {
+
+namespace {
+
+template <typename T>
+struct Law {
+  V3<T> F;    // force on body b
+  V3<T> u;    // capped: the new history; otherwise the increment to add
+  bool capped;
+};
+
+// Eq. (2b)-(4) for one active contact: n from a to b, dn > 0, vrel = velocity
+// of b minus velocity of a at the contact point, u the stored history.
+template <typename T>
+__device__ __forceinline__ Law<T> contact_law(const PairMat<T>& pm, T h, V3<T> n, T dn, V3<T> vrel,
+                                              V3<T> u, T Rbar, T mbar) {
+  Law<T> r;
+  const T vns = dot(vrel, n);
+  const V3<T> vt = vrel - vns * n;                  // Eq. (2b), (2c)
+  const V3<T> up = u + h * vt;                      // Eq. (3)
+  const T upn = dot(up, n);
+  const V3<T> upt = up - upn * n;
+  const T f = sqrt(Rbar * dn);                      // Eq. (1c)
+  const T sfm = sqrt(f * mbar);
+  const T fns = f * pm.kn * dn - pm.cn * sfm * vns; // Eq. (1a) along n
+  const V3<T> Ft = (-f * pm.kt) * upt - (pm.ct * sfm) * vt;  // Eq. (1b)
+  const T fn = fabs(fns), ft = sqrt(dot(Ft, Ft));
+  if (ft > pm.mu * fn) {                            // Eq. (4)
+    const T s = ft > T(0) ? pm.mu * fn / ft : T(0);
+    const T ul = sqrt(dot(upt, upt));
+    const T us = ul > T(0) ? pm.mu * fn / (f * pm.kt) / ul : T(0);
+    r.F = fns * n + s * Ft;
+    r.u = us * upt;
+    r.capped = true;
+  } else {
+    r.F = fns * n + Ft;
+    r.u = h * vt - upn * n;  // u' - u
+    r.capped = false;
+  }
+  return r;
+}
+
+__device__ __forceinline__ void warp_count(bool active, unsigned long long* ctr) {
+  const unsigned m = __activemask();
+  const unsigned b = __ballot_sync(m, active);
+  if ((threadIdx.x & 31) == __ffs(m) - 1 && b) atomicAdd(ctr, (unsigned long long)__popc(b));
+}
+
+__device__ __forceinline__ void add_clump64(double* acc, int c, V3<double> F, V3<double> T) {
+  double* p = acc + 8 * (long long)c;
+  atomicAdd(p + 0, F.x); atomicAdd(p + 1, F.y); atomicAdd(p + 2, F.z);
+  atomicAdd(p + 3, T.x); atomicAdd(p + 4, T.y); atomicAdd(p + 5, T.z);
+}
+__device__ __forceinline__ void add_clump32(float* acc, int c, V3<float> F, V3<float> T) {
+  float* p = acc + 8 * (long long)c;
+  red_add_v4(p, F.x, F.y, F.z, T.x);
+  red_add_v2(p + 4, T.y, T.z);
+}
+
+// ---------------------------------------------------------------------------
+// sphere-sphere contacts
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int count_active) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.n; i += stride) {
+    const int a = l.pa[i];
+    const uint32_t bw = l.pb[i];
+    const uint32_t b = bw & ~kHistFlag;
+    const SphA32 A = d.sa32[a];
+    const SphA32 B = d.sa32[b];
+    const long long dxl = B.x - A.x, dyl = B.y - A.y, dzl = B.z - A.z;
+    // cheap rejection of clear false positives
+    const float fx = __ll2float_rn(dxl) * kFixToM, fy = __ll2float_rn(dyl) * kFixToM,
+                fz = __ll2float_rn(dzl) * kFixToM;
+    const float s_est = fx * fx + fy * fy + fz * fz;
+    const float rs = A.r + B.r;
+    float dn = -1.f;
+    float dist = 0.f;
+    if (s_est <= rs * rs * 1.0001f) {
+      // overlap rho - |d| = (rho^2 - |d|^2) / (rho + |d|), numerator in float-float
+      const ff dx = fix_to_ff(dxl), dy = fix_to_ff(dyl), dz = fix_to_ff(dzl);
+      const ff s = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+      const ff rho = two_sum(A.r, B.r);
+      const ff diff = ff_sub(ff_mul(rho, rho), s);
+      dist = sqrtf(s.h);
+      dn = ff_to_float(diff) / (ff_to_float(rho) + dist);
+    }
+    const bool active = dn > 0.f;
+    if (count_active) warp_count(active, d.counters);
+    if (!active) {
+      if (bw & kHistFlag) l.pb[i] = b;  // history reset (false positive)
+      continue;
+    }
+    const V3<float> n = {fx / dist, fy / dist, fz / dist};
+    const float4 RA = d.sb32[a], RB = d.sb32[b];
+    const float4 va = d.mv32[A.owner], wa = d.mw32[A.owner];
+    const float4 vb = d.mv32[B.owner], wb = d.mw32[B.owner];
+    const float sa = A.r - 0.5f * dn, sb = B.r - 0.5f * dn;
+    const V3<float> ca = V3<float>{RA.x, RA.y, RA.z} + sa * n;
+    const V3<float> cb = V3<float>{RB.x, RB.y, RB.z} - sb * n;
+    const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
+    const V3<float> vB = V3<float>{vb.x, vb.y, vb.z} + cross(V3<float>{wb.x, wb.y, wb.z}, cb);
+    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+    if (bw & kHistFlag) {
+      u0 = l.u[i];
+      u1 = l.u[l.cap + i];
+      u2 = l.u[2 * l.cap + i];
+    }
+    const PairMat<float> pm = d.pm32[__float_as_int(RA.w) * d.nmat + __float_as_int(RB.w)];
+    const float Rbar = A.r * B.r / (A.r + B.r);
+    const float mbar = va.w * vb.w / (va.w + vb.w);
+    const Law<float> law = contact_law<float>(pm, (float)d.h, n, dn, vB - vA,
+                                              V3<float>{(float)u0, (float)u1, (float)u2}, Rbar, mbar);
+    // tangential history: FP64 accumulation of the float increment
+    if (law.capped) {
+      u0 = (double)law.u.x; u1 = (double)law.u.y; u2 = (double)law.u.z;
+    } else {
+      u0 += (double)law.u.x; u1 += (double)law.u.y; u2 += (double)law.u.z;
+    }
+    l.u[i] = u0;
+    l.u[l.cap + i] = u1;
+    l.u[2 * l.cap + i] = u2;
+    if (!(bw & kHistFlag)) l.pb[i] = b | kHistFlag;
+    const V3<float> F = law.F;
+    add_clump32(d.acc32, B.owner, F, cross(cb, F));
+    add_clump32(d.acc32, A.owner, -1.f * F, -1.f * cross(ca, F));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int count_active) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.n; i += stride) {
+    const int a = l.pa[i];
+    const uint32_t bw = l.pb[i];
+    const uint32_t b = bw & ~kHistFlag;
+    const SphA64 A = d.sa64[a];
+    const SphA64 B = d.sa64[b];
+    const V3<double> dv = {B.x - A.x, B.y - A.y, B.z - A.z};
+    const double dist = sqrt(dot(dv, dv));
+    const double dn = (A.r + B.r) - dist;
+    const bool active = dn > 0.0;
+    if (count_active) warp_count(active, d.counters);
+    if (!active) {
+      if (bw & kHistFlag) l.pb[i] = b;
+      continue;
+    }
+    const V3<double> n = (1.0 / dist) * dv;
+    const double4_32a RA = d.sb64[a], RB = d.sb64[b];
+    const long long ia = __double_as_longlong(RA.w), ib = __double_as_longlong(RB.w);
+    const int oa = (int)(ia & 0xffffffff), ob = (int)(ib & 0xffffffff);
+    const int ma = (int)(ia >> 32), mb = (int)(ib >> 32);
+    const double4_32a va = d.mv64[oa], wa = d.mw64[oa], vb = d.mv64[ob], wb = d.mw64[ob];
+    const double sa = A.r - 0.5 * dn, sb = B.r - 0.5 * dn;
+    const V3<double> ca = V3<double>{RA.x, RA.y, RA.z} + sa * n;
+    const V3<double> cb = V3<double>{RB.x, RB.y, RB.z} - sb * n;
+    const V3<double> vA = V3<double>{va.x, va.y, va.z} + cross(V3<double>{wa.x, wa.y, wa.z}, ca);
+    const V3<double> vB = V3<double>{vb.x, vb.y, vb.z} + cross(V3<double>{wb.x, wb.y, wb.z}, cb);
+    V3<double> u = {0.0, 0.0, 0.0};
+    if (bw & kHistFlag) u = {l.u[i], l.u[l.cap + i], l.u[2 * l.cap + i]};
+    const PairMat<double> pm = d.pm64[ma * d.nmat + mb];
+    const double Rbar = A.r * B.r / (A.r + B.r);
+    const double mbar = va.w * vb.w / (va.w + vb.w);
+    const Law<double> law = contact_law<double>(pm, d.h, n, dn, vB - vA, u, Rbar, mbar);
+    const V3<double> un = law.capped ? law.u : u + law.u;
+    l.u[i] = un.x;
+    l.u[l.cap + i] = un.y;
+    l.u[2 * l.cap + i] = un.z;
+    if (!(bw & kHistFlag)) l.pb[i] = b | kHistFlag;
+    add_clump64(d.acc64, ob, law.F, cross(cb, law.F));
+    add_clump64(d.acc64, oa, -1.0 * law.F, -1.0 * cross(ca, law.F));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sphere-wall contacts (body a = the sphere's clump, body b = the wall)
+// ---------------------------------------------------------------------------
+__global__ void k_walls32(DevState d, ContactList l, int count_active) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.nw; i += stride) {
+    const int s = l.ws[i];
+    const uint32_t wwv = l.ww[i];
+    const uint32_t w = wwv & ~kHistFlag;
+    const SphA32 S = d.sa32[s];
+    const WallDev& W = d.walls[w];
+    V3<float> n;
+    const float dn = wall_geom32(W, d.wfix + 3 * (long long)w, S.x, S.y, S.z, S.r, n);
+    const bool active = dn > 0.f;
+    if (count_active) warp_count(active, d.counters);
+    if (!active) {
+      if (wwv & kHistFlag) l.ww[i] = w;
+      continue;
+    }
+    const float4 RS = d.sb32[s];
+    const float4 va = d.mv32[S.owner], wa = d.mw32[S.owner];
+    const V3<float> ca = V3<float>{RS.x, RS.y, RS.z} + (S.r - 0.5f * dn) * n;
+    const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
+    const V3<float> vW = {(float)W.vel[0], (float)W.vel[1], (float)W.vel[2]};
+    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+    if (wwv & kHistFlag) {
+      u0 = l.uw[i];
+      u1 = l.uw[l.capw + i];
+      u2 = l.uw[2 * l.capw + i];
+    }
+    const PairMat<float> pm = d.pm32[__float_as_int(RS.w) * d.nmat + W.material];
+    const Law<float> law = contact_law<float>(pm, (float)d.h, n, dn, vW - vA,
+                                              V3<float>{(float)u0, (float)u1, (float)u2}, S.r, va.w);
+    if (law.capped) {
+      u0 = (double)law.u.x; u1 = (double)law.u.y; u2 = (double)law.u.z;
+    } else {
+      u0 += (double)law.u.x; u1 += (double)law.u.y; u2 += (double)law.u.z;
+    }
+    l.uw[i] = u0;
+    l.uw[l.capw + i] = u1;
+    l.uw[2 * l.capw + i] = u2;
+    if (!(wwv & kHistFlag)) l.ww[i] = w | kHistFlag;
+    add_clump32(d.acc32, S.owner, -1.f * law.F, -1.f * cross(ca, law.F));
+    double* fw = d.wforce + 3 * (long long)w;
+    atomicAdd(fw, (double)law.F.x);
+    atomicAdd(fw + 1, (double)law.F.y);
+    atomicAdd(fw + 2, (double)law.F.z);
+  }
+}
+
+__global__ void k_walls64(DevState d, ContactList l, double t, int count_active) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.nw; i += stride) {
+    const int s = l.ws[i];
+    const uint32_t wwv = l.ww[i];
+    const uint32_t w = wwv & ~kHistFlag;
+    const SphA64 S = d.sa64[s];
+    const WallDev& W = d.walls[w];
+    const double x[3] = {S.x, S.y, S.z};
+    double nw[3];
+    const double dist = wall_distance64(W, t, x, nw);
+    const double dn = S.r - dist;
+    const bool active = dn > 0.0;
+    if (count_active) warp_count(active, d.counters);
+    if (!active) {
+      if (wwv & kHistFlag) l.ww[i] = w;
+      continue;
+    }
+    const V3<double> n = {-nw[0], -nw[1], -nw[2]};
+    const double4_32a RS = d.sb64[s];
+    const long long is = __double_as_longlong(RS.w);
+    const int os = (int)(is & 0xffffffff), ms = (int)(is >> 32);
+    const double4_32a va = d.mv64[os], wa = d.mw64[os];
+    const V3<double> ca = V3<double>{RS.x, RS.y, RS.z} + (S.r - 0.5 * dn) * n;
+    const V3<double> vA = V3<double>{va.x, va.y, va.z} + cross(V3<double>{wa.x, wa.y, wa.z}, ca);
+    const V3<double> vW = {W.vel[0], W.vel[1], W.vel[2]};
+    V3<double> u = {0.0, 0.0, 0.0};
+    if (wwv & kHistFlag) u = {l.uw[i], l.uw[l.capw + i], l.uw[2 * l.capw + i]};
+    const PairMat<double> pm = d.pm64[ms * d.nmat + W.material];
+    const Law<double> law = contact_law<double>(pm, d.h, n, dn, vW - vA, u, S.r, va.w);
+    const V3<double> un = law.capped ? law.u : u + law.u;
+    l.uw[i] = un.x;
+    l.uw[l.capw + i] = un.y;
+    l.uw[2 * l.capw + i] = un.z;
+    if (!(wwv & kHistFlag)) l.ww[i] = w | kHistFlag;
+    add_clump64(d.acc64, os, -1.0 * law.F, -1.0 * cross(ca, law.F));
+    double* fw = d.wforce + 3 * (long long)w;
+    atomicAdd(fw, law.F.x);
+    atomicAdd(fw + 1, law.F.y);
+    atomicAdd(fw + 2, law.F.z);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// clump update: Eq. (5) + sphere poses
+// ---------------------------------------------------------------------------
+constexpr int kUpd = 128;
+
+__device__ __forceinline__ void quat_mul(const double a[4], const double b[4], double c[4]) {
+  c[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  c[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  c[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  c[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+__device__ __forceinline__ void quat_mulf(const float a[4], const float b[4], float c[4]) {
+  c[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  c[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  c[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  c[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+__device__ __forceinline__ bool finite4(double4_32a v) {
+  return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+}
+
+// FP64 mode.
+__global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, float margin,
+                                                   int check_cert) {
+  __shared__ double sR[kUpd][9];
+  __shared__ double sX[kUpd][3];
+  const long long c0 = (long long)blockIdx.x * kUpd;
+  const long long c = c0 + threadIdx.x;
+  if (c < d.ncl) {
+    const int tpl = d.cinfo[c].x;
+    double4_32a X = d.cpos[c], q4 = d.cq[c], v = d.cv[c], w = d.cw[c];
+    const double mass = d.tmass[tpl];
+    const double I[3] = {d.tinert[3 * tpl], d.tinert[3 * tpl + 1], d.tinert[3 * tpl + 2]};
+    double q[4] = {q4.x, q4.y, q4.z, q4.w};
+    double R[9];
+    if (integrate) {
+      double* acc = d.acc64 + 8 * c;
+      const V3<double> F = {acc[0], acc[1], acc[2]}, T = {acc[3], acc[4], acc[5]};
+      for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+      const double h = d.h;
+      // Eq. (5a), semi-implicit Euler
+      v.x += h * (F.x / mass + d.g[0]);
+      v.y += h * (F.y / mass + d.g[1]);
+      v.z += h * (F.z / mass + d.g[2]);
+      X.x += h * v.x; X.y += h * v.y; X.z += h * v.z;
+      // Eq. (5b) in the principal frame with the gyroscopic term
+      quat_to_mat(q[0], q[1], q[2], q[3], R);
+      const V3<double> tb = mat_tmul(R, T);
+      const V3<double> wb = {w.x, w.y, w.z};
+      const V3<double> Iw = {I[0] * wb.x, I[1] * wb.y, I[2] * wb.z};
+      const V3<double> gy = cross(wb, Iw);
+      w.x += h * (tb.x - gy.x) / I[0];
+      w.y += h * (tb.y - gy.y) / I[1];
+      w.z += h * (tb.z - gy.z) / I[2];
+      const double wl = sqrt(w.x * w.x + w.y * w.y + w.z * w.z);
+      double dq[4] = {1.0, 0.0, 0.0, 0.0};
+      if (wl > 0.0) {
+        double sn, cs;
+        sincos(0.5 * h * wl, &sn, &cs);
+        const double sc = sn / wl;
+        dq[0] = cs; dq[1] = sc * w.x; dq[2] = sc * w.y; dq[3] = sc * w.z;
+      }
+      double qn[4];
+      quat_mul(q, dq, qn);
+      const double ql = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+      for (int k = 0; k < 4; ++k) q[k] = qn[k] / ql;
+      q4 = make_double4_32a(q[0], q[1], q[2], q[3]);
+      if (!(finite4(X) && finite4(v) && finite4(w) && finite4(q4))) atomicOr(d.flags, kFlagNonFinite);
+      d.cpos[c] = X; d.cq[c] = q4; d.cv[c] = v; d.cw[c] = w;
+      if (check_cert) {
+        const double4_32a X0 = d.ref_pos[c];
+        const float4 r0 = d.ref_q[c];
+        const float dx = (float)(X.x - X0.x), dy = (float)(X.y - X0.y), dz = (float)(X.z - X0.z);
+        // |vec(conj(q0) q)| = sin(angle / 2)
+        const float a[4] = {r0.x, -r0.y, -r0.z, -r0.w};
+        const float b[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+        float e[4];
+        quat_mulf(a, b, e);
+        const float disp = sqrtf(dx * dx + dy * dy + dz * dz) +
+                           2.f * d.tpbound[tpl] * sqrtf(e[1] * e[1] + e[2] * e[2] + e[3] * e[3]);
+        const float mlim = d.cmargin ? d.cmargin[c] : margin;
+        if (disp * 1.00001f + 1e-12f > mlim) {
+          atomicOr(d.flags, kFlagGuard);
+          atomicAdd(d.counters + 1, 1ull);
+        }
+      }
+    }
+    quat_to_mat(q[0], q[1], q[2], q[3], R);
+    const V3<double> ww = mat_mul(R, V3<double>{w.x, w.y, w.z});
+    d.mv64[c] = make_double4_32a(v.x, v.y, v.z, mass);
+    d.mw64[c] = make_double4_32a(ww.x, ww.y, ww.z, 0.0);
+    for (int k = 0; k < 9; ++k) sR[threadIdx.x][k] = R[k];
+    sX[threadIdx.x][0] = X.x; sX[threadIdx.x][1] = X.y; sX[threadIdx.x][2] = X.z;
+  }
+  __syncthreads();
+  const long long c1 = c0 + kUpd < d.ncl ? c0 + kUpd : d.ncl;
+  if (c0 >= c1) return;
+  const long long s0 = d.csph[c0], s1 = d.csph[c1];
+  for (long long s = s0 + threadIdx.x; s < s1; s += kUpd) {
+    const int2 si = d.sinfo[s];
+    const int lc = (int)(si.x - c0);
+    const double4_32a tp = d.tp64[si.y];
+    const V3<double> rel = mat_mul(sR[lc], V3<double>{tp.x, tp.y, tp.z});
+    SphA64 A;
+    A.x = sX[lc][0] + rel.x; A.y = sX[lc][1] + rel.y; A.z = sX[lc][2] + rel.z; A.r = tp.w;
+    d.sa64[s] = A;
+    const long long bits = (long long)(uint32_t)si.x | ((long long)d.tmat[si.y] << 32);
+    d.sb64[s] = make_double4_32a(rel.x, rel.y, rel.z, __longlong_as_double(bits));
+  }
+}
+
+// FP32_VOXEL mode.
+__global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, float margin,
+                                                   int check_cert) {
+  __shared__ float sRh[kUpd][9];
+  __shared__ float sRl[kUpd][9];
+  __shared__ int4 sVox[kUpd];
+  __shared__ float4 sOff[kUpd];
+  const long long c0 = (long long)blockIdx.x * kUpd;
+  const long long c = c0 + threadIdx.x;
+  if (c < d.ncl) {
+    const int tpl = d.cinfo[c].x;
+    int4 vox = d.cvox[c];
+    float4 off = d.coff[c];
+    double4_32a q4 = d.cq[c], v = d.cv[c], w = d.cw[c];
+    const float mass = (float)d.tmass[tpl];
+    if (integrate) {
+      float* acc = d.acc32 + 8 * c;
+      const float4 a0 = *reinterpret_cast<const float4*>(acc);
+      const float4 a1 = *reinterpret_cast<const float4*>(acc + 4);
+      *reinterpret_cast<float4*>(acc) = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(acc + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+      const double h = d.h;
+      const float hf = (float)h;
+      const float im = 1.f / mass;
+      // Eq. (5a): double velocity accumulation of the float acceleration
+      v.x += h * ((double)(a0.x * im) + d.g[0]);
+      v.y += h * ((double)(a0.y * im) + d.g[1]);
+      v.z += h * ((double)(a0.z * im) + d.g[2]);
+      double o[3] = {(double)off.x + h * v.x, (double)off.y + h * v.y, (double)off.z + h * v.z};
+      int vx[3] = {vox.x, vox.y, vox.z};
+      for (int k = 0; k < 3; ++k) {
+        if (fabs(o[k]) > 0.5 * kVoxel) {
+          const double m = rint(o[k] * (1.0 / kVoxel));
+          vx[k] += (int)m;
+          o[k] -= m * kVoxel;
+        }
+      }
+      vox = make_int4(vx[0], vx[1], vx[2], vox.w);
+      off = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
+      // Eq. (5b): body frame, float angular acceleration, double accumulation
+      float Rf[9];
+      quat_to_mat((float)q4.x, (float)q4.y, (float)q4.z, (float)q4.w, Rf);
+      const V3<float> tb = mat_tmul(Rf, V3<float>{a0.w, a1.x, a1.y});
+      const V3<float> wf = {(float)w.x, (float)w.y, (float)w.z};
+      const float I0 = (float)d.tinert[3 * tpl], I1 = (float)d.tinert[3 * tpl + 1],
+                  I2 = (float)d.tinert[3 * tpl + 2];
+      const V3<float> gy = cross(wf, V3<float>{I0 * wf.x, I1 * wf.y, I2 * wf.z});
+      w.x += h * (double)((tb.x - gy.x) / I0);
+      w.y += h * (double)((tb.y - gy.y) / I1);
+      w.z += h * (double)((tb.z - gy.z) / I2);
+      // orientation: q <- q * exp(h w / 2); the increment q * (dq - 1) in float,
+      // accumulated in double, then one Newton step towards unit length
+      const V3<float> wn = {(float)w.x, (float)w.y, (float)w.z};
+      const float th = 0.5f * hf * sqrtf(dot(wn, wn));
+      const float th2 = th * th;
+      const float cm1 = -0.5f * th2 + th2 * th2 * (1.f / 24.f);  // cos(th) - 1
+      const float sc = 0.5f * hf * (1.f - th2 * (1.f / 6.f) + th2 * th2 * (1.f / 120.f));
+      float dqm[4] = {cm1, sc * wn.x, sc * wn.y, sc * wn.z};
+      if (th > 1e-2f) {
+        const float sn = sinf(th), cs = cosf(th);
+        const float s2 = sn / (2.f * th / hf);
+        dqm[0] = cs - 1.f; dqm[1] = s2 * wn.x; dqm[2] = s2 * wn.y; dqm[3] = s2 * wn.z;
+      }
+      const float qf[4] = {(float)q4.x, (float)q4.y, (float)q4.z, (float)q4.w};
+      float inc[4];
+      quat_mulf(qf, dqm, inc);
+      double qd[4] = {q4.x + (double)inc[0], q4.y + (double)inc[1], q4.z + (double)inc[2],
+                      q4.w + (double)inc[3]};
+      const double n2 = qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2] + qd[3] * qd[3];
+      const double sn = 1.5 - 0.5 * n2;
+      q4 = make_double4_32a(qd[0] * sn, qd[1] * sn, qd[2] * sn, qd[3] * sn);
+      if (!(finite4(v) && finite4(w) && finite4(q4) && isfinite(off.x) && isfinite(off.y) &&
+            isfinite(off.z)))
+        atomicOr(d.flags, kFlagNonFinite);
+      d.cvox[c] = vox; d.coff[c] = off; d.cq[c] = q4; d.cv[c] = v; d.cw[c] = w;
+      if (check_cert) {
+        const int4 v0 = d.ref_vox[c];
+        const float4 o0 = d.ref_off[c];
+        const float kV = (float)kVoxel;
+        const float dx = (float)(vox.x - v0.x) * kV + (off.x - o0.x);
+        const float dy = (float)(vox.y - v0.y) * kV + (off.y - o0.y);
+        const float dz = (float)(vox.z - v0.z) * kV + (off.z - o0.z);
+        const float4 r0 = d.ref_q[c];
+        const float a[4] = {r0.x, -r0.y, -r0.z, -r0.w};
+        const float b[4] = {(float)q4.x, (float)q4.y, (float)q4.z, (float)q4.w};
+        float e[4];
+        quat_mulf(a, b, e);
+        const float disp = sqrtf(dx * dx + dy * dy + dz * dz) +
+                           2.f * d.tpbound[tpl] * sqrtf(e[1] * e[1] + e[2] * e[2] + e[3] * e[3]);
+        const float mlim = d.cmargin ? d.cmargin[c] : margin;
+        if (disp * 1.00001f + 1e-12f > mlim) {
+          atomicOr(d.flags, kFlagGuard);
+          atomicAdd(d.counters + 1, 1ull);
+        }
+      }
+    }
+    // rotation matrix as float-float from the double orientation
+    const ff qw = ff_from_double(q4.x), qx = ff_from_double(q4.y), qy = ff_from_double(q4.z),
+             qz = ff_from_double(q4.w);
+    const ff xx = ff_mul(qx, qx), yy = ff_mul(qy, qy), zz = ff_mul(qz, qz);
+    const ff xy = ff_mul(qx, qy), xz = ff_mul(qx, qz), yz = ff_mul(qy, qz);
+    const ff wx = ff_mul(qw, qx), wy = ff_mul(qw, qy), wz = ff_mul(qw, qz);
+    const ff one = {1.f, 0.f};
+    ff R[9];
+    R[0] = ff_sub(one, ff_scale2(ff_add(yy, zz), 2.f));
+    R[1] = ff_scale2(ff_sub(xy, wz), 2.f);
+    R[2] = ff_scale2(ff_add(xz, wy), 2.f);
+    R[3] = ff_scale2(ff_add(xy, wz), 2.f);
+    R[4] = ff_sub(one, ff_scale2(ff_add(xx, zz), 2.f));
+    R[5] = ff_scale2(ff_sub(yz, wx), 2.f);
+    R[6] = ff_scale2(ff_sub(xz, wy), 2.f);
+    R[7] = ff_scale2(ff_add(yz, wx), 2.f);
+    R[8] = ff_sub(one, ff_scale2(ff_add(xx, yy), 2.f));
+    float Rf[9];
+    for (int k = 0; k < 9; ++k) {
+      sRh[threadIdx.x][k] = R[k].h;
+      sRl[threadIdx.x][k] = R[k].l;
+      Rf[k] = R[k].h;
+    }
+    const V3<float> wf = {(float)w.x, (float)w.y, (float)w.z};
+    const V3<float> ww = mat_mul(Rf, wf);
+    d.mv32[c] = make_float4((float)v.x, (float)v.y, (float)v.z, mass);
+    d.mw32[c] = make_float4(ww.x, ww.y, ww.z, 0.f);
+    sVox[threadIdx.x] = vox;
+    sOff[threadIdx.x] = off;
+  }
+  __syncthreads();
+  const long long c1 = c0 + kUpd < d.ncl ? c0 + kUpd : d.ncl;
+  if (c0 >= c1) return;
+  const long long s0 = d.csph[c0], s1 = d.csph[c1];
+  for (long long s = s0 + threadIdx.x; s < s1; s += kUpd) {
+    const int2 si = d.sinfo[s];
+    const int lc = (int)(si.x - c0);
+    const float4 tp = d.tp32[si.y];
+    const float p[3] = {tp.x, tp.y, tp.z};
+    ff rel[3];
+    for (int i = 0; i < 3; ++i) {
+      ff acc = ff_mulf({sRh[lc][3 * i], sRl[lc][3 * i]}, p[0]);
+      acc = ff_add(acc, ff_mulf({sRh[lc][3 * i + 1], sRl[lc][3 * i + 1]}, p[1]));
+      acc = ff_add(acc, ff_mulf({sRh[lc][3 * i + 2], sRl[lc][3 * i + 2]}, p[2]));
+      rel[i] = acc;
+    }
+    const int4 vox = sVox[lc];
+    const float4 off = sOff[lc];
+    const int vv[3] = {vox.x, vox.y, vox.z};
+    const float oo[3] = {off.x, off.y, off.z};
+    long long P[3];
+    for (int i = 0; i < 3; ++i) {
+      const ff t = ff_add(two_sum(oo[i], rel[i].h), {rel[i].l, 0.f});
+      P[i] = ((long long)vv[i] << (kFixBits - kVoxLog2)) + __float2ll_rn(t.h * kMToFix) +
+             __float2ll_rn(t.l * kMToFix);
+    }
+    SphA32 A;
+    A.x = P[0]; A.y = P[1]; A.z = P[2]; A.r = tp.w; A.owner = si.x;
+    d.sa32[s] = A;
+    d.sb32[s] = make_float4(rel[0].h, rel[1].h, rel[2].h, __int_as_float(d.tmat[si.y]));
+  }
+}
+
+__global__ void k_walls_at(DevState d, double t) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= d.nwalls) return;
+  const WallDev W = d.walls[w];
+  const SceneGrid g = d.grids[d.wall_scene[w]];
+  for (int k = 0; k < 3; ++k) {
+    const double p = W.p[k] + W.vel[k] * t;
+    d.wpos[3 * w + k] = p;
+    d.wfix[3 * w + k] = __double2ll_rn((p - g.lo[k]) * 17592186044416.0);
+  }
+}
+
+__global__ void k_set_ref(DevState d) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.ncl) return;
+  const double4_32a q = d.cq[c];
+  d.ref_q[c] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+  if (d.prec == 0) {
+    d.ref_pos[c] = d.cpos[c];
+  } else {
+    d.ref_vox[c] = d.cvox[c];
+    d.ref_off[c] = d.coff[c];
+  }
+}
+
+__global__ void k_get_state(DevState d, double* pos, double* quat, double* vel, double* angvel) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.ncl) return;
+  const double4_32a q = d.cq[c];
+  if (pos) {
+    if (d.prec == 0) {
+      const double4_32a X = d.cpos[c];
+      pos[3 * c] = X.x; pos[3 * c + 1] = X.y; pos[3 * c + 2] = X.z;
+    } else {
+      const SceneGrid g = d.grids[d.cinfo[c].y];
+      const int4 v = d.cvox[c];
+      const float4 o = d.coff[c];
+      pos[3 * c] = g.lo[0] + ((double)v.x * kVoxel + (double)o.x);
+      pos[3 * c + 1] = g.lo[1] + ((double)v.y * kVoxel + (double)o.y);
+      pos[3 * c + 2] = g.lo[2] + ((double)v.z * kVoxel + (double)o.z);
+    }
+  }
+  if (quat) {
+    quat[4 * c] = q.x; quat[4 * c + 1] = q.y; quat[4 * c + 2] = q.z; quat[4 * c + 3] = q.w;
+  }
+  if (vel) {
+    const double4_32a v = d.cv[c];
+    vel[3 * c] = v.x; vel[3 * c + 1] = v.y; vel[3 * c + 2] = v.z;
+  }
+  if (angvel) {
+    double R[9];
+    quat_to_mat(q.x, q.y, q.z, q.w, R);
+    const double4_32a w = d.cw[c];
+    const V3<double> ww = mat_mul(R, V3<double>{w.x, w.y, w.z});
+    angvel[3 * c] = ww.x; angvel[3 * c + 1] = ww.y; angvel[3 * c + 2] = ww.z;
+  }
+}
+
+__global__ void k_get_forces(DevState d, double* F, double* T) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.ncl) return;
+  for (int k = 0; k < 3; ++k) {
+    if (d.prec == 0) {
+      F[3 * c + k] = d.acc64[8 * c + k];
+      T[3 * c + k] = d.acc64[8 * c + 3 + k];
+    } else {
+      F[3 * c + k] = (double)d.acc32[8 * c + k];
+      T[3 * c + k] = (double)d.acc32[8 * c + 3 + k];
+    }
+  }
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int g_sm_count = 0;
+int sm_count() {
+  if (g_sm_count == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sm_count <= 0) g_sm_count = 132;
+  }
+  return g_sm_count;
+}
+
+}  // namespace
+
+void launch_force_pairs(const DevState& d, ContactList& l, bool count_active, cudaStream_t st) {
+  if (l.n == 0) return;
+  const long long want = (l.n + 255) / 256;
+  const long long cap = (long long)sm_count() * 8;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (d.prec == 0)
+    { k_pairs64<<<grid, 256, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
+  else
+    { k_pairs32<<<grid, 256, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
+}
+
+void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_active,
+                        cudaStream_t st) {
+  if (l.nw == 0) return;
+  const long long want = (l.nw + 127) / 128;
+  const long long cap = (long long)sm_count() * 8;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (d.prec == 0)
+    { k_walls64<<<grid, 128, 0, st>>>(d, l, t, count_active ? 1 : 0); count_launch(); }
+  else
+    { k_walls32<<<grid, 128, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
+}
+
+void launch_update(const DevState& d, bool integrate, double t_next, double margin,
+                   bool check_cert, cudaStream_t st) {
+  if (d.ncl > 0) {
+    if (d.prec == 0)
+      { k_update64<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
+                                                      check_cert ? 1 : 0); count_launch(); }
+    else
+      { k_update32<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
+                                                      check_cert ? 1 : 0); count_launch(); }
+  }
+  launch_walls_at(d, t_next, st);
+}
+
+void launch_walls_at(const DevState& d, double t, cudaStream_t st) {
+  if (d.nwalls > 0) { k_walls_at<<<nblk(d.nwalls, 64), 64, 0, st>>>(d, t); count_launch(); }
+}
+
+void launch_set_cert_ref(const DevState& d, cudaStream_t st) {
+  if (d.ncl > 0) { k_set_ref<<<nblk(d.ncl, 256), 256, 0, st>>>(d); count_launch(); }
+}
+
+void launch_get_state(const DevState& d, double* pos, double* quat, double* vel, double* angvel,
+                      cudaStream_t st) {
+  if (d.ncl > 0) { k_get_state<<<nblk(d.ncl, 256), 256, 0, st>>>(d, pos, quat, vel, angvel); count_launch(); }
+}
+
+void launch_get_forces(const DevState& d, double* F, double* T, cudaStream_t st) {
+  if (d.ncl > 0) { k_get_forces<<<nblk(d.ncl, 256), 256, 0, st>>>(d, F, T); count_launch(); }
+}
+
+}  // namespace dem

@@ -204,6 +204,33 @@ def lattice_positions(n, spacing, x0, x1, y0, y1, z0, rng=None, jitter=0.0):
     return P
 
 
+def layered_positions(bound, x0, x1, y0, y1, z0, gap=2e-4, rng=None, jitter=0.0):
+    """Spawn sites for clumps of bounding radii ``bound``: clumps sorted from
+    the largest, filled layer by layer on square lattices whose spacing is set
+    by the largest clump of the layer (the paper's batch spawning with gaps
+    set by the largest element, applied per size class).  Returns positions in
+    the input order."""
+    bound = np.asarray(bound, float)
+    order = np.argsort(-bound, kind="stable")
+    P = np.zeros((len(bound), 3))
+    i, z = 0, z0
+    while i < len(order):
+        s = 2.0 * bound[order[i]] + gap
+        nx = max(1, int((x1 - x0) // s))
+        ny = max(1, int((y1 - y0) // s))
+        k = min(nx * ny, len(order) - i)
+        idx = order[i:i + k]
+        j = np.arange(k)
+        P[idx, 0] = x0 + (j % nx + 0.5) * s
+        P[idx, 1] = y0 + (j // nx + 0.5) * s
+        P[idx, 2] = z + 0.5 * s
+        if rng is not None and jitter > 0:
+            P[idx, :2] += rng.uniform(-jitter, jitter, size=(k, 2))
+        z += s
+        i += k
+    return P
+
+
 def _finish(sc: Scene, rng, pos, tpl, vel_scale=0.0, ang_scale=0.0):
     n = len(tpl)
     sc.tpl = np.asarray(tpl, np.int32)
@@ -352,7 +379,7 @@ def batched_scene(seed, n_clumps, mu):
 # small dense scenes for parity tests
 # ---------------------------------------------------------------------------
 def packed_scene(seed, n_clumps, precision=PREC_FP64, compress=0.92, n_templates=8,
-                 vel_scale=0.05, ang_scale=20.0, n_mat=3, walls=True):
+                 vel_scale=0.05, ang_scale=20.0, n_mat=3, walls=True, jitter=0.15):
     """A small lattice of polydisperse clumps squeezed below their bounding
     diameter, so that many sphere pairs overlap by a spread of depths, with
     random linear and angular velocities and several materials."""
@@ -371,7 +398,7 @@ def packed_scene(seed, n_clumps, precision=PREC_FP64, compress=0.92, n_templates
     tpl = rng.integers(0, n_templates, size=n_clumps)
     spacing = compress * 2.0 * float(np.mean(bound[tpl]))
     side = spacing * math.ceil(n_clumps ** (1.0 / 3.0))
-    P = lattice_positions(n_clumps, spacing, 0.0, side, 0.0, side, 0.0, rng, 0.15 * spacing)
+    P = lattice_positions(n_clumps, spacing, 0.0, side, 0.0, side, 0.0, rng, jitter * spacing)
     P += 0.01
     sc.lo = (0.0, 0.0, 0.0)
     top = float(P[:, 2].max()) + 0.02

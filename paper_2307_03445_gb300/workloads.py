@@ -1,0 +1,87 @@
+"""Benchmark workloads built with the library itself.
+
+The paper-scale bed (11,000,000 clumps, ~34,000,000 spheres in a 4 x 2 m box
+with a plate sliding on top) is prepared the way the paper prepares its test
+beds (section 4.1): one patch of clumps is spawned on size-layered lattices,
+settled under gravity, then copy-pasted side by side to fill the box.  The
+patch is settled with softer contacts and a longer time step (a preparation
+setting, not the measured one); the measured run then uses the workload's own
+materials and dt = 1e-6 s from that settled, copied bed.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import Simulation, scenes
+
+
+def _prep_scene(base: scenes.Scene, n_patch: int, foot: float, rng):
+    sc = scenes.Scene(
+        "patch", base.tpl_off, base.tpl_pos, base.tpl_rad, base.tpl_mat, base.tpl_mass,
+        base.tpl_inertia, np.full(len(base.E), 5e7), np.full(len(base.E), 0.3),
+        np.full(len(base.E), 0.5), np.full(len(base.E), 0.2), h=5e-6, g=(0.0, 0.0, -9.81),
+        lo=(0.0, 0.0, 0.0), hi=(foot, foot, 2.0), bin_size=0.0,
+        walls=scenes.box_walls(0.0, foot, 0.0, foot, 0.0), precision=scenes.PREC_FP32)
+    tpl = rng.integers(0, len(base.tpl_mass), size=n_patch).astype(np.int32)
+    bound = sc.bounding_radius()[tpl]
+    P = scenes.layered_positions(bound, 0.0, foot, 0.0, foot, 0.0, gap=4e-4, rng=rng,
+                                 jitter=1e-4)
+    sc.tpl = tpl
+    sc.pos = P
+    sc.quat = scenes.random_quaternions(rng, n_patch)
+    sc.vel = np.zeros((n_patch, 3))
+    sc.angvel = np.zeros((n_patch, 3))
+    sc.hi = (foot, foot, float(P[:, 2].max()) + 0.05)
+    return sc
+
+
+def settle(sc: scenes.Scene, t_end: float, v_bound=6.0, K=10, log=None, chunk=2000):
+    """Runs the scene until simulated time t_end; returns the final state."""
+    sim = Simulation(sc, margin=v_bound * sc.h * K * 1.5, rebuild_interval=K)
+    n = int(round(t_end / sc.h))
+    done = 0
+    t0 = time.time()
+    while done < n:
+        k = min(chunk, n - done)
+        sim.step(k)
+        done += k
+    if log:
+        st = sim.stats()
+        log(f"settled {sc.n_clumps} clumps for {n} steps in {time.time() - t0:.1f} s "
+            f"({st['rebuilds']} rebuilds, {st['n_pairs']} pairs)")
+    out = sim.state()
+    sim.close()
+    return out
+
+
+def bed_c5(n_clumps=11_000_000, lx=4.0, ly=2.0, patch=0.25, seed=1239, log=None,
+           settle_time=None):
+    """The paper-scale bed: a settled patch copy-pasted over lx x ly."""
+    base = scenes.config5(seed=seed, n_clumps=1, lx=lx, ly=ly)
+    rng = np.random.default_rng(seed + 1)
+    nx, ny = int(round(lx / patch)), int(round(ly / patch))
+    tiles = nx * ny
+    n_patch = int(math.ceil(n_clumps / tiles))
+    psc = _prep_scene(base, n_patch, patch, rng)
+    fall = math.sqrt(2.0 * float(psc.pos[:, 2].max()) / 9.81)
+    t_end = settle_time if settle_time is not None else fall + 0.15
+    pos, quat, vel, angvel = settle(psc, t_end, log=log)
+    # copy-paste the patch over the box
+    P = np.concatenate([pos + np.array([i * patch, j * patch, 0.0])
+                        for j in range(ny) for i in range(nx)])[:n_clumps]
+    Q = np.concatenate([quat] * tiles)[:n_clumps]
+    T = np.concatenate([psc.tpl] * tiles)[:n_clumps]
+    top = float((P[:, 2] + base.bounding_radius()[T]).max())
+    sc = base
+    sc.tpl = T
+    sc.pos = P
+    sc.quat = Q
+    sc.vel = np.zeros((len(T), 3))
+    sc.angvel = np.zeros((len(T), 3))
+    plate = top + 1e-4
+    sc.walls = scenes.box_walls(0.0, lx, 0.0, ly, 0.0, top=plate, top_vel=(0.2, 0.0, 0.0))
+    sc.hi = (lx, ly, plate + 0.01)
+    return sc

@@ -1,0 +1,274 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bin registrations, pair lists and wall lists: bit-exact (integer predicate
+on the same lattice).  Per-clump force and torque totals: within 1e-12 (FP64)
+or 1e-5 (FP32_VOXEL) of the oracle, relative to the sum of the magnitudes of
+the contributions to that total (the scale that bounds the rounding of a sum).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2307_03445_gb300 import scenes
+from tests.helpers import set_clumps, single_sphere_scene
+
+pytestmark = pytest.mark.gpu
+
+TOL = {scenes.PREC_FP64: 1e-12, scenes.PREC_FP32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def dem():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_03445_gb300 as dem
+
+    dem.load_library()
+    return dem
+
+
+def _scene(seed, n, prec, compress=0.92, walls=True, bin_scale=1.0, margin=1e-4, **kw):
+    sc = scenes.packed_scene(seed, n, precision=prec, compress=compress, walls=walls, **kw)
+    if prec == scenes.PREC_FP32:
+        # templates and state exactly representable in the FP32 voxel layout
+        sc.tpl_pos = sc.tpl_pos.astype(np.float32).astype(np.float64)
+        sc.tpl_rad = sc.tpl_rad.astype(np.float32).astype(np.float64)
+        scenes.snap_to_voxel_grid(sc)
+    sc.bin_size = bin_scale * scenes.default_bin_size(sc, margin)
+    return sc
+
+
+def _oracle_lists(oracle_mod, sc, margin, K):
+    om = oracle_mod.OracleModel(sc)
+    xs, owner, tsph = om.sphere_centres(sc.tpl, sc.pos, sc.quat)
+    qc, rho = om.detect_coords(xs, tsph, margin)
+    keys, ids = om.bin_entries(qc, rho)
+    a, b = om.pairs_binned(owner, qc, rho)
+    ws, ww = om.wall_candidates(xs, tsph, margin, 0.0, sc.h * K)
+    return om, keys, ids, a, b, ws, ww
+
+
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+@pytest.mark.parametrize("seed,n,bin_scale", [(1, 333, 1.0), (2, 517, 0.45), (3, 1000, 2.2)])
+def test_detection_bit_exact(dem, oracle_mod, prec, seed, n, bin_scale):
+    margin, K = 1e-4, 10
+    sc = _scene(seed, n, prec, bin_scale=bin_scale, margin=margin)
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        sim.rebuild()
+        keys, ids = sim.bins()
+        a, b, u, ws, ww, uw = sim.contacts()
+    om, k_o, i_o, a_o, b_o, ws_o, ww_o = _oracle_lists(oracle_mod, sc, margin, K)
+    assert len(a_o) > n  # a dense case with many candidate pairs
+    assert np.array_equal(keys, k_o) and np.array_equal(ids, i_o)
+    assert np.array_equal(a, a_o) and np.array_equal(b, b_o)
+    assert np.array_equal(ws, ws_o) and np.array_equal(ww, ww_o)
+    assert np.all(u == 0) and np.all(uw == 0)
+
+
+def _compare_forces(sc, F, T, Fo, To, mag, tol):
+    scaleF = np.maximum(mag[:, 0], 1e-300)
+    scaleT = np.maximum(mag[:, 1], 1e-300)
+    errF = np.abs(F - Fo).max(axis=1) / scaleF
+    errT = np.abs(T - To).max(axis=1) / scaleT
+    touched = mag[:, 0] > 0
+    assert touched.sum() > 0.3 * len(F)
+    assert errF[touched].max() <= tol, f"force error {errF[touched].max():.3e}"
+    assert errT[touched].max() <= tol, f"torque error {errT[touched].max():.3e}"
+    # untouched clumps get exactly nothing
+    assert np.all(F[~touched] == 0) and np.all(T[~touched] == 0)
+    return errF[touched].max(), errT[touched].max()
+
+
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+@pytest.mark.parametrize("seed,n", [(4, 300), (5, 777)])
+def test_forces_match_oracle(dem, oracle_mod, prec, seed, n):
+    margin, K = 1e-4, 10
+    sc = _scene(seed, n, prec, margin=margin)
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        F, T = sim.eval_forces()
+        Fw = sim.wall_forces()
+        st = sim.stats()
+    om, _, _, a, b, ws, ww = _oracle_lists(oracle_mod, sc, margin, K)
+    Fo, To, Fwo, _, _, act, mag = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, 0.0, a, b,
+                                            np.zeros((len(a), 3)), ws, ww, np.zeros((len(ws), 3)),
+                                            with_mag=True)
+    assert st["active_last"] == act
+    _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
+    if len(ws):
+        assert np.abs(Fw - Fwo).max() <= TOL[prec] * np.abs(Fwo).sum()
+
+
+def _run_both(dem, oracle_mod, sc, margin, K, nsteps, prec):
+    sim = dem.Simulation(sc, margin=margin, rebuild_interval=K, precision=prec)
+    sim.step(nsteps)
+    osim = oracle_mod.OracleSim(sc, margin, K)
+    osim.step(nsteps)
+    return sim, osim
+
+
+def test_fp64_trajectory_matches_oracle(dem, oracle_mod):
+    margin, K, nsteps = 2e-4, 10, 45
+    sc = _scene(7, 250, scenes.PREC_FP64, margin=margin)
+    sim, osim = _run_both(dem, oracle_mod, sc, margin, K, nsteps, scenes.PREC_FP64)
+    pos, quat, vel, w = sim.state()
+    po, qo, vo, wo = osim.state()
+    vs = np.abs(vo).max()
+    assert np.abs(pos - po).max() <= 1e-14 * (1 + np.abs(po).max())
+    assert np.abs(vel - vo).max() <= 1e-10 * vs
+    assert np.abs(quat - qo).max() <= 1e-12
+    assert np.abs(w - wo).max() <= 1e-9 * np.abs(wo).max()
+    a, b, u, ws, ww, uw = sim.contacts()
+    ao, bo, uo, wso, wwo, uwo = osim.contacts()
+    assert np.array_equal(a, ao) and np.array_equal(b, bo)
+    assert np.array_equal(ws, wso) and np.array_equal(ww, wwo)
+    assert np.abs(uo).max() > 0
+    assert np.abs(u - uo).max() <= 1e-8 * np.abs(uo).max()
+    if len(uwo):
+        assert np.abs(uw - uwo).max() <= 1e-8 * max(np.abs(uwo).max(), 1e-30)
+    sim.close()
+
+
+def test_fp32_voxel_trajectory_error_is_bounded(dem, oracle_mod):
+    """Precision mode FP32_VOXEL against the FP64 oracle over 45 steps: the
+    position and velocity errors stay at the level set by float forces."""
+    margin, K, nsteps = 2e-4, 10, 45
+    sc = _scene(8, 250, scenes.PREC_FP32, margin=margin, compress=1.0, jitter=0.05)
+    sim, osim = _run_both(dem, oracle_mod, sc, margin, K, nsteps, scenes.PREC_FP32)
+    pos, quat, vel, w = sim.state()
+    po, qo, vo, wo = osim.state()
+    dv = np.abs(vel - vo).max() / np.abs(vo - sc.vel).max()
+    dx = np.abs(pos - po).max() / np.abs(po - sc.pos).max()
+    # errors relative to the change over the run
+    assert dv < 1e-5, dv
+    assert dx < 1e-5, dx
+    a, b, *_ = sim.contacts()
+    ao, bo, *_ = osim.contacts()
+    assert np.array_equal(a, ao) and np.array_equal(b, bo)
+    sim.close()
+
+
+def _wall_scene(prec, seed=9):
+    """Clumps inside a cylinder with a floor, a cone pushed down through them
+    and a tilted moving plane; a few clumps are placed just inside the reach
+    of each wall so that every wall has contacts."""
+    rng = np.random.default_rng(seed)
+    half = math.radians(30.0)
+    H = 0.01 / math.tan(half)
+    tilt = np.array([0.0, -0.6, -0.8])
+    walls = [scenes.plane((0, 0, 0), (0, 0, 1)), scenes.cylinder((0.03, 0.03, 0), (0, 0, 1), 0.025),
+             scenes.cone((0.03, 0.03, 0.02), (0, 0, 1), half, H, vel=(0.0, 0.0, -0.01)),
+             scenes.plane((0, 0.05, 0.05), tilt, vel=(0.2, 0.0, 0.0))]
+    sc = scenes.packed_scene(seed, 400, precision=prec, compress=0.95, walls=False, vel_scale=0.02)
+    sc.walls = walls
+    n = len(sc.tpl)
+    bound = sc.bounding_radius()[sc.tpl]
+    r = 0.02 * np.sqrt(rng.random(n))
+    th = 2 * math.pi * rng.random(n)
+    z = 0.002 + 0.03 * rng.random(n)
+    P = np.stack([0.03 + r * np.cos(th), 0.03 + r * np.sin(th), z], axis=1)
+    near = rng.uniform(0.5, 1.1, size=n) * bound
+    for i in range(0, 40):          # floor
+        P[i, 2] = near[i]
+    for i in range(40, 80):         # cylinder wall, from inside
+        P[i, 0] = 0.03 + (0.025 - near[i]) * math.cos(th[i])
+        P[i, 1] = 0.03 + (0.025 - near[i]) * math.sin(th[i])
+    for i in range(80, 110):        # cone lateral surface, from outside
+        t = rng.uniform(0.2, 0.9)
+        on = np.array([t * H * math.tan(half), 0.0, t * H])
+        nout = np.array([math.cos(half), 0.0, -math.sin(half)])
+        q = on + near[i] * nout
+        c, s_ = math.cos(th[i]), math.sin(th[i])
+        P[i] = [0.03 + c * q[0], 0.03 + s_ * q[0], 0.02 + q[2]]
+    for i in range(110, 130):       # below the cone tip
+        P[i] = [0.03, 0.03, 0.02 - near[i]]
+    for i in range(130, 160):       # tilted plane, from the grains' side
+        base = np.array([rng.uniform(0.015, 0.045), 0.05, 0.05])
+        along = np.array([0.0, 0.8, -0.6]) * rng.uniform(-0.004, 0.004)
+        P[i] = base + along - tilt * near[i]
+    sc.pos = P
+    sc.lo, sc.hi = (0.0, 0.0, -1.0 / 128), (0.06, 0.06, 0.07)
+    if prec == scenes.PREC_FP32:
+        sc.tpl_pos = sc.tpl_pos.astype(np.float32).astype(np.float64)
+        sc.tpl_rad = sc.tpl_rad.astype(np.float32).astype(np.float64)
+        scenes.snap_to_voxel_grid(sc)
+    sc.bin_size = scenes.default_bin_size(sc, 1e-4)
+    return sc
+
+
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+def test_walls_plane_cylinder_cone(dem, oracle_mod, prec):
+    margin, K = 1e-4, 10
+    sc = _wall_scene(prec)
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        F, T = sim.eval_forces()
+        Fw = sim.wall_forces()
+        a, b, u, ws, ww, uw = sim.contacts()
+    om, _, _, ao, bo, wso, wwo = _oracle_lists(oracle_mod, sc, margin, K)
+    assert np.array_equal(ws, wso) and np.array_equal(ww, wwo)
+    assert set(np.unique(ww)) == {0, 1, 2, 3}
+    Fo, To, Fwo, _, _, act, mag = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, 0.0, ao,
+                                            bo, np.zeros((len(ao), 3)), wso, wwo,
+                                            np.zeros((len(wso), 3)), with_mag=True)
+    _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
+    for k in range(4):
+        assert np.abs(Fw[k] - Fwo[k]).max() <= TOL[prec] * max(np.abs(Fwo).sum(), 1e-30)
+
+
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+def test_audit_finds_no_miss_with_an_adequate_margin(dem, prec):
+    """While the displacement certificate holds (every clump moved less than
+    the margin since the last rebuild), the exact check finds no miss."""
+    sc = _scene(10, 400, prec, margin=2e-4, compress=1.2, jitter=0.02, vel_scale=0.05)
+    certified = 0
+    with dem.Simulation(sc, margin=2e-4, rebuild_interval=20) as sim:
+        for _ in range(6):
+            before = sim.stats()["guard_violations"]
+            sim.step(15)
+            if sim.stats()["guard_violations"] == before:
+                certified += 1
+                assert sim.audit() == 0
+        assert sim.stats()["n_pairs"] > 100
+    assert certified >= 3
+
+
+def test_guard_and_audit_catch_a_margin_that_is_too_small(dem):
+    sc = _scene(11, 300, scenes.PREC_FP64, margin=1e-7)
+    sc.vel = sc.vel * 20.0  # 1 m/s class speeds: 1e-4 m per 100 steps
+    with dem.Simulation(sc, margin=1e-7, rebuild_interval=100000) as sim:
+        sim.step(100)
+        assert sim.stats()["guard_violations"] > 0
+        assert sim.audit() > 0
+
+
+def test_degenerate_inputs(dem):
+    # no clumps at all
+    sc = single_sphere_scene([1e-3], g=(0, 0, -9.81))
+    set_clumps(sc, [], np.zeros((0, 3)))
+    with dem.Simulation(sc, margin=1e-5, rebuild_interval=5) as sim:
+        sim.step(3)
+        assert sim.contacts()[0].size == 0
+    # one clump: falls freely, no pairs
+    sc = single_sphere_scene([1e-3], g=(0, 0, -9.81), h=1e-5)
+    set_clumps(sc, [0], [[0.0, 0.0, 0.0]])
+    with dem.Simulation(sc, margin=1e-5, rebuild_interval=5) as sim:
+        sim.step(10)
+        pos, _, vel, _ = sim.state()
+        assert vel[0, 2] == pytest.approx(-9.81 * 1e-4, rel=1e-12)
+        assert pos[0, 2] == pytest.approx(-9.81 * 1e-10 * 55, rel=1e-12)
+        assert sim.contacts()[0].size == 0
+    # spheres outside the detection domain still collide
+    sc = single_sphere_scene([1e-3, 1e-3], lo=(0, 0, 0), hi=(0.01, 0.01, 0.01))
+    set_clumps(sc, [0, 1], [[-0.004, 0.005, 0.005], [-0.0021, 0.005, 0.005]])
+    with dem.Simulation(sc, margin=1e-5, rebuild_interval=5, bin_size=2e-3) as sim:
+        F, T = sim.eval_forces()
+        assert F[1, 0] > 0 and F[0, 0] < 0
+
+
+def test_non_finite_input_rejected(dem):
+    sc = single_sphere_scene([1e-3], g=(0, 0, -9.81))
+    set_clumps(sc, [0], [[0.0, 0.0, np.nan]])
+    with pytest.raises(dem.DemError, match="NONFINITE"):
+        dem.Simulation(sc, margin=1e-5)
