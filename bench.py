@@ -105,14 +105,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def oracle_sample_scene(n_clumps=1500, seed=1239):
     """Clumps of the workload (same templates, materials, dt) in a small box,
-    packed like a settled bed (lattice at the mean bounding diameter)."""
+    on a lattice squeezed to 0.88 of the mean bounding diameter, which lists
+    about as many pairs per sphere (~1.1) as the settled bed does."""
     from paper_2307_03445_gb300 import scenes
 
     base = scenes.config5(seed=seed, n_clumps=1)
     rng = np.random.default_rng(seed + 7)
     tpl = rng.integers(0, len(base.tpl_mass), size=n_clumps).astype(np.int32)
     bound = base.bounding_radius()[tpl]
-    spacing = 2.0 * float(np.mean(bound))
+    spacing = 0.88 * 2.0 * float(np.mean(bound))
     side = spacing * math.ceil((n_clumps / 2.0) ** 0.5)
     P = scenes.lattice_positions(n_clumps, spacing, 0.0, side, 0.0, side, 0.0, rng, 0.1 * spacing)
     P[:, 2] += float(bound.max())
@@ -213,10 +214,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")  # profilers select the timed launches by this range
         ev0.record(stream)
         sim.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)

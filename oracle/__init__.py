@@ -111,6 +111,11 @@ def _load():
                 "orc_sim_time": (C.c_double, [C.c_void_p]),
                 "orc_sim_active": (C.c_longlong, [C.c_void_p]),
                 "orc_sim_destroy": (None, [C.c_void_p]),
+                "orc_mlp_num_params": (C.c_int, []),
+                "orc_mlp_forward": (None, [_D, C.c_longlong, _D, _D]),
+                "orc_mlp_loss_grad": (C.c_double, [_D, C.c_longlong, _D, _D, _D]),
+                "orc_mlp_adam": (None, [_D, _D, _D, _D, C.c_int, C.c_double, C.c_double,
+                                        C.c_double, C.c_double]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -385,3 +390,36 @@ class OracleSim:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# learned lifetime regressor (FP64 reference of the GPU training kernels)
+# ---------------------------------------------------------------------------
+MLP_IN, MLP_H = 6, 64
+
+
+def mlp_num_params():
+    return int(_load().orc_mlp_num_params())
+
+
+def mlp_forward(params, x):
+    params, x = _f64(params), _f64(x).reshape(-1, MLP_IN)
+    y = np.zeros(len(x))
+    _load().orc_mlp_forward(_p(params, C.c_double), len(x), _p(x, C.c_double), _p(y, C.c_double))
+    return y
+
+
+def mlp_loss_grad(params, x, t):
+    params, x, t = _f64(params), _f64(x).reshape(-1, MLP_IN), _f64(t)
+    g = np.zeros(mlp_num_params())
+    loss = _load().orc_mlp_loss_grad(_p(params, C.c_double), len(x), _p(x, C.c_double),
+                                     _p(t, C.c_double), _p(g, C.c_double))
+    return float(loss), g
+
+
+def mlp_adam(params, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    params, m, v = (_f64(a).copy() for a in (params, m, v))
+    grad = _f64(grad)
+    _load().orc_mlp_adam(_p(params, C.c_double), _p(m, C.c_double), _p(v, C.c_double),
+                         _p(grad, C.c_double), int(step), lr, beta1, beta2, eps)
+    return params, m, v

@@ -725,3 +725,87 @@ void orc_sim_destroy(orc_sim* s) {
     free(s->pa); free(s->pb); free(s->up); free(s->ws); free(s->ww); free(s->uw);
     free(s);
 }
+
+/* ------------------------------------------------------------------ */
+/* learned lifetime regressor: plain dense layers, ReLU, MSE, Adam       */
+/* ------------------------------------------------------------------ */
+#define MLP_L 4
+static const int mlp_in[MLP_L] = {ORC_MLP_IN, ORC_MLP_H, ORC_MLP_H, ORC_MLP_H};
+static const int mlp_out[MLP_L] = {ORC_MLP_H, ORC_MLP_H, ORC_MLP_H, 1};
+
+int orc_mlp_num_params(void) {
+    int n = 0;
+    for (int l = 0; l < MLP_L; ++l) n += mlp_out[l] * mlp_in[l] + mlp_out[l];
+    return n;
+}
+
+/* Forward pass of one sample, keeping every layer's activations. */
+static double mlp_sample(const double* p, const double* x, double act[MLP_L + 1][ORC_MLP_H],
+                         double pre[MLP_L][ORC_MLP_H]) {
+    for (int i = 0; i < ORC_MLP_IN; ++i) act[0][i] = x[i];
+    const double* w = p;
+    for (int l = 0; l < MLP_L; ++l) {
+        const double* b = w + mlp_out[l] * mlp_in[l];
+        for (int o = 0; o < mlp_out[l]; ++o) {
+            double s = b[o];
+            for (int i = 0; i < mlp_in[l]; ++i) s += w[o * mlp_in[l] + i] * act[l][i];
+            pre[l][o] = s;
+            act[l + 1][o] = (l < MLP_L - 1) ? (s > 0.0 ? s : 0.0) : s;
+        }
+        w = b + mlp_out[l];
+    }
+    return act[MLP_L][0];
+}
+
+void orc_mlp_forward(const double* params, long long n, const double* x, double* y) {
+    double act[MLP_L + 1][ORC_MLP_H], pre[MLP_L][ORC_MLP_H];
+    for (long long k = 0; k < n; ++k) y[k] = mlp_sample(params, x + ORC_MLP_IN * k, act, pre);
+}
+
+double orc_mlp_loss_grad(const double* params, long long n, const double* x, const double* t,
+                         double* grad) {
+    const int np = orc_mlp_num_params();
+    if (grad) for (int i = 0; i < np; ++i) grad[i] = 0.0;
+    double loss = 0.0;
+    double act[MLP_L + 1][ORC_MLP_H], pre[MLP_L][ORC_MLP_H], delta[ORC_MLP_H], nd[ORC_MLP_H];
+    int off[MLP_L];
+    off[0] = 0;
+    for (int l = 1; l < MLP_L; ++l) off[l] = off[l - 1] + mlp_out[l - 1] * mlp_in[l - 1] + mlp_out[l - 1];
+    for (long long k = 0; k < n; ++k) {
+        const double y = mlp_sample(params, x + ORC_MLP_IN * k, act, pre);
+        const double e = y - t[k];
+        loss += e * e;
+        if (!grad) continue;
+        /* dL/dy for L = (1/n) sum e^2 */
+        delta[0] = 2.0 * e / (double)n;
+        for (int l = MLP_L - 1; l >= 0; --l) {
+            const double* w = params + off[l];
+            double* gw = grad + off[l];
+            double* gb = gw + mlp_out[l] * mlp_in[l];
+            for (int o = 0; o < mlp_out[l]; ++o) {
+                gb[o] += delta[o];
+                for (int i = 0; i < mlp_in[l]; ++i) gw[o * mlp_in[l] + i] += delta[o] * act[l][i];
+            }
+            if (l == 0) break;
+            /* back through W and the ReLU of the layer below */
+            for (int i = 0; i < mlp_in[l]; ++i) {
+                double s = 0.0;
+                for (int o = 0; o < mlp_out[l]; ++o) s += w[o * mlp_in[l] + i] * delta[o];
+                nd[i] = pre[l - 1][i] > 0.0 ? s : 0.0;
+            }
+            for (int i = 0; i < mlp_in[l]; ++i) delta[i] = nd[i];
+        }
+    }
+    return loss / (double)n;
+}
+
+void orc_mlp_adam(double* params, double* m, double* v, const double* grad, int step, double lr,
+                  double beta1, double beta2, double eps) {
+    const int np = orc_mlp_num_params();
+    const double c1 = 1.0 - pow(beta1, step), c2 = 1.0 - pow(beta2, step);
+    for (int i = 0; i < np; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
+        params[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

