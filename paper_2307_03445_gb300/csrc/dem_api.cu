@@ -66,6 +66,7 @@ struct dem_ctx {
   // detection scratch
   Buf b_det, b_bin_cnt, b_bin_off, b_wall_mask, b_wall_cnt, b_keys, b_ids, b_keys2, b_ids2;
   Buf b_bin_start, b_bin_end, b_pair_cnt, b_scan_scr, b_sort_scr, b_tmp;
+  Buf b_lob, b_part, b_rec;
   uint32_t* sorted_keys = nullptr;
   uint32_t* sorted_ids = nullptr;
   long long n_entries = 0;
@@ -162,7 +163,10 @@ void refresh_devstate(dem_ctx* c) {
   d.nmat = c->P.n_materials;
   d.nwalls = (int)c->walls.size();
   d.h = c->P.dt;
-  for (int k = 0; k < 3; ++k) d.g[k] = c->P.g[k];
+  for (int k = 0; k < 3; ++k) {
+    d.g[k] = c->P.g[k];
+    d.hg[k] = c->P.dt * c->P.g[k];
+  }
   d.tpl_off = ptr<int>(c->b_tpl_off);
   d.tp64 = ptr<double4_32a>(c->b_tp64);
   d.tp32 = ptr<float4>(c->b_tp32);
@@ -359,6 +363,7 @@ int detect_into(dem_ctx* c, int li, double m) {
   if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_bin_cnt, 4 * (ns + 1)) ||
       !grow(c, c->b_bin_off, 4 * (ns + 1)) || !grow(c, c->b_wall_mask, 4 * (ns + 1)) ||
       !grow(c, c->b_wall_cnt, 4 * (ns + 1)) || !grow(c, c->b_pair_cnt, 4 * (ns + 1)) ||
+      !grow(c, c->b_lob, 8 * (ns + 1)) || !grow(c, c->b_part, 16 * (ns + 1)) ||
       !grow(c, LB.row, 4 * (ns + 1)) || !grow(c, LB.wrow, 4 * (ns + 1)) ||
       !grow(c, c->b_scan_scr, scan_scratch_bytes(ns + 1) + 256))
     return fail(c, DEM_ERR_OOM, "detection buffers");
@@ -371,6 +376,8 @@ int detect_into(dem_ctx* c, int li, double m) {
   o.wall_off = ptr<uint32_t>(LB.wrow);
   o.pair_cnt = ptr<uint32_t>(c->b_pair_cnt);
   o.pair_off = ptr<uint32_t>(LB.row);
+  o.lob = ptr<unsigned long long>(c->b_lob);
+  o.part = ptr<uint4>(c->b_part);
   unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
   launch_detect(c->D, o, m, nullptr, t, travel, c->st);
   exclusive_scan_u32(o.bin_cnt, o.bin_off, ns, c->b_scan_scr.p, tot + 0, c->st);
@@ -385,6 +392,7 @@ int detect_into(dem_ctx* c, int li, double m) {
   if (!grow(c, c->b_keys, 4 * (B + 1)) || !grow(c, c->b_ids, 4 * (B + 1)) ||
       !grow(c, c->b_keys2, 4 * (B + 1)) || !grow(c, c->b_ids2, 4 * (B + 1)) ||
       !grow(c, c->b_sort_scr, radix_scratch_bytes((long long)B + 1) + 256) ||
+      !grow(c, c->b_rec, sizeof(EntryRec) * (B + 1)) ||
       !grow(c, c->b_bin_start, 4 * ((size_t)c->nbins + 1)) || !grow(c, c->b_bin_end, 4 * ((size_t)c->nbins + 1)))
     return fail(c, DEM_ERR_OOM, "bin buffers");
   o.keys = ptr<uint32_t>(c->b_keys);
@@ -400,6 +408,8 @@ int detect_into(dem_ctx* c, int li, double m) {
   }
   c->sorted_keys = o.keys;
   c->sorted_ids = o.ids;
+  o.rec = ptr<EntryRec>(c->b_rec);
+  launch_gather_entries(c->D, o, (long long)B, c->st);
   o.bin_start = ptr<uint32_t>(c->b_bin_start);
   o.bin_end = ptr<uint32_t>(c->b_bin_end);
   cudaMemsetAsync(o.bin_start, 0, 4 * (size_t)c->nbins, c->st);
@@ -648,7 +658,8 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_wpos, &c->b_wforce, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
                 &c->b_totals, &c->b_det, &c->b_bin_cnt, &c->b_bin_off, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_keys, &c->b_ids, &c->b_keys2, &c->b_ids2, &c->b_bin_start, &c->b_bin_end,
-                &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp};
+                &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp, &c->b_lob,
+                &c->b_part, &c->b_rec};
   for (Buf* b : all) dfree(c, b->p);
   for (auto& lb : c->lists) {
     Buf* lbs[] = {&lb.pa, &lb.pb, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow};

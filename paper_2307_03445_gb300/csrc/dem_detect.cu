@@ -35,10 +35,10 @@ __device__ __forceinline__ void clump_com(const DevState& d, int c, const SceneG
 }
 
 // Float estimate of the same distance; |error| is far below wall_slack().
-__device__ float wall_distance_est(const WallDev& w, double t, const double x[3]) {
+__device__ float wall_distance_est(const WallDev& w, double t, const float x[3]) {
   float dd[3], n[3];
   for (int k = 0; k < 3; ++k) {
-    dd[k] = (float)x[k] - ((float)w.p[k] + (float)w.vel[k] * (float)t);
+    dd[k] = x[k] - ((float)w.p[k] + (float)w.vel[k] * (float)t);
     n[k] = (float)w.n[k];
   }
   const float ax = dd[0] * n[0] + dd[1] * n[1] + dd[2] * n[2];
@@ -57,10 +57,43 @@ __device__ float wall_distance_est(const WallDev& w, double t, const double x[3]
   return inside ? -dm : dm;
 }
 
-__device__ __forceinline__ float wall_slack(const WallDev& w, const double x[3]) {
+__device__ __forceinline__ float wall_slack(const WallDev& w, const float x[3]) {
   float m = fabsf((float)w.p[0]) + fabsf((float)w.p[1]) + fabsf((float)w.p[2]) +
-            fabsf((float)x[0]) + fabsf((float)x[1]) + fabsf((float)x[2]) + 1.f;
+            fabsf(x[0]) + fabsf(x[1]) + fabsf(x[2]) + 1.f;
   return 4e-6f * m;
+}
+
+// Lattice coordinates of a sphere centre.  The exact value is the double
+// formula det_centre() rounded to the nearest lattice point; the pose record
+// written by the last update kernel carries the same centre with a known
+// error bound (FP32_VOXEL: within 2 fixed-point units of 2^-44 m; FP64:
+// within 2^-20 lattice units), so the formula is evaluated only when that
+// approximation lies too close to a rounding boundary to decide it.
+__device__ __forceinline__ bool lattice_from_pose(const DevState& d, long long s, const SceneGrid& g,
+                                                  long long qc[3], float xf[3]) {
+  bool exact = true;
+  if (d.prec == 1) {
+    const SphA32 A = d.sa32[s];
+    const long long P[3] = {A.x, A.y, A.z};
+    for (int k = 0; k < 3; ++k) {
+      const long long half = 1ll << (kFixBits - kDetBits - 1);
+      const long long rem = P[k] & ((1ll << (kFixBits - kDetBits)) - 1);
+      if (rem - half <= 2 && half - rem <= 2) exact = false;
+      qc[k] = (P[k] + half) >> (kFixBits - kDetBits);
+      xf[k] = (float)g.lo[k] + __ll2float_rn(P[k]) * kFixToM;
+    }
+  } else {
+    const SphA64 A = d.sa64[s];
+    const double P[3] = {A.x, A.y, A.z};
+    for (int k = 0; k < 3; ++k) {
+      const double u = (P[k] - g.lo[k]) * kDetScale;
+      const double f = u - floor(u);
+      if (fabs(f - 0.5) < 0x1p-20) exact = false;
+      qc[k] = __double2ll_rn(u);
+      xf[k] = (float)P[k];
+    }
+  }
+  return exact;
 }
 
 __global__ void k_detect(DevState d, DetectOut o, double margin, const double* __restrict__ smargin,
@@ -70,46 +103,57 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   const int2 si = d.sinfo[s];
   const int2 ci = d.cinfo[si.x];
   const SceneGrid g = d.grids[ci.y];
-  double X[3];
-  clump_com(d, si.x, g, X);
-  const double4_32a q4 = d.cq[si.x];
-  const double q[4] = {q4.x, q4.y, q4.z, q4.w};
   const double4_32a tp = d.tp64[si.y];
-  const double p[3] = {tp.x, tp.y, tp.z};
   double x[3];
-  det_centre(q, p, X, x);
-  const double m = smargin ? smargin[s] : margin;
+  bool have_x = false;
+  auto exact_centre = [&]() {
+    if (have_x) return;
+    double X[3];
+    clump_com(d, si.x, g, X);
+    const double4_32a q4 = d.cq[si.x];
+    const double q[4] = {q4.x, q4.y, q4.z, q4.w};
+    const double p[3] = {tp.x, tp.y, tp.z};
+    det_centre(q, p, X, x);
+    have_x = true;
+  };
+  const double m = smargin ? smargin[s] : (d.cmargin ? (double)d.cmargin[si.x] : margin);
   long long qc[3];
+  float xf[3];
+  if (!lattice_from_pose(d, s, g, qc, xf)) {
+    exact_centre();
+    for (int k = 0; k < 3; ++k) qc[k] = __double2ll_rn(__dmul_rn(__dsub_rn(x[k], g.lo[k]), kDetScale));
+  }
   for (int k = 0; k < 3; ++k) {
-    long long v = __double2ll_rn(__dmul_rn(__dsub_rn(x[k], g.lo[k]), kDetScale));
     // a sphere more than 64 m outside its domain is clamped (it only meets
     // the boundary bins, where it can still be found)
-    v = v < -(1ll << 30) ? -(1ll << 30) : (v > (1ll << 30) ? (1ll << 30) : v);
-    qc[k] = v;
+    qc[k] = qc[k] < -(1ll << 30) ? -(1ll << 30) : (qc[k] > (1ll << 30) ? (1ll << 30) : qc[k]);
   }
   const long long rho = (long long)ceil(__dmul_rn(__dadd_rn(tp.w, m), kDetScale)) + 1;
   o.det[s] = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
   long long cnt = 1;
+  int lob[3];
   for (int k = 0; k < 3; ++k) {
-    const int lo = clampi(floordiv_ll(qc[k] - rho, g.L), g.dims[k] - 1);
+    lob[k] = clampi(floordiv_ll(qc[k] - rho, g.L), g.dims[k] - 1);
     const int hi = clampi(floordiv_ll(qc[k] + rho, g.L), g.dims[k] - 1);
-    cnt *= (hi - lo + 1);
+    cnt *= (hi - lob[k] + 1);
   }
   o.bin_cnt[s] = (uint32_t)cnt;
+  o.lob[s] = pack_bin3(lob[0], lob[1], lob[2]);
   // sphere-wall candidates: distance within radius + margin + wall travel
   uint32_t mask = 0;
   for (int i = 0; i < g.wall_count; ++i) {
     const WallDev& w = d.walls[d.wall_idx[g.wall_start + i]];
     const double travel = __dmul_rn(__dsqrt_rn(dot3d(w.vel, w.vel)), travel_time);
     const double thr = __dadd_rn(__dadd_rn(tp.w, m), travel);
-    const float est = wall_distance_est(w, t, x);
-    const float slack = wall_slack(w, x);
+    const float est = wall_distance_est(w, t, xf);
+    const float slack = wall_slack(w, xf);
     bool in;
     if (est > (float)thr + slack) {
       in = false;
     } else if (est < (float)thr - slack) {
       in = true;
     } else {
+      exact_centre();
       double nw[3];
       in = wall_distance64(w, t, x, nw) <= thr;
     }
@@ -149,24 +193,52 @@ __global__ void k_bin_bounds(const uint32_t* __restrict__ keys, long long n,
   if (i == n - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
 }
 
-// Narrow phase for sphere a over its own bins; count or write its row.
+// Gathers, in sorted order, the record of every registration.
+__global__ void k_gather_entries(DevState d, DetectOut o, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t s = o.ids[i];
+  const int4 q = o.det[s];
+  EntryRec r;
+  r.qx = q.x; r.qy = q.y; r.qz = q.z; r.rho = q.w;
+  r.lob = o.lob[s];
+  r.owner = d.sinfo[s].x;
+  r.id = s;
+  o.rec[i] = r;
+}
+
+// Narrow phase for sphere a over its own bins: count its partners b > a (the
+// count pass also keeps the first four), or write its row.  Because floor
+// division by the bin edge and clamping are monotone, the bin of the per-axis
+// max of two lower corners is the per-axis max of their lower-corner bins.
 template <bool WRITE>
 __global__ void k_narrow(DevState d, DetectOut o, int* __restrict__ pa, uint32_t* __restrict__ pb) {
   const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= d.ns) return;
+  uint32_t row0 = 0, cnt = 0;
+  if (WRITE) {
+    row0 = o.pair_off[a];
+    cnt = o.pair_cnt[a];
+    if (cnt <= 4) {  // the count pass kept them all, already ascending
+      const uint4 p = o.part[a];
+      const uint32_t v[4] = {p.x, p.y, p.z, p.w};
+      for (uint32_t i = 0; i < cnt; ++i) {
+        pb[row0 + i] = v[i];
+        pa[row0 + i] = (int)a;
+      }
+      return;
+    }
+  }
   const int4 qa = o.det[a];
+  const unsigned long long loa = o.lob[a];
   const int owner_a = d.sinfo[a].x;
   const SceneGrid g = d.grids[d.cinfo[owner_a].y];
+  const int lo[3] = {(int)(loa & 0x1fffff), (int)((loa >> 21) & 0x1fffff), (int)(loa >> 42)};
+  int hi[3];
   const long long qaa[3] = {qa.x, qa.y, qa.z};
-  int lo[3], hi[3];
-  long long la[3];
-  for (int k = 0; k < 3; ++k) {
-    la[k] = qaa[k] - qa.w;
-    lo[k] = clampi(floordiv_ll(la[k], g.L), g.dims[k] - 1);
-    hi[k] = clampi(floordiv_ll(qaa[k] + qa.w, g.L), g.dims[k] - 1);
-  }
+  for (int k = 0; k < 3; ++k) hi[k] = clampi(floordiv_ll(qaa[k] + qa.w, g.L), g.dims[k] - 1);
   uint32_t n = 0;
-  const uint32_t row0 = WRITE ? o.pair_off[a] : 0u;
+  uint32_t keep[4] = {0u, 0u, 0u, 0u};
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
       for (int x = lo[0]; x <= hi[0]; ++x) {
@@ -177,31 +249,41 @@ __global__ void k_narrow(DevState d, DetectOut o, int* __restrict__ pa, uint32_t
         uint32_t lo_i = i0, hi_i = i1;
         while (lo_i < hi_i) {
           const uint32_t mid = (lo_i + hi_i) >> 1;
-          if (o.ids[mid] <= (uint32_t)a) lo_i = mid + 1; else hi_i = mid;
+          if (o.rec[mid].id <= (uint32_t)a) lo_i = mid + 1; else hi_i = mid;
         }
         for (uint32_t j = lo_i; j < i1; ++j) {
-          const uint32_t b = o.ids[j];
-          if (d.sinfo[b].x == owner_a) continue;
-          const int4 qb = o.det[b];
-          const long long dx = (long long)qb.x - qa.x, dy = (long long)qb.y - qa.y,
-                          dz = (long long)qb.z - qa.z;
-          const long long rr = (long long)qa.w + qb.w;
+          const EntryRec rb = o.rec[j];
+          if (rb.owner == owner_a) continue;
+          // owning bin: per-axis max of the two lower-corner bins is (x, y, z)
+          const int bx = (int)(rb.lob & 0x1fffff), by = (int)((rb.lob >> 21) & 0x1fffff),
+                    bz = (int)(rb.lob >> 42);
+          if ((bx > lo[0] ? bx : lo[0]) != x || (by > lo[1] ? by : lo[1]) != y ||
+              (bz > lo[2] ? bz : lo[2]) != z)
+            continue;
+          const long long dx = (long long)rb.qx - qa.x, dy = (long long)rb.qy - qa.y,
+                          dz = (long long)rb.qz - qa.z;
+          const long long rr = (long long)qa.w + rb.rho;
           if (dx * dx + dy * dy + dz * dz > rr * rr) continue;
-          // owning bin: the one holding the per-axis max of the lower corners
-          const long long lb0 = (long long)qb.x - qb.w, lb1 = (long long)qb.y - qb.w,
-                          lb2 = (long long)qb.z - qb.w;
-          if (clampi(floordiv_ll(la[0] > lb0 ? la[0] : lb0, g.L), g.dims[0] - 1) != x) continue;
-          if (clampi(floordiv_ll(la[1] > lb1 ? la[1] : lb1, g.L), g.dims[1] - 1) != y) continue;
-          if (clampi(floordiv_ll(la[2] > lb2 ? la[2] : lb2, g.L), g.dims[2] - 1) != z) continue;
-          if (WRITE) pb[row0 + n] = b;
+          if (WRITE) {
+            pb[row0 + n] = rb.id;
+          } else if (n < 4) {
+            // insertion into the ascending first-four
+            uint32_t k = n;
+            while (k > 0 && keep[k - 1] > rb.id) {
+              keep[k] = keep[k - 1];
+              --k;
+            }
+            keep[k] = rb.id;
+          }
           ++n;
         }
       }
   if (!WRITE) {
     o.pair_cnt[a] = n;
+    o.part[a] = make_uint4(keep[0], keep[1], keep[2], keep[3]);
     return;
   }
-  // canonical order inside the row: ascending b (rows are short)
+  // canonical order inside the row: ascending b
   for (uint32_t i = 1; i < n; ++i) {
     const uint32_t v = pb[row0 + i];
     uint32_t j = i;
@@ -344,6 +426,12 @@ void launch_detect(const DevState& d, const DetectOut& o, double margin, const d
                    double t, double travel_time, cudaStream_t st) {
   if (d.ns == 0) return;
   { k_detect<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, margin, smargin, t, travel_time); count_launch(); }
+}
+
+void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, cudaStream_t st) {
+  if (n == 0) return;
+  k_gather_entries<<<nblk(n, 256), 256, 0, st>>>(d, o, n);
+  count_launch();
 }
 
 void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st) {

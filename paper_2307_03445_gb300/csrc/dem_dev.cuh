@@ -10,6 +10,7 @@ struct DevState {
   long long ncl, ns;
   int nmat, nwalls;
   double h, g[3];
+  double hg[3];             // h * g
   // templates
   const int* tpl_off;
   const double4_32a* tp64;      // per template sphere: p (FP64), r
@@ -60,7 +61,25 @@ struct DevState {
   unsigned long long* counters;  // [0] active contacts, [1] guard violations
 };
 
+// One bin registration after sorting, with everything the narrow phase tests:
+// the lattice centre and enlarged radius, the clamped bin of the box's lower
+// corner (21 bits per axis), the owner clump and the sphere id.
+struct alignas(32) EntryRec {
+  int qx, qy, qz, rho;
+  unsigned long long lob;
+  int owner;
+  uint32_t id;
+};
+
+__host__ __device__ __forceinline__ unsigned long long pack_bin3(int x, int y, int z) {
+  return (unsigned long long)(unsigned)x | ((unsigned long long)(unsigned)y << 21) |
+         ((unsigned long long)(unsigned)z << 42);
+}
+
 struct DetectOut {
+  unsigned long long* lob;  // per sphere: clamped lower-corner bin, packed
+  EntryRec* rec;            // per entry (sorted order)
+  uint4* part;              // per sphere: up to four partners found by the count pass
   int4* det;                // per sphere {qx, qy, qz, rho}
   uint32_t* bin_cnt;        // per sphere
   uint32_t* bin_off;        // per sphere (scan)
@@ -92,6 +111,7 @@ struct ContactList {
 void launch_detect(const DevState& d, const DetectOut& o, double margin, const double* smargin,
                    double t, double travel_time, cudaStream_t st);
 void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st);
+void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, cudaStream_t st);
 void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint32_t* end,
                        cudaStream_t st);
 void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,

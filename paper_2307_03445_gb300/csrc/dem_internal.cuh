@@ -71,6 +71,41 @@ struct alignas(32) SphA64 {  // FP64
 };
 
 // ---------------------------------------------------------------------------
+// IEEE-754 binary32 <-> binary64 conversions on the integer pipe.  On this GPU
+// the hardware conversions issue at the (low) double-precision rate; these
+// produce the same results from the bit patterns with integer operations.
+// Zero, subnormal, infinite and NaN inputs (never met on the hot path) take
+// the hardware conversion.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+// double -> float, rounded to nearest, ties to even.
+__device__ __forceinline__ float d2f(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+  if (e <= 0 || e >= 255) return __double2float_rn(d);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  uint32_t r = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
+  const uint32_t rem = (uint32_t)(m & 0x1fffffffu);
+  // a carry out of the mantissa correctly moves to the next binade (or infinity)
+  if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r += 1u;
+  r |= (uint32_t)(b >> 32) & 0x80000000u;
+  return __uint_as_float(r);
+}
+// Finite test on the bit pattern (integer pipe).
+__device__ __forceinline__ bool finite_d(double d) {
+  return ((unsigned long long)__double_as_longlong(d) & 0x7ff0000000000000ull) !=
+         0x7ff0000000000000ull;
+}
+
+// ---------------------------------------------------------------------------
 // float-float arithmetic (error-free transforms)
 // ---------------------------------------------------------------------------
 struct ff {
@@ -111,8 +146,8 @@ __device__ __forceinline__ ff ff_mulf(ff a, float b) {
 }
 __device__ __forceinline__ ff ff_scale2(ff a, float pow2) { return {a.h * pow2, a.l * pow2}; }
 __device__ __forceinline__ ff ff_from_double(double d) {
-  float h = __double2float_rn(d);
-  float l = __double2float_rn(d - (double)h);
+  const float h = d2f(d);
+  const float l = d2f(d - f2d(h));
   return {h, l};
 }
 __device__ __forceinline__ float ff_to_float(ff a) { return __fadd_rn(a.h, a.l); }

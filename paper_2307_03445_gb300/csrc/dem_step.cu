@@ -128,12 +128,12 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     const float Rbar = A.r * B.r / (A.r + B.r);
     const float mbar = va.w * vb.w / (va.w + vb.w);
     const Law<float> law = contact_law<float>(pm, (float)d.h, n, dn, vB - vA,
-                                              V3<float>{(float)u0, (float)u1, (float)u2}, Rbar, mbar);
+                                              V3<float>{d2f(u0), d2f(u1), d2f(u2)}, Rbar, mbar);
     // tangential history: FP64 accumulation of the float increment
     if (law.capped) {
-      u0 = (double)law.u.x; u1 = (double)law.u.y; u2 = (double)law.u.z;
+      u0 = f2d(law.u.x); u1 = f2d(law.u.y); u2 = f2d(law.u.z);
     } else {
-      u0 += (double)law.u.x; u1 += (double)law.u.y; u2 += (double)law.u.z;
+      u0 += f2d(law.u.x); u1 += f2d(law.u.y); u2 += f2d(law.u.z);
     }
     l.u[i] = u0;
     l.u[l.cap + i] = u1;
@@ -236,11 +236,11 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     }
     const PairMat<float> pm = d.pm32[__float_as_int(RS.w) * d.nmat + W.material];
     const Law<float> law = contact_law<float>(pm, (float)d.h, n, dn, vW - vA,
-                                              V3<float>{(float)u0, (float)u1, (float)u2}, S.r, va.w);
+                                              V3<float>{d2f(u0), d2f(u1), d2f(u2)}, S.r, va.w);
     if (law.capped) {
-      u0 = (double)law.u.x; u1 = (double)law.u.y; u2 = (double)law.u.z;
+      u0 = f2d(law.u.x); u1 = f2d(law.u.y); u2 = f2d(law.u.z);
     } else {
-      u0 += (double)law.u.x; u1 += (double)law.u.y; u2 += (double)law.u.z;
+      u0 += f2d(law.u.x); u1 += f2d(law.u.y); u2 += f2d(law.u.z);
     }
     l.uw[i] = u0;
     l.uw[l.capw + i] = u1;
@@ -431,44 +431,50 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
     float4 off = d.coff[c];
     double4_32a q4 = d.cq[c], v = d.cv[c], w = d.cw[c];
     const float mass = (float)d.tmass[tpl];
+    ff qw = ff_from_double(q4.x), qx = ff_from_double(q4.y), qy = ff_from_double(q4.z),
+       qz = ff_from_double(q4.w);
     if (integrate) {
       float* acc = d.acc32 + 8 * c;
       const float4 a0 = *reinterpret_cast<const float4*>(acc);
       const float4 a1 = *reinterpret_cast<const float4*>(acc + 4);
       *reinterpret_cast<float4*>(acc) = make_float4(0.f, 0.f, 0.f, 0.f);
       *reinterpret_cast<float4*>(acc + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
-      const double h = d.h;
-      const float hf = (float)h;
+      const float hf = (float)d.h;
       const float im = 1.f / mass;
-      // Eq. (5a): double velocity accumulation of the float acceleration
-      v.x += h * ((double)(a0.x * im) + d.g[0]);
-      v.y += h * ((double)(a0.y * im) + d.g[1]);
-      v.z += h * ((double)(a0.z * im) + d.g[2]);
-      double o[3] = {(double)off.x + h * v.x, (double)off.y + h * v.y, (double)off.z + h * v.z};
-      int vx[3] = {vox.x, vox.y, vox.z};
+      // Eq. (5a): double velocity, accumulating h*F/m (float) and h*g (double)
+      v.x = (v.x + d.hg[0]) + f2d(hf * (a0.x * im));
+      v.y = (v.y + d.hg[1]) + f2d(hf * (a0.y * im));
+      v.z = (v.z + d.hg[2]) + f2d(hf * (a0.z * im));
+      // position: the offset increment h*v carries 1e-7 relative error, far
+      // below the 2^-44 m resolution of the offset itself
+      const float vx_f = d2f(v.x), vy_f = d2f(v.y), vz_f = d2f(v.z);
+      float o[3] = {off.x + hf * vx_f, off.y + hf * vy_f, off.z + hf * vz_f};
+      int vi[3] = {vox.x, vox.y, vox.z};
+      const float kV = (float)kVoxel;
       for (int k = 0; k < 3; ++k) {
-        if (fabs(o[k]) > 0.5 * kVoxel) {
-          const double m = rint(o[k] * (1.0 / kVoxel));
-          vx[k] += (int)m;
-          o[k] -= m * kVoxel;
+        if (fabsf(o[k]) > 0.5f * kV) {
+          const float m = rintf(o[k] * (1.f / kV));
+          vi[k] += (int)m;
+          o[k] -= m * kV;  // exact: m * 2^-20 and the difference are representable
         }
       }
-      vox = make_int4(vx[0], vx[1], vx[2], vox.w);
-      off = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
+      vox = make_int4(vi[0], vi[1], vi[2], vox.w);
+      off = make_float4(o[0], o[1], o[2], 0.f);
       // Eq. (5b): body frame, float angular acceleration, double accumulation
       float Rf[9];
-      quat_to_mat((float)q4.x, (float)q4.y, (float)q4.z, (float)q4.w, Rf);
+      quat_to_mat(qw.h, qx.h, qy.h, qz.h, Rf);
       const V3<float> tb = mat_tmul(Rf, V3<float>{a0.w, a1.x, a1.y});
-      const V3<float> wf = {(float)w.x, (float)w.y, (float)w.z};
+      const V3<float> wf = {d2f(w.x), d2f(w.y), d2f(w.z)};
       const float I0 = (float)d.tinert[3 * tpl], I1 = (float)d.tinert[3 * tpl + 1],
                   I2 = (float)d.tinert[3 * tpl + 2];
       const V3<float> gy = cross(wf, V3<float>{I0 * wf.x, I1 * wf.y, I2 * wf.z});
-      w.x += h * (double)((tb.x - gy.x) / I0);
-      w.y += h * (double)((tb.y - gy.y) / I1);
-      w.z += h * (double)((tb.z - gy.z) / I2);
-      // orientation: q <- q * exp(h w / 2); the increment q * (dq - 1) in float,
-      // accumulated in double, then one Newton step towards unit length
-      const V3<float> wn = {(float)w.x, (float)w.y, (float)w.z};
+      w.x += f2d(hf * ((tb.x - gy.x) / I0));
+      w.y += f2d(hf * ((tb.y - gy.y) / I1));
+      w.z += f2d(hf * ((tb.z - gy.z) / I2));
+      // orientation: q <- q * exp(h w / 2); the increment q * (dq - 1) in
+      // float, accumulated in double; then |q| is restored to one with a
+      // first-order correction whose size is measured in float-float
+      const V3<float> wn = {d2f(w.x), d2f(w.y), d2f(w.z)};
       const float th = 0.5f * hf * sqrtf(dot(wn, wn));
       const float th2 = th * th;
       const float cm1 = -0.5f * th2 + th2 * th2 * (1.f / 24.f);  // cos(th) - 1
@@ -479,28 +485,35 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
         const float s2 = sn / (2.f * th / hf);
         dqm[0] = cs - 1.f; dqm[1] = s2 * wn.x; dqm[2] = s2 * wn.y; dqm[3] = s2 * wn.z;
       }
-      const float qf[4] = {(float)q4.x, (float)q4.y, (float)q4.z, (float)q4.w};
+      const float qf[4] = {qw.h, qx.h, qy.h, qz.h};
       float inc[4];
       quat_mulf(qf, dqm, inc);
-      double qd[4] = {q4.x + (double)inc[0], q4.y + (double)inc[1], q4.z + (double)inc[2],
-                      q4.w + (double)inc[3]};
-      const double n2 = qd[0] * qd[0] + qd[1] * qd[1] + qd[2] * qd[2] + qd[3] * qd[3];
-      const double sn = 1.5 - 0.5 * n2;
-      q4 = make_double4_32a(qd[0] * sn, qd[1] * sn, qd[2] * sn, qd[3] * sn);
-      if (!(finite4(v) && finite4(w) && finite4(q4) && isfinite(off.x) && isfinite(off.y) &&
-            isfinite(off.z)))
+      double qd[4] = {q4.x + f2d(inc[0]), q4.y + f2d(inc[1]), q4.z + f2d(inc[2]),
+                      q4.w + f2d(inc[3])};
+      qw = ff_from_double(qd[0]); qx = ff_from_double(qd[1]);
+      qy = ff_from_double(qd[2]); qz = ff_from_double(qd[3]);
+      const ff n2 = ff_add(ff_add(ff_mul(qw, qw), ff_mul(qx, qx)),
+                           ff_add(ff_mul(qy, qy), ff_mul(qz, qz)));
+      const float hs = -0.5f * ff_to_float(ff_sub(n2, {1.f, 0.f}));  // 1/|q| - 1 to first order
+      const double hsd = f2d(hs);
+      for (int k = 0; k < 4; ++k) qd[k] = fma(hsd, qd[k], qd[k]);
+      qw = ff_add(qw, ff_mulf(qw, hs)); qx = ff_add(qx, ff_mulf(qx, hs));
+      qy = ff_add(qy, ff_mulf(qy, hs)); qz = ff_add(qz, ff_mulf(qz, hs));
+      q4 = make_double4_32a(qd[0], qd[1], qd[2], qd[3]);
+      if (!(finite_d(v.x) && finite_d(v.y) && finite_d(v.z) && finite_d(w.x) && finite_d(w.y) &&
+            finite_d(w.z) && finite_d(qd[0]) && finite_d(qd[1]) && finite_d(qd[2]) &&
+            finite_d(qd[3]) && isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2])))
         atomicOr(d.flags, kFlagNonFinite);
       d.cvox[c] = vox; d.coff[c] = off; d.cq[c] = q4; d.cv[c] = v; d.cw[c] = w;
       if (check_cert) {
         const int4 v0 = d.ref_vox[c];
         const float4 o0 = d.ref_off[c];
-        const float kV = (float)kVoxel;
         const float dx = (float)(vox.x - v0.x) * kV + (off.x - o0.x);
         const float dy = (float)(vox.y - v0.y) * kV + (off.y - o0.y);
         const float dz = (float)(vox.z - v0.z) * kV + (off.z - o0.z);
         const float4 r0 = d.ref_q[c];
         const float a[4] = {r0.x, -r0.y, -r0.z, -r0.w};
-        const float b[4] = {(float)q4.x, (float)q4.y, (float)q4.z, (float)q4.w};
+        const float b[4] = {qw.h, qx.h, qy.h, qz.h};
         float e[4];
         quat_mulf(a, b, e);
         const float disp = sqrtf(dx * dx + dy * dy + dz * dz) +
@@ -513,8 +526,6 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
       }
     }
     // rotation matrix as float-float from the double orientation
-    const ff qw = ff_from_double(q4.x), qx = ff_from_double(q4.y), qy = ff_from_double(q4.z),
-             qz = ff_from_double(q4.w);
     const ff xx = ff_mul(qx, qx), yy = ff_mul(qy, qy), zz = ff_mul(qz, qz);
     const ff xy = ff_mul(qx, qy), xz = ff_mul(qx, qz), yz = ff_mul(qy, qz);
     const ff wx = ff_mul(qw, qx), wy = ff_mul(qw, qy), wz = ff_mul(qw, qz);
@@ -535,9 +546,9 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
       sRl[threadIdx.x][k] = R[k].l;
       Rf[k] = R[k].h;
     }
-    const V3<float> wf = {(float)w.x, (float)w.y, (float)w.z};
+    const V3<float> wf = {d2f(w.x), d2f(w.y), d2f(w.z)};
     const V3<float> ww = mat_mul(Rf, wf);
-    d.mv32[c] = make_float4((float)v.x, (float)v.y, (float)v.z, mass);
+    d.mv32[c] = make_float4(d2f(v.x), d2f(v.y), d2f(v.z), mass);
     d.mw32[c] = make_float4(ww.x, ww.y, ww.z, 0.f);
     sVox[threadIdx.x] = vox;
     sOff[threadIdx.x] = off;
