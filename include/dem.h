@@ -197,6 +197,11 @@ int dem_reset_stats(dem_ctx* ctx);
  * context stream; they are read once at the end of each dem_step call, so
  * the steps themselves are not serialised. */
 int dem_set_timing(dem_ctx* ctx, int timing);
+/* enabled = 1 runs the steps between two rebuilds of the plain rule as one
+ * CUDA graph launch (captured on first use per list buffer, step count and
+ * margin, and recaptured after any buffer is reallocated).  Results are those
+ * of the ordinary launches.  Ignored while timing is on.  Default 0. */
+int dem_set_graphs(dem_ctx* ctx, int enabled);
 
 /* ---- inspection (tests, tools) ----------------------------------------- */
 
@@ -234,6 +239,67 @@ int dem_get_bins(dem_ctx* ctx, long long cap, unsigned int* keys, int* ids, long
  * current state compared with the current list.  *missed receives the number
  * of touching sphere pairs and sphere-wall contacts that are not listed. */
 int dem_audit(dem_ctx* ctx, long long* missed);
+
+/* ---- learned list lifetime (an extension: the paper uses a fixed margin) --
+ * A small regressor predicts, per detection bin, how many steps the contact
+ * list built with a given margin stays valid for the clumps of that bin.
+ * Inputs (dem_trace documents them): 6 floats per sample; output: the natural
+ * log of the number of steps.  Network: 6 -> 64 -> 64 -> 64 -> 1 with ReLU,
+ * BF16 weights and FP32 accumulation on the GPU; parameters are one flat
+ * float vector, layer by layer, each layer W (row-major [out][in]) then b. */
+typedef struct dem_mlp dem_mlp;
+
+/* Number of parameters (8833). */
+int dem_mlp_num_params(void);
+/* Creates a regressor on `device` with a fixed-seed initialisation. */
+int dem_mlp_create(int device, dem_mlp** out);
+void dem_mlp_destroy(dem_mlp* mlp);
+/* Sets / reads the FP32 master parameters (host arrays of num_params);
+ * setting resets the Adam moments. */
+int dem_mlp_set_params(dem_mlp* mlp, const float* params);
+int dem_mlp_get_params(dem_mlp* mlp, float* params);
+/* y[k] for k < n from x[6k .. 6k+5] (host arrays). */
+int dem_mlp_forward(dem_mlp* mlp, long long n, const float* x, float* y);
+/* Mean squared error of predictions against targets t (host), and its
+ * gradient with respect to the parameters (host, may be NULL). */
+int dem_mlp_loss_grad(dem_mlp* mlp, long long n, const float* x, const float* t, double* loss,
+                      float* grad);
+/* `steps` Adam steps (lr, beta 0.9/0.999, eps 1e-8) on minibatches of `batch`
+ * samples drawn without replacement per epoch (seeded); *final_loss gets the
+ * loss over all n samples after training. */
+int dem_mlp_train(dem_mlp* mlp, long long n, const float* x, const float* t, int steps, int batch,
+                  float lr, unsigned long long seed, double* final_loss);
+
+/* Learned rebuild rule.  At each rebuild, for every occupied bin, the
+ * regressor is queried at each candidate margin (ascending, in metres); the
+ * clumps of the bin get the smallest candidate whose predicted lifetime is at
+ * least interval * safety (the largest candidate otherwise), and the list is
+ * rebuilt every `interval` steps.  Every step checks that no clump moved
+ * further than its margin since the rebuild (which guarantees that no contact
+ * is missing from the list); if that fails anywhere in an interval, the state
+ * and tangential history are rolled back to the rebuild and the interval is
+ * replayed with the plain rule (margin and rebuild_interval of dem_params).
+ * mlp = NULL restores the plain rule.  The regressor must outlive its use. */
+typedef struct {
+    int interval;
+    double safety;
+    int n_candidates;
+    const double* candidates;
+} dem_learned_params;
+int dem_set_learned_policy(dem_ctx* ctx, dem_mlp* mlp, const dem_learned_params* params);
+
+/* Training traces from the plain rule.  Runs `windows` windows of `window`
+ * steps; at the start of each window every occupied bin yields, for each
+ * candidate margin m, the features
+ *   x = [ln(1 + clumps in bin), ln(h vmax / m), ln(h vmean / m),
+ *        ln(h^2 amax / m), ln(m / r_mean), ln(h^2 |g| / m)]
+ * (vmax, vmean: largest and mean clump speed bound |v| + |w| r_bound; amax:
+ * largest clump acceleration in the last step; r_mean: mean sphere radius)
+ * and the target t = ln(T), T the first step of the window at which a clump
+ * of the bin has moved further than m (T = window if none did).  Writes up
+ * to cap samples into x (6 * cap) and t (cap); *n receives the count. */
+int dem_trace(dem_ctx* ctx, int windows, int window, int n_candidates, const double* candidates,
+              long long cap, float* x, float* t, long long* n);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ from . import capi
 from .capi import (DEM_FP32_VOXEL, DEM_FP64, DEM_GUARD_COUNT, DEM_GUARD_OFF,
                    DEM_GUARD_ROLLBACK, DemError)
 
-__all__ = ["Simulation", "DemError", "DEM_FP64", "DEM_FP32_VOXEL", "DEM_GUARD_OFF",
+__all__ = ["Simulation", "Regressor", "DemError", "DEM_FP64", "DEM_FP32_VOXEL", "DEM_GUARD_OFF",
            "DEM_GUARD_COUNT", "DEM_GUARD_ROLLBACK", "load_library"]
 
 
@@ -208,6 +208,35 @@ class Simulation:
     def set_timing(self, on=True):
         self._check(self.lib.dem_set_timing(self.ctx, 1 if on else 0))
 
+    def set_graphs(self, on=True):
+        """Run the steps between rebuilds as one captured CUDA graph."""
+        self._check(self.lib.dem_set_graphs(self.ctx, 1 if on else 0))
+
+    def set_learned_policy(self, regressor, interval=40, safety=1.5, candidates=None):
+        """Learned rebuild rule (see include/dem.h); regressor=None restores the plain rule."""
+        if regressor is None:
+            self._check(self.lib.dem_set_learned_policy(self.ctx, None, None))
+            self._regressor = None
+            return
+        cand = _f64(candidates)
+        self._cand = cand
+        lp = capi.DemLearnedParams(int(interval), float(safety), len(cand), _pd(cand))
+        self._check(self.lib.dem_set_learned_policy(self.ctx, regressor.h, C.byref(lp)))
+        self._regressor = regressor  # keep it alive while in use
+
+    def trace(self, windows, window, candidates, cap=None):
+        """Training samples (x: n x 6, t: n) from `windows` windows of the plain rule."""
+        cand = _f64(candidates)
+        if cap is None:
+            cap = 1 << 22
+        x = np.zeros((cap, 6), np.float32)
+        t = np.zeros(cap, np.float32)
+        n = C.c_longlong()
+        self._check(self.lib.dem_trace(self.ctx, int(windows), int(window), len(cand), _pd(cand),
+                                       int(cap), x.ctypes.data_as(C.POINTER(C.c_float)),
+                                       t.ctypes.data_as(C.POINTER(C.c_float)), C.byref(n)))
+        return x[: n.value].copy(), t[: n.value].copy()
+
     def close(self):
         if getattr(self, "ctx", None):
             self.lib.dem_destroy(self.ctx)
@@ -224,3 +253,70 @@ class Simulation:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _pf(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Regressor:
+    """The learned list-lifetime regressor of libdem.so (6 -> 3x64 ReLU -> 1,
+    BF16 weights, FP32 accumulation, Adam), trained and run on the GPU."""
+
+    def __init__(self, device=0, params=None):
+        self.lib = capi.load()
+        h = C.c_void_p()
+        rc = self.lib.dem_mlp_create(int(device), C.byref(h))
+        if rc != 0:
+            raise DemError(rc, "dem_mlp_create failed")
+        self.h = h
+        self.n_params = int(self.lib.dem_mlp_num_params())
+        if params is not None:
+            self.set_params(params)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DemError(rc, "regressor call failed")
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.n_params
+        self._check(self.lib.dem_mlp_set_params(self.h, _pf(p)))
+
+    def params(self):
+        p = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.dem_mlp_get_params(self.h, _pf(p)))
+        return p
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, 6)
+        y = np.zeros(len(x), np.float32)
+        self._check(self.lib.dem_mlp_forward(self.h, len(x), _pf(x), _pf(y)))
+        return y
+
+    def loss_grad(self, x, t):
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, 6)
+        t = np.ascontiguousarray(t, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_double()
+        self._check(self.lib.dem_mlp_loss_grad(self.h, len(x), _pf(x), _pf(t), C.byref(loss), _pf(g)))
+        return loss.value, g
+
+    def train(self, x, t, steps=500, batch=4096, lr=1e-3, seed=0):
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, 6)
+        t = np.ascontiguousarray(t, np.float32)
+        loss = C.c_double()
+        self._check(self.lib.dem_mlp_train(self.h, len(x), _pf(x), _pf(t), int(steps), int(batch),
+                                           float(lr), int(seed), C.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dem_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -57,8 +57,14 @@ class DemStats(C.Structure):
 
 
 _D = C.POINTER(C.c_double)
+_F = C.POINTER(C.c_float)
 _I = C.POINTER(C.c_int)
 _V = C.c_void_p
+
+
+class DemLearnedParams(C.Structure):
+    _fields_ = [("interval", C.c_int), ("safety", C.c_double), ("n_candidates", C.c_int),
+                ("candidates", C.POINTER(C.c_double))]
 
 # name -> (restype, argtypes); the exported symbols of include/dem.h
 SIGNATURES = {
@@ -74,6 +80,7 @@ SIGNATURES = {
     "dem_get_stats": (C.c_int, [_V, C.POINTER(DemStats)]),
     "dem_reset_stats": (C.c_int, [_V]),
     "dem_set_timing": (C.c_int, [_V, C.c_int]),
+    "dem_set_graphs": (C.c_int, [_V, C.c_int]),
     "dem_rebuild": (C.c_int, [_V]),
     "dem_eval_forces": (C.c_int, [_V]),
     "dem_get_forces": (C.c_int, [_V, _D, _D]),
@@ -83,6 +90,18 @@ SIGNATURES = {
     "dem_get_bins": (C.c_int, [_V, C.c_longlong, C.POINTER(C.c_uint), _I,
                                C.POINTER(C.c_longlong)]),
     "dem_audit": (C.c_int, [_V, C.POINTER(C.c_longlong)]),
+    "dem_mlp_num_params": (C.c_int, []),
+    "dem_mlp_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "dem_mlp_destroy": (None, [_V]),
+    "dem_mlp_set_params": (C.c_int, [_V, _F]),
+    "dem_mlp_get_params": (C.c_int, [_V, _F]),
+    "dem_mlp_forward": (C.c_int, [_V, C.c_longlong, _F, _F]),
+    "dem_mlp_loss_grad": (C.c_int, [_V, C.c_longlong, _F, _F, C.POINTER(C.c_double), _F]),
+    "dem_mlp_train": (C.c_int, [_V, C.c_longlong, _F, _F, C.c_int, C.c_int, C.c_float,
+                                C.c_ulonglong, C.POINTER(C.c_double)]),
+    "dem_set_learned_policy": (C.c_int, [_V, _V, C.c_void_p]),
+    "dem_trace": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, _D, C.c_longlong, _F, _F,
+                            C.POINTER(C.c_longlong)]),
 }
 
 _lib = None

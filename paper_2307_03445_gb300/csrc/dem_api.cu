@@ -16,6 +16,8 @@
 #include "../../include/dem.h"
 #include "dem_dev.cuh"
 #include "dem_prims.cuh"
+#include "dem_learn.cuh"
+#include "dem_mlp.cuh"
 
 using namespace dem;
 
@@ -46,6 +48,7 @@ struct dem_ctx {
   std::vector<int> tpl_off, tpl_mat;
   std::vector<double> tpl_pos, tpl_rad, tpl_mass, tpl_inert;
   double r_max = 0.0;
+  double r_mean = 1e-3, r_sum = 0.0;
   // scenes and walls
   std::vector<SceneH> scenes;
   std::vector<WallDev> walls;
@@ -57,12 +60,12 @@ struct dem_ctx {
   long long ncl = 0, ns = 0;
   // all device buffers
   std::vector<Buf*> owned;
-  Buf b_tpl_off, b_tp64, b_tp32, b_tmat, b_tmass, b_tinert, b_tpbound;
+  Buf b_tpl_off, b_tp64, b_tp32, b_tmat, b_tmass, b_tinert, b_tpbound, b_tmassf, b_tinertf;
   Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cv, b_cw, b_mv64, b_mw64, b_mv32, b_mw32;
   Buf b_acc64, b_acc32, b_ref_pos, b_ref_vox, b_ref_off, b_ref_q;
   Buf b_sinfo, b_sa64, b_sb64, b_sa32, b_sb32;
   Buf b_grids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
-  Buf b_flags, b_counters, b_totals;
+  Buf b_flags, b_counters, b_totals, b_dstep;
   // detection scratch
   Buf b_det, b_bin_cnt, b_bin_off, b_wall_mask, b_wall_cnt, b_keys, b_ids, b_keys2, b_ids2;
   Buf b_bin_start, b_bin_end, b_pair_cnt, b_scan_scr, b_sort_scr, b_tmp;
@@ -72,7 +75,7 @@ struct dem_ctx {
   long long n_entries = 0;
   // contact lists (current, next) and an audit list
   struct ListBufs {
-    Buf pa, pb, u, row, ws, ww, uw, wrow;
+    Buf pa, pb, u, row, ws, ww, uw, wrow, dnb;
     ContactList L{};
   } lists[3];
   int cur = 0;
@@ -87,6 +90,27 @@ struct dem_ctx {
   DevState D{};
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> evpool;  // 4 per timed step, read at the end of dem_step
+  // learned rebuild rule (extension) and rollback snapshots
+  dem_mlp* mlp = nullptr;
+  int l_interval = 0;
+  double l_safety = 1.0;
+  std::vector<double> l_cand;
+  long long n_occ = 0;
+  Buf b_alast, b_chome, b_cmargin, b_bcnt, b_bvmax, b_bvsum, b_bamax, b_occ, b_nocc, b_binm, b_cand;
+  Buf b_feat, b_pred, b_dmax, b_T, b_tr_vox, b_tr_off, b_tr_pos, b_tr_q, b_tx, b_tt, b_tcount;
+  Buf s_state, s_pb, s_u, s_ww, s_uw;
+  long long snap_step = 0;
+  // CUDA graphs of the steps between rebuilds (plain rule)
+  int use_graphs = 0;
+  long long layout = 0;        // bumped whenever a device buffer is reallocated
+  long long graph_layout = -1;
+  struct GraphEntry {
+    int cur, m, cert;
+    double margin;
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::vector<GraphEntry> graphs;
 };
 
 namespace {
@@ -120,6 +144,7 @@ bool grow(dem_ctx* c, Buf& b, size_t bytes, size_t keep = 0) {
   nb = (nb + 255) & ~(size_t)255;
   void* p = dalloc(c, nb);
   if (!p) return false;
+  c->layout++;
   if (keep && b.p) cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->st);
   dfree(c, b.p);
   b.p = p;
@@ -173,6 +198,9 @@ void refresh_devstate(dem_ctx* c) {
   d.tmat = ptr<int>(c->b_tmat);
   d.tmass = ptr<double>(c->b_tmass);
   d.tinert = ptr<double>(c->b_tinert);
+  d.tmassf = ptr<float>(c->b_tmassf);
+  d.tinertf = ptr<float>(c->b_tinertf);
+  d.hf = (float)c->P.dt;
   d.tpbound = ptr<float>(c->b_tpbound);
   d.cinfo = ptr<int2>(c->b_cinfo);
   d.csph = ptr<int>(c->b_csph);
@@ -193,6 +221,7 @@ void refresh_devstate(dem_ctx* c) {
   d.ref_off = ptr<float4>(c->b_ref_off);
   d.ref_q = ptr<float4>(c->b_ref_q);
   d.cmargin = nullptr;
+  d.alast = ptr<float>(c->b_alast);
   d.sinfo = ptr<int2>(c->b_sinfo);
   d.sa64 = ptr<SphA64>(c->b_sa64);
   d.sb64 = ptr<double4_32a>(c->b_sb64);
@@ -209,6 +238,7 @@ void refresh_devstate(dem_ctx* c) {
   d.pm32 = ptr<PairMat<float>>(c->b_pm32);
   d.flags = ptr<int>(c->b_flags);
   d.counters = ptr<unsigned long long>(c->b_counters);
+  d.dstep = ptr<long long>(c->b_dstep);
 }
 
 ContactList& curL(dem_ctx* c) { return c->lists[c->cur].L; }
@@ -266,6 +296,8 @@ int finalize(dem_ctx* c) {
   if (c->finalized) return DEM_OK;
   if (c->n_tpl == 0) return fail(c, DEM_ERR_STATE, "no clump templates loaded");
   c->margin = current_margin(c);
+  // the detection lattice holds r + m in 31 bits (2^-24 m units)
+  if (!(c->r_max + c->margin < 32.0)) return fail(c, DEM_ERR_INVALID_ARG, "sphere radius plus margin must be below 32 m");
   // detection grids
   c->grids.clear();
   uint64_t base = 0;
@@ -277,6 +309,7 @@ int finalize(dem_ctx* c) {
     if (L < 1) L = 1;
     for (int k = 0; k < 3; ++k) {
       g.lo[k] = sh.lo[k];
+      g.lof[k] = (float)sh.lo[k];
       long long ext = std::llrint((sh.hi[k] - sh.lo[k]) * kDetScale);
       long long dd = (ext + L - 1) / L;
       if (dd < 1) dd = 1;
@@ -319,7 +352,15 @@ int finalize(dem_ctx* c) {
       split_ff(std::sin(uw.half_angle), d.sh, d.sl);
       split_ff(uw.height, d.hh, d.hl);
       split_ff(d.rb, d.rbh, d.rbl);
-      d.speed = (float)std::sqrt(uw.vel[0] * uw.vel[0] + uw.vel[1] * uw.vel[1] + uw.vel[2] * uw.vel[2]);
+      d.speed_d = std::sqrt((uw.vel[0] * uw.vel[0] + uw.vel[1] * uw.vel[1]) + uw.vel[2] * uw.vel[2]);
+      d.speed = (float)d.speed_d;
+      for (int k = 0; k < 3; ++k) {
+        d.pf[k] = (float)uw.p[k];
+        d.vf[k] = (float)uw.vel[k];
+      }
+      d.radf = (float)uw.radius;
+      d.heightf = (float)uw.height;
+      d.rbf = (float)d.rb;
       idx.push_back((int)c->walls.size());
       c->wall_user.push_back((int)w);
       c->wall_scene.push_back((int)s);
@@ -334,7 +375,8 @@ int finalize(dem_ctx* c) {
       !grow(c, c->b_walls, sizeof(WallDev) * nw) || !grow(c, c->b_wall_idx, sizeof(int) * std::max<size_t>(1, idx.size())) ||
       !grow(c, c->b_wall_scene, sizeof(int) * nw) || !grow(c, c->b_wfix, 3 * sizeof(long long) * nw) ||
       !grow(c, c->b_wpos, 3 * sizeof(double) * nw) || !grow(c, c->b_wforce, 3 * sizeof(double) * nw) ||
-      !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->b_totals, 64))
+      !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->b_totals, 64) ||
+      !grow(c, c->b_dstep, 64))
     return fail(c, DEM_ERR_OOM, "scene tables");
   cudaMemcpyAsync(c->b_grids.p, c->grids.data(), sizeof(SceneGrid) * c->grids.size(), cudaMemcpyHostToDevice, c->st);
   if (!c->walls.empty()) {
@@ -349,16 +391,17 @@ int finalize(dem_ctx* c) {
   c->finalized = true;
   refresh_devstate(c);
   // sphere poses and mirrors of the initial state, walls at the current time
-  launch_update(c->D, false, (double)c->step * c->P.dt, c->margin, false, c->st);
+  launch_update(c->D, false, c->step, c->margin, false, c->st);
   cudaStreamSynchronize(c->st);
   return cuda_check(c, "finalize");
 }
 
-// Detection into lists[li] with margin m (rebuild) -- also used by the audit.
-int detect_into(dem_ctx* c, int li, double m) {
+// Detection into lists[li] with margin m (per clump from D.cmargin when set),
+// for a list that must last K steps (wall travel) -- also used by the audit.
+int detect_into(dem_ctx* c, int li, double m, int K) {
   const long long ns = c->ns;
   const double t = (double)c->step * c->P.dt;
-  const double travel = c->P.dt * (double)std::max(1, c->P.rebuild_interval);
+  const double travel = c->P.dt * (double)std::max(1, K);
   auto& LB = c->lists[li];
   if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_bin_cnt, 4 * (ns + 1)) ||
       !grow(c, c->b_bin_off, 4 * (ns + 1)) || !grow(c, c->b_wall_mask, 4 * (ns + 1)) ||
@@ -448,9 +491,13 @@ int detect_into(dem_ctx* c, int li, double m) {
   L.ww = ptr<uint32_t>(LB.ww);
   L.uw = ptr<double>(LB.uw);
   L.wrow = ptr<uint32_t>(LB.wrow);
+  if (!grow(c, LB.dnb, 16)) return fail(c, DEM_ERR_OOM, "list lengths");
+  L.dn = ptr<long long>(LB.dnb);
   L.n = (long long)NP;
   L.nw = (long long)NW;
   const uint32_t np32 = (uint32_t)NP, nw32 = (uint32_t)NW;
+  const long long lens[2] = {(long long)NP, (long long)NW};
+  cudaMemcpyAsync(L.dn, lens, sizeof(lens), cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(L.row + ns, &np32, 4, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(L.wrow + ns, &nw32, 4, cudaMemcpyHostToDevice, c->st);
   launch_narrow(c->D, o, true, L.pa, L.pb, c->st);
@@ -459,10 +506,12 @@ int detect_into(dem_ctx* c, int li, double m) {
   return cuda_check(c, "detect_into");
 }
 
-int rebuild(dem_ctx* c) {
+// Rebuilds the current list with margin m (per clump when D.cmargin is set)
+// for a list meant to last K steps; history is carried from the old list.
+int rebuild(dem_ctx* c, double m, int K) {
   const int nxt = c->cur == 0 ? 1 : 0;
   if (c->timing) cudaEventRecord(c->ev[0], c->st);
-  int rc = detect_into(c, nxt, c->margin);
+  int rc = detect_into(c, nxt, m, K);
   if (rc) return rc;
   ContactList& N = c->lists[nxt].L;
   if (c->have_list) launch_hist_map(curL(c), N, c->list_ns, c->st);
@@ -485,6 +534,7 @@ int rebuild(dem_ctx* c) {
   }
   return cuda_check(c, "rebuild");
 }
+int rebuild(dem_ctx* c) { return rebuild(c, c->margin, c->P.rebuild_interval); }
 
 // Sphere-sphere then sphere-wall contact forces; `mid` (optional) is recorded
 // between the two kernels.
@@ -503,7 +553,9 @@ int force_pass(dem_ctx* c, bool count_active, cudaEvent_t mid = nullptr) {
   return DEM_OK;
 }
 
-int read_flags(dem_ctx* c) {
+// Reads and clears the device flags and counters; *guard_hit tells whether the
+// displacement certificate failed since the last read.
+int read_flags(dem_ctx* c, bool* guard_hit = nullptr) {
   int flags = 0;
   unsigned long long ctr[2] = {0, 0};
   cudaMemcpyAsync(&flags, c->b_flags.p, sizeof(int), cudaMemcpyDeviceToHost, c->st);
@@ -511,13 +563,290 @@ int read_flags(dem_ctx* c) {
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "step");
   cudaMemsetAsync(c->b_flags.p, 0, sizeof(int), c->st);
   cudaMemsetAsync(c->b_counters.p, 0, 2 * sizeof(unsigned long long), c->st);
-  c->stats.active_last = (long long)ctr[0];
+  if (ctr[0]) c->stats.active_last = (long long)ctr[0];
   c->stats.guard_violations += (long long)ctr[1];
+  if (guard_hit) *guard_hit = (flags & kFlagGuard) != 0;
   if (flags & kFlagNonFinite) return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
-  if ((flags & kFlagGuard) && c->P.guard == DEM_GUARD_ROLLBACK)
-    return fail(c, DEM_ERR_GUARD, "a clump moved further than the margin since the last rebuild");
   return cuda_check(c, "step");
 }
+
+// ---------------------------------------------------------------------------
+// learned rebuild rule
+// ---------------------------------------------------------------------------
+FeatureScales feature_scales(const dem_ctx* c) {
+  FeatureScales f;
+  f.h = (float)c->P.dt;
+  f.rmean = (float)c->r_mean;
+  f.gmag = (float)std::sqrt(c->P.g[0] * c->P.g[0] + c->P.g[1] * c->P.g[1] + c->P.g[2] * c->P.g[2]);
+  return f;
+}
+
+// Per-clump margins from the regressor (sets D.cmargin).
+int predict_margins(dem_ctx* c) {
+  const long long ncl = c->ncl, nb = c->nbins;
+  const int nc = (int)c->l_cand.size();
+  if (!grow(c, c->b_chome, 4 * (ncl + 1)) || !grow(c, c->b_cmargin, 4 * (ncl + 1)) ||
+      !grow(c, c->b_bcnt, 4 * (nb + 1)) || !grow(c, c->b_bvmax, 4 * (nb + 1)) ||
+      !grow(c, c->b_bvsum, 4 * (nb + 1)) || !grow(c, c->b_bamax, 4 * (nb + 1)) ||
+      !grow(c, c->b_occ, 4 * (nb + 1)) || !grow(c, c->b_binm, 4 * (nb + 1)) ||
+      !grow(c, c->b_nocc, 64) || !grow(c, c->b_cand, 4 * (size_t)nc))
+    return fail(c, DEM_ERR_OOM, "learned-rule buffers");
+  std::vector<float> cf(c->l_cand.begin(), c->l_cand.end());
+  cudaMemcpyAsync(c->b_cand.p, cf.data(), 4 * (size_t)nc, cudaMemcpyHostToDevice, c->st);
+  BinStats bs{ptr<uint32_t>(c->b_chome), ptr<uint32_t>(c->b_bcnt), ptr<int>(c->b_bvmax),
+              ptr<float>(c->b_bvsum), ptr<int>(c->b_bamax)};
+  cudaMemsetAsync(bs.cnt, 0, 4 * (size_t)nb, c->st);
+  cudaMemsetAsync(bs.vmax, 0, 4 * (size_t)nb, c->st);
+  cudaMemsetAsync(bs.vsum, 0, 4 * (size_t)nb, c->st);
+  cudaMemsetAsync(bs.amax, 0, 4 * (size_t)nb, c->st);
+  cudaMemsetAsync(c->b_nocc.p, 0, 4, c->st);
+  c->D.cmargin = nullptr;
+  launch_clump_home(c->D, bs, c->st);
+  launch_bin_compact(bs.cnt, nb, ptr<uint32_t>(c->b_occ), ptr<uint32_t>(c->b_nocc), c->st);
+  uint32_t nocc = 0;
+  cudaMemcpyAsync(&nocc, c->b_nocc.p, 4, cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  c->n_occ = nocc;
+  const long long rows = (long long)nocc * nc;
+  if (!grow(c, c->b_feat, 4 * (size_t)(rows + 1) * kMlpIn) || !grow(c, c->b_pred, 4 * (size_t)(rows + 1)))
+    return fail(c, DEM_ERR_OOM, "feature buffers");
+  launch_bin_features(bs, ptr<uint32_t>(c->b_occ), nocc, nc, ptr<float>(c->b_cand), feature_scales(c),
+                      ptr<float>(c->b_feat), c->st);
+  if (c->mlp) {
+    mlp_forward_dev(mlp_weights(c->mlp), ptr<float>(c->b_feat), rows, ptr<float>(c->b_pred), c->st);
+    const float ln_need = (float)std::log(std::max(1.0, c->l_interval * c->l_safety));
+    launch_choose_margin(ptr<uint32_t>(c->b_occ), nocc, nc, ptr<float>(c->b_cand),
+                         ptr<float>(c->b_pred), ln_need, ptr<float>(c->b_binm), c->st);
+    launch_clump_margin(ncl, bs.chome, ptr<float>(c->b_binm), ptr<float>(c->b_cmargin), c->st);
+    c->D.cmargin = ptr<float>(c->b_cmargin);
+  }
+  return cuda_check(c, "predict margins");
+}
+
+// State and list history at a rebuild, for a rollback.
+int take_snapshot(dem_ctx* c) {
+  const size_t n = (size_t)c->ncl;
+  const bool f64 = c->P.precision == DEM_FP64;
+  ContactList& L = curL(c);
+  if (!grow(c, c->s_state, 128 * (n + 1)) || !grow(c, c->s_pb, 4 * (size_t)(L.n + 1)) ||
+      !grow(c, c->s_u, 24 * (size_t)(L.n + 1)) || !grow(c, c->s_ww, 4 * (size_t)(L.nw + 1)) ||
+      !grow(c, c->s_uw, 24 * (size_t)(L.nw + 1)))
+    return fail(c, DEM_ERR_OOM, "snapshot");
+  char* s = (char*)c->s_state.p;
+  if (f64) {
+    cudaMemcpyAsync(s, c->b_cpos.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    cudaMemcpyAsync(s, c->b_cvox.p, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(s + 16 * n, c->b_coff.p, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+  }
+  cudaMemcpyAsync(s + 32 * n, c->b_cq.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(s + 64 * n, c->b_cv.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(s + 96 * n, c->b_cw.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->s_pb.p, L.pb, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, c->st);
+  for (int k = 0; k < 3; ++k)
+    cudaMemcpyAsync((double*)c->s_u.p + k * L.n, L.u + k * L.cap, 8 * (size_t)L.n,
+                    cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->s_ww.p, L.ww, 4 * (size_t)L.nw, cudaMemcpyDeviceToDevice, c->st);
+  for (int k = 0; k < 3; ++k)
+    cudaMemcpyAsync((double*)c->s_uw.p + k * L.nw, L.uw + k * L.capw, 8 * (size_t)L.nw,
+                    cudaMemcpyDeviceToDevice, c->st);
+  c->snap_step = c->step;
+  return cuda_check(c, "snapshot");
+}
+
+int restore_snapshot(dem_ctx* c) {
+  const size_t n = (size_t)c->ncl;
+  const bool f64 = c->P.precision == DEM_FP64;
+  ContactList& L = curL(c);
+  const char* s = (const char*)c->s_state.p;
+  if (f64) {
+    cudaMemcpyAsync(c->b_cpos.p, s, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    cudaMemcpyAsync(c->b_cvox.p, s, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(c->b_coff.p, s + 16 * n, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+  }
+  cudaMemcpyAsync(c->b_cq.p, s + 32 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->b_cv.p, s + 64 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->b_cw.p, s + 96 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(L.pb, c->s_pb.p, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, c->st);
+  for (int k = 0; k < 3; ++k)
+    cudaMemcpyAsync(L.u + k * L.cap, (double*)c->s_u.p + k * L.n, 8 * (size_t)L.n,
+                    cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(L.ww, c->s_ww.p, 4 * (size_t)L.nw, cudaMemcpyDeviceToDevice, c->st);
+  for (int k = 0; k < 3; ++k)
+    cudaMemcpyAsync(L.uw + k * L.capw, (double*)c->s_uw.p + k * L.nw, 8 * (size_t)L.nw,
+                    cudaMemcpyDeviceToDevice, c->st);
+  c->step = c->snap_step;
+  // accumulators are zero after every update; poses, mirrors and walls follow the state
+  c->D.cmargin = nullptr;
+  launch_update(c->D, false, c->step, c->margin, false, c->st);
+  return cuda_check(c, "restore");
+}
+
+
+void drop_graphs(dem_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+// Captures (once per list buffer, step count and margin) and launches a graph
+// of m force + update steps with the current list.
+int launch_graph_steps(dem_ctx* c, int m, double margin, bool cert) {
+  if (c->graph_layout != c->layout) {
+    drop_graphs(c);
+    c->graph_layout = c->layout;
+  }
+  dem_ctx::GraphEntry* ge = nullptr;
+  for (auto& g : c->graphs)
+    if (g.cur == c->cur && g.m == m && g.cert == (int)cert && g.margin == margin) ge = &g;
+  if (!ge) {
+    if (c->acc_dirty) force_pass(c, false);  // never: accumulators are clean between steps
+    const long long k0 = g_kernel_launches;
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return cuda_check(c, "begin capture");
+    for (int j = 0; j < m; ++j) {
+      force_pass(c, false);
+      launch_update(c->D, true, c->step + j + 1, margin, cert, c->st);
+    }
+    if (cudaStreamEndCapture(c->st, &graph) != cudaSuccess) return cuda_check(c, "end capture");
+    cudaGraphExec_t exec;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_check(c, "instantiate");
+    }
+    cudaGraphDestroy(graph);
+    const long long kernels = g_kernel_launches - k0;
+    g_kernel_launches = k0;
+    c->graphs.push_back({c->cur, m, (int)cert, margin, exec, kernels});
+    ge = &c->graphs.back();
+  }
+  if (cudaGraphLaunch(ge->exec, c->st) != cudaSuccess) return cuda_check(c, "graph launch");
+  g_kernel_launches += ge->kernels;
+  return DEM_OK;
+}
+
+// Runs steps on the context stream.  The plain rule rebuilds every K steps;
+// the guarded path runs blocks that start with a rebuild and a snapshot and,
+// when the displacement certificate failed inside a block, rolls back and
+// replays it with the plain rule, or with a rebuild every step if that fails
+// too.  Per-phase events are recorded for the first 8192 steps of a call.
+struct StepRunner {
+  dem_ctx* c;
+  int n_calls;
+  int n_timed = 0;
+  int it = 0;
+  StepRunner(dem_ctx* cc, int n) : c(cc), n_calls(n) {}
+  int init() {
+    n_timed = c->timing ? 8192 : 0;
+    while ((int)c->evpool.size() < 4 * n_timed) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return cuda_check(c, "event pool");
+      c->evpool.push_back(e);
+    }
+    return DEM_OK;
+  }
+  // one force evaluation + update with the current list
+  void step(double margin, bool cert, bool last) {
+    const bool tm = it < n_timed;
+    cudaEvent_t* ev = tm ? &c->evpool[4 * (size_t)it] : nullptr;
+    if (tm) cudaEventRecord(ev[0], c->st);
+    force_pass(c, last, tm ? ev[1] : nullptr);
+    if (tm) cudaEventRecord(ev[2], c->st);
+    launch_update(c->D, true, c->step + 1, margin, cert, c->st);
+    if (tm) cudaEventRecord(ev[3], c->st);
+    ++it;
+    c->step++;
+    c->since++;
+    c->stats.steps++;
+    c->stats.pair_steps += curL(c).n + curL(c).nw;
+  }
+  int run_plain(int n, double margin, int K, bool last_counts) {
+    const bool cert = c->P.guard != DEM_GUARD_OFF && margin > 0.0;
+    c->D.cmargin = nullptr;
+    for (int i = 0; i < n;) {
+      if (c->need_rebuild || !c->have_list || c->since >= K) {
+        int rc = rebuild(c, margin, K);
+        if (rc) return rc;
+      }
+      // steps left on this list; the call's last step runs on its own so that
+      // it can count the active contacts
+      int m = std::min(K - c->since, n - i);
+      if (last_counts && i + m == n) --m;
+      if (c->use_graphs && !c->timing && m >= 2) {
+        int rc = launch_graph_steps(c, m, margin, cert);
+        if (rc) return rc;
+        for (int j = 0; j < m; ++j) {
+          c->step++;
+          c->since++;
+          c->stats.steps++;
+          c->stats.pair_steps += curL(c).n + curL(c).nw;
+        }
+        i += m;
+        continue;
+      }
+      step(margin, cert, last_counts && i == n - 1);
+      ++i;
+    }
+    return DEM_OK;
+  }
+  int run_guarded(int n) {
+    while (n > 0) {
+      const bool learned = c->mlp != nullptr;
+      const int K = learned ? c->l_interval : std::max(1, c->P.rebuild_interval);
+      const int nb = std::min(n, K);
+      int rc;
+      if (learned) {
+        if ((rc = predict_margins(c))) return rc;
+      } else {
+        c->D.cmargin = nullptr;
+      }
+      const float* cm = c->D.cmargin;
+      if ((rc = rebuild(c, c->margin, K))) return rc;
+      if ((rc = take_snapshot(c))) return rc;
+      bool hit = false;
+      if ((rc = read_flags(c, &hit))) return rc;  // clears flags before the block
+      for (int i = 0; i < nb; ++i) {
+        c->D.cmargin = cm;
+        step(c->margin, true, i == nb - 1);
+      }
+      if ((rc = read_flags(c, &hit))) return rc;
+      if (hit) {
+        // roll back and replay the block with the plain rule
+        c->stats.rollbacks++;
+        if ((rc = restore_snapshot(c))) return rc;
+        c->need_rebuild = true;
+        if ((rc = run_plain(nb, c->margin, std::max(1, c->P.rebuild_interval), true))) return rc;
+        if ((rc = read_flags(c, &hit))) return rc;
+        if (hit) {
+          // the speed bound of the plain rule was exceeded too: rebuild every step
+          c->stats.rollbacks++;
+          if ((rc = restore_snapshot(c))) return rc;
+          c->need_rebuild = true;
+          if ((rc = run_plain(nb, 0.0, 1, true))) return rc;
+        }
+      }
+      c->need_rebuild = true;  // the next block starts with its own rebuild
+      n -= nb;
+    }
+    c->D.cmargin = nullptr;
+    return DEM_OK;
+  }
+  void finish() {
+    const int nt = std::min(it, n_timed);
+    for (int k = 0; k < nt; ++k) {
+      const cudaEvent_t* ev = &c->evpool[4 * (size_t)k];
+      float a = 0.f, b = 0.f, u = 0.f;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      cudaEventElapsedTime(&u, ev[2], ev[3]);
+      c->stats.ms_pairs += a;
+      c->stats.ms_walls += b;
+      c->stats.ms_update += u;
+      c->stats.timed_steps++;
+    }
+  }
+};
 
 int upload_clumps(dem_ctx* c, long long first, int n, const int* tpl, const double* pos,
                   const double* quat, const double* vel, const double* angvel) {
@@ -652,20 +981,25 @@ void dem_destroy(dem_ctx* c) {
   cudaSetDevice(c->P.device);
   Buf* all[] = {&c->b_tpl_off, &c->b_tp64, &c->b_tp32, &c->b_tmat, &c->b_tmass, &c->b_tinert, &c->b_tpbound,
                 &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cv, &c->b_cw,
-                &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
+                &c->b_tmassf, &c->b_tinertf, &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
                 &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_sa32,
                 &c->b_sb32, &c->b_grids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
                 &c->b_wpos, &c->b_wforce, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
                 &c->b_totals, &c->b_det, &c->b_bin_cnt, &c->b_bin_off, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_keys, &c->b_ids, &c->b_keys2, &c->b_ids2, &c->b_bin_start, &c->b_bin_end,
                 &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp, &c->b_lob,
-                &c->b_part, &c->b_rec};
+                &c->b_part, &c->b_rec, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
+                &c->b_bcnt, &c->b_bvmax, &c->b_bvsum, &c->b_bamax, &c->b_occ, &c->b_nocc,
+                &c->b_binm, &c->b_cand, &c->b_feat, &c->b_pred, &c->b_dmax, &c->b_T, &c->b_tr_vox,
+                &c->b_tr_off, &c->b_tr_pos, &c->b_tr_q, &c->b_tx, &c->b_tt, &c->b_tcount,
+                &c->s_state, &c->s_pb, &c->s_u, &c->s_ww, &c->s_uw};
   for (Buf* b : all) dfree(c, b->p);
   for (auto& lb : c->lists) {
-    Buf* lbs[] = {&lb.pa, &lb.pb, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow};
+    Buf* lbs[] = {&lb.pa, &lb.pb, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow, &lb.dnb};
     for (Buf* b : lbs) dfree(c, b->p);
   }
   cudaStreamSynchronize(c->st);
+  drop_graphs(c);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->st);
@@ -713,7 +1047,8 @@ int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double
     }
   if (!grow(c, c->b_tpl_off, 4 * (n_tpl + 1)) || !grow(c, c->b_tp64, 32 * S) || !grow(c, c->b_tp32, 16 * S) ||
       !grow(c, c->b_tmat, 4 * S) || !grow(c, c->b_tmass, 8 * n_tpl) || !grow(c, c->b_tinert, 24 * n_tpl) ||
-      !grow(c, c->b_tpbound, 4 * n_tpl))
+      !grow(c, c->b_tpbound, 4 * n_tpl) || !grow(c, c->b_tmassf, 4 * n_tpl) ||
+      !grow(c, c->b_tinertf, 12 * n_tpl))
     return fail(c, DEM_ERR_OOM, "template tables");
   cudaMemcpyAsync(c->b_tpl_off.p, off, 4 * (n_tpl + 1), cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tp64.p, tp64.data(), 32 * (size_t)S, cudaMemcpyHostToDevice, c->st);
@@ -721,6 +1056,9 @@ int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double
   cudaMemcpyAsync(c->b_tmat.p, material, 4 * (size_t)S, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tmass.p, mass, 8 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tinert.p, inertia, 24 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
+  std::vector<float> mf(mass, mass + n_tpl), inf(inertia, inertia + 3 * n_tpl);
+  cudaMemcpyAsync(c->b_tmassf.p, mf.data(), 4 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tinertf.p, inf.data(), 12 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tpbound.p, pb.data(), 4 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   cudaStreamSynchronize(c->st);
   return cuda_check(c, "load templates");
@@ -761,6 +1099,7 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
   bool ok = grow(c, c->b_cinfo, 8 * ncl, 8 * k0) && grow(c, c->b_csph, 4 * (ncl + 1), 4 * k0) &&
             grow(c, c->b_cq, 32 * ncl, 32 * k0) && grow(c, c->b_cv, 32 * ncl, 32 * k0) &&
             grow(c, c->b_cw, 32 * ncl, 32 * k0) && grow(c, c->b_ref_q, 16 * ncl) &&
+            grow(c, c->b_alast, 4 * ncl, 4 * k0) &&
             grow(c, c->b_sinfo, 8 * ns, 8 * s0);
   if (c->P.precision == DEM_FP64) {
     ok = ok && grow(c, c->b_cpos, 32 * ncl, 32 * k0) && grow(c, c->b_mv64, 32 * ncl) &&
@@ -797,11 +1136,18 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
   if (rc) return rc;
   c->stats.n_clumps = ncl;
   c->stats.n_spheres = ns;
+  {
+    double rs = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = c->tpl_off[tpl[i]]; j < c->tpl_off[tpl[i] + 1]; ++j) rs += c->tpl_rad[j];
+    c->r_sum += rs;
+    c->r_mean = c->r_sum / (double)ns;
+  }
   c->need_rebuild = true;
   c->acc_dirty = true;
   if (c->finalized) {
     refresh_devstate(c);
-    launch_update(c->D, false, (double)c->step * c->P.dt, c->margin, false, c->st);
+    launch_update(c->D, false, c->step, c->margin, false, c->st);
     cudaStreamSynchronize(c->st);
   }
   return cuda_check(c, "add clumps");
@@ -814,45 +1160,19 @@ int dem_step(dem_ctx* c, int n_steps) {
   int rc = finalize(c);
   if (rc) return rc;
   refresh_devstate(c);
-  const int K = std::max(1, c->P.rebuild_interval);
-  const bool cert = c->P.guard != DEM_GUARD_OFF;
   const long long launches0 = g_kernel_launches;
-  const int n_timed = c->timing ? std::min(n_steps, 8192) : 0;
-  while ((int)c->evpool.size() < 4 * n_timed) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return cuda_check(c, "event pool");
-    c->evpool.push_back(e);
+  StepRunner R(c, n_steps);
+  if ((rc = R.init())) return rc;
+  if (!c->mlp && c->P.guard != DEM_GUARD_ROLLBACK) {
+    // plain rule: rebuild every rebuild_interval steps with the fixed margin
+    rc = R.run_plain(n_steps, c->margin, std::max(1, c->P.rebuild_interval), true);
+  } else {
+    rc = R.run_guarded(n_steps);
   }
-  for (int it = 0; it < n_steps; ++it) {
-    if (c->need_rebuild || !c->have_list || c->since >= K) {
-      rc = rebuild(c);
-      if (rc) return rc;
-    }
-    const bool tm = it < n_timed;
-    cudaEvent_t* ev = tm ? &c->evpool[4 * (size_t)it] : nullptr;
-    if (tm) cudaEventRecord(ev[0], c->st);
-    force_pass(c, it == n_steps - 1, tm ? ev[1] : nullptr);
-    if (tm) cudaEventRecord(ev[2], c->st);
-    launch_update(c->D, true, (double)(c->step + 1) * c->P.dt, c->margin, cert, c->st);
-    if (tm) cudaEventRecord(ev[3], c->st);
-    c->step++;
-    c->since++;
-    c->stats.steps++;
-    c->stats.pair_steps += curL(c).n + curL(c).nw;
-  }
+  if (rc) return rc;
   c->stats.time = (double)c->step * c->P.dt;
   rc = read_flags(c);
-  for (int it = 0; it < n_timed; ++it) {
-    const cudaEvent_t* ev = &c->evpool[4 * (size_t)it];
-    float a = 0.f, b = 0.f, u = 0.f;
-    cudaEventElapsedTime(&a, ev[0], ev[1]);
-    cudaEventElapsedTime(&b, ev[1], ev[2]);
-    cudaEventElapsedTime(&u, ev[2], ev[3]);
-    c->stats.ms_pairs += a;
-    c->stats.ms_walls += b;
-    c->stats.ms_update += u;
-    c->stats.timed_steps++;
-  }
+  R.finish();
   c->stats.launches += g_kernel_launches - launches0;
   return rc;
 }
@@ -893,7 +1213,7 @@ int dem_set_state(dem_ctx* c, const double* pos, const double* quat, const doubl
   c->acc_dirty = true;
   if (c->finalized) {
     refresh_devstate(c);
-    launch_update(c->D, false, (double)c->step * c->P.dt, c->margin, false, c->st);
+    launch_update(c->D, false, c->step, c->margin, false, c->st);
     cudaStreamSynchronize(c->st);
   }
   return cuda_check(c, "set_state");
@@ -1023,6 +1343,103 @@ int dem_get_bins(dem_ctx* c, long long cap, unsigned int* keys, int* ids, long l
   return cuda_check(c, "get_bins");
 }
 
+
+int dem_set_graphs(dem_ctx* c, int enabled) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  c->use_graphs = enabled ? 1 : 0;
+  return DEM_OK;
+}
+
+int dem_set_learned_policy(dem_ctx* c, dem_mlp* mlp, const dem_learned_params* lp) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  if (!mlp) {
+    c->mlp = nullptr;
+    return DEM_OK;
+  }
+  if (!lp || lp->interval < 1 || !(lp->safety > 0) || lp->n_candidates < 1 || !lp->candidates)
+    return fail(c, DEM_ERR_INVALID_ARG, "learned policy parameters");
+  for (int j = 0; j < lp->n_candidates; ++j) {
+    if (!(lp->candidates[j] > 0) || !(c->r_max + lp->candidates[j] < 32.0))
+      return fail(c, DEM_ERR_INVALID_ARG, "candidate margins must be > 0 and below 32 m minus the largest radius");
+    if (j && !(lp->candidates[j] > lp->candidates[j - 1]))
+      return fail(c, DEM_ERR_INVALID_ARG, "candidate margins must ascend");
+  }
+  if (c->P.guard == DEM_GUARD_OFF) return fail(c, DEM_ERR_STATE, "the learned rule needs the guard");
+  c->mlp = mlp;
+  c->l_interval = lp->interval;
+  c->l_safety = lp->safety;
+  c->l_cand.assign(lp->candidates, lp->candidates + lp->n_candidates);
+  c->need_rebuild = true;
+  return DEM_OK;
+}
+
+int dem_trace(dem_ctx* c, int windows, int window, int n_candidates, const double* candidates,
+              long long cap, float* x, float* t, long long* n_out) {
+  if (!c || windows < 0 || window < 1 || n_candidates < 1 || !candidates || cap < 0 ||
+      (cap > 0 && (!x || !t)) || !n_out)
+    return DEM_ERR_INVALID_ARG;
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  refresh_devstate(c);
+  dem_mlp* saved = c->mlp;
+  std::vector<double> saved_cand = c->l_cand;
+  c->mlp = nullptr;  // features only
+  c->l_cand.assign(candidates, candidates + n_candidates);
+  const int nc = n_candidates;
+  const long long ncl = c->ncl;
+  long long total = 0;
+  const size_t capb = (size_t)std::max<long long>(cap, 1);
+  if (!grow(c, c->b_tx, 4 * capb * kMlpIn) || !grow(c, c->b_tt, 4 * capb) || !grow(c, c->b_tcount, 64) ||
+      !grow(c, c->b_tr_q, 16 * (ncl + 1)) || !grow(c, c->b_tr_vox, 16 * (ncl + 1)) ||
+      !grow(c, c->b_tr_off, 16 * (ncl + 1)) || !grow(c, c->b_tr_pos, 32 * (ncl + 1)) ||
+      !grow(c, c->b_dmax, 4 * ((size_t)c->nbins + 1))) {
+    c->mlp = saved;
+    c->l_cand = saved_cand;
+    return fail(c, DEM_ERR_OOM, "trace buffers");
+  }
+  cudaMemsetAsync(c->b_tcount.p, 0, 8, c->st);
+  cudaMemsetAsync(c->b_dmax.p, 0, 4 * (size_t)c->nbins, c->st);
+  TraceRef tr{ptr<int4>(c->b_tr_vox), ptr<float4>(c->b_tr_off), ptr<double4_32a>(c->b_tr_pos),
+              ptr<float4>(c->b_tr_q)};
+  StepRunner R(c, windows * window);
+  if ((rc = R.init())) goto done;
+  for (int w = 0; w < windows; ++w) {
+    if ((rc = predict_margins(c))) goto done;
+    {
+      const long long rows = c->n_occ * nc;
+      if (!grow(c, c->b_T, 4 * (size_t)(rows + 1))) { rc = fail(c, DEM_ERR_OOM, "trace labels"); goto done; }
+      cudaMemsetAsync(c->b_T.p, 0, 4 * (size_t)rows, c->st);
+      launch_trace_ref(c->D, tr, c->st);
+      for (int s = 1; s <= window; ++s) {
+        if ((rc = R.run_plain(1, c->margin, std::max(1, c->P.rebuild_interval), false))) goto done;
+        launch_trace_step(c->D, tr, ptr<uint32_t>(c->b_chome), ptr<int>(c->b_dmax),
+                          ptr<uint32_t>(c->b_occ), c->n_occ, nc, ptr<float>(c->b_cand),
+                          ptr<int>(c->b_T), s, c->st);
+      }
+      launch_trace_emit(rows, ptr<float>(c->b_feat), ptr<int>(c->b_T), window, ptr<float>(c->b_tx),
+                        ptr<float>(c->b_tt), ptr<unsigned long long>(c->b_tcount), cap, c->st);
+      total += rows;
+    }
+  }
+  if ((rc = read_flags(c))) goto done;
+  {
+    const long long n = std::min(total, cap);
+    if (n > 0) {
+      cudaMemcpyAsync(x, c->b_tx.p, 4 * (size_t)n * kMlpIn, cudaMemcpyDeviceToHost, c->st);
+      cudaMemcpyAsync(t, c->b_tt.p, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->st);
+      cudaStreamSynchronize(c->st);
+    }
+    *n_out = n;
+  }
+  R.finish();
+done:
+  c->mlp = saved;
+  c->l_cand = saved_cand;
+  c->stats.time = (double)c->step * c->P.dt;
+  return rc ? rc : cuda_check(c, "trace");
+}
+
 int dem_audit(dem_ctx* c, long long* missed) {
   if (!c || !missed) return DEM_ERR_INVALID_ARG;
   cudaSetDevice(c->P.device);
@@ -1033,7 +1450,10 @@ int dem_audit(dem_ctx* c, long long* missed) {
     rc = rebuild(c);
     if (rc) return rc;
   }
-  rc = detect_into(c, 2, 0.0);
+  const float* saved_cm = c->D.cmargin;
+  c->D.cmargin = nullptr;  // the exact check uses no margin
+  rc = detect_into(c, 2, 0.0, 1);
+  c->D.cmargin = saved_cm;
   if (rc) return rc;
   const ContactList& F = c->lists[2].L;
   unsigned long long* d_m = ptr<unsigned long long>(c->b_totals) + 4;

@@ -35,18 +35,18 @@ __device__ __forceinline__ void clump_com(const DevState& d, int c, const SceneG
 }
 
 // Float estimate of the same distance; |error| is far below wall_slack().
-__device__ float wall_distance_est(const WallDev& w, double t, const float x[3]) {
+__device__ float wall_distance_est(const WallDev& w, float t, const float x[3]) {
   float dd[3], n[3];
   for (int k = 0; k < 3; ++k) {
-    dd[k] = x[k] - ((float)w.p[k] + (float)w.vel[k] * (float)t);
-    n[k] = (float)w.n[k];
+    dd[k] = x[k] - (w.pf[k] + w.vf[k] * t);
+    n[k] = w.nh[k];
   }
   const float ax = dd[0] * n[0] + dd[1] * n[1] + dd[2] * n[2];
   if (w.type == 0) return ax;
   float rv[3] = {dd[0] - ax * n[0], dd[1] - ax * n[1], dd[2] - ax * n[2]};
   const float rho = sqrtf(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
-  if (w.type == 1) return (float)w.radius - rho;
-  const float H = (float)w.height, Rb = (float)w.rb;
+  if (w.type == 1) return w.radf - rho;
+  const float H = w.heightf, Rb = w.rbf;
   float tl = (rho * Rb + ax * H) / (Rb * Rb + H * H);
   tl = fminf(fmaxf(tl, 0.f), 1.f);
   const float dl = sqrtf((rho - tl * Rb) * (rho - tl * Rb) + (ax - tl * H) * (ax - tl * H));
@@ -58,7 +58,7 @@ __device__ float wall_distance_est(const WallDev& w, double t, const float x[3])
 }
 
 __device__ __forceinline__ float wall_slack(const WallDev& w, const float x[3]) {
-  float m = fabsf((float)w.p[0]) + fabsf((float)w.p[1]) + fabsf((float)w.p[2]) +
+  float m = fabsf(w.pf[0]) + fabsf(w.pf[1]) + fabsf(w.pf[2]) +
             fabsf(x[0]) + fabsf(x[1]) + fabsf(x[2]) + 1.f;
   return 4e-6f * m;
 }
@@ -80,7 +80,7 @@ __device__ __forceinline__ bool lattice_from_pose(const DevState& d, long long s
       const long long rem = P[k] & ((1ll << (kFixBits - kDetBits)) - 1);
       if (rem - half <= 2 && half - rem <= 2) exact = false;
       qc[k] = (P[k] + half) >> (kFixBits - kDetBits);
-      xf[k] = (float)g.lo[k] + __ll2float_rn(P[k]) * kFixToM;
+      xf[k] = g.lof[k] + ff_to_float(fix_to_ff(P[k]));
     }
   } else {
     const SphA64 A = d.sa64[s];
@@ -116,7 +116,7 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
     det_centre(q, p, X, x);
     have_x = true;
   };
-  const double m = smargin ? smargin[s] : (d.cmargin ? (double)d.cmargin[si.x] : margin);
+  const double m = smargin ? smargin[s] : (d.cmargin ? f2d(d.cmargin[si.x]) : margin);
   long long qc[3];
   float xf[3];
   if (!lattice_from_pose(d, s, g, qc, xf)) {
@@ -128,7 +128,9 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
     // the boundary bins, where it can still be found)
     qc[k] = qc[k] < -(1ll << 30) ? -(1ll << 30) : (qc[k] > (1ll << 30) ? (1ll << 30) : qc[k]);
   }
-  const long long rho = (long long)ceil(__dmul_rn(__dadd_rn(tp.w, m), kDetScale)) + 1;
+  const double rm = __dadd_rn(tp.w, m);  // enlarged radius r + m
+  const long long rho = ceil_pos_d2ll(__dmul_rn(rm, kDetScale)) + 1;
+  const float tf = d2f(t);
   o.det[s] = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
   long long cnt = 1;
   int lob[3];
@@ -143,14 +145,15 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   uint32_t mask = 0;
   for (int i = 0; i < g.wall_count; ++i) {
     const WallDev& w = d.walls[d.wall_idx[g.wall_start + i]];
-    const double travel = __dmul_rn(__dsqrt_rn(dot3d(w.vel, w.vel)), travel_time);
-    const double thr = __dadd_rn(__dadd_rn(tp.w, m), travel);
-    const float est = wall_distance_est(w, t, xf);
+    const double travel = __dmul_rn(w.speed_d, travel_time);
+    const double thr = __dadd_rn(rm, travel);
+    const float thrf = d2f(thr);
+    const float est = wall_distance_est(w, tf, xf);
     const float slack = wall_slack(w, xf);
     bool in;
-    if (est > (float)thr + slack) {
+    if (est > thrf + slack) {
       in = false;
-    } else if (est < (float)thr - slack) {
+    } else if (est < thrf - slack) {
       in = true;
     } else {
       exact_centre();
@@ -263,7 +266,14 @@ __global__ void k_narrow(DevState d, DetectOut o, int* __restrict__ pa, uint32_t
           const long long dx = (long long)rb.qx - qa.x, dy = (long long)rb.qy - qa.y,
                           dz = (long long)rb.qz - qa.z;
           const long long rr = (long long)qa.w + rb.rho;
-          if (dx * dx + dy * dy + dz * dz > rr * rr) continue;
+          // per-axis reject; past it every |d| <= rr < 2^31, so each square is a
+          // single widening 32x32 multiply and the sum fits in 64 unsigned bits
+          if (dx > rr || -dx > rr || dy > rr || -dy > rr || dz > rr || -dz > rr) continue;
+          const int ix = (int)dx, iy = (int)dy, iz = (int)dz;
+          const unsigned long long d2 = (unsigned long long)((long long)ix * ix) +
+                                        (unsigned long long)((long long)iy * iy) +
+                                        (unsigned long long)((long long)iz * iz);
+          if (d2 > (unsigned long long)(rr * rr)) continue;
           if (WRITE) {
             pb[row0 + n] = rb.id;
           } else if (n < 4) {

@@ -11,6 +11,7 @@ struct DevState {
   int nmat, nwalls;
   double h, g[3];
   double hg[3];             // h * g
+  float hf;                 // h as float
   // templates
   const int* tpl_off;
   const double4_32a* tp64;      // per template sphere: p (FP64), r
@@ -18,6 +19,8 @@ struct DevState {
   const int* tmat;          // per template sphere: material
   const double* tmass;      // per template
   const double* tinert;     // per template, 3 principal moments
+  const float* tmassf;      // the same two tables as float
+  const float* tinertf;
   const float* tpbound;     // per template: max |p| over its spheres
   // clumps
   const int2* cinfo;        // {template, scene}
@@ -40,6 +43,7 @@ struct DevState {
   float4* ref_off;
   float4* ref_q;            // orientation at the last rebuild (float)
   const float* cmargin;     // per clump margin for the certificate (or NULL)
+  float* alast;             // per clump |F|/m of the last step (or NULL)
   // spheres
   const int2* sinfo;        // {owner, template sphere}
   SphA64* sa64;
@@ -59,6 +63,7 @@ struct DevState {
   const PairMat<float>* pm32;
   int* flags;
   unsigned long long* counters;  // [0] active contacts, [1] guard violations
+  long long* dstep;         // device step counter: forces of step s see time s * h
 };
 
 // One bin registration after sorting, with everything the narrow phase tests:
@@ -105,6 +110,8 @@ struct ContactList {
   double* uw;               // 3 * capacity (SoA)
   uint32_t* wrow;           // ns + 1
   long long nw, capw;
+  long long* dn;            // device copy of {n, nw}: the per-step kernels read the
+                            // lengths from here, so captured graphs stay valid
 };
 
 // detection
@@ -129,9 +136,9 @@ void launch_audit(const DevState& d, const DetectOut& o, const ContactList& cur,
 void launch_force_pairs(const DevState& d, ContactList& l, bool count_active, cudaStream_t st);
 void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_active,
                         cudaStream_t st);
-void launch_update(const DevState& d, bool integrate, double t_next, double margin,
+void launch_update(const DevState& d, bool integrate, long long step, double margin,
                    bool check_cert, cudaStream_t st);
-void launch_walls_at(const DevState& d, double t, cudaStream_t st);
+void launch_walls_at(const DevState& d, long long step, cudaStream_t st);
 void launch_set_cert_ref(const DevState& d, cudaStream_t st);
 void launch_get_state(const DevState& d, double* pos, double* quat, double* vel, double* angvel,
                       cudaStream_t st);

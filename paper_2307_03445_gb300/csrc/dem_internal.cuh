@@ -43,6 +43,7 @@ struct SceneGrid {
   uint32_t key_base; // first bin key of this scene
   int wall_start;    // this scene's walls: wall_idx[wall_start .. wall_start+wall_count)
   int wall_count;
+  float lof[3];      // lo as float (estimates only)
 };
 
 // Wall description on the device (both precisions).  For FP32_VOXEL the
@@ -58,6 +59,9 @@ struct WallDev {
   float hh, hl;       // cone height as float-float
   float rbh, rbl;     // cone base radius as float-float
   float speed;        // |vel|
+  double speed_d;     // |vel| = sqrt((vx^2 + vy^2) + vz^2), evaluated on the host
+  float pf[3], vf[3]; // reference point and velocity as float (estimates, wall speed)
+  float radf, heightf, rbf;
 };
 
 // Sphere pose record used by the contact kernels (written every step).
@@ -99,6 +103,50 @@ __device__ __forceinline__ float d2f(double d) {
   r |= (uint32_t)(b >> 32) & 0x80000000u;
   return __uint_as_float(r);
 }
+// Integer -> float for |v| < 2^22, exact: the float 1.5 * 2^23 has a unit
+// last place, so adding v to its bit pattern and subtracting it is exact.
+__device__ __forceinline__ float small_i2f(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+// float -> nearest integer (ties to even) for |x| < 2^22, same trick.
+__device__ __forceinline__ int small_f2i(float x) {
+  return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
+// int64 -> float-float (exact for |v| < 2^44), integer pipe only.
+__device__ __forceinline__ void ll_split(long long v, float& hi, float& lo) {
+  const int h = (int)(v >> 22);                 // |h| < 2^22
+  const int l = (int)(v & ((1ll << 22) - 1));   // 0 <= l < 2^22
+  hi = small_i2f(h) * 4194304.0f;               // exact: times 2^22
+  lo = small_i2f(l);
+}
+// float -> nearest int64 (ties to even), integer pipe; exact for |x| < 2^62.
+__device__ __forceinline__ long long f2ll_rn(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xffu) - 127;
+  if (e < 22) return (long long)small_f2i(x);
+  const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
+  long long v;
+  if (e >= 23) {
+    v = m << (e - 23);
+  } else {  // e == 22: one fractional bit
+    v = m >> 1;
+    if ((m & 1) && (v & 1)) ++v;
+  }
+  return (u >> 31) ? -v : v;
+}
+
+// ceil(d) for finite 0 <= d < 2^62, integer pipe.
+__device__ __forceinline__ long long ceil_pos_d2ll(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  if (e < 0) return (b << 1) != 0ull ? 1ll : 0ll;  // 0 < d < 1 -> 1; +-0 -> 0
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+  if (e >= 52) return (long long)(m << (e - 52));
+  const int sh = 52 - e;
+  const long long v = (long long)(m >> sh);
+  return (m & ((1ull << sh) - 1ull)) ? v + 1 : v;
+}
+
 // Finite test on the bit pattern (integer pipe).
 __device__ __forceinline__ bool finite_d(double d) {
   return ((unsigned long long)__double_as_longlong(d) & 0x7ff0000000000000ull) !=
@@ -159,12 +207,20 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
   float corr = __fdiv_rn(__fadd_rn(__fsub_rn(a.h, s2.h), __fsub_rn(a.l, s2.l)), 2.f * s);
   return fast_two_sum(s, corr);
 }
-// int64 fixed-point value -> float-float metres (exact residual)
+// int64 fixed-point value (2^-44 m) -> float-float metres, integer pipe: the
+// value is cut into three exact 22-bit pieces and summed without error.
 __device__ __forceinline__ ff fix_to_ff(long long v) {
-  float h = __ll2float_rn(v);
-  long long rem = v - __float2ll_rn(h);
-  float l = __ll2float_rn(rem);
-  return {h * kFixToM, l * kFixToM};
+  const long long v1 = v >> 22;
+  const float c0 = small_i2f((int)(v & 0x3fffff));
+  const float c1 = small_i2f((int)(v1 & 0x3fffff)) * 4194304.0f;        // 2^22
+  const float c2 = small_i2f((int)(v1 >> 22)) * 17592186044416.0f;      // 2^44
+  ff s = two_sum(c2, c1);
+  s = ff_add(s, {c0, 0.f});
+  return {s.h * kFixToM, s.l * kFixToM};
+}
+// Float estimate of a fixed-point value with |v| < 2^44 (neighbour differences).
+__device__ __forceinline__ float fix_to_float(long long v) {
+  return fmaf(small_i2f((int)(v >> 22)), 4194304.0f, small_i2f((int)(v & 0x3fffff))) * kFixToM;
 }
 
 // ---------------------------------------------------------------------------

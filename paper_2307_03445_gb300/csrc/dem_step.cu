@@ -80,7 +80,8 @@ __device__ __forceinline__ void add_clump32(float* acc, int c, V3<float> F, V3<f
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int count_active) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.n; i += stride) {
+  const long long ln = l.dn[0];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ln; i += stride) {
     const int a = l.pa[i];
     const uint32_t bw = l.pb[i];
     const uint32_t b = bw & ~kHistFlag;
@@ -88,8 +89,7 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     const SphA32 B = d.sa32[b];
     const long long dxl = B.x - A.x, dyl = B.y - A.y, dzl = B.z - A.z;
     // cheap rejection of clear false positives
-    const float fx = __ll2float_rn(dxl) * kFixToM, fy = __ll2float_rn(dyl) * kFixToM,
-                fz = __ll2float_rn(dzl) * kFixToM;
+    const float fx = fix_to_float(dxl), fy = fix_to_float(dyl), fz = fix_to_float(dzl);
     const float s_est = fx * fx + fy * fy + fz * fz;
     const float rs = A.r + B.r;
     float dn = -1.f;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     const PairMat<float> pm = d.pm32[__float_as_int(RA.w) * d.nmat + __float_as_int(RB.w)];
     const float Rbar = A.r * B.r / (A.r + B.r);
     const float mbar = va.w * vb.w / (va.w + vb.w);
-    const Law<float> law = contact_law<float>(pm, (float)d.h, n, dn, vB - vA,
+    const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vB - vA,
                                               V3<float>{d2f(u0), d2f(u1), d2f(u2)}, Rbar, mbar);
     // tangential history: FP64 accumulation of the float increment
     if (law.capped) {
@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
 
 __global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int count_active) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.n; i += stride) {
+  const long long ln = l.dn[0];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ln; i += stride) {
     const int a = l.pa[i];
     const uint32_t bw = l.pb[i];
     const uint32_t b = bw & ~kHistFlag;
@@ -209,7 +210,8 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
   for (int i = threadIdx.x; i < 3 * kMaxBlockWalls; i += blockDim.x) s_wf[i] = 0.f;
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.nw; i += stride) {
+  const long long lnw = l.dn[1];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < lnw; i += stride) {
     const int s = l.ws[i];
     const uint32_t wwv = l.ww[i];
     const uint32_t w = wwv & ~kHistFlag;
@@ -227,7 +229,7 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     const float4 va = d.mv32[S.owner], wa = d.mw32[S.owner];
     const V3<float> ca = V3<float>{RS.x, RS.y, RS.z} + (S.r - 0.5f * dn) * n;
     const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
-    const V3<float> vW = {(float)W.vel[0], (float)W.vel[1], (float)W.vel[2]};
+    const V3<float> vW = {W.vf[0], W.vf[1], W.vf[2]};
     double u0 = 0.0, u1 = 0.0, u2 = 0.0;
     if (wwv & kHistFlag) {
       u0 = l.uw[i];
@@ -235,7 +237,7 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
       u2 = l.uw[2 * l.capw + i];
     }
     const PairMat<float> pm = d.pm32[__float_as_int(RS.w) * d.nmat + W.material];
-    const Law<float> law = contact_law<float>(pm, (float)d.h, n, dn, vW - vA,
+    const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vW - vA,
                                               V3<float>{d2f(u0), d2f(u1), d2f(u2)}, S.r, va.w);
     if (law.capped) {
       u0 = f2d(law.u.x); u1 = f2d(law.u.y); u2 = f2d(law.u.z);
@@ -261,9 +263,11 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
   if (shared_wf) wall_force_flush(d, s_wf);
 }
 
-__global__ void k_walls64(DevState d, ContactList l, double t, int count_active) {
+__global__ void k_walls64(DevState d, ContactList l, int count_active) {
+  const double t = (double)(*d.dstep) * d.h;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < l.nw; i += stride) {
+  const long long lnw = l.dn[1];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < lnw; i += stride) {
     const int s = l.ws[i];
     const uint32_t wwv = l.ww[i];
     const uint32_t w = wwv & ~kHistFlag;
@@ -345,6 +349,7 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
       const V3<double> F = {acc[0], acc[1], acc[2]}, T = {acc[3], acc[4], acc[5]};
       for (int k = 0; k < 6; ++k) acc[k] = 0.0;
       const double h = d.h;
+      if (d.alast) d.alast[c] = (float)(sqrt(F.x * F.x + F.y * F.y + F.z * F.z) / mass);
       // Eq. (5a), semi-implicit Euler
       v.x += h * (F.x / mass + d.g[0]);
       v.y += h * (F.y / mass + d.g[1]);
@@ -430,7 +435,7 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
     int4 vox = d.cvox[c];
     float4 off = d.coff[c];
     double4_32a q4 = d.cq[c], v = d.cv[c], w = d.cw[c];
-    const float mass = (float)d.tmass[tpl];
+    const float mass = d.tmassf[tpl];
     ff qw = ff_from_double(q4.x), qx = ff_from_double(q4.y), qy = ff_from_double(q4.z),
        qz = ff_from_double(q4.w);
     if (integrate) {
@@ -439,8 +444,9 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
       const float4 a1 = *reinterpret_cast<const float4*>(acc + 4);
       *reinterpret_cast<float4*>(acc) = make_float4(0.f, 0.f, 0.f, 0.f);
       *reinterpret_cast<float4*>(acc + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float hf = (float)d.h;
+      const float hf = d.hf;
       const float im = 1.f / mass;
+      if (d.alast) d.alast[c] = sqrtf(a0.x * a0.x + a0.y * a0.y + a0.z * a0.z) * im;
       // Eq. (5a): double velocity, accumulating h*F/m (float) and h*g (double)
       v.x = (v.x + d.hg[0]) + f2d(hf * (a0.x * im));
       v.y = (v.y + d.hg[1]) + f2d(hf * (a0.y * im));
@@ -465,8 +471,8 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
       quat_to_mat(qw.h, qx.h, qy.h, qz.h, Rf);
       const V3<float> tb = mat_tmul(Rf, V3<float>{a0.w, a1.x, a1.y});
       const V3<float> wf = {d2f(w.x), d2f(w.y), d2f(w.z)};
-      const float I0 = (float)d.tinert[3 * tpl], I1 = (float)d.tinert[3 * tpl + 1],
-                  I2 = (float)d.tinert[3 * tpl + 2];
+      const float I0 = d.tinertf[3 * tpl], I1 = d.tinertf[3 * tpl + 1],
+                  I2 = d.tinertf[3 * tpl + 2];
       const V3<float> gy = cross(wf, V3<float>{I0 * wf.x, I1 * wf.y, I2 * wf.z});
       w.x += f2d(hf * ((tb.x - gy.x) / I0));
       w.y += f2d(hf * ((tb.y - gy.y) / I1));
@@ -576,8 +582,8 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
     long long P[3];
     for (int i = 0; i < 3; ++i) {
       const ff t = ff_add(two_sum(oo[i], rel[i].h), {rel[i].l, 0.f});
-      P[i] = ((long long)vv[i] << (kFixBits - kVoxLog2)) + __float2ll_rn(t.h * kMToFix) +
-             __float2ll_rn(t.l * kMToFix);
+      P[i] = ((long long)vv[i] << (kFixBits - kVoxLog2)) + f2ll_rn(t.h * kMToFix) +
+             f2ll_rn(t.l * kMToFix);
     }
     SphA32 A;
     A.x = P[0]; A.y = P[1]; A.z = P[2]; A.r = tp.w; A.owner = si.x;
@@ -586,16 +592,32 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
   }
 }
 
-__global__ void k_walls_at(DevState d, double t) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= d.nwalls) return;
-  const WallDev W = d.walls[w];
-  const SceneGrid g = d.grids[d.wall_scene[w]];
-  for (int k = 0; k < 3; ++k) {
-    const double p = W.p[k] + W.vel[k] * t;
-    d.wpos[3 * w + k] = p;
-    d.wfix[3 * w + k] = __double2ll_rn((p - g.lo[k]) * 17592186044416.0);
+__device__ __forceinline__ void place_walls(const DevState& d, double t) {
+  for (int w = threadIdx.x; w < d.nwalls; w += blockDim.x) {
+    const WallDev& W = d.walls[w];
+    const SceneGrid& g = d.grids[d.wall_scene[w]];
+    for (int k = 0; k < 3; ++k) {
+      const double p = W.p[k] + W.vel[k] * t;
+      d.wpos[3 * w + k] = p;
+      d.wfix[3 * w + k] = __double2ll_rn((p - g.lo[k]) * 17592186044416.0);
+    }
   }
+}
+
+// Places the walls at step `step` and sets the device step counter (one block).
+__global__ void k_walls_at(DevState d, long long step) {
+  place_walls(d, (double)step * d.h);
+  if (threadIdx.x == 0) *d.dstep = step;
+}
+
+// After an integration: advances the device step counter and places the walls
+// at the new time (one block).
+__global__ void k_walls_advance(DevState d) {
+  const long long next = *d.dstep + 1;
+  __syncthreads();
+  place_walls(d, (double)next * d.h);
+  __syncthreads();
+  if (threadIdx.x == 0) *d.dstep = next;
 }
 
 __global__ void k_set_ref(DevState d) {
@@ -673,11 +695,11 @@ int sm_count() {
 
 }  // namespace
 
+// The contact kernels read the list lengths from device memory and run on a
+// persistent grid of fixed size, so one launch (or one captured graph) serves
+// every list the buffers will hold.
 void launch_force_pairs(const DevState& d, ContactList& l, bool count_active, cudaStream_t st) {
-  if (l.n == 0) return;
-  const long long want = (l.n + 255) / 256;
-  const long long cap = (long long)sm_count() * 8;
-  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  const unsigned grid = (unsigned)sm_count() * 8;
   if (d.prec == 0)
     { k_pairs64<<<grid, 256, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
   else
@@ -686,17 +708,20 @@ void launch_force_pairs(const DevState& d, ContactList& l, bool count_active, cu
 
 void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_active,
                         cudaStream_t st) {
-  if (l.nw == 0) return;
-  const long long want = (l.nw + 127) / 128;
-  const long long cap = (long long)sm_count() * 8;
-  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  (void)t;
+  if (d.nwalls == 0) return;
+  const unsigned grid = (unsigned)sm_count() * 2;
   if (d.prec == 0)
-    { k_walls64<<<grid, 128, 0, st>>>(d, l, t, count_active ? 1 : 0); count_launch(); }
+    { k_walls64<<<grid, 128, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
   else
     { k_walls32<<<grid, 128, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
 }
 
-void launch_update(const DevState& d, bool integrate, double t_next, double margin,
+// integrate: one explicit step of every clump, then the device step counter
+// advances and the walls move to the new time.  Otherwise the sphere poses
+// and mirrors are recomputed from the state and the walls are placed at
+// `step` (which also sets the device step counter).
+void launch_update(const DevState& d, bool integrate, long long step, double margin,
                    bool check_cert, cudaStream_t st) {
   if (d.ncl > 0) {
     if (d.prec == 0)
@@ -706,11 +731,17 @@ void launch_update(const DevState& d, bool integrate, double t_next, double marg
       { k_update32<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
                                                       check_cert ? 1 : 0); count_launch(); }
   }
-  launch_walls_at(d, t_next, st);
+  if (integrate) {
+    k_walls_advance<<<1, 256, 0, st>>>(d);
+    count_launch();
+  } else {
+    launch_walls_at(d, step, st);
+  }
 }
 
-void launch_walls_at(const DevState& d, double t, cudaStream_t st) {
-  if (d.nwalls > 0) { k_walls_at<<<nblk(d.nwalls, 64), 64, 0, st>>>(d, t); count_launch(); }
+void launch_walls_at(const DevState& d, long long step, cudaStream_t st) {
+  k_walls_at<<<1, 256, 0, st>>>(d, step);
+  count_launch();
 }
 
 void launch_set_cert_ref(const DevState& d, cudaStream_t st) {

@@ -1,5 +1,6 @@
-// Test program: the integer-pipe f32<->f64 conversions of the library against
-// the hardware conversions, on random bit patterns and edge cases.
+// Test program: the integer-pipe conversions of the library (f32<->f64,
+// f32->int64, ceil of a double, int64->float-float) against the hardware
+// conversions, on random bit patterns and edge cases.
 // Prints "mismatches <n> checked <m>" and exits 0 when n == 0.
 #include <cstdio>
 #include <cstdint>
@@ -30,7 +31,19 @@ __global__ void k_check(unsigned long long n, unsigned long long* bad) {
   const double hwd = (double)fv, swd = dem::f2d(fv);
   const bool same_d = (__double_as_longlong(hwd) == __double_as_longlong(swd)) ||
                       (hwd != hwd && swd != swd);
-  if (!same_f || !same_d) atomicAdd(bad, 1ull);
+  // float -> int64 (nearest, ties to even) for |x| < 2^62
+  const float fx = ldexpf(1.0f + (float)(r >> 41) * 0x1p-23f, (int)((r >> 5) % 62) - 2) *
+                   ((r & 2) ? -1.0f : 1.0f);
+  const bool same_ll = dem::f2ll_rn(fx) == __float2ll_rn(fx);
+  // ceil of a non-negative double below 2^62
+  const double cd = (i % 5 == 0) ? (double)(r >> 40) : fabs(dv);
+  const bool same_c = !(cd < 0x1p62) || dem::ceil_pos_d2ll(cd) == (long long)ceil(cd);
+  // int64 -> float-float is exact below 2^44
+  const long long v = (long long)(r >> 21) - (1ll << 42);
+  float hi, lo;
+  dem::ll_split(v, hi, lo);
+  const bool same_s = (long long)hi + (long long)lo == v;
+  if (!same_f || !same_d || !same_ll || !same_c || !same_s) atomicAdd(bad, 1ull);
 }
 
 int main() {

@@ -1,0 +1,160 @@
+"""The learned list-lifetime regressor and the learned rebuild rule on the GPU.
+
+Regressor: forward pass and loss gradient of the GPU kernels (BF16 weights,
+FP32 accumulation) against the FP64 oracle evaluated at the same BF16-rounded
+weights; training reduces the loss.  Rule: traces from the plain rule, a
+forced rollback, zero missed contacts, and the gain over the plain rule."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2307_03445_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dem():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_03445_gb300 as dem
+
+    dem.load_library()
+    return dem
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (nearest, ties to even) and back."""
+    a = np.ascontiguousarray(a, np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(n, 6)).astype(np.float32)
+    t = (np.tanh(x[:, 0]) + 0.3 * x[:, 1] * x[:, 2]).astype(np.float32)
+    return x, t
+
+
+def test_forward_matches_oracle(dem, oracle_mod):
+    reg = dem.Regressor()
+    p = reg.params()
+    x, _ = _data(5000, 1)
+    y = reg.forward(x)
+    want = oracle_mod.mlp_forward(_bf16(p).astype(np.float64), x.astype(np.float64))
+    scale = np.abs(want).max()
+    assert np.abs(y - want).max() <= 1e-5 * max(scale, 1.0)
+
+
+def test_gradient_matches_oracle(dem, oracle_mod):
+    rng = np.random.default_rng(2)
+    p = (rng.normal(size=oracle_mod.mlp_num_params()) * 0.2).astype(np.float32)
+    reg = dem.Regressor(params=p)
+    x, t = _data(3000, 3)
+    loss, g = reg.loss_grad(x, t)
+    loss_o, g_o = oracle_mod.mlp_loss_grad(_bf16(p).astype(np.float64), x.astype(np.float64),
+                                           t.astype(np.float64))
+    assert loss == pytest.approx(loss_o, rel=1e-5)
+    assert np.linalg.norm(g - g_o) <= 1e-4 * np.linalg.norm(g_o)
+    # per layer too (a transposed or misplaced block would show here)
+    sizes = [64 * 6, 64, 64 * 64, 64, 64 * 64, 64, 64, 1]
+    k = 0
+    for s in sizes:
+        a, b = g[k:k + s], g_o[k:k + s]
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-12
+        k += s
+
+
+def test_training_reduces_the_loss(dem):
+    reg = dem.Regressor()
+    x, t = _data(20000, 4)
+    l0, _ = reg.loss_grad(x, t)
+    l1 = reg.train(x, t, steps=400, batch=2048, lr=2e-3, seed=1)
+    assert l1 < 0.1 * l0
+
+
+@pytest.fixture(scope="module")
+def bed(dem):
+    """A settled 0.25 x 0.25 m bed of the workload's clumps with the plate
+    sliding on top (prepared like the benchmark bed, one patch)."""
+    from paper_2307_03445_gb300 import workloads
+
+    return workloads.bed_c5(n_clumps=6000, lx=0.25, ly=0.25, patch=0.25)
+
+
+CAND = [1e-6, 2e-6, 4e-6, 8e-6, 1.6e-5, 3.2e-5]
+
+
+def test_traces_are_well_formed(dem, bed):
+    sc = bed
+    with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
+        x, t = sim.trace(3, 40, CAND)
+    assert len(x) > 100 and len(x) % len(CAND) == 0
+    assert np.all(np.isfinite(x)) and np.all(np.isfinite(t))
+    assert t.min() >= 0.0 and t.max() <= math.log(40) + 1e-6
+    # a larger margin never fails earlier than a smaller one in the same bin
+    T = t.reshape(-1, len(CAND))
+    assert np.all(np.diff(T, axis=1) >= -1e-6)
+
+
+def test_forced_rollback_keeps_the_list_valid(dem, bed):
+    """A regressor that predicts everlasting lists with the smallest margin:
+    the certificate fails (the plate drags clumps), the interval is rolled back
+    and replayed with the plain rule, and no contact is ever missing."""
+    sc = bed
+    reg = dem.Regressor()
+    p = np.zeros(reg.n_params, np.float32)
+    p[-1] = 20.0  # output bias: ln(lifetime) = 20 for every query
+    reg.set_params(p)
+    with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
+        sim.set_learned_policy(reg, interval=200, safety=1.0, candidates=CAND)
+        sim.step(400)
+        st = sim.stats()
+        assert st["rollbacks"] >= 1
+        assert sim.audit() == 0
+    # the replayed run agrees with a run of the plain rule
+    with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as plain:
+        plain.step(400)
+        pos_p = plain.state()[0]
+    with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
+        sim.set_learned_policy(reg, interval=200, safety=1.0, candidates=CAND)
+        sim.step(400)
+        pos_l = sim.state()[0]
+    moved = np.abs(pos_p - sc.pos).max()
+    assert moved > 1e-6
+    assert np.abs(pos_l - pos_p).max() <= 1e-3 * moved
+
+
+def test_trained_rule_beats_the_plain_rule(dem, bed):
+    """Trained on traces of the plain rule, the learned rule lists fewer pairs
+    and rebuilds less often than the plain rule, with zero missed contacts."""
+    sc = bed
+    plain_K, plain_m = 20, 2e-5
+    with dem.Simulation(sc, margin=plain_m, rebuild_interval=plain_K) as sim:
+        sim.step(200)  # past the initial transient
+        state = sim.state()
+        x, t = sim.trace(6, 120, CAND)
+    reg = dem.Regressor()
+    reg.train(x, t, steps=600, batch=4096, lr=2e-3, seed=2)
+    sc2 = scenes.Scene(**{**sc.__dict__, "pos": state[0], "quat": state[1], "vel": state[2],
+                          "angvel": state[3]})
+    n = 400
+    with dem.Simulation(sc2, margin=plain_m, rebuild_interval=plain_K) as plain:
+        plain.step(n)
+        sp = plain.stats()
+        assert plain.audit() == 0
+    with dem.Simulation(sc2, margin=plain_m, rebuild_interval=plain_K) as sim:
+        # the target interval times the safety factor stays inside the
+        # traced window, where predicted lifetimes are not capped
+        sim.set_learned_policy(reg, interval=60, safety=1.5, candidates=CAND)
+        sim.step(n)
+        sl = sim.stats()
+        assert sim.audit() == 0
+    # replays after a rollback count towards the learned run's work
+    assert sl["rebuilds"] < sp["rebuilds"], (sl, sp)
+    assert sl["pair_steps"] < sp["pair_steps"], (sl, sp)

@@ -101,18 +101,22 @@ def test_forces_match_oracle(dem, oracle_mod, prec, seed, n):
         assert np.abs(Fw - Fwo).max() <= TOL[prec] * np.abs(Fwo).sum()
 
 
-def _run_both(dem, oracle_mod, sc, margin, K, nsteps, prec):
+def _run_both(dem, oracle_mod, sc, margin, K, nsteps, prec, graphs=False):
     sim = dem.Simulation(sc, margin=margin, rebuild_interval=K, precision=prec)
+    sim.set_graphs(graphs)
     sim.step(nsteps)
     osim = oracle_mod.OracleSim(sc, margin, K)
     osim.step(nsteps)
     return sim, osim
 
 
-def test_fp64_trajectory_matches_oracle(dem, oracle_mod):
+@pytest.mark.parametrize("graphs", [False, True])
+def test_fp64_trajectory_matches_oracle(dem, oracle_mod, graphs):
+    """45 steps with a rebuild every 10, as ordinary launches and as one
+    captured CUDA graph per list interval."""
     margin, K, nsteps = 2e-4, 10, 45
     sc = _scene(7, 250, scenes.PREC_FP64, margin=margin)
-    sim, osim = _run_both(dem, oracle_mod, sc, margin, K, nsteps, scenes.PREC_FP64)
+    sim, osim = _run_both(dem, oracle_mod, sc, margin, K, nsteps, scenes.PREC_FP64, graphs)
     pos, quat, vel, w = sim.state()
     po, qo, vo, wo = osim.state()
     vs = np.abs(vo).max()
@@ -131,12 +135,13 @@ def test_fp64_trajectory_matches_oracle(dem, oracle_mod):
     sim.close()
 
 
-def test_fp32_voxel_trajectory_error_is_bounded(dem, oracle_mod):
+@pytest.mark.parametrize("graphs", [False, True])
+def test_fp32_voxel_trajectory_error_is_bounded(dem, oracle_mod, graphs):
     """Precision mode FP32_VOXEL against the FP64 oracle over 45 steps: the
     position and velocity errors stay at the level set by float forces."""
     margin, K, nsteps = 2e-4, 10, 45
     sc = _scene(8, 250, scenes.PREC_FP32, margin=margin, compress=1.0, jitter=0.05)
-    sim, osim = _run_both(dem, oracle_mod, sc, margin, K, nsteps, scenes.PREC_FP32)
+    sim, osim = _run_both(dem, oracle_mod, sc, margin, K, nsteps, scenes.PREC_FP32, graphs)
     pos, quat, vel, w = sim.state()
     po, qo, vo, wo = osim.state()
     dv = np.abs(vel - vo).max() / np.abs(vo - sc.vel).max()
