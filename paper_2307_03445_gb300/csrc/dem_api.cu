@@ -69,7 +69,7 @@ struct dem_ctx {
   // detection scratch
   Buf b_det, b_bin_cnt, b_bin_off, b_wall_mask, b_wall_cnt, b_keys, b_ids, b_keys2, b_ids2;
   Buf b_bin_start, b_bin_end, b_pair_cnt, b_scan_scr, b_sort_scr, b_tmp;
-  Buf b_lob, b_part, b_rec;
+  Buf b_lob, b_part, b_rec, b_trho;
   uint32_t* sorted_keys = nullptr;
   uint32_t* sorted_ids = nullptr;
   long long n_entries = 0;
@@ -313,10 +313,12 @@ int finalize(dem_ctx* c) {
       long long ext = std::llrint((sh.hi[k] - sh.lo[k]) * kDetScale);
       long long dd = (ext + L - 1) / L;
       if (dd < 1) dd = 1;
-      if (dd > (1ll << 30)) return fail(c, DEM_ERR_INVALID_ARG, "detection grid too fine");
+      // bin coordinates are packed in 21 bits per axis
+      if (dd >= (1ll << 21)) return fail(c, DEM_ERR_INVALID_ARG, "detection grid too fine (2^21 bins per axis)");
       g.dims[k] = (int)dd;
     }
     g.L = L;
+    g.invL = (float)(1.0 / (double)L);
     g.key_base = (uint32_t)base;
     base += (uint64_t)g.dims[0] * g.dims[1] * g.dims[2];
     if (base >= (1ull << 32) - 1) return fail(c, DEM_ERR_INVALID_ARG, "too many bins (> 2^32)");
@@ -406,7 +408,7 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
   if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_bin_cnt, 4 * (ns + 1)) ||
       !grow(c, c->b_bin_off, 4 * (ns + 1)) || !grow(c, c->b_wall_mask, 4 * (ns + 1)) ||
       !grow(c, c->b_wall_cnt, 4 * (ns + 1)) || !grow(c, c->b_pair_cnt, 4 * (ns + 1)) ||
-      !grow(c, c->b_lob, 8 * (ns + 1)) || !grow(c, c->b_part, 16 * (ns + 1)) ||
+      !grow(c, c->b_lob, 8 * (ns + 1)) ||
       !grow(c, LB.row, 4 * (ns + 1)) || !grow(c, LB.wrow, 4 * (ns + 1)) ||
       !grow(c, c->b_scan_scr, scan_scratch_bytes(ns + 1) + 256))
     return fail(c, DEM_ERR_OOM, "detection buffers");
@@ -420,7 +422,11 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
   o.pair_cnt = ptr<uint32_t>(c->b_pair_cnt);
   o.pair_off = ptr<uint32_t>(LB.row);
   o.lob = ptr<unsigned long long>(c->b_lob);
-  o.part = ptr<uint4>(c->b_part);
+  if (!c->D.cmargin) {  // one margin for all clumps: radii from a per template sphere table
+    o.n_tsph = (int)c->tpl_rad.size();
+    if (!grow(c, c->b_trho, 4 * (size_t)(o.n_tsph + 1))) return fail(c, DEM_ERR_OOM, "detection buffers");
+    o.trho = ptr<int>(c->b_trho);
+  }
   unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
   launch_detect(c->D, o, m, nullptr, t, travel, c->st);
   exclusive_scan_u32(o.bin_cnt, o.bin_off, ns, c->b_scan_scr.p, tot + 0, c->st);
@@ -458,6 +464,8 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
   cudaMemsetAsync(o.bin_start, 0, 4 * (size_t)c->nbins, c->st);
   cudaMemsetAsync(o.bin_end, 0, 4 * (size_t)c->nbins, c->st);
   launch_bin_bounds(o.keys, (long long)B, o.bin_start, o.bin_end, c->st);
+  o.nbins = c->nbins;
+  cudaMemsetAsync(o.pair_cnt, 0, 4 * (size_t)ns, c->st);
   launch_narrow(c->D, o, false, nullptr, nullptr, c->st);
   exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
   cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
@@ -538,12 +546,17 @@ int rebuild(dem_ctx* c) { return rebuild(c, c->margin, c->P.rebuild_interval); }
 
 // Sphere-sphere then sphere-wall contact forces; `mid` (optional) is recorded
 // between the two kernels.
+// Zeroes the per-clump force / torque accumulators if something other than
+// the update kernel (which clears them as it reads them) left them dirty.
+void clear_acc(dem_ctx* c) {
+  if (!c->acc_dirty) return;
+  if (c->P.precision == DEM_FP64) cudaMemsetAsync(c->b_acc64.p, 0, 64 * (size_t)c->ncl, c->st);
+  else cudaMemsetAsync(c->b_acc32.p, 0, 32 * (size_t)c->ncl, c->st);
+  c->acc_dirty = false;
+}
+
 int force_pass(dem_ctx* c, bool count_active, cudaEvent_t mid = nullptr) {
-  if (c->acc_dirty) {
-    if (c->P.precision == DEM_FP64) cudaMemsetAsync(c->b_acc64.p, 0, 64 * (size_t)c->ncl, c->st);
-    else cudaMemsetAsync(c->b_acc32.p, 0, 32 * (size_t)c->ncl, c->st);
-    c->acc_dirty = false;
-  }
+  clear_acc(c);
   if (!c->walls.empty()) cudaMemsetAsync(c->b_wforce.p, 0, 24 * c->walls.size(), c->st);
   const double t = (double)c->step * c->P.dt;
   ContactList& L = curL(c);
@@ -567,6 +580,7 @@ int read_flags(dem_ctx* c, bool* guard_hit = nullptr) {
   c->stats.guard_violations += (long long)ctr[1];
   if (guard_hit) *guard_hit = (flags & kFlagGuard) != 0;
   if (flags & kFlagNonFinite) return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
+  if (flags & kFlagBounds) return fail(c, DEM_ERR_STATE, "internal: narrow-phase row overflow");
   return cuda_check(c, "step");
 }
 
@@ -692,6 +706,9 @@ void drop_graphs(dem_ctx* c) {
 // Captures (once per list buffer, step count and margin) and launches a graph
 // of m force + update steps with the current list.
 int launch_graph_steps(dem_ctx* c, int m, double margin, bool cert) {
+  // accumulators left dirty are cleared on the stream, before and outside the
+  // graph (so the captured force passes hold no clear)
+  clear_acc(c);
   if (c->graph_layout != c->layout) {
     drop_graphs(c);
     c->graph_layout = c->layout;
@@ -700,7 +717,6 @@ int launch_graph_steps(dem_ctx* c, int m, double margin, bool cert) {
   for (auto& g : c->graphs)
     if (g.cur == c->cur && g.m == m && g.cert == (int)cert && g.margin == margin) ge = &g;
   if (!ge) {
-    if (c->acc_dirty) force_pass(c, false);  // never: accumulators are clean between steps
     const long long k0 = g_kernel_launches;
     cudaGraph_t graph;
     if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -988,7 +1004,7 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_totals, &c->b_det, &c->b_bin_cnt, &c->b_bin_off, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_keys, &c->b_ids, &c->b_keys2, &c->b_ids2, &c->b_bin_start, &c->b_bin_end,
                 &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp, &c->b_lob,
-                &c->b_part, &c->b_rec, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
+                &c->b_part, &c->b_rec, &c->b_trho, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
                 &c->b_bcnt, &c->b_bvmax, &c->b_bvsum, &c->b_bamax, &c->b_occ, &c->b_nocc,
                 &c->b_binm, &c->b_cand, &c->b_feat, &c->b_pred, &c->b_dmax, &c->b_T, &c->b_tr_vox,
                 &c->b_tr_off, &c->b_tr_pos, &c->b_tr_q, &c->b_tx, &c->b_tt, &c->b_tcount,
@@ -1094,7 +1110,7 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
   long long add_s = 0;
   for (int i = 0; i < n; ++i) add_s += c->tpl_off[tpl[i] + 1] - c->tpl_off[tpl[i]];
   const long long ncl = c->ncl + n, ns = c->ns + add_s;
-  if (ns >= (1ll << 31) - 1) return fail(c, DEM_ERR_INVALID_ARG, "more than 2^31 spheres");
+  if (ns >= (1ll << kIdBits)) return fail(c, DEM_ERR_INVALID_ARG, "more than 2^29 spheres");
   const size_t k0 = (size_t)c->ncl, s0 = (size_t)c->ns;
   bool ok = grow(c, c->b_cinfo, 8 * ncl, 8 * k0) && grow(c, c->b_csph, 4 * (ncl + 1), 4 * k0) &&
             grow(c, c->b_cq, 32 * ncl, 32 * k0) && grow(c, c->b_cv, 32 * ncl, 32 * k0) &&
@@ -1339,6 +1355,7 @@ int dem_get_bins(dem_ctx* c, long long cap, unsigned int* keys, int* ids, long l
     cudaMemcpyAsync(keys, c->sorted_keys, 4 * m, cudaMemcpyDeviceToHost, c->st);
     cudaMemcpyAsync(ids, c->sorted_ids, 4 * m, cudaMemcpyDeviceToHost, c->st);
     cudaStreamSynchronize(c->st);
+    for (long long i = 0; i < m; ++i) ids[i] = (int)((uint32_t)ids[i] & kIdMask);  // drop the owning-bin mask
   }
   return cuda_check(c, "get_bins");
 }

@@ -96,14 +96,24 @@ __device__ __forceinline__ bool lattice_from_pose(const DevState& d, long long s
   return exact;
 }
 
+// ceil((r + m) 2^24) + 1 with r + m rounded to double (the scaling by 2^24 is exact).
+__device__ __forceinline__ long long tpl_rho(double r, double m) {
+  return ceil_pos_d2ll(__dmul_rn(__dadd_rn(r, m), kDetScale)) + 1;
+}
+
+__global__ void k_tpl_rho(DevState d, double margin, int n, int* __restrict__ trho) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) trho[i] = (int)tpl_rho(d.tp64[i].w, margin);
+}
+
 __global__ void k_detect(DevState d, DetectOut o, double margin, const double* __restrict__ smargin,
                          double t, double travel_time) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= d.ns) return;
   const int2 si = d.sinfo[s];
   const int2 ci = d.cinfo[si.x];
+  const float ttf = d2f(travel_time);
   const SceneGrid g = d.grids[ci.y];
-  const double4_32a tp = d.tp64[si.y];
   double x[3];
   bool have_x = false;
   auto exact_centre = [&]() {
@@ -111,6 +121,7 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
     double X[3];
     clump_com(d, si.x, g, X);
     const double4_32a q4 = d.cq[si.x];
+    const double4_32a tp = d.tp64[si.y];
     const double q[4] = {q4.x, q4.y, q4.z, q4.w};
     const double p[3] = {tp.x, tp.y, tp.z};
     det_centre(q, p, X, x);
@@ -128,15 +139,17 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
     // the boundary bins, where it can still be found)
     qc[k] = qc[k] < -(1ll << 30) ? -(1ll << 30) : (qc[k] > (1ll << 30) ? (1ll << 30) : qc[k]);
   }
-  const double rm = __dadd_rn(tp.w, m);  // enlarged radius r + m
-  const long long rho = ceil_pos_d2ll(__dmul_rn(rm, kDetScale)) + 1;
+  // enlarged lattice radius ceil((r + m) 2^24) + 1: from the per template
+  // sphere table when every clump has the same margin
+  const long long rho = o.trho ? (long long)o.trho[si.y] : tpl_rho(d.tp64[si.y].w, m);
   const float tf = d2f(t);
+  const float rmf = d.tp32[si.y].w + d2f(m);  // r + m for the estimates
   o.det[s] = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
   long long cnt = 1;
   int lob[3];
   for (int k = 0; k < 3; ++k) {
-    lob[k] = clampi(floordiv_ll(qc[k] - rho, g.L), g.dims[k] - 1);
-    const int hi = clampi(floordiv_ll(qc[k] + rho, g.L), g.dims[k] - 1);
+    lob[k] = clampi(floordiv_bin(qc[k] - rho, g.L, g.invL), g.dims[k] - 1);
+    const int hi = clampi(floordiv_bin(qc[k] + rho, g.L, g.invL), g.dims[k] - 1);
     cnt *= (hi - lob[k] + 1);
   }
   o.bin_cnt[s] = (uint32_t)cnt;
@@ -145,9 +158,8 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   uint32_t mask = 0;
   for (int i = 0; i < g.wall_count; ++i) {
     const WallDev& w = d.walls[d.wall_idx[g.wall_start + i]];
-    const double travel = __dmul_rn(w.speed_d, travel_time);
-    const double thr = __dadd_rn(rm, travel);
-    const float thrf = d2f(thr);
+    // float threshold (r + m) + |v| travel_time; its error is far below slack
+    const float thrf = rmf + w.speed * ttf;
     const float est = wall_distance_est(w, tf, xf);
     const float slack = wall_slack(w, xf);
     bool in;
@@ -158,6 +170,7 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
     } else {
       exact_centre();
       double nw[3];
+      const double thr = __dadd_rn(__dadd_rn(d.tp64[si.y].w, m), __dmul_rn(w.speed_d, travel_time));
       in = wall_distance64(w, t, x, nw) <= thr;
     }
     if (in) mask |= 1u << i;
@@ -174,15 +187,17 @@ __global__ void k_emit_bins(DevState d, DetectOut o) {
   int lo[3], hi[3];
   const int qq[3] = {q.x, q.y, q.z};
   for (int k = 0; k < 3; ++k) {
-    lo[k] = clampi(floordiv_ll((long long)qq[k] - q.w, g.L), g.dims[k] - 1);
-    hi[k] = clampi(floordiv_ll((long long)qq[k] + q.w, g.L), g.dims[k] - 1);
+    lo[k] = clampi(floordiv_bin((long long)qq[k] - q.w, g.L, g.invL), g.dims[k] - 1);
+    hi[k] = clampi(floordiv_bin((long long)qq[k] + q.w, g.L, g.invL), g.dims[k] - 1);
   }
   uint32_t off = o.bin_off[s];
+  const uint32_t d0 = (uint32_t)g.dims[0], d01 = d0 * (uint32_t)g.dims[1];
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
       for (int x = lo[0]; x <= hi[0]; ++x) {
-        o.keys[off] = g.key_base + (uint32_t)((z * g.dims[1] + y) * g.dims[0] + x);
-        o.ids[off] = (uint32_t)s;
+        o.keys[off] = g.key_base + (uint32_t)z * d01 + (uint32_t)y * d0 + (uint32_t)x;
+        const uint32_t mask = (x == lo[0] ? 1u : 0u) | (y == lo[1] ? 2u : 0u) | (z == lo[2] ? 4u : 0u);
+        o.ids[off] = (uint32_t)s | (mask << kIdBits);
         ++off;
       }
 }
@@ -200,110 +215,108 @@ __global__ void k_bin_bounds(const uint32_t* __restrict__ keys, long long n,
 __global__ void k_gather_entries(DevState d, DetectOut o, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint32_t s = o.ids[i];
+  const uint32_t v = o.ids[i];
+  const uint32_t s = v & kIdMask;
   const int4 q = o.det[s];
   EntryRec r;
   r.qx = q.x; r.qy = q.y; r.qz = q.z; r.rho = q.w;
-  r.lob = o.lob[s];
   r.owner = d.sinfo[s].x;
   r.id = s;
+  r.mask = v >> kIdBits;
+  r.pad = 0u;
   o.rec[i] = r;
 }
 
-// Narrow phase for sphere a over its own bins: count its partners b > a (the
-// count pass also keeps the first four), or write its row.  Because floor
-// division by the bin edge and clamping are monotone, the bin of the per-axis
-// max of two lower corners is the per-axis max of their lower-corner bins.
+// Narrow phase, one warp per bin (persistent warps striding over the bins).
+// The bin's registrations, sorted by sphere id, are taken 32 at a time: lane
+// l holds registration i; every later registration j of the bin is staged in
+// shared memory and tested by all lanes at once, so the loops are uniform
+// across the warp.  A pair (a = id_i < b = id_j) is kept when the spheres
+// belong to different clumps, the bin owns the pair (owning-bin masks) and
+// the enlarged spheres overlap on the 2^-24 m lattice:
+// |q_b - q_a|^2 <= (rho_a + rho_b)^2, exact in integers.
+constexpr int kNarrowWarps = 8;
+
 template <bool WRITE>
-__global__ void k_narrow(DevState d, DetectOut o, int* __restrict__ pa, uint32_t* __restrict__ pb) {
-  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= d.ns) return;
-  uint32_t row0 = 0, cnt = 0;
-  if (WRITE) {
-    row0 = o.pair_off[a];
-    cnt = o.pair_cnt[a];
-    if (cnt <= 4) {  // the count pass kept them all, already ascending
-      const uint4 p = o.part[a];
-      const uint32_t v[4] = {p.x, p.y, p.z, p.w};
-      for (uint32_t i = 0; i < cnt; ++i) {
-        pb[row0 + i] = v[i];
-        pa[row0 + i] = (int)a;
-      }
-      return;
-    }
-  }
-  const int4 qa = o.det[a];
-  const unsigned long long loa = o.lob[a];
-  const int owner_a = d.sinfo[a].x;
-  const SceneGrid g = d.grids[d.cinfo[owner_a].y];
-  const int lo[3] = {(int)(loa & 0x1fffff), (int)((loa >> 21) & 0x1fffff), (int)(loa >> 42)};
-  int hi[3];
-  const long long qaa[3] = {qa.x, qa.y, qa.z};
-  for (int k = 0; k < 3; ++k) hi[k] = clampi(floordiv_ll(qaa[k] + qa.w, g.L), g.dims[k] - 1);
-  uint32_t n = 0;
-  uint32_t keep[4] = {0u, 0u, 0u, 0u};
-  for (int z = lo[2]; z <= hi[2]; ++z)
-    for (int y = lo[1]; y <= hi[1]; ++y)
-      for (int x = lo[0]; x <= hi[0]; ++x) {
-        const uint32_t key = g.key_base + (uint32_t)((z * g.dims[1] + y) * g.dims[0] + x);
-        uint32_t i0 = o.bin_start[key], i1 = o.bin_end[key];
-        if (i1 <= i0) continue;
-        // members are sorted by id: skip to the first id > a
-        uint32_t lo_i = i0, hi_i = i1;
-        while (lo_i < hi_i) {
-          const uint32_t mid = (lo_i + hi_i) >> 1;
-          if (o.rec[mid].id <= (uint32_t)a) lo_i = mid + 1; else hi_i = mid;
+__global__ void __launch_bounds__(32 * kNarrowWarps)
+    k_narrow_bins(DetectOut o, uint32_t* __restrict__ pb, int* __restrict__ flags) {
+  __shared__ int4 sq[kNarrowWarps][32];   // qx, qy, qz, rho
+  __shared__ int4 sm[kNarrowWarps][32];   // owner, id, mask
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long nw = (long long)gridDim.x * kNarrowWarps;
+  for (long long bin = (long long)blockIdx.x * kNarrowWarps + wib; bin < (long long)o.nbins;
+       bin += nw) {
+    const uint32_t s = o.bin_start[bin], e = o.bin_end[bin];
+    if (e <= s + 1u) continue;  // empty bins have start = end = 0
+    for (uint32_t i0 = s; i0 < e; i0 += 32u) {
+      const uint32_t i = i0 + (uint32_t)lane;
+      const bool vi = i < e;
+      EntryRec A{};
+      if (vi) A = o.rec[i];
+      uint32_t n = 0, row = 0;
+      if (WRITE && vi) row = o.pair_off[A.id];
+      for (uint32_t j0 = i0; j0 < e; j0 += 32u) {
+        const uint32_t jl = j0 + (uint32_t)lane;
+        if (jl < e) {
+          const EntryRec R = o.rec[jl];
+          sq[wib][lane] = make_int4(R.qx, R.qy, R.qz, R.rho);
+          sm[wib][lane] = make_int4(R.owner, (int)R.id, (int)R.mask, 0);
         }
-        for (uint32_t j = lo_i; j < i1; ++j) {
-          const EntryRec rb = o.rec[j];
-          if (rb.owner == owner_a) continue;
-          // owning bin: per-axis max of the two lower-corner bins is (x, y, z)
-          const int bx = (int)(rb.lob & 0x1fffff), by = (int)((rb.lob >> 21) & 0x1fffff),
-                    bz = (int)(rb.lob >> 42);
-          if ((bx > lo[0] ? bx : lo[0]) != x || (by > lo[1] ? by : lo[1]) != y ||
-              (bz > lo[2] ? bz : lo[2]) != z)
+        __syncwarp();
+        const int jn = (int)min(32u, e - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+          const int4 q = sq[wib][jj];
+          const int4 mm = sm[wib][jj];
+          if (!vi || j0 + (uint32_t)jj <= i || mm.x == A.owner || ((A.mask | (uint32_t)mm.z) != 7u))
             continue;
-          const long long dx = (long long)rb.qx - qa.x, dy = (long long)rb.qy - qa.y,
-                          dz = (long long)rb.qz - qa.z;
-          const long long rr = (long long)qa.w + rb.rho;
-          // per-axis reject; past it every |d| <= rr < 2^31, so each square is a
-          // single widening 32x32 multiply and the sum fits in 64 unsigned bits
+          const long long rr = (long long)A.rho + q.w;
+          const long long dx = (long long)q.x - A.qx, dy = (long long)q.y - A.qy,
+                          dz = (long long)q.z - A.qz;
+          // per-axis reject; past it every |d| <= rr < 2^31 and the sum of
+          // the three squares fits in 63 bits
           if (dx > rr || -dx > rr || dy > rr || -dy > rr || dz > rr || -dz > rr) continue;
           const int ix = (int)dx, iy = (int)dy, iz = (int)dz;
-          const unsigned long long d2 = (unsigned long long)((long long)ix * ix) +
-                                        (unsigned long long)((long long)iy * iy) +
-                                        (unsigned long long)((long long)iz * iz);
-          if (d2 > (unsigned long long)(rr * rr)) continue;
+          const long long d2 = (long long)ix * ix + (long long)iy * iy + (long long)iz * iz;
+          if (d2 > rr * rr) continue;
           if (WRITE) {
-            pb[row0 + n] = rb.id;
-          } else if (n < 4) {
-            // insertion into the ascending first-four
-            uint32_t k = n;
-            while (k > 0 && keep[k - 1] > rb.id) {
-              keep[k] = keep[k - 1];
-              --k;
+            // rows fill from the end; k_sort_rows orders them.  The count
+            // pass found the same pairs, so the row never overflows; the
+            // check only keeps a broken invariant from writing out of bounds.
+            const uint32_t left = atomicSub(&o.pair_cnt[A.id], 1u);
+            if (left == 0u) {
+              atomicAdd(&o.pair_cnt[A.id], 1u);
+              atomicOr(flags, kFlagBounds);
+            } else {
+              pb[row + left - 1u] = (uint32_t)mm.y;
             }
-            keep[k] = rb.id;
+          } else {
+            ++n;
           }
-          ++n;
         }
+        __syncwarp();
       }
-  if (!WRITE) {
-    o.pair_cnt[a] = n;
-    o.part[a] = make_uint4(keep[0], keep[1], keep[2], keep[3]);
-    return;
+      if (!WRITE && n) atomicAdd(&o.pair_cnt[A.id], n);
+    }
   }
-  // canonical order inside the row: ascending b
-  for (uint32_t i = 1; i < n; ++i) {
-    const uint32_t v = pb[row0 + i];
+}
+
+// Sorts every row of the new list by b (insertion sort: rows are short) and
+// fills in the row owner a.
+__global__ void k_sort_rows(long long ns, const uint32_t* __restrict__ row, int* __restrict__ pa,
+                            uint32_t* __restrict__ pb) {
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= ns) return;
+  const uint32_t r0 = row[a], r1 = row[a + 1];
+  for (uint32_t i = r0 + 1; i < r1; ++i) {
+    const uint32_t v = pb[i];
     uint32_t j = i;
-    while (j > 0 && pb[row0 + j - 1] > v) {
-      pb[row0 + j] = pb[row0 + j - 1];
+    while (j > r0 && pb[j - 1] > v) {
+      pb[j] = pb[j - 1];
       --j;
     }
-    pb[row0 + j] = v;
+    pb[j] = v;
   }
-  for (uint32_t i = 0; i < n; ++i) pa[row0 + i] = (int)a;
+  for (uint32_t i = r0; i < r1; ++i) pa[i] = (int)a;
 }
 
 __global__ void k_wall_emit(DevState d, DetectOut o, int* __restrict__ ws, uint32_t* __restrict__ ww) {
@@ -435,6 +448,10 @@ inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 void launch_detect(const DevState& d, const DetectOut& o, double margin, const double* smargin,
                    double t, double travel_time, cudaStream_t st) {
   if (d.ns == 0) return;
+  if (o.trho) {
+    k_tpl_rho<<<(o.n_tsph + 127) / 128, 128, 0, st>>>(d, margin, o.n_tsph, o.trho);
+    count_launch();
+  }
   { k_detect<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, margin, smargin, t, travel_time); count_launch(); }
 }
 
@@ -457,11 +474,19 @@ void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint3
 
 void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
                    cudaStream_t st) {
-  if (d.ns == 0) return;
-  if (write)
-    { k_narrow<true><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, pa, pb); count_launch(); }
-  else
-    { k_narrow<false><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, pa, pb); count_launch(); }
+  if (d.ns == 0 || o.nbins == 0) return;
+  const long long want = ((long long)o.nbins + kNarrowWarps - 1) / kNarrowWarps;
+  const long long cap = (long long)device_sms() * 8;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (write) {
+    k_narrow_bins<true><<<grid, 32 * kNarrowWarps, 0, st>>>(o, pb, d.flags);
+    count_launch();
+    k_sort_rows<<<nblk(d.ns, 256), 256, 0, st>>>(d.ns, o.pair_off, pa, pb);
+    count_launch();
+  } else {
+    k_narrow_bins<false><<<grid, 32 * kNarrowWarps, 0, st>>>(o, pb, d.flags);
+    count_launch();
+  }
 }
 
 void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,

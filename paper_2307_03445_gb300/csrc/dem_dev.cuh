@@ -67,14 +67,24 @@ struct DevState {
 };
 
 // One bin registration after sorting, with everything the narrow phase tests:
-// the lattice centre and enlarged radius, the clamped bin of the box's lower
-// corner (21 bits per axis), the owner clump and the sphere id.
+// the lattice centre and enlarged radius, the owner clump, the sphere id and
+// the owning-bin mask: bit k is set when the clamped bin of the box's lower
+// corner equals this bin's coordinate on axis k.  A pair registered in a bin
+// belongs to that bin iff the two masks together cover all three axes
+// (floor division and clamping are monotone, so the bin of the per-axis max
+// of two lower corners is the per-axis max of their lower-corner bins, and
+// both of those are <= this bin's coordinates).
 struct alignas(32) EntryRec {
   int qx, qy, qz, rho;
-  unsigned long long lob;
   int owner;
   uint32_t id;
+  uint32_t mask;
+  uint32_t pad;
 };
+
+// Registrations carry the owning-bin mask in the top bits of the sphere id.
+constexpr int kIdBits = 29;
+constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
 
 __host__ __device__ __forceinline__ unsigned long long pack_bin3(int x, int y, int z) {
   return (unsigned long long)(unsigned)x | ((unsigned long long)(unsigned)y << 21) |
@@ -84,7 +94,6 @@ __host__ __device__ __forceinline__ unsigned long long pack_bin3(int x, int y, i
 struct DetectOut {
   unsigned long long* lob;  // per sphere: clamped lower-corner bin, packed
   EntryRec* rec;            // per entry (sorted order)
-  uint4* part;              // per sphere: up to four partners found by the count pass
   int4* det;                // per sphere {qx, qy, qz, rho}
   uint32_t* bin_cnt;        // per sphere
   uint32_t* bin_off;        // per sphere (scan)
@@ -95,8 +104,12 @@ struct DetectOut {
   uint32_t* ids;            // per entry
   uint32_t* bin_start;      // per bin
   uint32_t* bin_end;        // per bin
+  uint32_t nbins;
   uint32_t* pair_cnt;       // per sphere
   uint32_t* pair_off;       // per sphere (scan) -> row pointer (ns + 1 entries)
+  int* trho;                // per template sphere: enlarged lattice radius, when all
+                            //   clumps share one margin (else NULL: per sphere)
+  int n_tsph;               // template spheres
 };
 
 struct ContactList {
@@ -121,6 +134,9 @@ void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st);
 void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, cudaStream_t st);
 void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint32_t* end,
                        cudaStream_t st);
+// Narrow phase over the bins.  Count pass: o.pair_cnt[a] += partners b > a
+// (pair_cnt zeroed by the caller).  Write pass (after the scan of pair_cnt
+// into pair_off): rows pa / pb, each sorted by b; consumes pair_cnt.
 void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
                    cudaStream_t st);
 void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,

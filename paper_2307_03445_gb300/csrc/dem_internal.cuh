@@ -44,6 +44,7 @@ struct SceneGrid {
   int wall_start;    // this scene's walls: wall_idx[wall_start .. wall_start+wall_count)
   int wall_count;
   float lof[3];      // lo as float (estimates only)
+  float invL;        // 1 / L as float (division estimates only)
 };
 
 // Wall description on the device (both precisions).  For FP32_VOXEL the
@@ -77,31 +78,52 @@ struct alignas(32) SphA64 {  // FP64
 // ---------------------------------------------------------------------------
 // IEEE-754 binary32 <-> binary64 conversions on the integer pipe.  On this GPU
 // the hardware conversions issue at the (low) double-precision rate; these
-// produce the same results from the bit patterns with integer operations.
-// Zero, subnormal, infinite and NaN inputs (never met on the hot path) take
-// the hardware conversion.
+// produce the same results from the bit patterns with integer operations only,
+// for every input class (zero, subnormal, infinite and NaN included), so that
+// no branch the compiler may predicate brings a hardware conversion back.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
-                                  ((unsigned long long)(e + (1023u - 127u)) << 52) |
-                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  const uint32_t m = u & 0x7fffffu;
+  unsigned long long bits = (unsigned long long)(u >> 31) << 63;
+  if (e == 0xffu) {  // infinity, or NaN made quiet
+    bits |= 0x7ff0000000000000ull | ((unsigned long long)m << 29) |
+            (m ? 0x0008000000000000ull : 0ull);
+  } else if (e != 0u) {
+    bits |= ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)m << 29);
+  } else if (m != 0u) {  // subnormal float m * 2^-149: a normal double
+    const int p = 31 - __clz((int)m);  // position of the leading one, 0..22
+    bits |= ((unsigned long long)(p + 874) << 52) |
+            (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+  }
   return __longlong_as_double((long long)bits);
 }
 // double -> float, rounded to nearest, ties to even.
 __device__ __forceinline__ float d2f(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
-  if (e <= 0 || e >= 255) return __double2float_rn(d);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int ed = (int)((b >> 52) & 0x7ffu);
   const unsigned long long m = b & 0xfffffffffffffull;
-  uint32_t r = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
-  const uint32_t rem = (uint32_t)(m & 0x1fffffffu);
-  // a carry out of the mantissa correctly moves to the next binade (or infinity)
-  if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r += 1u;
-  r |= (uint32_t)(b >> 32) & 0x80000000u;
-  return __uint_as_float(r);
+  if (ed == 0x7ff)  // infinity, or NaN made quiet
+    return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u | (uint32_t)(m >> 29) : 0u));
+  const int e = ed - 1023 + 127;
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);  // overflows to infinity
+  if (e > 0) {
+    uint32_t r = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
+    const uint32_t rem = (uint32_t)(m & 0x1fffffffu);
+    // a carry out of the mantissa correctly moves to the next binade (or infinity)
+    if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r += 1u;
+    return __uint_as_float(r | sign);
+  }
+  // float subnormal or zero: the value in units of 2^-149 is M * 2^-sh
+  const int sh = 926 - ed;  // >= 30 here
+  if (ed == 0 || sh >= 64) return __uint_as_float(sign);
+  const unsigned long long M = m | 0x10000000000000ull;
+  uint32_t q = (uint32_t)(M >> sh);
+  const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  if (rem > half || (rem == half && (q & 1u))) q += 1u;  // may reach the smallest normal
+  return __uint_as_float(sign | q);
 }
 // Integer -> float for |v| < 2^22, exact: the float 1.5 * 2^23 has a unit
 // last place, so adding v to its bit pattern and subtracting it is exact.
@@ -193,10 +215,29 @@ __device__ __forceinline__ ff ff_mulf(ff a, float b) {
   return fast_two_sum(p.h, e);
 }
 __device__ __forceinline__ ff ff_scale2(ff a, float pow2) { return {a.h * pow2, a.l * pow2}; }
+// d as float-float: h = d rounded to float, l = (d - h) rounded to float, on
+// the integer pipe.  The residual d - h is exact in double; it is formed from
+// the significands.  For |d| outside [2^-96, 2^127) (and non-finite d) the low
+// part is dropped.
 __device__ __forceinline__ ff ff_from_double(double d) {
   const float h = d2f(d);
-  const float l = d2f(d - f2d(h));
-  return {h, l};
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int ed = (int)((b >> 52) & 0x7ffu);
+  if (ed < 1023 - 96 || ed >= 1023 + 127) return {h, 0.f};
+  const long long M = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  const uint32_t hu = __float_as_uint(h);
+  const int eh = (int)((hu >> 23) & 0xffu);
+  const long long Mh = (long long)((hu & 0x7fffffu) | 0x800000u) << (29 + (eh - 127) - (ed - 1023));
+  const long long diff = M - Mh;  // |diff| <= 2^28, in units of 2^(ed - 1075)
+  // one rounding of the exact sum of two exactly represented parts
+  float l = __fadd_rn(small_i2f((int)(diff >> 7)) * 128.f, small_i2f((int)(diff & 127)));
+  const int k = ed - 1075;  // -148 .. 75
+  if (k >= -126) {
+    l *= __int_as_float((k + 127) << 23);
+  } else {
+    l = (l * 5.42101086242752217e-20f) * __int_as_float((k + 64 + 127) << 23);  // 2^-64 * 2^(k+64)
+  }
+  return {h, (b >> 63) ? -l : l};
 }
 __device__ __forceinline__ float ff_to_float(ff a) { return __fadd_rn(a.h, a.l); }
 // sqrt of a non-negative float-float to float-float accuracy (one Newton step)
@@ -294,6 +335,17 @@ __device__ __forceinline__ void det_centre(const double q[4], const double p[3],
 
 __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
   return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+// floor(a / L) for |a| < 2^31: a float reciprocal estimate, corrected by one
+// integer step.  With L >= 1024 and the bin index below 2^21 the estimate is
+// off by at most one; smaller L takes the integer division.
+__device__ __forceinline__ long long floordiv_bin(long long a, long long L, float invL) {
+  if (L < 1024) return floordiv_ll(a, L);
+  long long q = (long long)__float2int_rd(__int2float_rn((int)a) * invL);
+  const long long r = a - q * L;
+  if (r < 0) --q;
+  else if (r >= L) ++q;
+  return q;
 }
 __device__ __forceinline__ int clampi(long long v, int hi) {
   return v < 0 ? 0 : (v > hi ? hi : (int)v);

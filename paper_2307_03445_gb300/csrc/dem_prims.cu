@@ -124,6 +124,19 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, void* sc
 
 long long g_kernel_launches = 0;
 
+int device_sms() {
+  static int n = 0;
+  if (n <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 148;
+    }
+  }
+  return n;
+}
+
 // ---------------------------------------------------------------------------
 // radix sort
 // ---------------------------------------------------------------------------

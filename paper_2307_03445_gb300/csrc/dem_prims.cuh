@@ -10,6 +10,9 @@ namespace dem {
 extern long long g_kernel_launches;
 inline void count_launch(int n = 1) { g_kernel_launches += n; }
 
+// Multiprocessors of the current device (read once).
+int device_sms();
+
 // Scratch bytes needed by exclusive_scan_u32 for n elements.
 size_t scan_scratch_bytes(long long n);
 // out[i] = sum of in[0..i-1] (32-bit); *d_total (device) = the 64-bit sum of all

@@ -115,12 +115,12 @@ def union_mass_properties(centres, radii, density=DENSITY, cells=96):
     return m, com, I
 
 
-def make_template(rng, radii, spread, density=DENSITY):
+def make_template(rng, radii, spread, density=DENSITY, cells=96):
     """Component spheres with centres uniform in a ball of radius ``spread``,
     expressed in the principal frame about the union's centre of mass."""
     radii = np.asarray(radii, float)
     c = _ball_points(rng, len(radii), spread) if len(radii) > 1 else np.zeros((1, 3))
-    m, com, I = union_mass_properties(c, radii, density)
+    m, com, I = union_mass_properties(c, radii, density, cells)
     w, V = np.linalg.eigh(I)
     if np.linalg.det(V) < 0:
         V[:, 0] = -V[:, 0]
@@ -128,10 +128,10 @@ def make_template(rng, radii, spread, density=DENSITY):
     return p, radii, m, w
 
 
-def _templates_from_lists(rng, radius_lists, spreads, n_mat):
+def _templates_from_lists(rng, radius_lists, spreads, n_mat, cells=96):
     off, pos, rad, mat, mass, inert = [0], [], [], [], [], []
     for radii, spread in zip(radius_lists, spreads):
-        p, r, m, I = make_template(rng, radii, spread)
+        p, r, m, I = make_template(rng, radii, spread, cells=cells)
         pos.append(p)
         rad.append(r)
         mat.append(rng.integers(0, n_mat, size=len(r)))
@@ -268,10 +268,10 @@ def config1(seed=1235, n_clumps=1000, n_templates=None):
     return sc
 
 
-def polydisperse_templates(rng, n_templates, counts, median, sigma, rmin, rmax, n_mat):
+def polydisperse_templates(rng, n_templates, counts, median, sigma, rmin, rmax, n_mat, cells=96):
     radius_lists = [lognormal_radii(rng, int(k), median, sigma, rmin, rmax) for k in counts]
     spreads = [0.8 * float(np.mean(r)) for r in radius_lists]
-    return _templates_from_lists(rng, radius_lists, spreads, n_mat)
+    return _templates_from_lists(rng, radius_lists, spreads, n_mat, cells)
 
 
 def four_materials(rng):
@@ -352,13 +352,63 @@ def config4_scene_sizes(seed=1238, n_scenes=64, lo=5_000, hi=100_000):
     return np.round(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_scenes))).astype(np.int64)
 
 
+def config4(seed=1238, n_scenes=64, lo=5_000, hi=100_000):
+    """The batched sensitivity sweep: n_scenes independent box-settling scenes
+    of log-uniform size, each with its own friction coefficient and template
+    set, merged into one template / material table (merge_batch)."""
+    rng = np.random.default_rng(seed)
+    sizes = config4_scene_sizes(seed, n_scenes, lo, hi)
+    mus = rng.uniform(0.2, 0.9, size=n_scenes)
+    return [batched_scene(seed * 1000 + i, int(n), float(mu)) for i, (n, mu) in enumerate(zip(sizes, mus))]
+
+
+def merge_batch(parts):
+    """Scenes with their own templates and materials -> (first, rest) for one
+    context: `first` carries the concatenated template and material tables,
+    and the clumps of every scene refer to them through shifted ids.  All
+    scenes must share dt, g and precision."""
+    first = parts[0]
+    for p in parts[1:]:
+        if p.h != first.h or tuple(p.g) != tuple(first.g) or p.precision != first.precision:
+            raise ValueError("batched scenes must share dt, g and precision")
+    off, pos, rad, mat, mass, inert = [np.zeros(1, np.int32)], [], [], [], [], []
+    E, nu, mu, cor = [], [], [], []
+    t_base, s_base, m_base = 0, 0, 0
+    out = []
+    for p in parts:
+        off.append(np.asarray(p.tpl_off[1:], np.int32) + s_base)
+        pos.append(p.tpl_pos)
+        rad.append(p.tpl_rad)
+        mat.append(np.asarray(p.tpl_mat, np.int32) + m_base)
+        mass.append(p.tpl_mass)
+        inert.append(p.tpl_inertia)
+        E.append(p.E); nu.append(p.nu); mu.append(p.mu); cor.append(p.cor)
+        q = Scene(**{**p.__dict__})
+        q.tpl = np.asarray(p.tpl, np.int32) + t_base
+        out.append(q)
+        t_base += len(p.tpl_mass)
+        s_base += int(p.tpl_off[-1])
+        m_base += len(p.E)
+    tables = dict(tpl_off=np.concatenate(off), tpl_pos=np.concatenate(pos),
+                  tpl_rad=np.concatenate(rad), tpl_mat=np.concatenate(mat),
+                  tpl_mass=np.concatenate(mass), tpl_inertia=np.concatenate(inert),
+                  E=np.concatenate(E), nu=np.concatenate(nu), mu=np.concatenate(mu),
+                  cor=np.concatenate(cor))
+    for q in out:
+        for k, v in tables.items():
+            setattr(q, k, v)
+    return out[0], out[1:]
+
+
 def batched_scene(seed, n_clumps, mu):
     """One scene of the batched sensitivity sweep: its own friction coefficient
     and template set of U{1..5} spheres, box footprint proportional to sqrt(N)."""
     rng = np.random.default_rng(seed)
     counts = rng.integers(1, 6, size=10)
+    # coarser voxel sampling of the template mass properties (64 scenes x 10
+    # templates); the values are inputs, shared by every consumer
     off, pos, rad, mat, mass, inert = polydisperse_templates(rng, 10, counts, 1.5e-3, 0.4,
-                                                             0.5e-3, 5e-3, 1)
+                                                             0.5e-3, 5e-3, 1, cells=48)
     spacing = 0.0
     foot = 0.0
     sc = Scene("c4", off, pos, rad, mat, mass, inert, np.array([1e8]), np.array([0.3]),

@@ -1,5 +1,5 @@
 // Test program: the integer-pipe conversions of the library (f32<->f64,
-// f32->int64, ceil of a double, int64->float-float) against the hardware
+// f32->int64, ceil of a double, int64->float-float, double->float-float) against the hardware
 // conversions, on random bit patterns and edge cases.
 // Prints "mismatches <n> checked <m>" and exits 0 when n == 0.
 #include <cstdio>
@@ -43,7 +43,15 @@ __global__ void k_check(unsigned long long n, unsigned long long* bad) {
   float hi, lo;
   dem::ll_split(v, hi, lo);
   const bool same_s = (long long)hi + (long long)lo == v;
-  if (!same_f || !same_d || !same_ll || !same_c || !same_s) atomicAdd(bad, 1ull);
+  // double -> float-float against its definition with hardware arithmetic
+  bool same_ff = true;
+  if (fabs(dv) >= 0x1p-96 && fabs(dv) < 0x1p127) {
+    const dem::ff p = dem::ff_from_double(dv);
+    const float h0 = __double2float_rn(dv);
+    const float l0 = __double2float_rn(dv - (double)h0);
+    same_ff = __float_as_uint(p.h) == __float_as_uint(h0) && p.l == l0;
+  }
+  if (!same_f || !same_d || !same_ll || !same_c || !same_s || !same_ff) atomicAdd(bad, 1ull);
 }
 
 int main() {
