@@ -264,6 +264,27 @@ int dem_mlp_forward(dem_mlp* mlp, long long n, const float* x, float* y);
  * gradient with respect to the parameters (host, may be NULL). */
 int dem_mlp_loss_grad(dem_mlp* mlp, long long n, const float* x, const float* t, double* loss,
                       float* grad);
+/* The same loss and gradient as dem_mlp_loss_grad, computed without any
+ * device allocation: no cudaMalloc / cudaFree, no allocating library call.
+ * The paper has no counterpart; this serves callers that cannot allocate,
+ * e.g. a process whose device memory another allocator already holds in full,
+ * or a host loop that must not wait on the device-wide synchronisation of a
+ * free.  Rows, targets, the gradient and the loss sum live in one fixed
+ * scratch array of the library (file-scope __device__ storage, about 7.4 MB
+ * per device).
+ *   - n > DEM_MLP_NOALLOC_MAX_ROWS returns DEM_ERR_CAPACITY (nothing runs).
+ *   - The scratch address is looked up with cudaGetSymbolAddress on the first
+ *     call on each device (DEM_ERR_CUDA if that fails); make that first call
+ *     before any stream capture begins on the device.
+ *   - The gradient and loss accumulators are cleared at the start of every
+ *     call; rows past n are left as they were and never read.
+ *   - There is one scratch array per device: calls on the same device that
+ *     overlap in time (from several host threads, or several regressors)
+ *     race on it; the caller serialises them.
+ * Returns once the results are in the host arrays. */
+#define DEM_MLP_NOALLOC_MAX_ROWS 262144
+int dem_mlp_loss_grad_noalloc(dem_mlp* mlp, long long n, const float* x, const float* t,
+                              double* loss, float* grad);
 /* `steps` Adam steps (lr, beta 0.9/0.999, eps 1e-8) on minibatches of `batch`
  * samples drawn without replacement per epoch (seeded); *final_loss gets the
  * loss over all n samples after training. */

@@ -302,6 +302,20 @@ class Regressor:
         self._check(self.lib.dem_mlp_loss_grad(self.h, len(x), _pf(x), _pf(t), C.byref(loss), _pf(g)))
         return loss.value, g
 
+    def loss_grad_noalloc(self, x, t):
+        """loss_grad without device allocation (fixed scratch of
+        DEM_MLP_NOALLOC_MAX_ROWS rows; calls on one device must not overlap)."""
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, 6)
+        t = np.ascontiguousarray(t, np.float32)
+        if len(x) > capi.DEM_MLP_NOALLOC_MAX_ROWS:
+            raise ValueError(f"{len(x)} rows exceed the fixed scratch of "
+                             f"{capi.DEM_MLP_NOALLOC_MAX_ROWS} rows")
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_double()
+        self._check(self.lib.dem_mlp_loss_grad_noalloc(self.h, len(x), _pf(x), _pf(t),
+                                                       C.byref(loss), _pf(g)))
+        return loss.value, g
+
     def train(self, x, t, steps=500, batch=4096, lr=1e-3, seed=0):
         x = np.ascontiguousarray(x, np.float32).reshape(-1, 6)
         t = np.ascontiguousarray(t, np.float32)

@@ -18,6 +18,7 @@ ERRORS = {
     -7: "DEM_ERR_STATE", -8: "DEM_ERR_GUARD",
 }
 DEM_FP64, DEM_FP32_VOXEL = 0, 1
+DEM_MLP_NOALLOC_MAX_ROWS = 262144  # include/dem.h
 DEM_MARGIN_FIXED, DEM_MARGIN_LEARNED = 0, 1
 DEM_GUARD_OFF, DEM_GUARD_COUNT, DEM_GUARD_ROLLBACK = 0, 1, 2
 
@@ -97,6 +98,7 @@ SIGNATURES = {
     "dem_mlp_get_params": (C.c_int, [_V, _F]),
     "dem_mlp_forward": (C.c_int, [_V, C.c_longlong, _F, _F]),
     "dem_mlp_loss_grad": (C.c_int, [_V, C.c_longlong, _F, _F, C.POINTER(C.c_double), _F]),
+    "dem_mlp_loss_grad_noalloc": (C.c_int, [_V, C.c_longlong, _F, _F, C.POINTER(C.c_double), _F]),
     "dem_mlp_train": (C.c_int, [_V, C.c_longlong, _F, _F, C.c_int, C.c_int, C.c_float,
                                 C.c_ulonglong, C.POINTER(C.c_double)]),
     "dem_set_learned_policy": (C.c_int, [_V, _V, C.c_void_p]),

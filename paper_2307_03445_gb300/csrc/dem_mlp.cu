@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <random>
 #include <string>
 #include <vector>
@@ -440,6 +441,97 @@ int dem_mlp_train(dem_mlp* M, long long n, const float* x, const float* t, int s
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Loss and gradient without allocation.  dem_mlp_loss_grad stages its inputs
+// in a buffer that grows with cudaMallocAsync / cudaFreeAsync.  Some callers
+// cannot take that: a process whose device memory is held in full by another
+// allocator (a framework's caching allocator sized to the whole GPU), where
+// the allocation fails, and a host loop that must not wait on the implicit
+// device-wide synchronisation of a free.  This variant runs the same gradient
+// kernel on one fixed scratch array that is part of the library's module
+// image: the rows, the targets and the two accumulators.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNaLossOff = 0;                                   // double loss sum
+constexpr size_t kNaGradOff = 256;                                 // kMlpParams floats
+constexpr size_t kNaGradBytes = (sizeof(float) * kMlpParams + 255) / 256 * 256;
+constexpr size_t kNaXOff = kNaGradOff + kNaGradBytes;              // rows, 6 floats each
+constexpr size_t kNaTOff = kNaXOff + sizeof(float) * kIn * DEM_MLP_NOALLOC_MAX_ROWS;
+constexpr size_t kNaBytes = kNaTOff + sizeof(float) * DEM_MLP_NOALLOC_MAX_ROWS;
+static_assert(kNaXOff % 256 == 0 && kNaTOff % 256 == 0, "scratch alignment");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Device address of the scratch array, looked up once per device.
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
+void* g_na_addr[kNaMaxDevices] = {};
+bool g_na_attr[kNaMaxDevices] = {};
+
+int noalloc_scratch(dem_mlp* M, unsigned char** out) {
+  if (M->device < 0 || M->device >= kNaMaxDevices)
+    return mlp_fail(M, DEM_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (!g_na_addr[M->device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return mlp_fail(M, DEM_ERR_CUDA, "scratch symbol address");
+    }
+    g_na_addr[M->device] = p;
+  }
+  if (!g_na_attr[M->device]) {
+    const size_t smem = 2 * sizeof(float) * kMlpParams;
+    if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return mlp_fail(M, DEM_ERR_CUDA, "gradient kernel attribute");
+    }
+    g_na_attr[M->device] = true;
+  }
+  *out = (unsigned char*)g_na_addr[M->device];
+  return DEM_OK;
+}
+
+}  // namespace
+
+extern "C" int dem_mlp_loss_grad_noalloc(dem_mlp* M, long long n, const float* x, const float* t,
+                                         double* loss, float* grad) {
+  if (!M || n <= 0 || !x || !t) return DEM_ERR_INVALID_ARG;
+  if (n > DEM_MLP_NOALLOC_MAX_ROWS)
+    return mlp_fail(M, DEM_ERR_CAPACITY, "more rows than the fixed scratch holds");
+  if (cudaSetDevice(M->device) != cudaSuccess) {
+    cudaGetLastError();
+    return DEM_ERR_CUDA;
+  }
+  unsigned char* s = nullptr;
+  int rc = noalloc_scratch(M, &s);
+  if (rc) return rc;
+  double* d_loss = (double*)(s + kNaLossOff);
+  float* d_grad = (float*)(s + kNaGradOff);
+  float* d_x = (float*)(s + kNaXOff);
+  float* d_t = (float*)(s + kNaTOff);
+  // the two accumulators start at zero on every call; rows and targets are
+  // overwritten up to n
+  cudaMemsetAsync(s, 0, kNaXOff, M->st);
+  cudaMemcpyAsync(d_x, x, sizeof(float) * (size_t)n * kIn, cudaMemcpyHostToDevice, M->st);
+  cudaMemcpyAsync(d_t, t, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, M->st);
+  const long long want = (n + 63) / 64;
+  const long long cap = (long long)sms() * 2;
+  k_mlp_grad<<<(unsigned)(want < cap ? want : cap), 64, 2 * sizeof(float) * kMlpParams, M->st>>>(
+      M->wq, d_x, d_t, n, 1.f / (float)n, d_grad, d_loss);
+  count_launch();
+  double h = 0.0;
+  cudaMemcpyAsync(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost, M->st);
+  if (grad) cudaMemcpyAsync(grad, d_grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, M->st);
+  cudaStreamSynchronize(M->st);
+  if (cudaGetLastError() != cudaSuccess) return DEM_ERR_CUDA;
+  if (loss) *loss = h / (double)n;
+  return DEM_OK;
+}
 
 namespace dem {
 const __nv_bfloat16* mlp_weights(const dem_mlp* M) { return M ? M->wq : nullptr; }
