@@ -163,6 +163,101 @@ def time_oracle(budget_s=15.0, n_clumps=1500, max_steps=None):
 
 
 # ---------------------------------------------------------------------------
+# the learned-margin and batched forms
+# ---------------------------------------------------------------------------
+LEARN_CAND = [1e-6, 2e-6, 4e-6, 8e-6, 1.6e-5, 3.2e-5]  # candidate margins [m]
+BIN_FACTORS = (0.35, 0.5, 0.7, 1.0)  # bin edge / (2 x largest enlarged radius) tried
+
+
+def _timed_steps(sim, stream, n):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
+    """The learned rebuild rule on the same bed, from the current state:
+    traces of the plain rule, training on the GPU, then `steps` steps timed
+    (halt mode: a failed certificate ends an interval early), and an exact
+    audit of the final list."""
+    t0 = time.time()
+    x, t = sim.trace(2, 120, LEARN_CAND, cap=1 << 24)
+    reg = dem.Regressor(device=sim_device(sim))
+    loss = reg.train(x, t, steps=800, batch=8192, lr=2e-3, seed=1)
+    log(f"learned form: {len(x)} trace samples, loss {loss:.4f}, {time.time() - t0:.1f} s")
+    sim.set_learned_policy(reg, interval=60, safety=1.5, candidates=LEARN_CAND)
+    sim.reset_stats()
+    ms = _timed_steps(sim, stream, steps)
+    st = sim.stats()
+    missed = sim.audit()
+    sim.set_learned_policy(None)
+    reg.close()
+    pair_steps_plain = plain_st["pair_steps"] / max(1, plain_st["steps"])
+    return {"value": ns * steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / steps,
+            "vs_plain": plain_ms_step / (ms / steps), "rebuilds": st["rebuilds"],
+            "early_rebuilds": st["early_rebuilds"], "rollbacks": st["rollbacks"],
+            "listed_per_step": st["pair_steps"] / max(1, st["steps"]),
+            "listed_per_step_plain": pair_steps_plain, "missed_contacts": missed,
+            "rule": "6->3x64->1 MLP (BF16 weights) per bin, candidates 1-32 um, target "
+                    "interval 60 x 1.5, halt on certificate; trained on 2 x 120-step traces"}
+
+
+def sim_device(sim):
+    import torch
+
+    return torch.cuda.current_device()
+
+
+def batched_form(dem, steps, device, log):
+    """The batched sweep (64 box-settling scenes of 5,000-100,000 clumps, own
+    friction and templates): one context with graph-captured steps against
+    the same scenes run one context after another."""
+    import torch
+
+    from paper_2307_03445_gb300 import scenes
+
+    t0 = time.time()
+    parts = scenes.config4()
+    first, rest = scenes.merge_batch(parts)
+    ns = sum(p.n_spheres for p in parts)
+    log(f"batched form: {len(parts)} scenes, {ns} spheres, generated in {time.time() - t0:.1f} s")
+    margin = MARGIN_VBOUND * first.h * K_REBUILD
+    stream = torch.cuda.Stream()
+    sim = dem.Simulation(first, margin=margin, rebuild_interval=K_REBUILD,
+                         precision=dem.DEM_FP32_VOXEL, device=device, stream=stream.cuda_stream,
+                         extra_scenes=rest)
+    sim.set_graphs(True)
+    sim.step(K_REBUILD)
+    fb, _ = sim.autotune_bins(BIN_FACTORS, reps=1)
+    sim.step(K_REBUILD)
+    ms_b = _timed_steps(sim, stream, steps)
+    sim.close()
+    ms_s = 0.0
+    for p in parts:
+        one = dem.Simulation(p, margin=margin, rebuild_interval=K_REBUILD,
+                             precision=dem.DEM_FP32_VOXEL, device=device, stream=stream.cuda_stream)
+        one.set_graphs(True)
+        one.step(K_REBUILD)
+        one.autotune_bins(BIN_FACTORS, reps=1)
+        one.step(K_REBUILD)
+        ms_s += _timed_steps(one, stream, steps)
+        one.close()
+    return {"value": ns * steps / (ms_b / 1000.0), "unit": UNIT, "ms_per_step": ms_b / steps,
+            "per_scene_value": ns * steps / (ms_s / 1000.0),
+            "vs_per_scene": ms_s / ms_b, "n_scenes": len(parts), "n_spheres": ns,
+            "bin_factor": fb,
+            "workload": "64 box-settling scenes, 5,000-100,000 clumps (log-uniform), own mu "
+                        "0.2-0.9 and 10 templates of 1-5 spheres each, FP32 voxel, one context "
+                        "with graph-captured steps vs one context per scene"}
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,6 +268,8 @@ def main():
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the learned-margin and batched forms")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -220,6 +317,9 @@ def main():
     sim = dem.Simulation(sc, margin=margin, rebuild_interval=K_REBUILD,
                          precision=dem.DEM_FP32_VOXEL, device=local, stream=stream.cuda_stream)
     ns, ncl = sc.n_spheres, sc.n_clumps
+    sim.step(args.warmup)
+    bin_factor, bin_ms = sim.autotune_bins(BIN_FACTORS, reps=1)
+    log(f"bin autotune: factor {bin_factor} ({bin_ms})")
     sim.step(args.warmup)
     sim.reset_stats()
     sim.set_timing(True)
@@ -281,7 +381,12 @@ def main():
                "h2d_bytes_per_step": bytes_state / k2, "d2h_bytes_per_step": bytes_state / k2,
                "steps": k2}
         del out
+    forms = None
+    if not args.no_forms:
+        forms = {"learned": learned_form(dem, sim, stream, args.steps, ns, st, ms_step, log)}
     sim.close()
+    if forms is not None:
+        forms["batched"] = batched_form(dem, args.steps, local, log)
 
     if rank != 0:
         return
@@ -298,12 +403,14 @@ def main():
                    "listed_pairs": n_pairs, "active_contacts": n_active,
                    "wall_contacts": st["n_wall_contacts"], "margin_m": margin,
                    "rebuild_interval": K_REBUILD, "dt": sc.h, "rebuilds": st["rebuilds"],
+                   "bin_factor": bin_factor, "bin_autotune_ms": bin_ms,
                    "guard_violations": st["guard_violations"],
                    "l2": "inputs larger than L2 (state ~GBs)", "parallelism": f"replicas{world}",
                    "phase_ms": {"pairs": pair_ms,
                                 "walls": st["ms_walls"] / max(1, st["timed_steps"]),
                                 "update": st["ms_update"] / max(1, st["timed_steps"]),
                                 "rebuild_total": st["ms_detect"]}},
+        "forms": forms,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -122,6 +122,8 @@ typedef struct {
     double ms_detect, ms_pairs, ms_walls, ms_update;
     long long timed_steps;
     long long launches;         /* kernels this library launched                    */
+    long long early_rebuilds;   /* learned-rule intervals cut short by a failed     */
+                                /*   displacement certificate (see below)           */
 } dem_stats;
 
 typedef struct dem_ctx dem_ctx;
@@ -197,6 +199,18 @@ int dem_reset_stats(dem_ctx* ctx);
  * context stream; they are read once at the end of each dem_step call, so
  * the steps themselves are not serialised. */
 int dem_set_timing(dem_ctx* ctx, int timing);
+/* Bin-size autotuner (the paper fixes no bin size; this picks one by timing).
+ * For each of the n factors, the bin edge of every scene becomes the factor
+ * times the scene's base edge (its bin_size, else twice the largest enlarged
+ * radius), the contact list is rebuilt once to size the buffers, then `reps`
+ * more times under CUDA events.  The fastest factor is kept (*best) and the
+ * list is rebuilt with it.  ms (n doubles, may be NULL) receives the mean
+ * rebuild time per factor, -1 for a factor that gives no valid grid (more
+ * than 2^21 bins along an axis or 2^32 in all).  The state is unchanged: a
+ * rebuild carries the tangential history over. */
+int dem_autotune_bins(dem_ctx* ctx, int n, const double* factors, int reps, double* best,
+                      double* ms);
+
 /* enabled = 1 runs the steps between two rebuilds of the plain rule as one
  * CUDA graph launch (captured on first use per list buffer, step count and
  * margin, and recaptured after any buffer is reallocated).  Results are those
@@ -296,16 +310,27 @@ int dem_mlp_train(dem_mlp* mlp, long long n, const float* x, const float* t, int
  * clumps of the bin get the smallest candidate whose predicted lifetime is at
  * least interval * safety (the largest candidate otherwise), and the list is
  * rebuilt every `interval` steps.  Every step checks that no clump moved
- * further than its margin since the rebuild (which guarantees that no contact
- * is missing from the list); if that fails anywhere in an interval, the state
- * and tangential history are rolled back to the rebuild and the interval is
- * replayed with the plain rule (margin and rebuild_interval of dem_params).
+ * further than its margin since the rebuild (a certificate that no contact is
+ * missing from the list).  What a failed certificate does depends on mode:
+ *   DEM_LEARNED_HALT (0): the failing step completes its integration, and
+ *     every later step of the interval is skipped on the device before it
+ *     computes a force (its kernels see the halt step and return); the list
+ *     is rebuilt at once and stepping continues.  Nothing is rolled back; no
+ *     force is ever computed with a list that lacks a contact.
+ *   DEM_LEARNED_ROLLBACK (1): the interval runs to its end; it is then judged
+ *     by the certificate and by the exact check against a fresh zero-margin
+ *     detection (as dem_audit); on a failure or a missing contact the state
+ *     and tangential history are rolled back to the rebuild and the interval
+ *     is replayed with the plain rule (margin and rebuild_interval of
+ *     dem_params), and with a rebuild every step if that fails too.
  * mlp = NULL restores the plain rule.  The regressor must outlive its use. */
+enum { DEM_LEARNED_HALT = 0, DEM_LEARNED_ROLLBACK = 1 };
 typedef struct {
     int interval;
     double safety;
     int n_candidates;
     const double* candidates;
+    int mode;                 /* DEM_LEARNED_HALT or DEM_LEARNED_ROLLBACK */
 } dem_learned_params;
 int dem_set_learned_policy(dem_ctx* ctx, dem_mlp* mlp, const dem_learned_params* params);
 

@@ -208,11 +208,22 @@ class Simulation:
     def set_timing(self, on=True):
         self._check(self.lib.dem_set_timing(self.ctx, 1 if on else 0))
 
+    def autotune_bins(self, factors=(0.35, 0.5, 0.7, 1.0, 1.5), reps=2):
+        """Times rebuilds at each bin-edge factor and keeps the fastest.
+        Returns (best factor, {factor: mean rebuild ms or None})."""
+        f = _f64(factors)
+        ms = np.zeros(len(f))
+        best = C.c_double()
+        self._check(self.lib.dem_autotune_bins(self.ctx, len(f), _pd(f), int(reps), C.byref(best),
+                                               _pd(ms)))
+        return best.value, {float(a): (float(b) if b >= 0 else None) for a, b in zip(f, ms)}
+
     def set_graphs(self, on=True):
         """Run the steps between rebuilds as one captured CUDA graph."""
         self._check(self.lib.dem_set_graphs(self.ctx, 1 if on else 0))
 
-    def set_learned_policy(self, regressor, interval=40, safety=1.5, candidates=None):
+    def set_learned_policy(self, regressor, interval=40, safety=1.5, candidates=None,
+                           mode=capi.DEM_LEARNED_HALT):
         """Learned rebuild rule (see include/dem.h); regressor=None restores the plain rule."""
         if regressor is None:
             self._check(self.lib.dem_set_learned_policy(self.ctx, None, None))
@@ -220,7 +231,7 @@ class Simulation:
             return
         cand = _f64(candidates)
         self._cand = cand
-        lp = capi.DemLearnedParams(int(interval), float(safety), len(cand), _pd(cand))
+        lp = capi.DemLearnedParams(int(interval), float(safety), len(cand), _pd(cand), int(mode))
         self._check(self.lib.dem_set_learned_policy(self.ctx, regressor.h, C.byref(lp)))
         self._regressor = regressor  # keep it alive while in use
 

@@ -54,7 +54,7 @@ class DemStats(C.Structure):
                 ("missed_contacts", C.c_longlong), ("margin", C.c_double), ("time", C.c_double),
                 ("ms_detect", C.c_double), ("ms_pairs", C.c_double), ("ms_walls", C.c_double),
                 ("ms_update", C.c_double), ("timed_steps", C.c_longlong),
-                ("launches", C.c_longlong)]
+                ("launches", C.c_longlong), ("early_rebuilds", C.c_longlong)]
 
 
 _D = C.POINTER(C.c_double)
@@ -65,7 +65,10 @@ _V = C.c_void_p
 
 class DemLearnedParams(C.Structure):
     _fields_ = [("interval", C.c_int), ("safety", C.c_double), ("n_candidates", C.c_int),
-                ("candidates", C.POINTER(C.c_double))]
+                ("candidates", C.POINTER(C.c_double)), ("mode", C.c_int)]
+
+
+DEM_LEARNED_HALT, DEM_LEARNED_ROLLBACK = 0, 1
 
 # name -> (restype, argtypes); the exported symbols of include/dem.h
 SIGNATURES = {
@@ -82,6 +85,7 @@ SIGNATURES = {
     "dem_reset_stats": (C.c_int, [_V]),
     "dem_set_timing": (C.c_int, [_V, C.c_int]),
     "dem_set_graphs": (C.c_int, [_V, C.c_int]),
+    "dem_autotune_bins": (C.c_int, [_V, C.c_int, _D, C.c_int, _D, _D]),
     "dem_rebuild": (C.c_int, [_V]),
     "dem_eval_forces": (C.c_int, [_V]),
     "dem_get_forces": (C.c_int, [_V, _D, _D]),

@@ -7,6 +7,7 @@
 // rebuild synchronises twice (to size the bin registrations and the pair
 // list); steps without a rebuild never synchronise.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,7 +70,9 @@ struct dem_ctx {
   // detection scratch
   Buf b_det, b_bin_cnt, b_bin_off, b_wall_mask, b_wall_cnt, b_keys, b_ids, b_keys2, b_ids2;
   Buf b_bin_start, b_bin_end, b_pair_cnt, b_scan_scr, b_sort_scr, b_tmp;
-  Buf b_lob, b_part, b_rec, b_trho;
+  Buf b_lob, b_part, b_rec, b_trho, b_upairs;
+  unsigned long long ucap = 0;  // capacity of the unordered pair buffer
+  double bin_factor = 1.0;      // bin edge multiplier chosen by dem_autotune_bins
   uint32_t* sorted_keys = nullptr;
   uint32_t* sorted_ids = nullptr;
   long long n_entries = 0;
@@ -94,6 +97,7 @@ struct dem_ctx {
   dem_mlp* mlp = nullptr;
   int l_interval = 0;
   double l_safety = 1.0;
+  int l_mode = 0;
   std::vector<double> l_cand;
   long long n_occ = 0;
   Buf b_alast, b_chome, b_cmargin, b_bcnt, b_bvmax, b_bvsum, b_bamax, b_occ, b_nocc, b_binm, b_cand;
@@ -239,6 +243,7 @@ void refresh_devstate(dem_ctx* c) {
   d.flags = ptr<int>(c->b_flags);
   d.counters = ptr<unsigned long long>(c->b_counters);
   d.dstep = ptr<long long>(c->b_dstep);
+  d.halt_at = nullptr;  // set by the learned rule's halting intervals only
 }
 
 ContactList& curL(dem_ctx* c) { return c->lists[c->cur].L; }
@@ -291,20 +296,15 @@ double current_margin(const dem_ctx* c) {
   return c->P.v_bound * c->P.dt * (double)std::max(1, c->P.rebuild_interval);
 }
 
-// Grids, walls and zeroed accumulators; called before the first step.
-int finalize(dem_ctx* c) {
-  if (c->finalized) return DEM_OK;
-  if (c->n_tpl == 0) return fail(c, DEM_ERR_STATE, "no clump templates loaded");
-  c->margin = current_margin(c);
-  // the detection lattice holds r + m in 31 bits (2^-24 m units)
-  if (!(c->r_max + c->margin < 32.0)) return fail(c, DEM_ERR_INVALID_ARG, "sphere radius plus margin must be below 32 m");
-  // detection grids
-  c->grids.clear();
+// Detection grids of all scenes (bin edge = the scene's base edge times
+// bin_factor); the wall ranges of existing grids are kept.
+int build_grids(dem_ctx* c) {
+  std::vector<SceneGrid> grids;
   uint64_t base = 0;
   for (size_t s = 0; s < c->scenes.size(); ++s) {
     const SceneH& sh = c->scenes[s];
     SceneGrid g{};
-    double bin = sh.bin > 0.0 ? sh.bin : 2.0 * (c->r_max + c->margin);
+    const double bin = (sh.bin > 0.0 ? sh.bin : 2.0 * (c->r_max + c->margin)) * c->bin_factor;
     long long L = (long long)std::ceil(bin * kDetScale);
     if (L < 1) L = 1;
     for (int k = 0; k < 3; ++k) {
@@ -322,9 +322,27 @@ int finalize(dem_ctx* c) {
     g.key_base = (uint32_t)base;
     base += (uint64_t)g.dims[0] * g.dims[1] * g.dims[2];
     if (base >= (1ull << 32) - 1) return fail(c, DEM_ERR_INVALID_ARG, "too many bins (> 2^32)");
-    c->grids.push_back(g);
+    if (s < c->grids.size()) {
+      g.wall_start = c->grids[s].wall_start;
+      g.wall_count = c->grids[s].wall_count;
+    }
+    grids.push_back(g);
   }
+  c->grids = grids;
   c->nbins = (uint32_t)base;
+  return DEM_OK;
+}
+
+// Grids, walls and zeroed accumulators; called before the first step.
+int finalize(dem_ctx* c) {
+  if (c->finalized) return DEM_OK;
+  if (c->n_tpl == 0) return fail(c, DEM_ERR_STATE, "no clump templates loaded");
+  c->margin = current_margin(c);
+  // the detection lattice holds r + m in 31 bits (2^-24 m units)
+  if (!(c->r_max + c->margin < 32.0)) return fail(c, DEM_ERR_INVALID_ARG, "sphere radius plus margin must be below 32 m");
+  c->grids.clear();
+  int rc = build_grids(c);
+  if (rc) return rc;
   // internal walls: one copy per scene they apply to
   c->walls.clear();
   c->wall_user.clear();
@@ -465,12 +483,27 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
   cudaMemsetAsync(o.bin_end, 0, 4 * (size_t)c->nbins, c->st);
   launch_bin_bounds(o.keys, (long long)B, o.bin_start, o.bin_end, c->st);
   o.nbins = c->nbins;
-  cudaMemsetAsync(o.pair_cnt, 0, 4 * (size_t)ns, c->st);
-  launch_narrow(c->D, o, false, nullptr, nullptr, c->st);
-  exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
-  cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
-  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "narrow phase");
-  const unsigned long long NP = h_tot[3];
+  o.d_np = tot + 5;
+  // the find pass appends the kept pairs to an unordered buffer sized from
+  // the last rebuild; if they did not fit it grows and the pass runs again
+  unsigned long long NP = 0;
+  for (int attempt = 0;; ++attempt) {
+    if (c->ucap == 0) c->ucap = (unsigned long long)std::max<long long>(2 * ns, 1 << 16);
+    if (!grow(c, c->b_upairs, 8 * (size_t)c->ucap)) return fail(c, DEM_ERR_OOM, "pair buffer");
+    o.upairs = ptr<uint2>(c->b_upairs);
+    o.ucap = c->ucap;
+    cudaMemsetAsync(o.pair_cnt, 0, 4 * (size_t)ns, c->st);
+    cudaMemsetAsync(o.d_np, 0, sizeof(unsigned long long), c->st);
+    launch_narrow(c->D, o, false, nullptr, nullptr, c->st);
+    exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
+    cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "narrow phase");
+    NP = h_tot[3];
+    if (NP <= c->ucap) break;
+    if (attempt > 0) return fail(c, DEM_ERR_STATE, "internal: pair buffer regrown twice");
+    c->ucap = NP + NP / 4 + 1024;
+  }
+  o.np = (long long)NP;
   if (NP >= (1ull << 31)) return fail(c, DEM_ERR_CAPACITY, "pair list exceeds 2^31 entries");
   if (c->P.max_contacts > 0 && (long long)NP > c->P.max_contacts)
     return fail(c, DEM_ERR_CAPACITY, "pair list exceeds max_contacts");
@@ -742,6 +775,8 @@ int launch_graph_steps(dem_ctx* c, int m, double margin, bool cert) {
   return DEM_OK;
 }
 
+int audit_now(dem_ctx* c, long long* missed);
+
 // Runs steps on the context stream.  The plain rule rebuilds every K steps;
 // the guarded path runs blocks that start with a rebuild and a snapshot and,
 // when the displacement certificate failed inside a block, rolls back and
@@ -806,6 +841,39 @@ struct StepRunner {
     }
     return DEM_OK;
   }
+  // Learned rule, halt mode: one interval of up to K steps with per-clump
+  // margins; the device skips every step after the first state that fails
+  // the certificate.  Returns the steps completed (>= 1) in *done.
+  int run_halting(int nb, int* done) {
+    long long* halt = ptr<long long>(c->b_dstep) + 1;
+    const long long big = LLONG_MAX;
+    cudaMemcpyAsync(halt, &big, sizeof(big), cudaMemcpyHostToDevice, c->st);
+    const float* cm = c->D.cmargin;
+    const long long step0 = c->step, n_list = curL(c).n + curL(c).nw;
+    c->D.halt_at = halt;
+    for (int i = 0; i < nb; ++i) {
+      c->D.cmargin = cm;
+      step(c->margin, true, i == nb - 1);
+    }
+    c->D.halt_at = nullptr;
+    long long dstep = 0;
+    cudaMemcpyAsync(&dstep, c->b_dstep.p, sizeof(dstep), cudaMemcpyDeviceToHost, c->st);
+    bool hit = false;
+    int rc = read_flags(c, &hit);  // synchronises: dstep and the halt value are in
+    if (rc) return rc;
+    const long long d = dstep - step0;
+    if (d < 1 || d > nb) return fail(c, DEM_ERR_STATE, "internal: halted interval out of range");
+    const long long undone = nb - d;
+    if (undone > 0) {
+      c->step -= undone;
+      c->since -= (int)undone;
+      c->stats.steps -= undone;
+      c->stats.pair_steps -= undone * n_list;
+      c->stats.early_rebuilds++;
+    }
+    *done = (int)d;
+    return DEM_OK;
+  }
   int run_guarded(int n) {
     while (n > 0) {
       const bool learned = c->mlp != nullptr;
@@ -819,6 +887,13 @@ struct StepRunner {
       }
       const float* cm = c->D.cmargin;
       if ((rc = rebuild(c, c->margin, K))) return rc;
+      if (learned && c->l_mode == DEM_LEARNED_HALT) {
+        int done = 0;
+        if ((rc = run_halting(nb, &done))) return rc;
+        c->need_rebuild = true;  // the next interval starts with its own prediction and rebuild
+        n -= done;
+        continue;
+      }
       if ((rc = take_snapshot(c))) return rc;
       bool hit = false;
       if ((rc = read_flags(c, &hit))) return rc;  // clears flags before the block
@@ -827,6 +902,13 @@ struct StepRunner {
         step(c->margin, true, i == nb - 1);
       }
       if ((rc = read_flags(c, &hit))) return rc;
+      if (!hit && learned) {
+        // the learned interval is also judged by the exact check against a
+        // fresh zero-margin detection
+        long long missed = 0;
+        if ((rc = audit_now(c, &missed))) return rc;
+        hit = missed > 0;
+      }
       if (hit) {
         // roll back and replay the block with the plain rule
         c->stats.rollbacks++;
@@ -1004,7 +1086,7 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_totals, &c->b_det, &c->b_bin_cnt, &c->b_bin_off, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_keys, &c->b_ids, &c->b_keys2, &c->b_ids2, &c->b_bin_start, &c->b_bin_end,
                 &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp, &c->b_lob,
-                &c->b_part, &c->b_rec, &c->b_trho, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
+                &c->b_part, &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
                 &c->b_bcnt, &c->b_bvmax, &c->b_bvsum, &c->b_bamax, &c->b_occ, &c->b_nocc,
                 &c->b_binm, &c->b_cand, &c->b_feat, &c->b_pred, &c->b_dmax, &c->b_T, &c->b_tr_vox,
                 &c->b_tr_off, &c->b_tr_pos, &c->b_tr_q, &c->b_tx, &c->b_tt, &c->b_tcount,
@@ -1361,6 +1443,62 @@ int dem_get_bins(dem_ctx* c, long long cap, unsigned int* keys, int* ids, long l
 }
 
 
+int dem_autotune_bins(dem_ctx* c, int n, const double* factors, int reps, double* best,
+                      double* ms_out) {
+  if (!c || n < 1 || !factors || reps < 1 || !best) return DEM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!(factors[i] > 0.0) || !std::isfinite(factors[i]))
+      return fail(c, DEM_ERR_INVALID_ARG, "bin factors must be finite and > 0");
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  refresh_devstate(c);
+  const dem_stats saved = c->stats;
+  const double f0 = c->bin_factor;
+  auto apply = [&](double f) -> int {
+    c->bin_factor = f;
+    int r = build_grids(c);
+    if (r) return r;
+    cudaMemcpyAsync(c->b_grids.p, c->grids.data(), sizeof(SceneGrid) * c->grids.size(),
+                    cudaMemcpyHostToDevice, c->st);
+    return rebuild(c);  // also sizes the buffers for this grid
+  };
+  double best_ms = 0.0;
+  int best_i = -1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int i = 0; i < n; ++i) {
+    double ms = -1.0;
+    if (apply(factors[i]) == DEM_OK) {
+      cudaEventRecord(e0, c->st);
+      for (int r = 0; r < reps && rc == DEM_OK; ++r) rc = rebuild(c);
+      cudaEventRecord(e1, c->st);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rc) break;
+      ms = (double)t / reps;
+      if (best_i < 0 || ms < best_ms) {
+        best_ms = ms;
+        best_i = i;
+      }
+    }
+    if (ms_out) ms_out[i] = ms;  // -1: this factor gives no valid grid
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  const double chosen = best_i >= 0 ? factors[best_i] : f0;
+  c->err.clear();
+  if ((rc = apply(chosen))) return rc;
+  // the trial rebuilds change no state; only the counters are restored
+  c->stats.rebuilds = saved.rebuilds;
+  c->stats.ms_detect = saved.ms_detect;
+  *best = chosen;
+  return cuda_check(c, "autotune");
+}
+
 int dem_set_graphs(dem_ctx* c, int enabled) {
   if (!c) return DEM_ERR_INVALID_ARG;
   c->use_graphs = enabled ? 1 : 0;
@@ -1383,8 +1521,11 @@ int dem_set_learned_policy(dem_ctx* c, dem_mlp* mlp, const dem_learned_params* l
   }
   if (c->P.guard == DEM_GUARD_OFF) return fail(c, DEM_ERR_STATE, "the learned rule needs the guard");
   c->mlp = mlp;
+  if (lp->mode != DEM_LEARNED_HALT && lp->mode != DEM_LEARNED_ROLLBACK)
+    return fail(c, DEM_ERR_INVALID_ARG, "learned policy mode");
   c->l_interval = lp->interval;
   c->l_safety = lp->safety;
+  c->l_mode = lp->mode;
   c->l_cand.assign(lp->candidates, lp->candidates + lp->n_candidates);
   c->need_rebuild = true;
   return DEM_OK;
@@ -1467,6 +1608,16 @@ int dem_audit(dem_ctx* c, long long* missed) {
     rc = rebuild(c);
     if (rc) return rc;
   }
+  return audit_now(c, missed);
+}
+
+}  // extern "C"
+
+namespace {
+// Touching contacts of the current state missing from the current list: a
+// fresh detection with zero margin into the spare list, compared with it.
+int audit_now(dem_ctx* c, long long* missed) {
+  int rc;
   const float* saved_cm = c->D.cmargin;
   c->D.cmargin = nullptr;  // the exact check uses no margin
   rc = detect_into(c, 2, 0.0, 1);
@@ -1484,5 +1635,4 @@ int dem_audit(dem_ctx* c, long long* missed) {
   c->stats.missed_contacts += (long long)h;
   return cuda_check(c, "audit");
 }
-
-}  // extern "C"
+}  // namespace

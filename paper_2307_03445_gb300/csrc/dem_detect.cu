@@ -235,14 +235,29 @@ __global__ void k_gather_entries(DevState d, DetectOut o, long long n) {
 // belong to different clumps, the bin owns the pair (owning-bin masks) and
 // the enlarged spheres overlap on the 2^-24 m lattice:
 // |q_b - q_a|^2 <= (rho_a + rho_b)^2, exact in integers.
+//
+// Kept pairs are appended, unordered, to o.upairs through a per-warp buffer
+// in shared memory that is flushed 32 pairs at a time (one global atomic per
+// flush); pairs past o.ucap are counted but not written, so the caller can
+// grow the buffer and run the pass again.  o.pair_cnt[a] counts the partners
+// of every sphere a.
 constexpr int kNarrowWarps = 8;
 
-template <bool WRITE>
-__global__ void __launch_bounds__(32 * kNarrowWarps)
-    k_narrow_bins(DetectOut o, uint32_t* __restrict__ pb, int* __restrict__ flags) {
+__device__ __forceinline__ void flush_pairs(const DetectOut& o, uint2* buf, int n, int lane) {
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(o.d_np, (unsigned long long)n);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (lane < n && base + (unsigned long long)lane < o.ucap) o.upairs[base + lane] = buf[lane];
+}
+
+__global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) {
   __shared__ int4 sq[kNarrowWarps][32];   // qx, qy, qz, rho
   __shared__ int4 sm[kNarrowWarps][32];   // owner, id, mask
+  __shared__ uint2 sbuf[kNarrowWarps][64];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  uint2* buf = sbuf[wib];
+  int nbuf = 0;  // warp-uniform
   const long long nw = (long long)gridDim.x * kNarrowWarps;
   for (long long bin = (long long)blockIdx.x * kNarrowWarps + wib; bin < (long long)o.nbins;
        bin += nw) {
@@ -253,8 +268,7 @@ __global__ void __launch_bounds__(32 * kNarrowWarps)
       const bool vi = i < e;
       EntryRec A{};
       if (vi) A = o.rec[i];
-      uint32_t n = 0, row = 0;
-      if (WRITE && vi) row = o.pair_off[A.id];
+      uint32_t n = 0;
       for (uint32_t j0 = i0; j0 < e; j0 += 32u) {
         const uint32_t jl = j0 + (uint32_t)lane;
         if (jl < e) {
@@ -267,37 +281,63 @@ __global__ void __launch_bounds__(32 * kNarrowWarps)
         for (int jj = 0; jj < jn; ++jj) {
           const int4 q = sq[wib][jj];
           const int4 mm = sm[wib][jj];
-          if (!vi || j0 + (uint32_t)jj <= i || mm.x == A.owner || ((A.mask | (uint32_t)mm.z) != 7u))
-            continue;
-          const long long rr = (long long)A.rho + q.w;
-          const long long dx = (long long)q.x - A.qx, dy = (long long)q.y - A.qy,
-                          dz = (long long)q.z - A.qz;
-          // per-axis reject; past it every |d| <= rr < 2^31 and the sum of
-          // the three squares fits in 63 bits
-          if (dx > rr || -dx > rr || dy > rr || -dy > rr || dz > rr || -dz > rr) continue;
-          const int ix = (int)dx, iy = (int)dy, iz = (int)dz;
-          const long long d2 = (long long)ix * ix + (long long)iy * iy + (long long)iz * iz;
-          if (d2 > rr * rr) continue;
-          if (WRITE) {
-            // rows fill from the end; k_sort_rows orders them.  The count
-            // pass found the same pairs, so the row never overflows; the
-            // check only keeps a broken invariant from writing out of bounds.
-            const uint32_t left = atomicSub(&o.pair_cnt[A.id], 1u);
-            if (left == 0u) {
-              atomicAdd(&o.pair_cnt[A.id], 1u);
-              atomicOr(flags, kFlagBounds);
-            } else {
-              pb[row + left - 1u] = (uint32_t)mm.y;
+          bool hit = false;
+          if (vi && j0 + (uint32_t)jj > i && mm.x != A.owner && ((A.mask | (uint32_t)mm.z) == 7u)) {
+            const long long rr = (long long)A.rho + q.w;
+            const long long dx = (long long)q.x - A.qx, dy = (long long)q.y - A.qy,
+                            dz = (long long)q.z - A.qz;
+            // per-axis reject; past it every |d| <= rr < 2^31 and the sum of
+            // the three squares fits in 63 bits
+            if (dx <= rr && -dx <= rr && dy <= rr && -dy <= rr && dz <= rr && -dz <= rr) {
+              const int ix = (int)dx, iy = (int)dy, iz = (int)dz;
+              const long long d2 = (long long)ix * ix + (long long)iy * iy + (long long)iz * iz;
+              hit = d2 <= rr * rr;
             }
-          } else {
-            ++n;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (m) {
+            if (hit) {
+              buf[nbuf + __popc(m & lt)] = make_uint2(A.id, (uint32_t)mm.y);
+              ++n;
+            }
+            nbuf += __popc(m);
+            if (nbuf >= 32) {
+              __syncwarp();
+              flush_pairs(o, buf, 32, lane);
+              __syncwarp();
+              const int rem = nbuf - 32;  // < 32: move them to the front
+              uint2 v = make_uint2(0u, 0u);
+              if (lane < rem) v = buf[32 + lane];
+              __syncwarp();
+              if (lane < rem) buf[lane] = v;
+              __syncwarp();
+              nbuf = rem;
+            }
           }
         }
         __syncwarp();
       }
-      if (!WRITE && n) atomicAdd(&o.pair_cnt[A.id], n);
+      if (n) atomicAdd(&o.pair_cnt[A.id], n);
     }
   }
+  __syncwarp();
+  if (nbuf > 0) flush_pairs(o, buf, nbuf, lane);
+}
+
+// Places every unordered pair into the row of its sphere a (slots taken from
+// the partner counts, which this consumes); rows are then sorted by b.
+__global__ void k_scatter_pairs(DetectOut o, long long np, uint32_t* __restrict__ pb,
+                                int* __restrict__ flags) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const uint2 p = o.upairs[k];
+  const uint32_t left = atomicSub(&o.pair_cnt[p.x], 1u);
+  if (left == 0u) {  // a broken invariant: never write outside the row
+    atomicAdd(&o.pair_cnt[p.x], 1u);
+    atomicOr(flags, kFlagBounds);
+    return;
+  }
+  pb[o.pair_off[p.x] + left - 1u] = p.y;
 }
 
 // Sorts every row of the new list by b (insertion sort: rows are short) and
@@ -475,16 +515,18 @@ void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint3
 void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
                    cudaStream_t st) {
   if (d.ns == 0 || o.nbins == 0) return;
-  const long long want = ((long long)o.nbins + kNarrowWarps - 1) / kNarrowWarps;
-  const long long cap = (long long)device_sms() * 8;
-  const unsigned grid = (unsigned)(want < cap ? want : cap);
   if (write) {
-    k_narrow_bins<true><<<grid, 32 * kNarrowWarps, 0, st>>>(o, pb, d.flags);
-    count_launch();
+    if (o.np > 0) {
+      k_scatter_pairs<<<nblk(o.np, 256), 256, 0, st>>>(o, o.np, pb, d.flags);
+      count_launch();
+    }
     k_sort_rows<<<nblk(d.ns, 256), 256, 0, st>>>(d.ns, o.pair_off, pa, pb);
     count_launch();
   } else {
-    k_narrow_bins<false><<<grid, 32 * kNarrowWarps, 0, st>>>(o, pb, d.flags);
+    const long long want = ((long long)o.nbins + kNarrowWarps - 1) / kNarrowWarps;
+    const long long cap = (long long)device_sms() * 8;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    k_narrow_bins<<<grid, 32 * kNarrowWarps, 0, st>>>(o);
     count_launch();
   }
 }

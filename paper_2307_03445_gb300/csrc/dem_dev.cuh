@@ -64,7 +64,17 @@ struct DevState {
   int* flags;
   unsigned long long* counters;  // [0] active contacts, [1] guard violations
   long long* dstep;         // device step counter: forces of step s see time s * h
+  long long* halt_at;       // learned rule, halt mode: the first step whose state failed
+                            //   the displacement certificate (LLONG_MAX: none); every
+                            //   per-step kernel of a later step returns at once.  NULL: off
 };
+
+// True when the kernels of the step that starts from state *d.dstep must not
+// run (its state failed the certificate).  Uniform across a launch: halt_at is
+// only lowered by the update kernel, to a step after the one it integrates.
+__device__ __forceinline__ bool halted(const DevState& d) {
+  return d.halt_at != nullptr && *d.dstep >= *d.halt_at;
+}
 
 // One bin registration after sorting, with everything the narrow phase tests:
 // the lattice centre and enlarged radius, the owner clump, the sphere id and
@@ -105,6 +115,10 @@ struct DetectOut {
   uint32_t* bin_start;      // per bin
   uint32_t* bin_end;        // per bin
   uint32_t nbins;
+  uint2* upairs;            // narrow phase: kept pairs (a, b), unordered
+  unsigned long long ucap;  //   capacity of upairs
+  unsigned long long* d_np; //   pairs found (may exceed ucap)
+  long long np;             //   pairs found, on the host (write pass)
   uint32_t* pair_cnt;       // per sphere
   uint32_t* pair_off;       // per sphere (scan) -> row pointer (ns + 1 entries)
   int* trho;                // per template sphere: enlarged lattice radius, when all
@@ -134,9 +148,11 @@ void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st);
 void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, cudaStream_t st);
 void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint32_t* end,
                        cudaStream_t st);
-// Narrow phase over the bins.  Count pass: o.pair_cnt[a] += partners b > a
-// (pair_cnt zeroed by the caller).  Write pass (after the scan of pair_cnt
-// into pair_off): rows pa / pb, each sorted by b; consumes pair_cnt.
+// Narrow phase over the bins.  Find pass: the kept pairs go to o.upairs
+// (count in *o.d_np, zeroed by the caller) and o.pair_cnt[a] += partners
+// b > a (pair_cnt zeroed by the caller).  Write pass (after the scan of
+// pair_cnt into pair_off, o.np set): rows pa / pb, each sorted by b;
+// consumes pair_cnt.
 void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
                    cudaStream_t st);
 void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,

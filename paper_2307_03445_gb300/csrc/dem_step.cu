@@ -79,6 +79,7 @@ __device__ __forceinline__ void add_clump32(float* acc, int c, V3<float> F, V3<f
 // sphere-sphere contacts
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int count_active) {
+  if (halted(d)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long ln = l.dn[0];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ln; i += stride) {
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
 }
 
 __global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int count_active) {
+  if (halted(d)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long ln = l.dn[0];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ln; i += stride) {
@@ -205,6 +207,7 @@ __device__ __forceinline__ void wall_force_flush(const DevState& d, float* s_wf)
 }
 
 __global__ void k_walls32(DevState d, ContactList l, int count_active) {
+  if (halted(d)) return;
   __shared__ float s_wf[3 * kMaxBlockWalls];
   const bool shared_wf = d.nwalls <= kMaxBlockWalls;
   for (int i = threadIdx.x; i < 3 * kMaxBlockWalls; i += blockDim.x) s_wf[i] = 0.f;
@@ -264,6 +267,7 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
 }
 
 __global__ void k_walls64(DevState d, ContactList l, int count_active) {
+  if (halted(d)) return;
   const double t = (double)(*d.dstep) * d.h;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long lnw = l.dn[1];
@@ -333,6 +337,7 @@ __device__ __forceinline__ bool finite4(double4_32a v) {
 // FP64 mode.
 __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, float margin,
                                                    int check_cert) {
+  if (integrate && halted(d)) return;
   __shared__ double sR[kUpd][9];
   __shared__ double sX[kUpd][3];
   const long long c0 = (long long)blockIdx.x * kUpd;
@@ -394,6 +399,9 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
         if (disp * 1.00001f + 1e-12f > mlim) {
           atomicOr(d.flags, kFlagGuard);
           atomicAdd(d.counters + 1, 1ull);
+          // the state of step *dstep + 1 may lack a listed contact
+          if (d.halt_at) atomicMin(reinterpret_cast<unsigned long long*>(d.halt_at),
+                                   (unsigned long long)(*d.dstep + 1));
         }
       }
     }
@@ -424,6 +432,7 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
 // FP32_VOXEL mode.
 __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, float margin,
                                                    int check_cert) {
+  if (integrate && halted(d)) return;
   __shared__ float sRh[kUpd][9];
   __shared__ float sRl[kUpd][9];
   __shared__ int4 sVox[kUpd];
@@ -528,6 +537,9 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
         if (disp * 1.00001f + 1e-12f > mlim) {
           atomicOr(d.flags, kFlagGuard);
           atomicAdd(d.counters + 1, 1ull);
+          // the state of step *dstep + 1 may lack a listed contact
+          if (d.halt_at) atomicMin(reinterpret_cast<unsigned long long*>(d.halt_at),
+                                   (unsigned long long)(*d.dstep + 1));
         }
       }
     }
@@ -613,6 +625,7 @@ __global__ void k_walls_at(DevState d, long long step) {
 // After an integration: advances the device step counter and places the walls
 // at the new time (one block).
 __global__ void k_walls_advance(DevState d) {
+  if (halted(d)) return;
   const long long next = *d.dstep + 1;
   __syncthreads();
   place_walls(d, (double)next * d.h);

@@ -102,28 +102,40 @@ def test_traces_are_well_formed(dem, bed):
     assert np.all(np.diff(T, axis=1) >= -1e-6)
 
 
-def test_forced_rollback_keeps_the_list_valid(dem, bed):
-    """A regressor that predicts everlasting lists with the smallest margin:
-    the certificate fails (the plate drags clumps), the interval is rolled back
-    and replayed with the plain rule, and no contact is ever missing."""
-    sc = bed
+def _everlasting(dem):
+    """A regressor that predicts everlasting lists: the smallest margin everywhere."""
     reg = dem.Regressor()
     p = np.zeros(reg.n_params, np.float32)
     p[-1] = 20.0  # output bias: ln(lifetime) = 20 for every query
     reg.set_params(p)
-    with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
-        sim.set_learned_policy(reg, interval=200, safety=1.0, candidates=CAND)
-        sim.step(400)
-        st = sim.stats()
-        assert st["rollbacks"] >= 1
-        assert sim.audit() == 0
-    # the replayed run agrees with a run of the plain rule
+    return reg
+
+
+@pytest.mark.parametrize("mode", ["halt", "rollback"])
+def test_bad_predictions_never_miss_a_contact(dem, bed, mode):
+    """With the smallest margin everywhere the certificate fails within a few
+    steps (the plate drags clumps).  Halt mode cuts the interval short on the
+    device and rebuilds; rollback mode replays the interval with the plain
+    rule.  Either way no contact is missing and the trajectory is that of
+    the plain rule."""
+    from paper_2307_03445_gb300 import capi
+
+    sc = bed
+    reg = _everlasting(dem)
+    m = capi.DEM_LEARNED_HALT if mode == "halt" else capi.DEM_LEARNED_ROLLBACK
     with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as plain:
         plain.step(400)
         pos_p = plain.state()[0]
     with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
-        sim.set_learned_policy(reg, interval=200, safety=1.0, candidates=CAND)
+        sim.set_learned_policy(reg, interval=200, safety=1.0, candidates=CAND, mode=m)
         sim.step(400)
+        st = sim.stats()
+        assert st["steps"] == 400 or mode == "rollback"
+        if mode == "halt":
+            assert st["early_rebuilds"] >= 1 and st["rollbacks"] == 0
+        else:
+            assert st["rollbacks"] >= 1
+        assert sim.audit() == 0
         pos_l = sim.state()[0]
     moved = np.abs(pos_p - sc.pos).max()
     assert moved > 1e-6

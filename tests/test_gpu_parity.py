@@ -68,6 +68,34 @@ def test_detection_bit_exact(dem, oracle_mod, prec, seed, n, bin_scale):
     assert np.all(u == 0) and np.all(uw == 0)
 
 
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+def test_autotuned_bins_stay_exact(dem, oracle_mod, prec):
+    """The bin-size autotuner keeps the fastest factor; the state is unchanged
+    and detection at the chosen bin edge is still the oracle's, bit for bit."""
+    import dataclasses
+
+    margin, K = 1e-4, 10
+    sc = _scene(4, 700, prec, margin=margin)
+    factors = (0.4, 0.7, 1.0, 2.0)
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        sim.rebuild()
+        before = sim.state()
+        best, ms = sim.autotune_bins(factors, reps=2)
+        assert best in factors and all(ms[f] is not None and ms[f] > 0 for f in factors)
+        assert ms[best] == min(ms.values())
+        after = sim.state()
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)
+        keys, ids = sim.bins()
+        a, b, *_ = sim.contacts()
+        sim.step(12)  # steps and rebuilds run on the tuned grid
+        assert sim.audit() == 0
+    sc2 = dataclasses.replace(sc, bin_size=sc.bin_size * best)
+    om, k_o, i_o, a_o, b_o, ws_o, ww_o = _oracle_lists(oracle_mod, sc2, margin, K)
+    assert np.array_equal(keys, k_o) and np.array_equal(ids, i_o)
+    assert np.array_equal(a, a_o) and np.array_equal(b, b_o)
+
+
 def _compare_forces(sc, F, T, Fo, To, mag, tol):
     scaleF = np.maximum(mag[:, 0], 1e-300)
     scaleT = np.maximum(mag[:, 1], 1e-300)
