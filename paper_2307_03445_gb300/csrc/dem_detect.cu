@@ -136,8 +136,10 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   }
   for (int k = 0; k < 3; ++k) {
     // a sphere more than 64 m outside its domain is clamped (it only meets
-    // the boundary bins, where it can still be found)
-    qc[k] = qc[k] < -(1ll << 30) ? -(1ll << 30) : (qc[k] > (1ll << 30) ? (1ll << 30) : qc[k]);
+    // the boundary bins, where it can still be found); the clamped range
+    // keeps every coordinate difference inside 32 bits
+    constexpr long long kQ = (1ll << 30) - 1;
+    qc[k] = qc[k] < -kQ ? -kQ : (qc[k] > kQ ? kQ : qc[k]);
   }
   // enlarged lattice radius ceil((r + m) 2^24) + 1: from the per template
   // sphere table when every clump has the same margin
@@ -278,20 +280,23 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
         }
         __syncwarp();
         const int jn = (int)min(32u, e - j0);
+#pragma unroll 2
         for (int jj = 0; jj < jn; ++jj) {
           const int4 q = sq[wib][jj];
           const int4 mm = sm[wib][jj];
           bool hit = false;
           if (vi && j0 + (uint32_t)jj > i && mm.x != A.owner && ((A.mask | (uint32_t)mm.z) == 7u)) {
-            const long long rr = (long long)A.rho + q.w;
-            const long long dx = (long long)q.x - A.qx, dy = (long long)q.y - A.qy,
-                            dz = (long long)q.z - A.qz;
-            // per-axis reject; past it every |d| <= rr < 2^31 and the sum of
-            // the three squares fits in 63 bits
-            if (dx <= rr && -dx <= rr && dy <= rr && -dy <= rr && dz <= rr && -dz <= rr) {
-              const int ix = (int)dx, iy = (int)dy, iz = (int)dz;
-              const long long d2 = (long long)ix * ix + (long long)iy * iy + (long long)iz * iz;
-              hit = d2 <= rr * rr;
+            // coordinates lie in [-(2^30 - 1), 2^30 - 1] and rr < 2^30 + 2, so
+            // the differences fit in 32 bits and -rr <= d <= rr is one
+            // unsigned comparison of d + rr (a wrapped sum lands above 2 rr)
+            const int rr = A.rho + q.w;
+            const int dx = q.x - A.qx, dy = q.y - A.qy, dz = q.z - A.qz;
+            const unsigned w = 2u * (unsigned)rr;
+            const unsigned ur = (unsigned)rr;
+            if ((unsigned)dx + ur <= w && (unsigned)dy + ur <= w && (unsigned)dz + ur <= w) {
+              // |d| <= rr < 2^30 + 2: the sum of the squares fits in 63 bits
+              const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+              hit = d2 <= (long long)rr * rr;
             }
           }
           const unsigned m = __ballot_sync(0xffffffffu, hit);

@@ -82,10 +82,18 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
   if (halted(d)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long ln = l.dn[0];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ln; i += stride) {
-    const int a = l.pa[i];
-    const uint32_t bw = l.pb[i];
+  // software pipeline: the ids of the next pair are loaded one iteration
+  // ahead, and its two pose records are prefetched into L2 once those ids
+  // have arrived, so the dependent loads of an iteration start from L2
+  long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int a_n = 0;
+  uint32_t bw_n = 0;
+  if (i0 < ln) { a_n = l.pa[i0]; bw_n = l.pb[i0]; }
+  for (long long i = i0; i < ln; i += stride) {
+    const int a = a_n;
+    const uint32_t bw = bw_n;
     const uint32_t b = bw & ~kHistFlag;
+    if (i + stride < ln) { a_n = l.pa[i + stride]; bw_n = l.pb[i + stride]; }
     const SphA32 A = d.sa32[a];
     const SphA32 B = d.sa32[b];
     const long long dxl = B.x - A.x, dyl = B.y - A.y, dzl = B.z - A.z;
@@ -106,6 +114,10 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     }
     const bool active = dn > 0.f;
     if (count_active) warp_count(active, d.counters);
+    if (i + stride < ln) {
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.sa32 + a_n));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.sa32 + (bw_n & ~kHistFlag)));
+    }
     if (!active) {
       if (bw & kHistFlag) l.pb[i] = b;  // history reset (false positive)
       continue;
