@@ -163,6 +163,24 @@ def time_oracle(budget_s=15.0, n_clumps=1500, max_steps=None):
 
 
 # ---------------------------------------------------------------------------
+# replicas: one per rank, no data-path collective
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms, device):
+    """The slowest rank's time (every rank receives it)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, steps, ms):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return world * units_per_rank * steps / (ms / 1000.0)
+
+
+# ---------------------------------------------------------------------------
 # the learned-margin and batched forms
 # ---------------------------------------------------------------------------
 LEARN_CAND = [1e-6, 2e-6, 4e-6, 8e-6, 1.6e-5, 3.2e-5]  # candidate margins [m]
@@ -187,11 +205,12 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
     (halt mode: a failed certificate ends an interval early), and an exact
     audit of the final list."""
     t0 = time.time()
-    x, t = sim.trace(2, 120, LEARN_CAND, cap=1 << 24)
+    x, t = sim.trace(2, 240, LEARN_CAND, cap=1 << 24)
     reg = dem.Regressor(device=sim_device(sim))
     loss = reg.train(x, t, steps=800, batch=8192, lr=2e-3, seed=1)
     log(f"learned form: {len(x)} trace samples, loss {loss:.4f}, {time.time() - t0:.1f} s")
-    sim.set_learned_policy(reg, interval=60, safety=1.5, candidates=LEARN_CAND)
+    # interval x safety stays inside the traced window, where lifetimes are not capped
+    sim.set_learned_policy(reg, interval=80, safety=1.5, candidates=LEARN_CAND)
     sim.reset_stats()
     ms = _timed_steps(sim, stream, steps)
     st = sim.stats()
@@ -205,7 +224,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
             "listed_per_step": st["pair_steps"] / max(1, st["steps"]),
             "listed_per_step_plain": pair_steps_plain, "missed_contacts": missed,
             "rule": "6->3x64->1 MLP (BF16 weights) per bin, candidates 1-32 um, target "
-                    "interval 60 x 1.5, halt on certificate; trained on 2 x 120-step traces"}
+                    "interval 80 x 1.5, halt on certificate; trained on 2 x 240-step traces"}
 
 
 def sim_device(sim):
@@ -339,12 +358,10 @@ def main():
     ms = ev0.elapsed_time(ev1)
     st = sim.stats()
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, torch.device("cuda", local))
     ms_step = ms / args.steps
-    value = world * ns * args.steps / (ms / 1000.0)
-    contacts_ps = world * st["pair_steps"] / (ms / 1000.0)
+    value = whole_job_rate(world, ns, args.steps, ms)
+    contacts_ps = whole_job_rate(world, st["pair_steps"], 1, ms)
 
     # dominant kernel: the sphere-sphere force kernel
     peaks = {}

@@ -231,12 +231,13 @@ __global__ void k_gather_entries(DevState d, DetectOut o, long long n) {
 
 // Narrow phase, one warp per bin (persistent warps striding over the bins).
 // The bin's registrations, sorted by sphere id, are taken 32 at a time: lane
-// l holds registration i; every later registration j of the bin is staged in
-// shared memory and tested by all lanes at once, so the loops are uniform
-// across the warp.  A pair (a = id_i < b = id_j) is kept when the spheres
-// belong to different clumps, the bin owns the pair (owning-bin masks) and
-// the enlarged spheres overlap on the 2^-24 m lattice:
-// |q_b - q_a|^2 <= (rho_a + rho_b)^2, exact in integers.
+// l holds registration i; the registrations of the same tile are paired by
+// rotation, and every later tile is staged in shared memory and tested by all
+// lanes at once, so the loops are uniform across the warp.  A pair
+// (a = min id < b = max id) is kept when the spheres belong to different
+// clumps, the bin owns the pair (owning-bin masks) and the enlarged spheres
+// overlap on the 2^-24 m lattice: |q_b - q_a|^2 <= (rho_a + rho_b)^2, exact
+// in integers.
 //
 // Kept pairs are appended, unordered, to o.upairs through a per-warp buffer
 // in shared memory that is flushed 32 pairs at a time (one global atomic per
@@ -252,6 +253,22 @@ __device__ __forceinline__ void flush_pairs(const DetectOut& o, uint2* buf, int 
   if (lane < n && base + (unsigned long long)lane < o.ucap) o.upairs[base + lane] = buf[lane];
 }
 
+// The pair test of two registrations of one bin (A held by the lane, B from
+// shared memory): different clumps, the bin owns the pair, enlarged spheres
+// overlap.  Coordinates lie in [-(2^30 - 1), 2^30 - 1] and rr < 2^30 + 2, so
+// the differences fit in 32 bits and -rr <= d <= rr is one unsigned
+// comparison of d + rr (a wrapped sum lands above 2 rr); past it every
+// |d| <= rr and the sum of the squares fits in 63 bits.
+__device__ __forceinline__ bool narrow_test(const EntryRec& A, const int4 q, const int4 mm) {
+  if (mm.x == A.owner || (A.mask | (uint32_t)mm.z) != 7u) return false;
+  const int rr = A.rho + q.w;
+  const int dx = q.x - A.qx, dy = q.y - A.qy, dz = q.z - A.qz;
+  const unsigned w = 2u * (unsigned)rr, ur = (unsigned)rr;
+  if ((unsigned)dx + ur > w || (unsigned)dy + ur > w || (unsigned)dz + ur > w) return false;
+  const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+  return d2 <= (long long)rr * rr;
+}
+
 __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) {
   __shared__ int4 sq[kNarrowWarps][32];   // qx, qy, qz, rho
   __shared__ int4 sm[kNarrowWarps][32];   // owner, id, mask
@@ -260,6 +277,34 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
   const unsigned lt = (1u << lane) - 1u;
   uint2* buf = sbuf[wib];
   int nbuf = 0;  // warp-uniform
+  // appends the kept pairs of one warp-wide test to the warp's buffer
+  auto emit = [&](bool hit, uint32_t a, uint32_t b) {
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (!m) return;
+    if (hit) buf[nbuf + __popc(m & lt)] = make_uint2(a, b);
+    nbuf += __popc(m);
+    if (nbuf >= 32) {
+      __syncwarp();
+      flush_pairs(o, buf, 32, lane);
+      __syncwarp();
+      const int rem = nbuf - 32;  // < 32: move them to the front
+      uint2 v = make_uint2(0u, 0u);
+      if (lane < rem) v = buf[32 + lane];
+      __syncwarp();
+      if (lane < rem) buf[lane] = v;
+      __syncwarp();
+      nbuf = rem;
+    }
+  };
+  auto stage = [&](uint32_t j0, uint32_t e) {
+    const uint32_t jl = j0 + (uint32_t)lane;
+    if (jl < e) {
+      const EntryRec R = o.rec[jl];
+      sq[wib][lane] = make_int4(R.qx, R.qy, R.qz, R.rho);
+      sm[wib][lane] = make_int4(R.owner, (int)R.id, (int)R.mask, 0);
+    }
+    __syncwarp();
+  };
   const long long nw = (long long)gridDim.x * kNarrowWarps;
   for (long long bin = (long long)blockIdx.x * kNarrowWarps + wib; bin < (long long)o.nbins;
        bin += nw) {
@@ -270,55 +315,36 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
       const bool vi = i < e;
       EntryRec A{};
       if (vi) A = o.rec[i];
+      const int nt = (int)min(32u, e - i0);
+      // pairs inside the lane's own tile, by rotation: at offset t lane l
+      // meets (l + t) mod nt, so every unordered pair comes up once for
+      // t < nt / 2 (and at t = nt / 2 from the lower half of the lanes)
+      stage(i0, e);
+      for (int t = 1; 2 * t <= nt; ++t) {
+        int pj = lane + t;
+        if (pj >= nt) pj -= nt;
+        const bool valid = lane < nt && (2 * t < nt || lane < t);
+        const int4 q = sq[wib][pj];
+        const int4 mm = sm[wib][pj];
+        const bool hit = valid && narrow_test(A, q, mm);
+        const uint32_t b = (uint32_t)mm.y;
+        const uint32_t lo = A.id < b ? A.id : b, hi = A.id < b ? b : A.id;
+        if (hit) atomicAdd(&o.pair_cnt[lo], 1u);
+        emit(hit, lo, hi);
+      }
+      __syncwarp();
+      // later tiles of the bin: ids above every id of this tile
       uint32_t n = 0;
-      for (uint32_t j0 = i0; j0 < e; j0 += 32u) {
-        const uint32_t jl = j0 + (uint32_t)lane;
-        if (jl < e) {
-          const EntryRec R = o.rec[jl];
-          sq[wib][lane] = make_int4(R.qx, R.qy, R.qz, R.rho);
-          sm[wib][lane] = make_int4(R.owner, (int)R.id, (int)R.mask, 0);
-        }
-        __syncwarp();
+      for (uint32_t j0 = i0 + 32u; j0 < e; j0 += 32u) {
+        stage(j0, e);
         const int jn = (int)min(32u, e - j0);
 #pragma unroll 2
         for (int jj = 0; jj < jn; ++jj) {
           const int4 q = sq[wib][jj];
           const int4 mm = sm[wib][jj];
-          bool hit = false;
-          if (vi && j0 + (uint32_t)jj > i && mm.x != A.owner && ((A.mask | (uint32_t)mm.z) == 7u)) {
-            // coordinates lie in [-(2^30 - 1), 2^30 - 1] and rr < 2^30 + 2, so
-            // the differences fit in 32 bits and -rr <= d <= rr is one
-            // unsigned comparison of d + rr (a wrapped sum lands above 2 rr)
-            const int rr = A.rho + q.w;
-            const int dx = q.x - A.qx, dy = q.y - A.qy, dz = q.z - A.qz;
-            const unsigned w = 2u * (unsigned)rr;
-            const unsigned ur = (unsigned)rr;
-            if ((unsigned)dx + ur <= w && (unsigned)dy + ur <= w && (unsigned)dz + ur <= w) {
-              // |d| <= rr < 2^30 + 2: the sum of the squares fits in 63 bits
-              const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-              hit = d2 <= (long long)rr * rr;
-            }
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, hit);
-          if (m) {
-            if (hit) {
-              buf[nbuf + __popc(m & lt)] = make_uint2(A.id, (uint32_t)mm.y);
-              ++n;
-            }
-            nbuf += __popc(m);
-            if (nbuf >= 32) {
-              __syncwarp();
-              flush_pairs(o, buf, 32, lane);
-              __syncwarp();
-              const int rem = nbuf - 32;  // < 32: move them to the front
-              uint2 v = make_uint2(0u, 0u);
-              if (lane < rem) v = buf[32 + lane];
-              __syncwarp();
-              if (lane < rem) buf[lane] = v;
-              __syncwarp();
-              nbuf = rem;
-            }
-          }
+          const bool hit = vi && narrow_test(A, q, mm);
+          n += hit ? 1u : 0u;
+          emit(hit, A.id, (uint32_t)mm.y);
         }
         __syncwarp();
       }

@@ -457,8 +457,17 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
     float4 off = d.coff[c];
     double4_32a q4 = d.cq[c], v = d.cv[c], w = d.cw[c];
     const float mass = d.tmassf[tpl];
-    ff qw = ff_from_double(q4.x), qx = ff_from_double(q4.y), qy = ff_from_double(q4.z),
-       qz = ff_from_double(q4.w);
+    // orientation as float-float; integrating needs only the high parts of
+    // the old one (the rotation matrix is built from the new orientation)
+    ff qw, qx, qy, qz;
+    V3<float> wf_new;  // the new angular velocity as float (integrating)
+    float vf_new[3];   // the new velocity as float (integrating)
+    if (integrate) {
+      qw = {d2f(q4.x), 0.f}; qx = {d2f(q4.y), 0.f}; qy = {d2f(q4.z), 0.f}; qz = {d2f(q4.w), 0.f};
+    } else {
+      qw = ff_from_double(q4.x); qx = ff_from_double(q4.y); qy = ff_from_double(q4.z);
+      qz = ff_from_double(q4.w);
+    }
     if (integrate) {
       float* acc = d.acc32 + 8 * c;
       const float4 a0 = *reinterpret_cast<const float4*>(acc);
@@ -475,6 +484,7 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
       // position: the offset increment h*v carries 1e-7 relative error, far
       // below the 2^-44 m resolution of the offset itself
       const float vx_f = d2f(v.x), vy_f = d2f(v.y), vz_f = d2f(v.z);
+      vf_new[0] = vx_f; vf_new[1] = vy_f; vf_new[2] = vz_f;
       float o[3] = {off.x + hf * vx_f, off.y + hf * vy_f, off.z + hf * vz_f};
       int vi[3] = {vox.x, vox.y, vox.z};
       const float kV = (float)kVoxel;
@@ -502,6 +512,7 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
       // float, accumulated in double; then |q| is restored to one with a
       // first-order correction whose size is measured in float-float
       const V3<float> wn = {d2f(w.x), d2f(w.y), d2f(w.z)};
+      wf_new = wn;
       const float th = 0.5f * hf * sqrtf(dot(wn, wn));
       const float th2 = th * th;
       const float cm1 = -0.5f * th2 + th2 * th2 * (1.f / 24.f);  // cos(th) - 1
@@ -576,9 +587,12 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
       sRl[threadIdx.x][k] = R[k].l;
       Rf[k] = R[k].h;
     }
-    const V3<float> wf = {d2f(w.x), d2f(w.y), d2f(w.z)};
-    const V3<float> ww = mat_mul(Rf, wf);
-    d.mv32[c] = make_float4(d2f(v.x), d2f(v.y), d2f(v.z), mass);
+    if (!integrate) {
+      wf_new = {d2f(w.x), d2f(w.y), d2f(w.z)};
+      vf_new[0] = d2f(v.x); vf_new[1] = d2f(v.y); vf_new[2] = d2f(v.z);
+    }
+    const V3<float> ww = mat_mul(Rf, wf_new);
+    d.mv32[c] = make_float4(vf_new[0], vf_new[1], vf_new[2], mass);
     d.mw32[c] = make_float4(ww.x, ww.y, ww.z, 0.f);
     sVox[threadIdx.x] = vox;
     sOff[threadIdx.x] = off;

@@ -231,6 +231,19 @@ def layered_positions(bound, x0, x1, y0, y1, z0, gap=2e-4, rng=None, jitter=0.0)
     return P
 
 
+def morton_order(pos, lo, cell):
+    """Permutation that sorts points along a Z-order (Morton) curve of cells
+    of edge ``cell`` from corner ``lo`` (21 bits per axis): neighbours in space
+    get nearby indices, so their records share cache lines."""
+    q = np.floor((np.asarray(pos, float) - np.asarray(lo, float)) / cell).astype(np.int64)
+    q = np.clip(q, 0, (1 << 21) - 1).astype(np.uint64)
+    key = np.zeros(len(q), np.uint64)
+    for bit in range(21):
+        for k in range(3):
+            key |= ((q[:, k] >> np.uint64(bit)) & np.uint64(1)) << np.uint64(3 * bit + k)
+    return np.argsort(key, kind="stable")
+
+
 def _finish(sc: Scene, rng, pos, tpl, vel_scale=0.0, ang_scale=0.0):
     n = len(tpl)
     sc.tpl = np.asarray(tpl, np.int32)

@@ -58,8 +58,9 @@ def settle(sc: scenes.Scene, t_end: float, v_bound=6.0, K=10, log=None, chunk=20
 
 
 def bed_c5(n_clumps=11_000_000, lx=4.0, ly=2.0, patch=0.25, seed=1239, log=None,
-           settle_time=None, stiffen_time=6e-3):
-    """The paper-scale bed: a settled patch copy-pasted over lx x ly."""
+           settle_time=None, stiffen_time=6e-3, spatial_order=True):
+    """The paper-scale bed: a settled patch copy-pasted over lx x ly; with
+    spatial_order the clumps are numbered along a space-filling curve."""
     base = scenes.config5(seed=seed, n_clumps=1, lx=lx, ly=ly)
     rng = np.random.default_rng(seed + 1)
     nx, ny = int(round(lx / patch)), int(round(ly / patch))
@@ -80,6 +81,10 @@ def bed_c5(n_clumps=11_000_000, lx=4.0, ly=2.0, patch=0.25, seed=1239, log=None,
                         for j in range(ny) for i in range(nx)])[:n_clumps]
     Q = np.concatenate([quat] * tiles)[:n_clumps]
     T = np.concatenate([psc.tpl] * tiles)[:n_clumps]
+    if spatial_order:
+        # number the clumps along a Morton curve (cells of the largest clump)
+        perm = scenes.morton_order(P, (0.0, 0.0, 0.0), 2.0 * float(base.bounding_radius().max()))
+        P, Q, T = P[perm], Q[perm], T[perm]
     top = float((P[:, 2] + base.bounding_radius()[T]).max())
     sc = base
     sc.tpl = T

@@ -300,6 +300,33 @@ def test_degenerate_inputs(dem):
         assert F[1, 0] > 0 and F[0, 0] < 0
 
 
+@pytest.mark.parametrize("case", ["one_bin", "wide_margin"])
+def test_detection_extremes_bit_exact(dem, oracle_mod, case):
+    """Degenerate binning: every registration in a single bin (the narrow phase
+    walks 25 tiles of one bin); and a margin wide enough that the pair list
+    outgrows the first pair buffer (2^16 pairs here; the find pass regrows
+    it and runs again)."""
+    if case == "one_bin":
+        margin, K = 1e-4, 10
+        sc = _scene(11, 300, scenes.PREC_FP64, margin=margin)
+        sc.bin_size = 2.0  # one bin covers the whole domain
+    else:
+        margin, K = 2.5e-3, 10
+        sc = _scene(12, 1500, scenes.PREC_FP64, margin=margin)
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        sim.rebuild()
+        keys, ids = sim.bins()
+        a, b, *_ = sim.contacts()
+        st = sim.stats()
+    om, k_o, i_o, a_o, b_o, ws_o, ww_o = _oracle_lists(oracle_mod, sc, margin, K)
+    if case == "one_bin":
+        assert len(np.unique(keys)) == 1 and len(keys) > 25 * 32 - 32
+    else:
+        assert len(a_o) > max(2 * st["n_spheres"], 1 << 16)
+    assert np.array_equal(keys, k_o) and np.array_equal(ids, i_o)
+    assert np.array_equal(a, a_o) and np.array_equal(b, b_o)
+
+
 def test_non_finite_input_rejected(dem):
     sc = single_sphere_scene([1e-3], g=(0, 0, -9.81))
     set_clumps(sc, [0], [[0.0, 0.0, np.nan]])
