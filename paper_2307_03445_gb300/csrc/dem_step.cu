@@ -442,14 +442,20 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
 }
 
 // FP32_VOXEL mode.
-__global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, float margin,
-                                                   int check_cert) {
-  if (integrate && halted(d)) return;
-  __shared__ float sRh[kUpd][9];
-  __shared__ float sRl[kUpd][9];
-  __shared__ int4 sVox[kUpd];
-  __shared__ float4 sOff[kUpd];
-  const long long c0 = (long long)blockIdx.x * kUpd;
+// One block's batch of kUpd clumps starting at c0 (FP32_VOXEL mode).
+struct UpdShared {
+  float Rh[kUpd][9];
+  float Rl[kUpd][9];
+  int4 vox[kUpd];
+  float4 off[kUpd];
+};
+
+__device__ __forceinline__ void update32_batch(const DevState& d, long long c0, int integrate,
+                                               float margin, int check_cert, UpdShared& sh) {
+  float (*sRh)[9] = sh.Rh;
+  float (*sRl)[9] = sh.Rl;
+  int4* sVox = sh.vox;
+  float4* sOff = sh.off;
   const long long c = c0 + threadIdx.x;
   if (c < d.ncl) {
     const int tpl = d.cinfo[c].x;
@@ -618,16 +624,52 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
     const int vv[3] = {vox.x, vox.y, vox.z};
     const float oo[3] = {off.x, off.y, off.z};
     long long P[3];
-    for (int i = 0; i < 3; ++i) {
-      const ff t = ff_add(two_sum(oo[i], rel[i].h), {rel[i].l, 0.f});
-      P[i] = ((long long)vv[i] << (kFixBits - kVoxLog2)) + f2ll_rn(t.h * kMToFix) +
-             f2ll_rn(t.l * kMToFix);
-    }
+    // fixed point = voxel + round(rel.h) + round(off) + round(rel.l), each term
+    // scaled to 2^-44 m units (|off| <= 2^-21 m and |rel.l| <= 2^-31 m fit a
+    // 32-bit integer): three roundings of half a unit plus the float-float
+    // error of R p (a small fraction of a unit) keep the record within 2 units
+    // of the exact centre, the bound the detection relies on
+    for (int i = 0; i < 3; ++i)
+      P[i] = ((long long)vv[i] << (kFixBits - kVoxLog2)) + f2ll_rn(rel[i].h * kMToFix) +
+             (long long)__float2int_rn(oo[i] * kMToFix) +
+             (long long)__float2int_rn(rel[i].l * kMToFix);
     SphA32 A;
     A.x = P[0]; A.y = P[1]; A.z = P[2]; A.r = tp.w; A.owner = si.x;
     d.sa32[s] = A;
     d.sb32[s] = make_float4(rel[0].h, rel[1].h, rel[2].h, __int_as_float(d.tmat[si.y]));
   }
+}
+
+// Sets L2 prefetches for the clump state of a later batch.
+__device__ __forceinline__ void prefetch_batch(const DevState& d, long long c0, int integrate,
+                                               int check_cert) {
+  const long long c = c0 + threadIdx.x;
+  if (c >= d.ncl) return;
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cvox + c));
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.coff + c));
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cq + c));
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cv + c));
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cw + c));
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cinfo + c));
+  if (integrate) {
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(d.acc32 + 8 * c));
+    if (check_cert) {
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.ref_vox + c));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.ref_off + c));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.ref_q + c));
+    }
+  }
+}
+
+// One block per batch of kUpd clumps.  Each block first prefetches into L2
+// the state of the batch `ahead` blocks later (about one wave of resident
+// blocks), which starts when a block of the current wave retires.
+__global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, float margin,
+                                                   int check_cert, int ahead) {
+  if (integrate && halted(d)) return;
+  __shared__ UpdShared sh;
+  prefetch_batch(d, ((long long)blockIdx.x + ahead) * kUpd, integrate, check_cert);
+  update32_batch(d, (long long)blockIdx.x * kUpd, integrate, margin, check_cert, sh);
 }
 
 __device__ __forceinline__ void place_walls(const DevState& d, double t) {
@@ -768,7 +810,8 @@ void launch_update(const DevState& d, bool integrate, long long step, double mar
                                                       check_cert ? 1 : 0); count_launch(); }
     else
       { k_update32<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
-                                                      check_cert ? 1 : 0); count_launch(); }
+                                                      check_cert ? 1 : 0, sm_count() * 7);
+        count_launch(); }
   }
   if (integrate) {
     k_walls_advance<<<1, 256, 0, st>>>(d);
