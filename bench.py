@@ -212,6 +212,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
     # interval x safety stays inside the traced window, where lifetimes are not capped
     sim.set_learned_policy(reg, interval=80, safety=1.5, candidates=LEARN_CAND)
     sim.reset_stats()
+    sim.set_timing(True)  # events only: the steps are not serialised
     ms = _timed_steps(sim, stream, steps)
     st = sim.stats()
     missed = sim.audit()
@@ -223,6 +224,8 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
             "early_rebuilds": st["early_rebuilds"], "rollbacks": st["rollbacks"],
             "listed_per_step": st["pair_steps"] / max(1, st["steps"]),
             "listed_per_step_plain": pair_steps_plain, "missed_contacts": missed,
+            "ms_predict_per_interval": st["ms_predict"] / max(1, st["rebuilds"]),
+            "ms_rebuild_per_interval": st["ms_detect"] / max(1, st["rebuilds"]),
             "rule": "6->3x64->1 MLP (BF16 weights) per bin, candidates 1-32 um, target "
                     "interval 80 x 1.5, halt on certificate; trained on 2 x 240-step traces"}
 

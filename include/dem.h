@@ -124,6 +124,8 @@ typedef struct {
     long long launches;         /* kernels this library launched                    */
     long long early_rebuilds;   /* learned-rule intervals cut short by a failed     */
                                 /*   displacement certificate (see below)           */
+    double ms_predict;          /* device time of the learned rule's margin        */
+                                /*   predictions [ms], while timing is on           */
 } dem_stats;
 
 typedef struct dem_ctx dem_ctx;

@@ -54,7 +54,8 @@ class DemStats(C.Structure):
                 ("missed_contacts", C.c_longlong), ("margin", C.c_double), ("time", C.c_double),
                 ("ms_detect", C.c_double), ("ms_pairs", C.c_double), ("ms_walls", C.c_double),
                 ("ms_update", C.c_double), ("timed_steps", C.c_longlong),
-                ("launches", C.c_longlong), ("early_rebuilds", C.c_longlong)]
+                ("launches", C.c_longlong), ("early_rebuilds", C.c_longlong),
+                ("ms_predict", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)

@@ -881,7 +881,15 @@ struct StepRunner {
       const int nb = std::min(n, K);
       int rc;
       if (learned) {
+        if (c->timing) cudaEventRecord(c->ev[2], c->st);
         if ((rc = predict_margins(c))) return rc;
+        if (c->timing) {
+          cudaEventRecord(c->ev[3], c->st);
+          cudaEventSynchronize(c->ev[3]);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+          c->stats.ms_predict += ms;
+        }
       } else {
         c->D.cmargin = nullptr;
       }
