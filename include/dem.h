@@ -281,6 +281,12 @@ int dem_mlp_set_params(dem_mlp* mlp, const float* params);
 int dem_mlp_get_params(dem_mlp* mlp, float* params);
 /* y[k] for k < n from x[6k .. 6k+5] (host arrays). */
 int dem_mlp_forward(dem_mlp* mlp, long long n, const float* x, float* y);
+/* The same forward pass on the tensor cores (tcgen05.mma, 128-row tiles):
+ * every layer's input is rounded to bfloat16 and the products are summed in
+ * FP32, so results differ from dem_mlp_forward by bfloat16 rounding of the
+ * activations.  The learned rule's predictions use this pass.
+ * DEM_ERR_TIMEOUT if a bounded wait on the tensor cores ran out. */
+int dem_mlp_forward_tc(dem_mlp* mlp, long long n, const float* x, float* y);
 /* Mean squared error of predictions against targets t (host), and its
  * gradient with respect to the parameters (host, may be NULL). */
 int dem_mlp_loss_grad(dem_mlp* mlp, long long n, const float* x, const float* t, double* loss,

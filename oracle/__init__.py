@@ -113,6 +113,7 @@ def _load():
                 "orc_sim_destroy": (None, [C.c_void_p]),
                 "orc_mlp_num_params": (C.c_int, []),
                 "orc_mlp_forward": (None, [_D, C.c_longlong, _D, _D]),
+                "orc_mlp_forward_bf16act": (None, [_D, C.c_longlong, _D, _D]),
                 "orc_mlp_loss_grad": (C.c_double, [_D, C.c_longlong, _D, _D, _D]),
                 "orc_mlp_adam": (None, [_D, _D, _D, _D, C.c_int, C.c_double, C.c_double,
                                         C.c_double, C.c_double]),
@@ -406,6 +407,15 @@ def mlp_forward(params, x):
     params, x = _f64(params), _f64(x).reshape(-1, MLP_IN)
     y = np.zeros(len(x))
     _load().orc_mlp_forward(_p(params, C.c_double), len(x), _p(x, C.c_double), _p(y, C.c_double))
+    return y
+
+
+def mlp_forward_bf16act(params, x):
+    """Forward pass with bfloat16-rounded layer inputs and double sums."""
+    params, x = _f64(params), _f64(x).reshape(-1, MLP_IN)
+    y = np.zeros(len(x))
+    _load().orc_mlp_forward_bf16act(_p(params, C.c_double), len(x), _p(x, C.c_double),
+                                    _p(y, C.c_double))
     return y
 
 

@@ -762,6 +762,37 @@ void orc_mlp_forward(const double* params, long long n, const double* x, double*
     for (long long k = 0; k < n; ++k) y[k] = mlp_sample(params, x + ORC_MLP_IN * k, act, pre);
 }
 
+/* The nearest bfloat16 (8 significant bits), ties to even. */
+static double round_bf16(double v) {
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    const double m = frexp(v, &e);           /* v = m 2^e, 0.5 <= |m| < 1 */
+    return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+/* The forward pass with every layer's input (the features and the three
+ * hidden activations after ReLU) rounded to bfloat16 before its products, the
+ * sums kept in double: the arithmetic of a tensor-core pass with bfloat16
+ * operands and wide accumulation.  The caller rounds the weights. */
+void orc_mlp_forward_bf16act(const double* params, long long n, const double* x, double* y) {
+    for (long long k = 0; k < n; ++k) {
+        double in[ORC_MLP_H], out[ORC_MLP_H];
+        for (int i = 0; i < ORC_MLP_IN; ++i) in[i] = round_bf16(x[ORC_MLP_IN * k + i]);
+        const double* w = params;
+        for (int l = 0; l < MLP_L; ++l) {
+            const double* b = w + mlp_out[l] * mlp_in[l];
+            for (int o = 0; o < mlp_out[l]; ++o) {
+                double s = b[o];
+                for (int i = 0; i < mlp_in[l]; ++i) s += w[o * mlp_in[l] + i] * in[i];
+                out[o] = (l < MLP_L - 1) ? round_bf16(s > 0.0 ? s : 0.0) : s;
+            }
+            for (int o = 0; o < mlp_out[l]; ++o) in[o] = out[o];
+            w = b + mlp_out[l];
+        }
+        y[k] = in[0];
+    }
+}
+
 double orc_mlp_loss_grad(const double* params, long long n, const double* x, const double* t,
                          double* grad) {
     const int np = orc_mlp_num_params();

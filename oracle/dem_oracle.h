@@ -124,6 +124,9 @@ void orc_integrate(const orc_model* m, int n, const int* tpl, double* pos, doubl
 #define ORC_MLP_H 64
 int orc_mlp_num_params(void);
 void orc_mlp_forward(const double* params, long long n, const double* x, double* y);
+/* As orc_mlp_forward with each layer's input rounded to bfloat16 (nearest,
+ * ties to even) and double sums: the tensor-core arithmetic. */
+void orc_mlp_forward_bf16act(const double* params, long long n, const double* x, double* y);
 /* Mean squared error over n samples and (grad != NULL) its gradient. */
 double orc_mlp_loss_grad(const double* params, long long n, const double* x, const double* t,
                          double* grad);

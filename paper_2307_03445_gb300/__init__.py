@@ -305,6 +305,13 @@ class Regressor:
         self._check(self.lib.dem_mlp_forward(self.h, len(x), _pf(x), _pf(y)))
         return y
 
+    def forward_tc(self, x):
+        """Forward pass on the tensor cores (bfloat16 layer inputs, FP32 sums)."""
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, 6)
+        y = np.zeros(len(x), np.float32)
+        self._check(self.lib.dem_mlp_forward_tc(self.h, len(x), _pf(x), _pf(y)))
+        return y
+
     def loss_grad(self, x, t):
         x = np.ascontiguousarray(x, np.float32).reshape(-1, 6)
         t = np.ascontiguousarray(t, np.float32)

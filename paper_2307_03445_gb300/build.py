@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdem.so")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
-SOURCES = ["dem_prims.cu", "dem_detect.cu", "dem_step.cu", "dem_api.cu", "dem_mlp.cu",
+SOURCES = ["dem_prims.cu", "dem_detect.cu", "dem_step.cu", "dem_api.cu", "dem_mlp.cu", "dem_mlp_tc.cu",
            "dem_learn.cu"]
 HEADERS = ["dem_internal.cuh", "dem_dev.cuh", "dem_prims.cuh", "dem_walls.cuh", "dem_mlp.cuh",
            "dem_learn.cuh"]

@@ -103,6 +103,7 @@ SIGNATURES = {
     "dem_mlp_get_params": (C.c_int, [_V, _F]),
     "dem_mlp_forward": (C.c_int, [_V, C.c_longlong, _F, _F]),
     "dem_mlp_loss_grad": (C.c_int, [_V, C.c_longlong, _F, _F, C.POINTER(C.c_double), _F]),
+    "dem_mlp_forward_tc": (C.c_int, [_V, C.c_longlong, _F, _F]),
     "dem_mlp_loss_grad_noalloc": (C.c_int, [_V, C.c_longlong, _F, _F, C.POINTER(C.c_double), _F]),
     "dem_mlp_train": (C.c_int, [_V, C.c_longlong, _F, _F, C.c_int, C.c_int, C.c_float,
                                 C.c_ulonglong, C.POINTER(C.c_double)]),

@@ -614,6 +614,7 @@ int read_flags(dem_ctx* c, bool* guard_hit = nullptr) {
   if (guard_hit) *guard_hit = (flags & kFlagGuard) != 0;
   if (flags & kFlagNonFinite) return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
   if (flags & kFlagBounds) return fail(c, DEM_ERR_STATE, "internal: narrow-phase row overflow");
+  if (flags & kFlagTimeout) return fail(c, DEM_ERR_TIMEOUT, "a bounded device wait ran out");
   return cuda_check(c, "step");
 }
 
@@ -660,7 +661,8 @@ int predict_margins(dem_ctx* c) {
   launch_bin_features(bs, ptr<uint32_t>(c->b_occ), nocc, nc, ptr<float>(c->b_cand), feature_scales(c),
                       ptr<float>(c->b_feat), c->st);
   if (c->mlp) {
-    mlp_forward_dev(mlp_weights(c->mlp), ptr<float>(c->b_feat), rows, ptr<float>(c->b_pred), c->st);
+    mlp_forward_tc_dev(mlp_weights(c->mlp), ptr<float>(c->b_feat), rows, ptr<float>(c->b_pred),
+                       ptr<int>(c->b_flags), c->st);
     const float ln_need = (float)std::log(std::max(1.0, c->l_interval * c->l_safety));
     launch_choose_margin(ptr<uint32_t>(c->b_occ), nocc, nc, ptr<float>(c->b_cand),
                          ptr<float>(c->b_pred), ln_need, ptr<float>(c->b_binm), c->st);

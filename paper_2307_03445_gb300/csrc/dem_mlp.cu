@@ -363,6 +363,28 @@ int dem_mlp_forward(dem_mlp* M, long long n, const float* x, float* y) {
   return cudaGetLastError() == cudaSuccess ? DEM_OK : DEM_ERR_CUDA;
 }
 
+int dem_mlp_forward_tc(dem_mlp* M, long long n, const float* x, float* y) {
+  if (!M || n < 0 || (n > 0 && (!x || !y))) return DEM_ERR_INVALID_ARG;
+  if (n == 0) return DEM_OK;
+  cudaSetDevice(M->device);
+  // rows, outputs and the timeout flag in one staging buffer
+  char* buf = (char*)stage(sizeof(float) * (size_t)n * (kIn + 1) + 16, M->st);
+  if (!buf) return mlp_fail(M, DEM_ERR_OOM, "staging");
+  float* dx = (float*)buf;
+  float* dy = dx + (size_t)n * kIn;
+  int* dflag = (int*)(dy + n);
+  cudaMemsetAsync(dflag, 0, sizeof(int), M->st);
+  cudaMemcpyAsync(dx, x, sizeof(float) * (size_t)n * kIn, cudaMemcpyHostToDevice, M->st);
+  mlp_forward_tc_dev(M->wq, dx, n, dy, dflag, M->st);
+  int flag = 0;
+  cudaMemcpyAsync(y, dy, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, M->st);
+  cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, M->st);
+  cudaStreamSynchronize(M->st);
+  if (cudaGetLastError() != cudaSuccess) return DEM_ERR_CUDA;
+  if (flag) return mlp_fail(M, DEM_ERR_TIMEOUT, "tensor-core forward: a barrier wait ran out");
+  return DEM_OK;
+}
+
 int dem_mlp_loss_grad(dem_mlp* M, long long n, const float* x, const float* t, double* loss,
                       float* grad) {
   if (!M || n <= 0 || !x || !t) return DEM_ERR_INVALID_ARG;

@@ -170,3 +170,61 @@ def test_trained_rule_beats_the_plain_rule(dem, bed):
     # replays after a rollback count towards the learned run's work
     assert sl["rebuilds"] < sp["rebuilds"], (sl, sp)
     assert sl["pair_steps"] < sp["pair_steps"], (sl, sp)
+
+
+def _sparse_exact_params(oracle_mod):
+    """Hidden unit o takes input o % 6 (x 0.5), then itself (x 2), then unit
+    o + 1 (x 1); the output sums the 64 units x 2^-6.  With inputs that are
+    small multiples of 1/4 every product and partial sum is exact, so a
+    misplaced row, column or K step shows up as an O(1) error."""
+    H, IN = 64, 6
+    p = np.zeros(oracle_mod.mlp_num_params(), np.float32)
+    k = 0
+    W1 = p[k:k + H * IN].reshape(H, IN)
+    for o in range(H):
+        W1[o, o % IN] = 0.5
+    k += H * IN + H
+    np.fill_diagonal(p[k:k + H * H].reshape(H, H), 2.0)
+    k += H * H + H
+    W3 = p[k:k + H * H].reshape(H, H)
+    for o in range(H):
+        W3[o, (o + 1) % H] = 1.0
+    k += H * H + H
+    p[k:k + H] = 2.0 ** -6
+    return p
+
+
+def test_tensor_core_forward_is_exact_on_an_exact_network(dem, oracle_mod):
+    p = _sparse_exact_params(oracle_mod)
+    reg = dem.Regressor(params=p)
+    rng = np.random.default_rng(9)
+    for n in (1, 127, 128, 129, 3001):
+        x = (rng.integers(-4, 8, size=(n, 6)) * 0.25).astype(np.float32)
+        want = oracle_mod.mlp_forward_bf16act(p.astype(np.float64), x.astype(np.float64))
+        assert np.array_equal(reg.forward_tc(x).astype(np.float64), want), n
+    reg.close()
+
+
+def test_tensor_core_forward_matches_oracle(dem, oracle_mod):
+    """The tcgen05 forward pass of a random network against the oracle pass
+    with bfloat16 layer inputs at the same bfloat16 weights, over ragged row
+    counts (partial last tiles).  The tensor cores sum the bfloat16 products
+    with less than IEEE FP32 care, so activations near a bfloat16 rounding
+    boundary may round the other way: the bound is a few bfloat16 steps."""
+    rng = np.random.default_rng(8)
+    p = (rng.normal(size=oracle_mod.mlp_num_params()) * 0.25).astype(np.float32)
+    reg = dem.Regressor(params=p)
+    pw = _bf16(p).astype(np.float64)
+    for n in (1, 127, 128, 129, 5000, 70001):
+        x = rng.normal(size=(n, 6)).astype(np.float32)
+        y = reg.forward_tc(x)
+        want = oracle_mod.mlp_forward_bf16act(pw, x.astype(np.float64))
+        scale = max(np.abs(want).max(), 1.0)
+        err = np.abs(y - want)
+        assert err.max() <= 2e-2 * scale, n
+        assert err.mean() <= 2e-3 * scale, n
+    # and it agrees with the FP32-activation pass to bfloat16 accuracy
+    x = rng.normal(size=(4096, 6)).astype(np.float32)
+    yf = reg.forward(x)
+    assert np.abs(reg.forward_tc(x) - yf).max() <= 5e-2 * max(np.abs(yf).max(), 1.0)
+    reg.close()

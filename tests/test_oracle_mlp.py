@@ -94,3 +94,56 @@ def test_training_reduces_the_loss(oracle_mod):
         p, m, v = oracle_mod.mlp_adam(p, m, v, g, k, lr=3e-3)
     l1, _ = oracle_mod.mlp_loss_grad(p, x, t)
     assert l1 < 0.05 * l0
+
+
+def _pass_through(oracle_mod):
+    """Parameters under which the network passes the first feature through
+    unit 0 of every layer (weights 1, everything else 0)."""
+    p = np.zeros(oracle_mod.mlp_num_params())
+    H, IN = 64, 6
+    k = 0
+    for n_in, n_out in ((IN, H), (H, H), (H, H), (H, 1)):
+        p[k + 0 * n_in + 0] = 1.0  # W[0][0]
+        k += n_in * n_out + n_out
+    return p
+
+
+def test_bf16_pass_rounds_every_layer_input(oracle_mod):
+    """Pinned by hand: 1 + 2^-8 lies halfway between the bfloat16 neighbours
+    1 and 1 + 2^-7 and rounds to the even one (1); 1 + 3 * 2^-8 rounds up to
+    1 + 2^-6; exact bfloat16 values pass unchanged; the double pass keeps them."""
+    p = _pass_through(oracle_mod)
+    x = np.zeros((4, 6))
+    x[:, 0] = [1 + 2 ** -8, 1 + 3 * 2 ** -8, 0.75, -2.0]
+    y16 = oracle_mod.mlp_forward_bf16act(p, x)
+    y64 = oracle_mod.mlp_forward(p, x)
+    assert list(y16) == [1.0, 1 + 2 ** -6, 0.75, 0.0]  # ReLU cuts the negative
+    assert list(y64) == [1 + 2 ** -8, 1 + 3 * 2 ** -8, 0.75, 0.0]
+
+
+def test_bf16_pass_equals_the_double_pass_on_exact_values(oracle_mod):
+    """A sparse network whose hidden activations are the inputs scaled by
+    powers of two (exact in bfloat16 for inputs with few significant bits):
+    the two passes agree exactly; with inputs that need more than 8 bits they
+    differ, by bfloat16 rounding only."""
+    H, IN = 64, 6
+    p = np.zeros(oracle_mod.mlp_num_params())
+    k = 0
+    W1 = p[k:k + H * IN].reshape(H, IN)
+    for o in range(H):
+        W1[o, o % IN] = 0.5
+    k += H * IN + H
+    W2 = p[k:k + H * H].reshape(H, H)
+    np.fill_diagonal(W2, 2.0)
+    k += H * H + H
+    W3 = p[k:k + H * H].reshape(H, H)
+    for o in range(H):
+        W3[o, (o + 1) % H] = 1.0
+    k += H * H + H
+    p[k:k + H] = 2.0 ** -6
+    rng = np.random.default_rng(5)
+    x = rng.integers(0, 8, size=(50, IN)) * 0.25
+    assert np.array_equal(oracle_mod.mlp_forward_bf16act(p, x), oracle_mod.mlp_forward(p, x))
+    x2 = x + 2.0 ** -12  # now 12+ significant bits
+    d = np.abs(oracle_mod.mlp_forward_bf16act(p, x2) - oracle_mod.mlp_forward(p, x2))
+    assert d.max() > 0 and d.max() <= 2.0 ** -8 * (1 + np.abs(x2).max())
