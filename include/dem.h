@@ -206,6 +206,15 @@ int dem_reset_stats(dem_ctx* ctx);
  * context stream; they are read once at the end of each dem_step call, so
  * the steps themselves are not serialised. */
 int dem_set_timing(dem_ctx* ctx, int timing);
+/* on = 1: deterministic reduction.  Every contact writes its force and
+ * moments to its own slot, and a per-clump pass adds the slots of each clump
+ * in a fixed order (slot lists built with each contact list), so that runs
+ * with the same inputs give bit-identical trajectories.  Costs one slot write
+ * and read per contact per step.  on = 0 (default): vector reductions into
+ * the accumulators, whose summation order varies from run to run.  The net
+ * forces on the walls are summed by atomics in both modes. */
+int dem_set_deterministic(dem_ctx* ctx, int on);
+
 /* Bin-size autotuner (the paper fixes no bin size; this picks one by timing).
  * For each of the n factors, the bin edge of every scene becomes the factor
  * times the scene's base edge (its bin_size, else twice the largest enlarged

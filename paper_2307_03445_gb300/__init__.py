@@ -218,6 +218,10 @@ class Simulation:
                                                _pd(ms)))
         return best.value, {float(a): (float(b) if b >= 0 else None) for a, b in zip(f, ms)}
 
+    def set_deterministic(self, on=True):
+        """Bit-reproducible force sums (per-contact slots summed in a fixed order)."""
+        self._check(self.lib.dem_set_deterministic(self.ctx, 1 if on else 0))
+
     def set_graphs(self, on=True):
         """Run the steps between rebuilds as one captured CUDA graph."""
         self._check(self.lib.dem_set_graphs(self.ctx, 1 if on else 0))

@@ -86,6 +86,7 @@ SIGNATURES = {
     "dem_reset_stats": (C.c_int, [_V]),
     "dem_set_timing": (C.c_int, [_V, C.c_int]),
     "dem_set_graphs": (C.c_int, [_V, C.c_int]),
+    "dem_set_deterministic": (C.c_int, [_V, C.c_int]),
     "dem_autotune_bins": (C.c_int, [_V, C.c_int, _D, C.c_int, _D, _D]),
     "dem_rebuild": (C.c_int, [_V]),
     "dem_eval_forces": (C.c_int, [_V]),

@@ -98,6 +98,10 @@ struct dem_ctx {
   int l_interval = 0;
   double l_safety = 1.0;
   int l_mode = 0;
+  // deterministic reduction: slot buffers and per-clump slot lists of the current list
+  int det = 0;
+  bool det_ready = false;
+  Buf b_det_cnt, b_det_fill, b_det_off, b_det_ids, b_det_pair, b_det_wall;
   std::vector<double> l_cand;
   long long n_occ = 0;
   Buf b_alast, b_chome, b_cmargin, b_bcnt, b_bvmax, b_bvsum, b_bamax, b_occ, b_nocc, b_binm, b_cand;
@@ -184,6 +188,19 @@ void qrot(const double* q, const double* p, double* o, bool transpose) {
   }
 }
 
+// Deterministic-reduction pointers of the device view (NULL unless the mode
+// is on and the slot lists of the current list exist).
+void set_det_pointers(dem_ctx* c) {
+  DevState& d = c->D;
+  const bool det = c->det && c->det_ready;
+  d.det_off = det ? ptr<uint32_t>(c->b_det_off) : nullptr;
+  d.det_ids = det ? ptr<uint32_t>(c->b_det_ids) : nullptr;
+  d.det_pair32 = det ? ptr<float4>(c->b_det_pair) : nullptr;
+  d.det_wall32 = det ? ptr<float4>(c->b_det_wall) : nullptr;
+  d.det_pair64 = det ? ptr<double4_32a>(c->b_det_pair) : nullptr;
+  d.det_wall64 = det ? ptr<double4_32a>(c->b_det_wall) : nullptr;
+}
+
 void refresh_devstate(dem_ctx* c) {
   DevState& d = c->D;
   d.prec = c->P.precision;
@@ -244,6 +261,36 @@ void refresh_devstate(dem_ctx* c) {
   d.counters = ptr<unsigned long long>(c->b_counters);
   d.dstep = ptr<long long>(c->b_dstep);
   d.halt_at = nullptr;  // set by the learned rule's halting intervals only
+  set_det_pointers(c);
+}
+
+ContactList& curL(dem_ctx* c);
+
+// Slot buffers and per-clump slot lists of the current list (deterministic
+// reduction); a no-op when the mode is off.
+int build_det_lists(dem_ctx* c) {
+  c->det_ready = false;
+  if (!c->det) {
+    set_det_pointers(c);
+    return DEM_OK;
+  }
+  ContactList& L = curL(c);
+  const long long ncl = c->ncl, n = L.n, nw = L.nw;
+  if (2 * n + nw >= (1ll << 32) - 1) return fail(c, DEM_ERR_CAPACITY, "deterministic mode: list too long");
+  const size_t slot = c->P.precision == DEM_FP64 ? 32 : 16;
+  if (!grow(c, c->b_det_cnt, 4 * (size_t)(ncl + 1)) || !grow(c, c->b_det_fill, 4 * (size_t)(ncl + 1)) ||
+      !grow(c, c->b_det_off, 4 * (size_t)(ncl + 1)) || !grow(c, c->b_det_ids, 4 * (size_t)(2 * n + nw + 1)) ||
+      !grow(c, c->b_det_pair, 3 * slot * (size_t)(L.cap + 1)) ||
+      !grow(c, c->b_det_wall, 2 * slot * (size_t)(L.capw + 1)))
+    return fail(c, DEM_ERR_OOM, "deterministic-mode buffers");
+  cudaMemsetAsync(c->b_det_cnt.p, 0, 4 * (size_t)(ncl + 1), c->st);
+  cudaMemsetAsync(c->b_det_fill.p, 0, 4 * (size_t)(ncl + 1), c->st);
+  launch_det_lists(c->D, L, n, nw, ptr<uint32_t>(c->b_det_cnt), ptr<uint32_t>(c->b_det_fill),
+                   ptr<uint32_t>(c->b_det_off), ptr<uint32_t>(c->b_det_ids), c->b_scan_scr.p,
+                   ptr<unsigned long long>(c->b_totals) + 6, c->st);
+  c->det_ready = true;
+  set_det_pointers(c);
+  return cuda_check(c, "deterministic lists");
 }
 
 ContactList& curL(dem_ctx* c) { return c->lists[c->cur].L; }
@@ -562,6 +609,7 @@ int rebuild(dem_ctx* c, double m, int K) {
   c->need_rebuild = false;
   c->since = 0;
   launch_set_cert_ref(c->D, c->st);
+  if ((rc = build_det_lists(c))) return rc;
   c->stats.rebuilds++;
   c->stats.bin_entries = c->n_entries;
   c->stats.n_pairs = N.n;
@@ -596,6 +644,7 @@ int force_pass(dem_ctx* c, bool count_active, cudaEvent_t mid = nullptr) {
   launch_force_pairs(c->D, L, count_active, c->st);
   if (mid) cudaEventRecord(mid, c->st);
   launch_force_walls(c->D, L, t, count_active, c->st);
+  if (c->D.det_off) launch_det_gather(c->D, L, c->st);
   return DEM_OK;
 }
 
@@ -1096,7 +1145,8 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_totals, &c->b_det, &c->b_bin_cnt, &c->b_bin_off, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_keys, &c->b_ids, &c->b_keys2, &c->b_ids2, &c->b_bin_start, &c->b_bin_end,
                 &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp, &c->b_lob,
-                &c->b_part, &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
+                &c->b_part, &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
+                &c->b_det_ids, &c->b_det_pair, &c->b_det_wall, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
                 &c->b_bcnt, &c->b_bvmax, &c->b_bvsum, &c->b_bamax, &c->b_occ, &c->b_nocc,
                 &c->b_binm, &c->b_cand, &c->b_feat, &c->b_pred, &c->b_dmax, &c->b_T, &c->b_tr_vox,
                 &c->b_tr_off, &c->b_tr_pos, &c->b_tr_q, &c->b_tx, &c->b_tt, &c->b_tcount,
@@ -1507,6 +1557,16 @@ int dem_autotune_bins(dem_ctx* c, int n, const double* factors, int reps, double
   c->stats.ms_detect = saved.ms_detect;
   *best = chosen;
   return cuda_check(c, "autotune");
+}
+
+int dem_set_deterministic(dem_ctx* c, int on) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  c->det = on ? 1 : 0;
+  c->det_ready = false;
+  c->need_rebuild = true;  // the slot lists are built with the next list
+  drop_graphs(c);
+  refresh_devstate(c);
+  return DEM_OK;
 }
 
 int dem_set_graphs(dem_ctx* c, int enabled) {

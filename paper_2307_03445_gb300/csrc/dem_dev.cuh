@@ -64,6 +64,15 @@ struct DevState {
   int* flags;
   unsigned long long* counters;  // [0] active contacts, [1] guard violations
   long long* dstep;         // device step counter: forces of step s see time s * h
+  // deterministic reduction (det_off NULL: vector reductions straight into
+  // the accumulators).  Each contact writes its force and moments to its own
+  // slot; a per-clump pass adds the slots of the clump in a fixed order.
+  float4* det_pair32;       // 3 per listed pair: F on b, moment on a, moment on b
+  float4* det_wall32;       // 2 per wall contact: F on the clump, its moment
+  double4_32a* det_pair64;  // FP64 mode, same layout
+  double4_32a* det_wall64;
+  const uint32_t* det_off;  // per clump: start of its slot ids (ncl + 1)
+  const uint32_t* det_ids;  // slot ids: 2k pair k side a, 2k + 1 side b, 2n + j wall contact j
   long long* halt_at;       // learned rule, halt mode: the first step whose state failed
                             //   the displacement certificate (LLONG_MAX: none); every
                             //   per-step kernel of a later step returns at once.  NULL: off
@@ -171,6 +180,13 @@ void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_
 void launch_update(const DevState& d, bool integrate, long long step, double margin,
                    bool check_cert, cudaStream_t st);
 void launch_walls_at(const DevState& d, long long step, cudaStream_t st);
+// Deterministic reduction: the clump slot lists of list l (cnt and fill are
+// ncl zeroed scratch words; off gets ncl + 1 entries, ids 2 n + nw), and the
+// per-clump sums of the slots into the accumulators.
+void launch_det_lists(const DevState& d, const ContactList& l, long long n, long long nw,
+                      uint32_t* cnt, uint32_t* fill, uint32_t* off, uint32_t* ids, void* scan_scratch,
+                      unsigned long long* d_total, cudaStream_t st);
+void launch_det_gather(const DevState& d, const ContactList& l, cudaStream_t st);
 void launch_set_cert_ref(const DevState& d, cudaStream_t st);
 void launch_get_state(const DevState& d, double* pos, double* quat, double* vel, double* angvel,
                       cudaStream_t st);

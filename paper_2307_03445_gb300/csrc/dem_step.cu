@@ -120,6 +120,10 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     }
     if (!active) {
       if (bw & kHistFlag) l.pb[i] = b;  // history reset (false positive)
+      if (d.det_off) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.det_pair32[3 * i] = z; d.det_pair32[3 * i + 1] = z; d.det_pair32[3 * i + 2] = z;
+      }
       continue;
     }
     const V3<float> n = {fx / dist, fy / dist, fz / dist};
@@ -153,8 +157,15 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     l.u[2 * l.cap + i] = u2;
     if (!(bw & kHistFlag)) l.pb[i] = b | kHistFlag;
     const V3<float> F = law.F;
-    add_clump32(d.acc32, B.owner, F, cross(cb, F));
-    add_clump32(d.acc32, A.owner, -1.f * F, -1.f * cross(ca, F));
+    const V3<float> Ta = -1.f * cross(ca, F), Tb = cross(cb, F);
+    if (d.det_off) {
+      d.det_pair32[3 * i] = make_float4(F.x, F.y, F.z, 0.f);
+      d.det_pair32[3 * i + 1] = make_float4(Ta.x, Ta.y, Ta.z, 0.f);
+      d.det_pair32[3 * i + 2] = make_float4(Tb.x, Tb.y, Tb.z, 0.f);
+    } else {
+      add_clump32(d.acc32, B.owner, F, Tb);
+      add_clump32(d.acc32, A.owner, -1.f * F, Ta);
+    }
   }
 }
 
@@ -175,6 +186,10 @@ __global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int 
     if (count_active) warp_count(active, d.counters);
     if (!active) {
       if (bw & kHistFlag) l.pb[i] = b;
+      if (d.det_off) {
+        const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        d.det_pair64[3 * i] = z; d.det_pair64[3 * i + 1] = z; d.det_pair64[3 * i + 2] = z;
+      }
       continue;
     }
     const V3<double> n = (1.0 / dist) * dv;
@@ -199,8 +214,15 @@ __global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int 
     l.u[l.cap + i] = un.y;
     l.u[2 * l.cap + i] = un.z;
     if (!(bw & kHistFlag)) l.pb[i] = b | kHistFlag;
-    add_clump64(d.acc64, ob, law.F, cross(cb, law.F));
-    add_clump64(d.acc64, oa, -1.0 * law.F, -1.0 * cross(ca, law.F));
+    const V3<double> Ta = -1.0 * cross(ca, law.F), Tb = cross(cb, law.F);
+    if (d.det_off) {
+      d.det_pair64[3 * i] = make_double4_32a(law.F.x, law.F.y, law.F.z, 0.0);
+      d.det_pair64[3 * i + 1] = make_double4_32a(Ta.x, Ta.y, Ta.z, 0.0);
+      d.det_pair64[3 * i + 2] = make_double4_32a(Tb.x, Tb.y, Tb.z, 0.0);
+    } else {
+      add_clump64(d.acc64, ob, law.F, Tb);
+      add_clump64(d.acc64, oa, -1.0 * law.F, Ta);
+    }
   }
 }
 
@@ -238,6 +260,10 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     if (count_active) warp_count(active, d.counters);
     if (!active) {
       if (wwv & kHistFlag) l.ww[i] = w;
+      if (d.det_off) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.det_wall32[2 * i] = z; d.det_wall32[2 * i + 1] = z;
+      }
       continue;
     }
     const float4 RS = d.sb32[s];
@@ -263,7 +289,13 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     l.uw[l.capw + i] = u1;
     l.uw[2 * l.capw + i] = u2;
     if (!(wwv & kHistFlag)) l.ww[i] = w | kHistFlag;
-    add_clump32(d.acc32, S.owner, -1.f * law.F, -1.f * cross(ca, law.F));
+    const V3<float> Fs = -1.f * law.F, Ts = -1.f * cross(ca, law.F);
+    if (d.det_off) {
+      d.det_wall32[2 * i] = make_float4(Fs.x, Fs.y, Fs.z, 0.f);
+      d.det_wall32[2 * i + 1] = make_float4(Ts.x, Ts.y, Ts.z, 0.f);
+    } else {
+      add_clump32(d.acc32, S.owner, Fs, Ts);
+    }
     if (shared_wf) {
       atomicAdd(&s_wf[3 * w], law.F.x);
       atomicAdd(&s_wf[3 * w + 1], law.F.y);
@@ -297,6 +329,10 @@ __global__ void k_walls64(DevState d, ContactList l, int count_active) {
     if (count_active) warp_count(active, d.counters);
     if (!active) {
       if (wwv & kHistFlag) l.ww[i] = w;
+      if (d.det_off) {
+        const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        d.det_wall64[2 * i] = z; d.det_wall64[2 * i + 1] = z;
+      }
       continue;
     }
     const V3<double> n = {-nw[0], -nw[1], -nw[2]};
@@ -316,7 +352,13 @@ __global__ void k_walls64(DevState d, ContactList l, int count_active) {
     l.uw[l.capw + i] = un.y;
     l.uw[2 * l.capw + i] = un.z;
     if (!(wwv & kHistFlag)) l.ww[i] = w | kHistFlag;
-    add_clump64(d.acc64, os, -1.0 * law.F, -1.0 * cross(ca, law.F));
+    const V3<double> Fs = -1.0 * law.F, Ts = -1.0 * cross(ca, law.F);
+    if (d.det_off) {
+      d.det_wall64[2 * i] = make_double4_32a(Fs.x, Fs.y, Fs.z, 0.0);
+      d.det_wall64[2 * i + 1] = make_double4_32a(Ts.x, Ts.y, Ts.z, 0.0);
+    } else {
+      add_clump64(d.acc64, os, Fs, Ts);
+    }
     double* fw = d.wforce + 3 * (long long)w;
     atomicAdd(fw, law.F.x);
     atomicAdd(fw + 1, law.F.y);
@@ -672,6 +714,98 @@ __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, fl
   update32_batch(d, (long long)blockIdx.x * kUpd, integrate, margin, check_cert, sh);
 }
 
+// ---------------------------------------------------------------------------
+// deterministic reduction: per-clump lists of contribution slots, built at a
+// rebuild, and the per-clump sums in list order
+// ---------------------------------------------------------------------------
+__global__ void k_det_count(DevState d, ContactList l, long long n, long long nw,
+                            uint32_t* __restrict__ cnt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    atomicAdd(&cnt[d.sinfo[l.pa[i]].x], 1u);
+    atomicAdd(&cnt[d.sinfo[l.pb[i] & ~kHistFlag].x], 1u);
+  } else if (i < n + nw) {
+    atomicAdd(&cnt[d.sinfo[l.ws[i - n]].x], 1u);
+  }
+}
+
+__global__ void k_det_fill(DevState d, ContactList l, long long n, long long nw,
+                           const uint32_t* __restrict__ off, uint32_t* __restrict__ fill,
+                           uint32_t* __restrict__ ids) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int ca = d.sinfo[l.pa[i]].x, cb = d.sinfo[l.pb[i] & ~kHistFlag].x;
+    ids[off[ca] + atomicAdd(&fill[ca], 1u)] = (uint32_t)(2 * i);
+    ids[off[cb] + atomicAdd(&fill[cb], 1u)] = (uint32_t)(2 * i + 1);
+  } else if (i < n + nw) {
+    const int c = d.sinfo[l.ws[i - n]].x;
+    ids[off[c] + atomicAdd(&fill[c], 1u)] = (uint32_t)(2 * n + (i - n));
+  }
+}
+
+// each clump's slot ids in ascending order (insertion sort: lists are short)
+__global__ void k_det_sort(long long ncl, const uint32_t* __restrict__ off, uint32_t* __restrict__ ids) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncl) return;
+  const uint32_t r0 = off[c], r1 = off[c + 1];
+  for (uint32_t i = r0 + 1; i < r1; ++i) {
+    const uint32_t v = ids[i];
+    uint32_t j = i;
+    while (j > r0 && ids[j - 1] > v) {
+      ids[j] = ids[j - 1];
+      --j;
+    }
+    ids[j] = v;
+  }
+}
+
+__global__ void k_det_gather(DevState d, ContactList l) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (halted(d) || c >= d.ncl) return;
+  const long long n2 = 2 * l.dn[0];
+  const uint32_t r0 = d.det_off[c], r1 = d.det_off[c + 1];
+  if (d.prec == 0) {
+    V3<double> F = {0.0, 0.0, 0.0}, T = {0.0, 0.0, 0.0};
+    for (uint32_t r = r0; r < r1; ++r) {
+      const long long id = d.det_ids[r];
+      if (id < n2) {
+        const long long k = id >> 1;
+        const double4_32a f = d.det_pair64[3 * k], t = d.det_pair64[3 * k + 1 + (id & 1)];
+        const double sg = (id & 1) ? 1.0 : -1.0;
+        F = F + sg * V3<double>{f.x, f.y, f.z};
+        T = T + V3<double>{t.x, t.y, t.z};
+      } else {
+        const long long j = id - n2;
+        const double4_32a f = d.det_wall64[2 * j], t = d.det_wall64[2 * j + 1];
+        F = F + V3<double>{f.x, f.y, f.z};
+        T = T + V3<double>{t.x, t.y, t.z};
+      }
+    }
+    double* acc = d.acc64 + 8 * c;
+    acc[0] = F.x; acc[1] = F.y; acc[2] = F.z; acc[3] = T.x; acc[4] = T.y; acc[5] = T.z;
+  } else {
+    V3<float> F = {0.f, 0.f, 0.f}, T = {0.f, 0.f, 0.f};
+    for (uint32_t r = r0; r < r1; ++r) {
+      const long long id = d.det_ids[r];
+      if (id < n2) {
+        const long long k = id >> 1;
+        const float4 f = d.det_pair32[3 * k], t = d.det_pair32[3 * k + 1 + (id & 1)];
+        const float sg = (id & 1) ? 1.f : -1.f;
+        F = F + sg * V3<float>{f.x, f.y, f.z};
+        T = T + V3<float>{t.x, t.y, t.z};
+      } else {
+        const long long j = id - n2;
+        const float4 f = d.det_wall32[2 * j], t = d.det_wall32[2 * j + 1];
+        F = F + V3<float>{f.x, f.y, f.z};
+        T = T + V3<float>{t.x, t.y, t.z};
+      }
+    }
+    float* acc = d.acc32 + 8 * c;
+    *reinterpret_cast<float4*>(acc) = make_float4(F.x, F.y, F.z, T.x);
+    *reinterpret_cast<float4*>(acc + 4) = make_float4(T.y, T.z, 0.f, 0.f);
+  }
+}
+
 __device__ __forceinline__ void place_walls(const DevState& d, double t) {
   for (int w = threadIdx.x; w < d.nwalls; w += blockDim.x) {
     const WallDev& W = d.walls[w];
@@ -823,6 +957,24 @@ void launch_update(const DevState& d, bool integrate, long long step, double mar
 
 void launch_walls_at(const DevState& d, long long step, cudaStream_t st) {
   k_walls_at<<<1, 256, 0, st>>>(d, step);
+  count_launch();
+}
+
+void launch_det_lists(const DevState& d, const ContactList& l, long long n, long long nw,
+                      uint32_t* cnt, uint32_t* fill, uint32_t* off, uint32_t* ids, void* scan_scratch,
+                      unsigned long long* d_total, cudaStream_t st) {
+  if (d.ncl == 0) return;
+  const long long m = n + nw;
+  if (m > 0) { k_det_count<<<nblk(m, 256), 256, 0, st>>>(d, l, n, nw, cnt); count_launch(); }
+  exclusive_scan_u32(cnt, off, d.ncl + 1, scan_scratch, d_total, st);
+  if (m > 0) { k_det_fill<<<nblk(m, 256), 256, 0, st>>>(d, l, n, nw, off, fill, ids); count_launch(); }
+  k_det_sort<<<nblk(d.ncl, 256), 256, 0, st>>>(d.ncl, off, ids);
+  count_launch();
+}
+
+void launch_det_gather(const DevState& d, const ContactList& l, cudaStream_t st) {
+  if (d.ncl == 0) return;
+  k_det_gather<<<nblk(d.ncl, 256), 256, 0, st>>>(d, l);
   count_launch();
 }
 
