@@ -210,7 +210,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
     loss = reg.train(x, t, steps=800, batch=8192, lr=2e-3, seed=1)
     log(f"learned form: {len(x)} trace samples, loss {loss:.4f}, {time.time() - t0:.1f} s")
     # interval x safety stays inside the traced window, where lifetimes are not capped
-    sim.set_learned_policy(reg, interval=80, safety=1.5, candidates=LEARN_CAND)
+    sim.set_learned_policy(reg, interval=80, safety=2.0, candidates=LEARN_CAND)
     sim.reset_stats()
     sim.set_timing(True)  # events only: the steps are not serialised
     ms = _timed_steps(sim, stream, steps)
@@ -227,7 +227,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
             "ms_predict_per_interval": st["ms_predict"] / max(1, st["rebuilds"]),
             "ms_rebuild_per_interval": st["ms_detect"] / max(1, st["rebuilds"]),
             "rule": "6->3x64->1 MLP (BF16 weights) per bin, candidates 1-32 um, target "
-                    "interval 80 x 1.5, halt on certificate; trained on 2 x 240-step traces"}
+                    "interval 80 x 2.0, halt on certificate; trained on 2 x 240-step traces"}
 
 
 def sim_device(sim):

@@ -500,6 +500,18 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
   float4* sOff = sh.off;
   const long long c = c0 + threadIdx.x;
   if (c < d.ncl) {
+    // every global load of the clump is issued first (one memory round trip)
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, ref_o = a0, ref_qv = a0;
+    int4 ref_v = make_int4(0, 0, 0, 0);
+    if (integrate) {
+      a0 = *reinterpret_cast<const float4*>(d.acc32 + 8 * c);
+      a1 = *reinterpret_cast<const float4*>(d.acc32 + 8 * c + 4);
+      if (check_cert) {
+        ref_v = d.ref_vox[c];
+        ref_o = d.ref_off[c];
+        ref_qv = d.ref_q[c];
+      }
+    }
     const int tpl = d.cinfo[c].x;
     int4 vox = d.cvox[c];
     float4 off = d.coff[c];
@@ -518,8 +530,6 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
     }
     if (integrate) {
       float* acc = d.acc32 + 8 * c;
-      const float4 a0 = *reinterpret_cast<const float4*>(acc);
-      const float4 a1 = *reinterpret_cast<const float4*>(acc + 4);
       *reinterpret_cast<float4*>(acc) = make_float4(0.f, 0.f, 0.f, 0.f);
       *reinterpret_cast<float4*>(acc + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
       const float hf = d.hf;
@@ -592,12 +602,12 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
         atomicOr(d.flags, kFlagNonFinite);
       d.cvox[c] = vox; d.coff[c] = off; d.cq[c] = q4; d.cv[c] = v; d.cw[c] = w;
       if (check_cert) {
-        const int4 v0 = d.ref_vox[c];
-        const float4 o0 = d.ref_off[c];
+        const int4 v0 = ref_v;
+        const float4 o0 = ref_o;
         const float dx = (float)(vox.x - v0.x) * kV + (off.x - o0.x);
         const float dy = (float)(vox.y - v0.y) * kV + (off.y - o0.y);
         const float dz = (float)(vox.z - v0.z) * kV + (off.z - o0.z);
-        const float4 r0 = d.ref_q[c];
+        const float4 r0 = ref_qv;
         const float a[4] = {r0.x, -r0.y, -r0.z, -r0.w};
         const float b[4] = {qw.h, qx.h, qy.h, qz.h};
         float e[4];
@@ -682,35 +692,11 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
   }
 }
 
-// Sets L2 prefetches for the clump state of a later batch.
-__device__ __forceinline__ void prefetch_batch(const DevState& d, long long c0, int integrate,
-                                               int check_cert) {
-  const long long c = c0 + threadIdx.x;
-  if (c >= d.ncl) return;
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cvox + c));
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.coff + c));
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cq + c));
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cv + c));
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cw + c));
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cinfo + c));
-  if (integrate) {
-    asm volatile("prefetch.global.L2 [%0];" :: "l"(d.acc32 + 8 * c));
-    if (check_cert) {
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.ref_vox + c));
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.ref_off + c));
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.ref_q + c));
-    }
-  }
-}
-
-// One block per batch of kUpd clumps.  Each block first prefetches into L2
-// the state of the batch `ahead` blocks later (about one wave of resident
-// blocks), which starts when a block of the current wave retires.
+// One block per batch of kUpd clumps.
 __global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, float margin,
-                                                   int check_cert, int ahead) {
+                                                   int check_cert) {
   if (integrate && halted(d)) return;
   __shared__ UpdShared sh;
-  prefetch_batch(d, ((long long)blockIdx.x + ahead) * kUpd, integrate, check_cert);
   update32_batch(d, (long long)blockIdx.x * kUpd, integrate, margin, check_cert, sh);
 }
 
@@ -944,7 +930,7 @@ void launch_update(const DevState& d, bool integrate, long long step, double mar
                                                       check_cert ? 1 : 0); count_launch(); }
     else
       { k_update32<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
-                                                      check_cert ? 1 : 0, sm_count() * 7);
+                                                      check_cert ? 1 : 0);
         count_launch(); }
   }
   if (integrate) {
