@@ -82,7 +82,7 @@ struct alignas(32) SphA64 {  // FP64
 // for every input class (zero, subnormal, infinite and NaN included), so that
 // no branch the compiler may predicate brings a hardware conversion back.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double f2d(float f) {
+static __device__ __noinline__ double f2d_rare(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t e = (u >> 23) & 0xffu;
   const uint32_t m = u & 0x7fffffu;
@@ -100,7 +100,7 @@ __device__ __forceinline__ double f2d(float f) {
   return __longlong_as_double((long long)bits);
 }
 // double -> float, rounded to nearest, ties to even.
-__device__ __forceinline__ float d2f(double d) {
+static __device__ __noinline__ float d2f_rare(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
   const int ed = (int)((b >> 52) & 0x7ffu);
@@ -124,6 +124,32 @@ __device__ __forceinline__ float d2f(double d) {
   const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
   if (rem > half || (rem == half && (q & 1u))) q += 1u;  // may reach the smallest normal
   return __uint_as_float(sign | q);
+}
+// Normal numbers and zeros inline; the other classes out of line, so that the
+// compiler does not predicate their code into every call.
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (e - 1u < 254u)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+  if ((u << 1) == 0u) return __longlong_as_double((long long)sign);
+  return f2d_rare(f);
+}
+__device__ __forceinline__ float d2f(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+  if ((unsigned)(e - 1) < 254u) {
+    const unsigned long long m = b & 0xfffffffffffffull;
+    uint32_t r = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
+    const uint32_t rem = (uint32_t)(m & 0x1fffffffu);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r += 1u;
+    return __uint_as_float(r | sign);
+  }
+  if ((b << 1) == 0ull) return __uint_as_float(sign);
+  return d2f_rare(d);
 }
 // Integer -> float for |v| < 2^22, exact: the float 1.5 * 2^23 has a unit
 // last place, so adding v to its bit pattern and subtracting it is exact.
