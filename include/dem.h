@@ -195,8 +195,14 @@ int dem_get_state(dem_ctx* ctx, double* pos, double* quat, double* vel, double* 
                   int on_device);
 
 /* Overwrites the state of all clumps (host pointers, same layout as
- * dem_get_state).  The next step rebuilds the list; tangential history is kept
- * for pairs that stay listed. */
+ * dem_get_state; page-locked memory makes the copies DMA transfers).  The next
+ * step rebuilds the list; tangential history is kept for pairs that stay
+ * listed.  Once the context has stepped or rebuilt, the arrays are copied as
+ * given into a device staging buffer (13 doubles per clump, kept by the
+ * context) and validated and converted there; before that they are converted
+ * on the host.  Errors: DEM_ERR_NONFINITE for a NaN or infinity,
+ * DEM_ERR_INVALID_ARG (FP32_VOXEL) for a position more than 2e9 voxels from
+ * its scene's corner; in both cases no clump record changes. */
 int dem_set_state(dem_ctx* ctx, const double* pos, const double* quat, const double* vel,
                   const double* angvel);
 

@@ -143,9 +143,16 @@ class Simulation:
     def step(self, n=1):
         self._check(self.lib.dem_step(self.ctx, int(n)))
 
-    def state(self):
+    def state(self, out=None):
+        """(pos, quat, vel, angvel) as float64 host arrays; `out` may give four
+        C-contiguous float64 arrays of shapes (n,3), (n,4), (n,3), (n,3) to
+        fill (e.g. views of pinned host memory)."""
         n = self.n
-        out = [np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 3)), np.zeros((n, 3))]
+        if out is None:
+            out = [np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 3)), np.zeros((n, 3))]
+        for o, w in zip(out, (3, 4, 3, 3)):
+            if o.dtype != np.float64 or o.shape != (n, w) or not o.flags.c_contiguous:
+                raise ValueError("state(out=...) wants C-contiguous float64 arrays of the state's shapes")
         self._check(self.lib.dem_get_state(self.ctx, *(o.ctypes.data for o in out), 0))
         return tuple(out)
 

@@ -1363,17 +1363,43 @@ int dem_set_state(dem_ctx* c, const double* pos, const double* quat, const doubl
   if (!c || !pos || !quat || !vel || !angvel) return DEM_ERR_INVALID_ARG;
   cudaSetDevice(c->P.device);
   const long long n = c->ncl;
-  if (!finite_all(pos, 3 * n) || !finite_all(quat, 4 * n) || !finite_all(vel, 3 * n) || !finite_all(angvel, 3 * n))
-    return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
-  int rc = upload_clumps(c, 0, (int)n, c->h_ctpl.data(), pos, quat, vel, angvel);
+  if (!c->finalized) {
+    // before the first step the scene grids do not exist yet: convert on the host
+    if (!finite_all(pos, 3 * n) || !finite_all(quat, 4 * n) || !finite_all(vel, 3 * n) ||
+        !finite_all(angvel, 3 * n))
+      return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
+    int rc = upload_clumps(c, 0, (int)n, c->h_ctpl.data(), pos, quat, vel, angvel);
+    if (rc) return rc;
+    c->need_rebuild = true;
+    c->acc_dirty = true;
+    return DEM_OK;
+  }
+  if (n == 0) return DEM_OK;
+  // stage the arrays as given (one copy each), validate and convert on the
+  // device; a rejected state leaves the clump records untouched
+  const size_t un = (size_t)n;
+  if (!grow(c, c->b_tmp, 8 * 13 * un + 16)) return fail(c, DEM_ERR_OOM, "staging");
+  double* t = ptr<double>(c->b_tmp);
+  int* err = reinterpret_cast<int*>(t + 13 * un);
+  cudaMemcpyAsync(t, pos, 24 * un, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(t + 3 * un, quat, 32 * un, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(t + 7 * un, vel, 24 * un, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(t + 10 * un, angvel, 24 * un, cudaMemcpyHostToDevice, c->st);
+  cudaMemsetAsync(err, 0, sizeof(int), c->st);
+  refresh_devstate(c);
+  launch_check_state(c->D, t, err, c->st);
+  int bad = 0;
+  cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  int rc = cuda_check(c, "set_state");
   if (rc) return rc;
+  if (bad & 1) return fail(c, DEM_ERR_NONFINITE, "non-finite clump state");
+  if (bad & 2) return fail(c, DEM_ERR_INVALID_ARG, "clump too far from its scene corner");
+  launch_set_state(c->D, t, c->st);
   c->need_rebuild = true;
   c->acc_dirty = true;
-  if (c->finalized) {
-    refresh_devstate(c);
-    launch_update(c->D, false, c->step, c->margin, false, c->st);
-    cudaStreamSynchronize(c->st);
-  }
+  launch_update(c->D, false, c->step, c->margin, false, c->st);
+  cudaStreamSynchronize(c->st);
   return cuda_check(c, "set_state");
 }
 

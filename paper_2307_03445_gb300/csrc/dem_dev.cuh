@@ -190,6 +190,9 @@ void launch_det_gather(const DevState& d, const ContactList& l, cudaStream_t st)
 void launch_set_cert_ref(const DevState& d, cudaStream_t st);
 void launch_get_state(const DevState& d, double* pos, double* quat, double* vel, double* angvel,
                       cudaStream_t st);
+// Staged state: pos (3n) | quat (4n) | vel (3n) | angvel (3n) doubles.
+void launch_check_state(const DevState& d, const double* staged, int* err, cudaStream_t st);
+void launch_set_state(const DevState& d, const double* staged, cudaStream_t st);
 void launch_get_forces(const DevState& d, double* F, double* T, cudaStream_t st);
 
 }  // namespace dem

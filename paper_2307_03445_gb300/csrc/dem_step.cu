@@ -867,6 +867,66 @@ __global__ void k_get_state(DevState d, double* pos, double* quat, double* vel, 
   }
 }
 
+// Voxel split of one position coordinate relative to the scene corner:
+// rel = m * 2^-20 + off with m = rint(rel * 2^20).  Both products are exact
+// (powers of two) and rel - m * 2^-20 is exact (Sterbenz), so the split is the
+// same whether or not the compiler contracts it.
+__device__ __forceinline__ double voxel_index(double x, double lo) { return rint((x - lo) / kVoxel); }
+
+// Validation pass over a staged state (pos 3n | quat 4n | vel 3n | angvel 3n
+// doubles): bit 0 of *err for a non-finite value, bit 1 for a position too far
+// from its scene corner for the int32 voxel index.  Nothing is written to the
+// clump state, so a rejected call leaves it as it was.
+__global__ void k_check_state(DevState d, const double* t, int* err) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.ncl) return;
+  const long long n = d.ncl;
+  bool finite = true;
+  for (int k = 0; k < 3; ++k) finite &= isfinite(t[3 * c + k]) && isfinite(t[7 * n + 3 * c + k]) &&
+                                        isfinite(t[10 * n + 3 * c + k]);
+  for (int k = 0; k < 4; ++k) finite &= isfinite(t[3 * n + 4 * c + k]);
+  int e = finite ? 0 : 1;
+  if (finite && d.prec != 0) {
+    const SceneGrid g = d.grids[d.cinfo[c].y];
+    for (int k = 0; k < 3; ++k)
+      if (fabs(voxel_index(t[3 * c + k], g.lo[k])) > 2.0e9) e |= 2;
+  }
+  if (e) atomicOr(err, e);
+}
+
+// Writes a validated staged state into the clump records: quaternion and
+// velocity as given, the angular velocity rotated into the body frame
+// (w_body = R(q)^T w), the position as FP64 or as voxel index + float offset.
+__global__ void k_set_state(DevState d, const double* t) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.ncl) return;
+  const long long n = d.ncl;
+  const double* p = t + 3 * c;
+  const double* q = t + 3 * n + 4 * c;
+  const double* v = t + 7 * n + 3 * c;
+  const double* w = t + 10 * n + 3 * c;
+  d.cq[c] = make_double4_32a(q[0], q[1], q[2], q[3]);
+  d.cv[c] = make_double4_32a(v[0], v[1], v[2], 0.0);
+  double R[9];
+  quat_to_mat(q[0], q[1], q[2], q[3], R);
+  const V3<double> wb = mat_tmul(R, V3<double>{w[0], w[1], w[2]});
+  d.cw[c] = make_double4_32a(wb.x, wb.y, wb.z, 0.0);
+  if (d.prec == 0) {
+    d.cpos[c] = make_double4_32a(p[0], p[1], p[2], 0.0);
+  } else {
+    const SceneGrid g = d.grids[d.cinfo[c].y];
+    int vox[3];
+    float off[3];
+    for (int k = 0; k < 3; ++k) {
+      const double m = voxel_index(p[k], g.lo[k]);
+      vox[k] = (int)m;
+      off[k] = (float)((p[k] - g.lo[k]) - m * kVoxel);
+    }
+    d.cvox[c] = make_int4(vox[0], vox[1], vox[2], 0);
+    d.coff[c] = make_float4(off[0], off[1], off[2], 0.f);
+  }
+}
+
 __global__ void k_get_forces(DevState d, double* F, double* T) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.ncl) return;
@@ -971,6 +1031,14 @@ void launch_set_cert_ref(const DevState& d, cudaStream_t st) {
 void launch_get_state(const DevState& d, double* pos, double* quat, double* vel, double* angvel,
                       cudaStream_t st) {
   if (d.ncl > 0) { k_get_state<<<nblk(d.ncl, 256), 256, 0, st>>>(d, pos, quat, vel, angvel); count_launch(); }
+}
+
+void launch_check_state(const DevState& d, const double* staged, int* err, cudaStream_t st) {
+  if (d.ncl > 0) { k_check_state<<<nblk(d.ncl, 256), 256, 0, st>>>(d, staged, err); count_launch(); }
+}
+
+void launch_set_state(const DevState& d, const double* staged, cudaStream_t st) {
+  if (d.ncl > 0) { k_set_state<<<nblk(d.ncl, 256), 256, 0, st>>>(d, staged); count_launch(); }
 }
 
 void launch_get_forces(const DevState& d, double* F, double* T, cudaStream_t st) {

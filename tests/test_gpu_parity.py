@@ -5,6 +5,7 @@ on the same lattice).  Per-clump force and torque totals: within 1e-12 (FP64)
 or 1e-5 (FP32_VOXEL) of the oracle, relative to the sum of the magnitudes of
 the contributions to that total (the scale that bounds the rounding of a sum).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -72,8 +73,6 @@ def test_detection_bit_exact(dem, oracle_mod, prec, seed, n, bin_scale):
 def test_autotuned_bins_stay_exact(dem, oracle_mod, prec):
     """The bin-size autotuner keeps the fastest factor; the state is unchanged
     and detection at the chosen bin edge is still the oracle's, bit for bit."""
-    import dataclasses
-
     margin, K = 1e-4, 10
     sc = _scene(4, 700, prec, margin=margin)
     factors = (0.4, 0.7, 1.0, 2.0)
@@ -332,6 +331,58 @@ def test_non_finite_input_rejected(dem):
     set_clumps(sc, [0], [[0.0, 0.0, np.nan]])
     with pytest.raises(dem.DemError, match="NONFINITE"):
         dem.Simulation(sc, margin=1e-5)
+
+
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+def test_set_state_converts_on_the_device(dem, oracle_mod, prec):
+    """A state set after the first rebuild is staged as given and converted by
+    kernels: quaternions and velocities unchanged; positions exact in FP64 and,
+    in FP32_VOXEL, split into rint((x - lo) 2^20) voxels plus the float of the
+    remainder (restated here in numpy); body-frame angular velocity that
+    rotates back to the given one; sphere poses refreshed, so the forces are
+    the oracle's for the new state.  Rejected states (a non-finite value, a
+    position beyond the int32 voxel range) leave the records untouched."""
+    margin, K, n = 1e-4, 10, 400
+    sc = _scene(6, n, prec, margin=margin)
+    rng = np.random.default_rng(17)
+    pos = sc.pos + rng.uniform(-2e-6, 2e-6, sc.pos.shape)  # off the voxel lattice
+    quat = scenes.random_quaternions(rng, n)
+    vel = rng.normal(scale=0.1, size=(n, 3))
+    angvel = rng.normal(scale=30.0, size=(n, 3))
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        sim.rebuild()  # finalized: the state goes through the device kernels
+        sim.set_state(pos, quat, vel, angvel)
+        P, Q, V, W = sim.state()
+        F, T = sim.eval_forces()
+        bad = pos.copy()
+        bad[7, 1] = np.inf
+        with pytest.raises(dem.DemError, match="NONFINITE"):
+            sim.set_state(bad, quat, vel, angvel)
+        if prec == scenes.PREC_FP32:
+            far = pos.copy()
+            far[3, 0] = sc.lo[0] + 3000.0  # 3000 * 2^20 voxels > 2^31
+            with pytest.raises(dem.DemError, match="INVALID"):
+                sim.set_state(far, quat, vel, angvel)
+        after = sim.state()
+    assert np.array_equal(Q, quat) and np.array_equal(V, vel)
+    if prec == scenes.PREC_FP64:
+        expect = pos
+    else:
+        lo = np.asarray(sc.lo, dtype=np.float64)
+        rel = pos - lo
+        m = np.rint(rel * 2.0**20)
+        off = (rel - m * 2.0**-20).astype(np.float32).astype(np.float64)
+        expect = lo + (m * 2.0**-20 + off)
+    assert np.array_equal(P, expect)
+    assert np.abs(W - angvel).max() <= 1e-13 * np.abs(angvel).max()
+    for x, y in zip(after, (P, Q, V, W)):
+        assert np.array_equal(x, y)
+    moved = dataclasses.replace(sc, pos=expect, quat=quat, vel=vel, angvel=angvel)
+    om, _, _, a, b, ws, ww = _oracle_lists(oracle_mod, moved, margin, K)
+    Fo, To, _, _, _, _, mag = om.forces(sc.tpl, expect, quat, vel, angvel, 0.0, a, b,
+                                        np.zeros((len(a), 3)), ws, ww, np.zeros((len(ws), 3)),
+                                        with_mag=True)
+    _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
