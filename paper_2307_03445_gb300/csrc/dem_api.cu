@@ -68,14 +68,14 @@ struct dem_ctx {
   Buf b_grids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
   Buf b_flags, b_counters, b_totals, b_dstep;
   // detection scratch
-  Buf b_det, b_bin_cnt, b_bin_off, b_wall_mask, b_wall_cnt, b_keys, b_ids, b_keys2, b_ids2;
-  Buf b_bin_start, b_bin_end, b_pair_cnt, b_scan_scr, b_sort_scr, b_tmp;
-  Buf b_lob, b_part, b_rec, b_trho, b_upairs;
+  Buf b_det, b_bin_size, b_wall_mask, b_wall_cnt, b_ids;
+  Buf b_bin_start, b_pair_cnt, b_scan_scr, b_tmp;
+  Buf b_rec, b_trho, b_upairs;
   unsigned long long ucap = 0;  // capacity of the unordered pair buffer
   double bin_factor = 1.0;      // bin edge multiplier chosen by dem_autotune_bins
-  uint32_t* sorted_keys = nullptr;
-  uint32_t* sorted_ids = nullptr;
-  long long n_entries = 0;
+  long long n_entries = 0;       // bin registrations of the last rebuild (ids in b_ids,
+                                 // bins delimited by b_bin_start)
+  long long n_entry_bins = 0;    // bins of that rebuild
   // contact lists (current, next) and an audit list
   struct ListBufs {
     Buf pa, pb, u, row, ws, ww, uw, wrow, dnb;
@@ -470,31 +470,34 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
   const double t = (double)c->step * c->P.dt;
   const double travel = c->P.dt * (double)std::max(1, K);
   auto& LB = c->lists[li];
-  if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_bin_cnt, 4 * (ns + 1)) ||
-      !grow(c, c->b_bin_off, 4 * (ns + 1)) || !grow(c, c->b_wall_mask, 4 * (ns + 1)) ||
+  const size_t nb = (size_t)c->nbins;
+  if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_wall_mask, 4 * (ns + 1)) ||
       !grow(c, c->b_wall_cnt, 4 * (ns + 1)) || !grow(c, c->b_pair_cnt, 4 * (ns + 1)) ||
-      !grow(c, c->b_lob, 8 * (ns + 1)) ||
+      !grow(c, c->b_bin_size, 4 * (nb + 1)) || !grow(c, c->b_bin_start, 4 * (nb + 1)) ||
       !grow(c, LB.row, 4 * (ns + 1)) || !grow(c, LB.wrow, 4 * (ns + 1)) ||
-      !grow(c, c->b_scan_scr, scan_scratch_bytes(ns + 1) + 256))
+      !grow(c, c->b_scan_scr, scan_scratch_bytes(std::max<size_t>(ns, nb) + 1) + 256))
     return fail(c, DEM_ERR_OOM, "detection buffers");
   DetectOut o{};
   o.det = ptr<int4>(c->b_det);
-  o.bin_cnt = ptr<uint32_t>(c->b_bin_cnt);
-  o.bin_off = ptr<uint32_t>(c->b_bin_off);
   o.wall_mask = ptr<uint32_t>(c->b_wall_mask);
   o.wall_cnt = ptr<uint32_t>(c->b_wall_cnt);
   o.wall_off = ptr<uint32_t>(LB.wrow);
   o.pair_cnt = ptr<uint32_t>(c->b_pair_cnt);
   o.pair_off = ptr<uint32_t>(LB.row);
-  o.lob = ptr<unsigned long long>(c->b_lob);
+  o.bin_size = ptr<uint32_t>(c->b_bin_size);
+  o.bin_start = ptr<uint32_t>(c->b_bin_start);
+  o.nbins = c->nbins;
   if (!c->D.cmargin) {  // one margin for all clumps: radii from a per template sphere table
     o.n_tsph = (int)c->tpl_rad.size();
     if (!grow(c, c->b_trho, 4 * (size_t)(o.n_tsph + 1))) return fail(c, DEM_ERR_OOM, "detection buffers");
     o.trho = ptr<int>(c->b_trho);
   }
   unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
+  // bin sort by counting: sizes (detection pass), starts (scan; the extra
+  // zero entry makes start[nbins] the total), then the scatter below
+  cudaMemsetAsync(o.bin_size, 0, 4 * (nb + 1), c->st);
   launch_detect(c->D, o, m, nullptr, t, travel, c->st);
-  exclusive_scan_u32(o.bin_cnt, o.bin_off, ns, c->b_scan_scr.p, tot + 0, c->st);
+  exclusive_scan_u32(o.bin_size, o.bin_start, (long long)nb + 1, c->b_scan_scr.p, tot + 0, c->st);
   exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 1, c->st);
   unsigned long long h_tot[4] = {0, 0, 0, 0};
   cudaMemcpyAsync(h_tot, tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
@@ -503,33 +506,13 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
   if (B >= (1ull << 32) || NW >= (1ull << 31))
     return fail(c, DEM_ERR_CAPACITY, "bin registrations exceed 2^32");
   c->n_entries = (long long)B;
-  if (!grow(c, c->b_keys, 4 * (B + 1)) || !grow(c, c->b_ids, 4 * (B + 1)) ||
-      !grow(c, c->b_keys2, 4 * (B + 1)) || !grow(c, c->b_ids2, 4 * (B + 1)) ||
-      !grow(c, c->b_sort_scr, radix_scratch_bytes((long long)B + 1) + 256) ||
-      !grow(c, c->b_rec, sizeof(EntryRec) * (B + 1)) ||
-      !grow(c, c->b_bin_start, 4 * ((size_t)c->nbins + 1)) || !grow(c, c->b_bin_end, 4 * ((size_t)c->nbins + 1)))
+  c->n_entry_bins = (long long)nb;
+  if (!grow(c, c->b_ids, 4 * (B + 1)) || !grow(c, c->b_rec, sizeof(EntryRec) * (B + 1)))
     return fail(c, DEM_ERR_OOM, "bin buffers");
-  o.keys = ptr<uint32_t>(c->b_keys);
   o.ids = ptr<uint32_t>(c->b_ids);
-  launch_emit_bins(c->D, o, c->st);
-  int bits = 1;
-  while (bits < 32 && (1ull << bits) < (unsigned long long)c->nbins) ++bits;
-  const int alt = radix_sort_pairs(o.keys, o.ids, ptr<uint32_t>(c->b_keys2), ptr<uint32_t>(c->b_ids2),
-                                   (long long)B, bits, c->b_sort_scr.p, tot + 2, c->st);
-  if (alt) {
-    o.keys = ptr<uint32_t>(c->b_keys2);
-    o.ids = ptr<uint32_t>(c->b_ids2);
-  }
-  c->sorted_keys = o.keys;
-  c->sorted_ids = o.ids;
+  launch_bin_scatter(c->D, o, c->st);
   o.rec = ptr<EntryRec>(c->b_rec);
   launch_gather_entries(c->D, o, (long long)B, c->st);
-  o.bin_start = ptr<uint32_t>(c->b_bin_start);
-  o.bin_end = ptr<uint32_t>(c->b_bin_end);
-  cudaMemsetAsync(o.bin_start, 0, 4 * (size_t)c->nbins, c->st);
-  cudaMemsetAsync(o.bin_end, 0, 4 * (size_t)c->nbins, c->st);
-  launch_bin_bounds(o.keys, (long long)B, o.bin_start, o.bin_end, c->st);
-  o.nbins = c->nbins;
   o.d_np = tot + 5;
   // the find pass appends the kept pairs to an unordered buffer sized from
   // the last rebuild; if they did not fit it grows and the pass runs again
@@ -1142,10 +1125,9 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_sa32,
                 &c->b_sb32, &c->b_grids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
                 &c->b_wpos, &c->b_wforce, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
-                &c->b_totals, &c->b_det, &c->b_bin_cnt, &c->b_bin_off, &c->b_wall_mask, &c->b_wall_cnt,
-                &c->b_keys, &c->b_ids, &c->b_keys2, &c->b_ids2, &c->b_bin_start, &c->b_bin_end,
-                &c->b_pair_cnt, &c->b_scan_scr, &c->b_sort_scr, &c->b_tmp, &c->b_lob,
-                &c->b_part, &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
+                &c->b_totals, &c->b_det, &c->b_bin_size, &c->b_wall_mask, &c->b_wall_cnt,
+                &c->b_ids, &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
+                &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
                 &c->b_det_ids, &c->b_det_pair, &c->b_det_wall, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
                 &c->b_bcnt, &c->b_bvmax, &c->b_bvsum, &c->b_bamax, &c->b_occ, &c->b_nocc,
                 &c->b_binm, &c->b_cand, &c->b_feat, &c->b_pred, &c->b_dmax, &c->b_T, &c->b_tr_vox,
@@ -1519,11 +1501,23 @@ int dem_get_bins(dem_ctx* c, long long cap, unsigned int* keys, int* ids, long l
   if (!c || !n) return DEM_ERR_INVALID_ARG;
   *n = c->n_entries;
   const long long m = std::min(cap, c->n_entries);
-  if (m > 0 && keys && ids && c->sorted_keys) {
-    cudaMemcpyAsync(keys, c->sorted_keys, 4 * m, cudaMemcpyDeviceToHost, c->st);
-    cudaMemcpyAsync(ids, c->sorted_ids, 4 * m, cudaMemcpyDeviceToHost, c->st);
-    cudaStreamSynchronize(c->st);
-    for (long long i = 0; i < m; ++i) ids[i] = (int)((uint32_t)ids[i] & kIdMask);  // drop the owning-bin mask
+  if (m > 0 && keys && ids && c->b_ids.p) {
+    // the device holds the ids grouped by bin in slot order: restore the
+    // bin key of every entry and sort each bin by sphere id
+    const long long B = c->n_entries, nb = c->n_entry_bins;
+    std::vector<uint32_t> start((size_t)nb + 1), v((size_t)B);
+    cudaMemcpyAsync(start.data(), c->b_bin_start.p, 4 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, c->st);
+    cudaMemcpyAsync(v.data(), c->b_ids.p, 4 * (size_t)B, cudaMemcpyDeviceToHost, c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "get_bins");
+    for (long long k = 0; k < nb; ++k) {
+      const uint32_t s0 = start[k], s1 = start[k + 1];
+      for (uint32_t i = s0; i < s1; ++i) v[i] &= kIdMask;  // drop the owning-bin mask
+      std::sort(v.begin() + s0, v.begin() + s1);
+      for (uint32_t i = s0; i < s1 && (long long)i < m; ++i) {
+        keys[i] = (unsigned int)k;
+        ids[i] = (int)v[i];
+      }
+    }
   }
   return cuda_check(c, "get_bins");
 }

@@ -2,9 +2,10 @@
 //
 // Every sphere, enlarged by the safety margin, is quantised onto the 2^-24 m
 // detection lattice and registered in every bin its enlarged box touches
-// (multi-bin registration).  The registrations are sorted by bin key with the
-// radix sort; each sphere then walks its own bins and tests the members with a
-// larger id from another clump with the exact int64 predicate
+// (multi-bin registration).  The registrations are grouped by bin key with a
+// counting sort (an LSD radix sort whose single digit is the whole key: count
+// per bin, exclusive scan, scatter into slots); each bin's members are then
+// tested pairwise, across clumps, with the exact integer predicate
 // |qa - qb|^2 <= (rho_a + rho_b)^2, keeping a pair only in the bin that holds
 // the per-axis maximum of the two boxes' lower corners, so each pair is found
 // once.  The output is a canonical list sorted by (a, b), one row per sphere,
@@ -147,15 +148,17 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   const float tf = d2f(t);
   const float rmf = d.tp32[si.y].w + d2f(m);  // r + m for the estimates
   o.det[s] = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
-  long long cnt = 1;
-  int lob[3];
+  // counting pass of the bin sort: one count per bin the enlarged box touches
+  int lo[3], hi[3];
   for (int k = 0; k < 3; ++k) {
-    lob[k] = clampi(floordiv_bin(qc[k] - rho, g.L, g.invL), g.dims[k] - 1);
-    const int hi = clampi(floordiv_bin(qc[k] + rho, g.L, g.invL), g.dims[k] - 1);
-    cnt *= (hi - lob[k] + 1);
+    lo[k] = clampi(floordiv_bin(qc[k] - rho, g.L, g.invL), g.dims[k] - 1);
+    hi[k] = clampi(floordiv_bin(qc[k] + rho, g.L, g.invL), g.dims[k] - 1);
   }
-  o.bin_cnt[s] = (uint32_t)cnt;
-  o.lob[s] = pack_bin3(lob[0], lob[1], lob[2]);
+  const uint32_t d0 = (uint32_t)g.dims[0], d01 = d0 * (uint32_t)g.dims[1];
+  for (int bz = lo[2]; bz <= hi[2]; ++bz)
+    for (int by = lo[1]; by <= hi[1]; ++by)
+      for (int bx = lo[0]; bx <= hi[0]; ++bx)
+        atomicAdd(&o.bin_size[g.key_base + (uint32_t)bz * d01 + (uint32_t)by * d0 + (uint32_t)bx], 1u);
   // sphere-wall candidates: distance within radius + margin + wall travel
   uint32_t mask = 0;
   for (int i = 0; i < g.wall_count; ++i) {
@@ -181,7 +184,12 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   o.wall_cnt[s] = __popc(mask);
 }
 
-__global__ void k_emit_bins(DevState d, DetectOut o) {
+// Scatter pass of the bin sort: every registration takes a slot of its bin
+// (counting the bin's size down to zero) and stores the sphere id with the
+// owning-bin mask in the top bits.  The order inside a bin is whatever the
+// atomics give; nothing downstream depends on it.  A slot request past the
+// counted size (a broken invariant) is dropped and flagged.
+__global__ void k_bin_scatter(DevState d, DetectOut o) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= d.ns) return;
   const int4 q = o.det[s];
@@ -192,25 +200,20 @@ __global__ void k_emit_bins(DevState d, DetectOut o) {
     lo[k] = clampi(floordiv_bin((long long)qq[k] - q.w, g.L, g.invL), g.dims[k] - 1);
     hi[k] = clampi(floordiv_bin((long long)qq[k] + q.w, g.L, g.invL), g.dims[k] - 1);
   }
-  uint32_t off = o.bin_off[s];
   const uint32_t d0 = (uint32_t)g.dims[0], d01 = d0 * (uint32_t)g.dims[1];
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
       for (int x = lo[0]; x <= hi[0]; ++x) {
-        o.keys[off] = g.key_base + (uint32_t)z * d01 + (uint32_t)y * d0 + (uint32_t)x;
+        const uint32_t key = g.key_base + (uint32_t)z * d01 + (uint32_t)y * d0 + (uint32_t)x;
+        const uint32_t left = atomicSub(&o.bin_size[key], 1u);
+        if (left == 0u) {
+          atomicAdd(&o.bin_size[key], 1u);
+          atomicOr(d.flags, kFlagBounds);
+          continue;
+        }
         const uint32_t mask = (x == lo[0] ? 1u : 0u) | (y == lo[1] ? 2u : 0u) | (z == lo[2] ? 4u : 0u);
-        o.ids[off] = (uint32_t)s | (mask << kIdBits);
-        ++off;
+        o.ids[o.bin_start[key] + left - 1u] = (uint32_t)s | (mask << kIdBits);
       }
-}
-
-__global__ void k_bin_bounds(const uint32_t* __restrict__ keys, long long n,
-                             uint32_t* __restrict__ start, uint32_t* __restrict__ end) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t k = keys[i];
-  if (i == 0 || keys[i - 1] != k) start[k] = (uint32_t)i;
-  if (i == n - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
 }
 
 // Gathers, in sorted order, the record of every registration.
@@ -230,8 +233,8 @@ __global__ void k_gather_entries(DevState d, DetectOut o, long long n) {
 }
 
 // Narrow phase, one warp per bin (persistent warps striding over the bins).
-// The bin's registrations, sorted by sphere id, are taken 32 at a time: lane
-// l holds registration i; the registrations of the same tile are paired by
+// The bin's registrations (in any order) are taken 32 at a time: lane l
+// holds registration i; the registrations of the same tile are paired by
 // rotation, and every later tile is staged in shared memory and tested by all
 // lanes at once, so the loops are uniform across the warp.  A pair
 // (a = min id < b = max id) is kept when the spheres belong to different
@@ -259,29 +262,61 @@ __device__ __forceinline__ void flush_pairs(const DetectOut& o, uint2* buf, int 
 // the differences fit in 32 bits and -rr <= d <= rr is one unsigned
 // comparison of d + rr (a wrapped sum lands above 2 rr); past it every
 // |d| <= rr and the sum of the squares fits in 63 bits.
-__device__ __forceinline__ bool narrow_test(const EntryRec& A, const int4 q, const int4 mm) {
-  if (mm.x == A.owner || (A.mask | (uint32_t)mm.z) != 7u) return false;
-  const int rr = A.rho + q.w;
-  const int dx = q.x - A.qx, dy = q.y - A.qy, dz = q.z - A.qz;
-  const unsigned w = 2u * (unsigned)rr, ur = (unsigned)rr;
-  if ((unsigned)dx + ur > w || (unsigned)dy + ur > w || (unsigned)dz + ur > w) return false;
-  const long long d2 = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-  return d2 <= (long long)rr * rr;
+//
+// The operands are pre-shifted so that an axis costs one subtraction and one
+// comparison: B is staged as (q_b + rho_b, 2 rho_b), the lane holds
+// (q_a - rho_a, 2 rho_a), and t = (q_b + rho_b) - (q_a - rho_a) = d + rr
+// (mod 2^32) lies in [0, 2 rr] exactly when |d| <= rr.  Every predicate is
+// evaluated and combined without branches (the 64-bit sum wraps harmlessly on
+// lanes whose box test failed).
+struct NarrowA {
+  uint32_t x, y, z;  // q_a - rho_a (two's complement)
+  uint32_t r2;       // 2 rho_a
+  int owner;
+  uint32_t mask;
+};
+
+__device__ __forceinline__ NarrowA narrow_a(const EntryRec& A) {
+  return {(uint32_t)A.qx - (uint32_t)A.rho, (uint32_t)A.qy - (uint32_t)A.rho,
+          (uint32_t)A.qz - (uint32_t)A.rho, 2u * (uint32_t)A.rho, A.owner, A.mask};
+}
+
+__device__ __forceinline__ int4 narrow_b(const EntryRec& R) {
+  return make_int4((int)((uint32_t)R.qx + (uint32_t)R.rho), (int)((uint32_t)R.qy + (uint32_t)R.rho),
+                   (int)((uint32_t)R.qz + (uint32_t)R.rho), (int)(2u * (uint32_t)R.rho));
+}
+
+__device__ __forceinline__ bool narrow_test(const NarrowA& A, const int4 q, const int4 mm) {
+  const uint32_t rr2 = A.r2 + (uint32_t)q.w;
+  const uint32_t tx = (uint32_t)q.x - A.x, ty = (uint32_t)q.y - A.y, tz = (uint32_t)q.z - A.z;
+  const bool box = (tx <= rr2) & (ty <= rr2) & (tz <= rr2);
+  const uint32_t rr = rr2 >> 1;
+  const int dx = (int)(tx - rr), dy = (int)(ty - rr), dz = (int)(tz - rr);
+  const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
+                                (unsigned long long)((long long)dy * dy) +
+                                (unsigned long long)((long long)dz * dz);
+  const bool sph = d2 <= (unsigned long long)rr * rr;
+  return box & sph & (mm.x != A.owner) & ((A.mask | (uint32_t)mm.z) == 7u);
 }
 
 __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) {
-  __shared__ int4 sq[kNarrowWarps][32];   // qx, qy, qz, rho
+  __shared__ int4 sq[kNarrowWarps][32];   // q + rho (x, y, z), 2 rho
   __shared__ int4 sm[kNarrowWarps][32];   // owner, id, mask
   __shared__ uint2 sbuf[kNarrowWarps][64];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint2* buf = sbuf[wib];
   int nbuf = 0;  // warp-uniform
-  // appends the kept pairs of one warp-wide test to the warp's buffer
+  // appends the kept pairs of one warp-wide test to the warp's buffer as
+  // (lower id, higher id) and counts a partner of the lower id
   auto emit = [&](bool hit, uint32_t a, uint32_t b) {
     const unsigned m = __ballot_sync(0xffffffffu, hit);
     if (!m) return;
-    if (hit) buf[nbuf + __popc(m & lt)] = make_uint2(a, b);
+    if (hit) {
+      const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+      atomicAdd(&o.pair_cnt[lo], 1u);
+      buf[nbuf + __popc(m & lt)] = make_uint2(lo, hi);
+    }
     nbuf += __popc(m);
     if (nbuf >= 32) {
       __syncwarp();
@@ -300,7 +335,7 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
     const uint32_t jl = j0 + (uint32_t)lane;
     if (jl < e) {
       const EntryRec R = o.rec[jl];
-      sq[wib][lane] = make_int4(R.qx, R.qy, R.qz, R.rho);
+      sq[wib][lane] = narrow_b(R);
       sm[wib][lane] = make_int4(R.owner, (int)R.id, (int)R.mask, 0);
     }
     __syncwarp();
@@ -308,13 +343,14 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
   const long long nw = (long long)gridDim.x * kNarrowWarps;
   for (long long bin = (long long)blockIdx.x * kNarrowWarps + wib; bin < (long long)o.nbins;
        bin += nw) {
-    const uint32_t s = o.bin_start[bin], e = o.bin_end[bin];
-    if (e <= s + 1u) continue;  // empty bins have start = end = 0
+    const uint32_t s = o.bin_start[bin], e = o.bin_start[bin + 1];
+    if (e <= s + 1u) continue;  // fewer than two registrations
     for (uint32_t i0 = s; i0 < e; i0 += 32u) {
       const uint32_t i = i0 + (uint32_t)lane;
       const bool vi = i < e;
       EntryRec A{};
       if (vi) A = o.rec[i];
+      const NarrowA na = narrow_a(A);
       const int nt = (int)min(32u, e - i0);
       // pairs inside the lane's own tile, by rotation: at offset t lane l
       // meets (l + t) mod nt, so every unordered pair comes up once for
@@ -326,15 +362,11 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
         const bool valid = lane < nt && (2 * t < nt || lane < t);
         const int4 q = sq[wib][pj];
         const int4 mm = sm[wib][pj];
-        const bool hit = valid && narrow_test(A, q, mm);
-        const uint32_t b = (uint32_t)mm.y;
-        const uint32_t lo = A.id < b ? A.id : b, hi = A.id < b ? b : A.id;
-        if (hit) atomicAdd(&o.pair_cnt[lo], 1u);
-        emit(hit, lo, hi);
+        const bool hit = valid & narrow_test(na, q, mm);
+        emit(hit, A.id, (uint32_t)mm.y);
       }
       __syncwarp();
-      // later tiles of the bin: ids above every id of this tile
-      uint32_t n = 0;
+      // later tiles of the bin, staged one at a time and met by every lane
       for (uint32_t j0 = i0 + 32u; j0 < e; j0 += 32u) {
         stage(j0, e);
         const int jn = (int)min(32u, e - j0);
@@ -342,13 +374,11 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
         for (int jj = 0; jj < jn; ++jj) {
           const int4 q = sq[wib][jj];
           const int4 mm = sm[wib][jj];
-          const bool hit = vi && narrow_test(A, q, mm);
-          n += hit ? 1u : 0u;
+          const bool hit = vi & narrow_test(na, q, mm);
           emit(hit, A.id, (uint32_t)mm.y);
         }
         __syncwarp();
       }
-      if (n) atomicAdd(&o.pair_cnt[A.id], n);
     }
   }
   __syncwarp();
@@ -532,15 +562,9 @@ void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, c
   count_launch();
 }
 
-void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st) {
+void launch_bin_scatter(const DevState& d, const DetectOut& o, cudaStream_t st) {
   if (d.ns == 0) return;
-  { k_emit_bins<<<nblk(d.ns, 128), 128, 0, st>>>(d, o); count_launch(); }
-}
-
-void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint32_t* end,
-                       cudaStream_t st) {
-  if (n == 0) return;
-  { k_bin_bounds<<<nblk(n, 256), 256, 0, st>>>(keys, n, start, end); count_launch(); }
+  { k_bin_scatter<<<nblk(d.ns, 128), 128, 0, st>>>(d, o); count_launch(); }
 }
 
 void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,

@@ -105,24 +105,15 @@ struct alignas(32) EntryRec {
 constexpr int kIdBits = 29;
 constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
 
-__host__ __device__ __forceinline__ unsigned long long pack_bin3(int x, int y, int z) {
-  return (unsigned long long)(unsigned)x | ((unsigned long long)(unsigned)y << 21) |
-         ((unsigned long long)(unsigned)z << 42);
-}
-
 struct DetectOut {
-  unsigned long long* lob;  // per sphere: clamped lower-corner bin, packed
-  EntryRec* rec;            // per entry (sorted order)
+  EntryRec* rec;            // per entry (bin order)
   int4* det;                // per sphere {qx, qy, qz, rho}
-  uint32_t* bin_cnt;        // per sphere
-  uint32_t* bin_off;        // per sphere (scan)
   uint32_t* wall_mask;      // per sphere
   uint32_t* wall_cnt;       // per sphere
   uint32_t* wall_off;       // per sphere (scan)
-  uint32_t* keys;           // per entry
-  uint32_t* ids;            // per entry
-  uint32_t* bin_start;      // per bin
-  uint32_t* bin_end;        // per bin
+  uint32_t* ids;            // per entry, grouped by bin: sphere id | owning-bin mask << kIdBits
+  uint32_t* bin_size;       // per bin (+1): registrations (counting pass)
+  uint32_t* bin_start;      // per bin (+1): first entry; bin k is [start[k], start[k + 1])
   uint32_t nbins;
   uint2* upairs;            // narrow phase: kept pairs (a, b), unordered
   unsigned long long ucap;  //   capacity of upairs
@@ -153,10 +144,12 @@ struct ContactList {
 // detection
 void launch_detect(const DevState& d, const DetectOut& o, double margin, const double* smargin,
                    double t, double travel_time, cudaStream_t st);
-void launch_emit_bins(const DevState& d, const DetectOut& o, cudaStream_t st);
+// Bin sort by counting: launch_detect adds every registration to o.bin_size
+// (zeroed by the caller); after the exclusive scan of bin_size into
+// o.bin_start (nbins + 1 entries), launch_bin_scatter places the ids and
+// leaves bin_size at zero.
+void launch_bin_scatter(const DevState& d, const DetectOut& o, cudaStream_t st);
 void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, cudaStream_t st);
-void launch_bin_bounds(const uint32_t* keys, long long n, uint32_t* start, uint32_t* end,
-                       cudaStream_t st);
 // Narrow phase over the bins.  Find pass: the kept pairs go to o.upairs
 // (count in *o.d_np, zeroed by the caller) and o.pair_cnt[a] += partners
 // b > a (pair_cnt zeroed by the caller).  Write pass (after the scan of
