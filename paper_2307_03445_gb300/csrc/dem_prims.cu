@@ -1,10 +1,7 @@
-// dem_prims.cu -- device-wide exclusive scan and stable LSD radix sort.
+// dem_prims.cu -- device-wide exclusive scan.
 //
-// Scan: reduce-then-scan over tiles of 4096 counts (uint32 in, uint32 out, a
-// uint64 grand total so that an overflow of the 32-bit offsets is detected).
-// Sort: 8-bit digits; per pass a per-tile digit histogram, a scan of the
-// (digit-major, tile-minor) histogram matrix, and a scatter in which every
-// tile ranks its keys stably with warp match/ballot and shared counters.
+// Reduce-then-scan over tiles of 4096 counts (uint32 in, uint32 out, a uint64
+// grand total so that an overflow of the 32-bit offsets is detected).
 #include "dem_prims.cuh"
 
 namespace dem {
@@ -135,108 +132,6 @@ int device_sms() {
     }
   }
   return n;
-}
-
-// ---------------------------------------------------------------------------
-// radix sort
-// ---------------------------------------------------------------------------
-namespace {
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kSortWarps = kSortThreads / 32;
-
-__global__ void k_radix_hist(const uint32_t* __restrict__ keys, long long n, int shift,
-                             long long ntiles, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const long long base = (long long)blockIdx.x * kSortTile;
-  for (int i = 0; i < kSortItems; ++i) {
-    long long idx = base + (long long)i * kSortThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-__global__ void k_radix_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                                long long n, int shift, long long ntiles,
-                                const uint32_t* __restrict__ offs, uint32_t* __restrict__ okeys,
-                                uint32_t* __restrict__ ovals) {
-  __shared__ uint32_t s_cnt[kSortWarps][256];
-  __shared__ uint32_t s_pre[kSortWarps][256];
-  __shared__ uint32_t s_run[256];
-  __shared__ uint32_t s_goff[256];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int w = 0; w < kSortWarps; ++w) s_cnt[w][tid] = 0;
-  s_run[tid] = 0;
-  s_goff[tid] = offs[(long long)tid * ntiles + blockIdx.x];
-  __syncthreads();
-  const unsigned lt_mask = (1u << lane) - 1u;
-  const long long base = (long long)blockIdx.x * kSortTile;
-  for (int it = 0; it < kSortItems; ++it) {
-    const long long idx = base + (long long)it * kSortThreads + tid;
-    const bool valid = idx < n;
-    uint32_t key = valid ? keys[idx] : 0u;
-    uint32_t val = valid ? vals[idx] : 0u;
-    // invalid lanes use digit 256 (never matches a real digit)
-    const uint32_t digit = valid ? ((key >> shift) & 255u) : 256u;
-    const unsigned peers = __match_any_sync(0xffffffffu, digit);
-    const uint32_t rank = __popc(peers & lt_mask);
-    const int leader = __ffs(peers) - 1;
-    if (valid && lane == leader) s_cnt[warp][digit] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t run = s_run[tid];
-      for (int w = 0; w < kSortWarps; ++w) {
-        s_pre[w][tid] = run;
-        run += s_cnt[w][tid];
-        s_cnt[w][tid] = 0;
-      }
-      s_run[tid] = run;
-    }
-    __syncthreads();
-    if (valid) {
-      const uint32_t dst = s_goff[digit] + s_pre[warp][digit] + rank;
-      okeys[dst] = key;
-      ovals[dst] = val;
-    }
-    __syncthreads();
-  }
-}
-}  // namespace
-
-size_t radix_scratch_bytes(long long n) {
-  long long ntiles = (n + kSortTile - 1) / kSortTile;
-  size_t hist = sizeof(uint32_t) * 256 * (size_t)(ntiles > 0 ? ntiles : 1);
-  return 2 * hist + scan_scratch_bytes(256 * (ntiles > 0 ? ntiles : 1)) + 64;
-}
-
-int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                     long long n, int key_bits, void* scratch, unsigned long long* d_total,
-                     cudaStream_t st) {
-  if (n <= 1) return 0;
-  const long long ntiles = (n + kSortTile - 1) / kSortTile;
-  uint32_t* hist = (uint32_t*)scratch;
-  uint32_t* offs = hist + 256 * ntiles;
-  void* sscr = (void*)(offs + 256 * ntiles);
-  // align the scan scratch to 16 bytes
-  sscr = (void*)(((uintptr_t)sscr + 15) & ~(uintptr_t)15);
-  int passes = (key_bits + 7) / 8;
-  if (passes < 1) passes = 1;
-  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
-  for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ki, n, shift, ntiles, hist);
-    exclusive_scan_u32(hist, offs, 256 * ntiles, sscr, d_total, st);
-    k_radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, st>>>(ki, vi, n, shift, ntiles, offs, ko,
-                                                                 vo);
-    count_launch(2);
-    uint32_t* t = ki; ki = ko; ko = t;
-    t = vi; vi = vo; vo = t;
-  }
-  return passes & 1;  // 1: the sorted data is in the *_alt buffers
 }
 
 }  // namespace dem

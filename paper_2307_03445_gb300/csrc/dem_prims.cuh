@@ -1,4 +1,4 @@
-// dem_prims.cuh -- device-wide scan and radix sort used by the binning.
+// dem_prims.cuh -- device-wide scan used by the binning and the list build.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -20,13 +20,5 @@ size_t scan_scratch_bytes(long long n);
 // in and out may alias.
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, void* scratch,
                         unsigned long long* d_total, cudaStream_t st);
-
-// Scratch bytes needed by radix_sort_pairs for n elements.
-size_t radix_scratch_bytes(long long n);
-// Stable sort of (key, value) pairs by the low key_bits bits of the key.
-// Returns 0 if the result is in keys/vals, 1 if it is in keys_alt/vals_alt.
-int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                     long long n, int key_bits, void* scratch, unsigned long long* d_total,
-                     cudaStream_t st);
 
 }  // namespace dem
