@@ -257,6 +257,7 @@ def batched_form(dem, steps, device, log):
     sim.set_graphs(True)
     sim.step(K_REBUILD)
     fb, _ = sim.autotune_bins(BIN_FACTORS, reps=1)
+    tiles = sim.autotune_tiles(steps=6, reps=1)
     sim.step(K_REBUILD)
     ms_b = _timed_steps(sim, stream, steps)
     sim.close()
@@ -267,13 +268,14 @@ def batched_form(dem, steps, device, log):
         one.set_graphs(True)
         one.step(K_REBUILD)
         one.autotune_bins(BIN_FACTORS, reps=1)
+        one.autotune_tiles(steps=6, reps=1)
         one.step(K_REBUILD)
         ms_s += _timed_steps(one, stream, steps)
         one.close()
     return {"value": ns * steps / (ms_b / 1000.0), "unit": UNIT, "ms_per_step": ms_b / steps,
             "per_scene_value": ns * steps / (ms_s / 1000.0),
             "vs_per_scene": ms_s / ms_b, "n_scenes": len(parts), "n_spheres": ns,
-            "bin_factor": fb,
+            "bin_factor": fb, "tiles": tiles,
             "workload": "64 box-settling scenes, 5,000-100,000 clumps (log-uniform), own mu "
                         "0.2-0.9 and 10 templates of 1-5 spheres each, FP32 voxel, one context "
                         "with graph-captured steps vs one context per scene"}
@@ -342,6 +344,8 @@ def main():
     sim.step(args.warmup)
     bin_factor, bin_ms = sim.autotune_bins(BIN_FACTORS, reps=1)
     log(f"bin autotune: factor {bin_factor} ({bin_ms})")
+    tiles = sim.autotune_tiles(steps=6, reps=1)
+    log(f"tile autotune: {tiles}")
     sim.step(args.warmup)
     sim.reset_stats()
     sim.set_timing(True)
@@ -436,7 +440,7 @@ def main():
                    "listed_pairs": n_pairs, "active_contacts": n_active,
                    "wall_contacts": st["n_wall_contacts"], "margin_m": margin,
                    "rebuild_interval": K_REBUILD, "dt": sc.h, "rebuilds": st["rebuilds"],
-                   "bin_factor": bin_factor, "bin_autotune_ms": bin_ms,
+                   "bin_factor": bin_factor, "bin_autotune_ms": bin_ms, "tiles": tiles,
                    "guard_violations": st["guard_violations"],
                    "l2": "inputs larger than L2 (state ~GBs)", "parallelism": f"replicas{world}",
                    "phase_ms": {"pairs": pair_ms,

@@ -233,6 +233,29 @@ int dem_set_deterministic(dem_ctx* ctx, int on);
 int dem_autotune_bins(dem_ctx* ctx, int n, const double* factors, int reps, double* best,
                       double* ms);
 
+/* Launch shapes of the hot kernels.  None of them changes a result: every
+ * per-contact and per-clump computation is the same whatever the grid, and
+ * in deterministic mode the trajectory is bit-identical across shapes. */
+typedef struct {
+    int pairs_blocks_per_sm;  /* blocks of 256 threads per SM for the pair force kernels
+                                 (grid-stride loop), 1..32; default 8 */
+    int update_block;         /* clumps per block of the FP32_VOXEL update kernel: 64,
+                                 128 (default) or 256 */
+    int narrow_chunk;         /* bins a narrow-phase warp claims at a time, 1..64; default 8 */
+} dem_tiles;
+/* DEM_ERR_INVALID_ARG for a value out of range (nothing changes then). */
+int dem_set_tiles(dem_ctx* ctx, const dem_tiles* tiles);
+int dem_get_tiles(dem_ctx* ctx, dem_tiles* tiles);
+/* Tile autotuner, one coordinate at a time: the narrow chunk over
+ * {2, 4, 8, 16, 32} timed on `reps` rebuilds each, then the pair blocks per
+ * SM over {2, 4, 8, 16} and the update block over {64, 128, 256}, each timed
+ * on `steps` force + update steps from a snapshot of the state and the list
+ * history taken at a fresh rebuild.  The snapshot is restored after the
+ * trials, so the state, the step count and the counters are unchanged; the
+ * fastest shapes are kept and written to *best.  Overwrites the rollback
+ * snapshot of the learned rule (call it outside dem_step). */
+int dem_autotune_tiles(dem_ctx* ctx, int steps, int reps, dem_tiles* best);
+
 /* enabled = 1 runs the steps between two rebuilds of the plain rule as one
  * CUDA graph launch (captured on first use per list buffer, step count and
  * margin, and recaptured after any buffer is reallocated).  Results are those
@@ -371,7 +394,9 @@ int dem_set_learned_policy(dem_ctx* ctx, dem_mlp* mlp, const dem_learned_params*
  * largest clump acceleration in the last step; r_mean: mean sphere radius)
  * and the target t = ln(T), T the first step of the window at which a clump
  * of the bin has moved further than m (T = window if none did).  Writes up
- * to cap samples into x (6 * cap) and t (cap); *n receives the count. */
+ * to cap samples into x (6 * cap) and t (cap); *n receives the count.
+ * Samples are ordered by window, then occupied bin, then candidate (the
+ * n_candidates samples of one bin are adjacent, in the given order). */
 int dem_trace(dem_ctx* ctx, int windows, int window, int n_candidates, const double* candidates,
               long long cap, float* x, float* t, long long* n);
 

@@ -225,6 +225,29 @@ class Simulation:
                                                _pd(ms)))
         return best.value, {float(a): (float(b) if b >= 0 else None) for a, b in zip(f, ms)}
 
+    def tiles(self):
+        """Launch shapes: {pairs_blocks_per_sm, update_block, narrow_chunk}."""
+        t = capi.DemTiles()
+        self._check(self.lib.dem_get_tiles(self.ctx, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in capi.DemTiles._fields_}
+
+    def set_tiles(self, **kw):
+        """Sets some launch shapes (the others keep their values)."""
+        cur = self.tiles()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown launch shapes {sorted(unknown)}")
+        cur.update(kw)
+        t = capi.DemTiles(**{k: int(v) for k, v in cur.items()})
+        self._check(self.lib.dem_set_tiles(self.ctx, C.byref(t)))
+
+    def autotune_tiles(self, steps=10, reps=2):
+        """Times the launch shapes one at a time and keeps the fastest; the
+        state is unchanged.  Returns the chosen shapes."""
+        t = capi.DemTiles()
+        self._check(self.lib.dem_autotune_tiles(self.ctx, int(steps), int(reps), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in capi.DemTiles._fields_}
+
     def set_deterministic(self, on=True):
         """Bit-reproducible force sums (per-contact slots summed in a fixed order)."""
         self._check(self.lib.dem_set_deterministic(self.ctx, 1 if on else 0))

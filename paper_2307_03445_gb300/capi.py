@@ -71,6 +71,11 @@ class DemLearnedParams(C.Structure):
 
 DEM_LEARNED_HALT, DEM_LEARNED_ROLLBACK = 0, 1
 
+
+class DemTiles(C.Structure):
+    _fields_ = [("pairs_blocks_per_sm", C.c_int), ("update_block", C.c_int),
+                ("narrow_chunk", C.c_int)]
+
 # name -> (restype, argtypes); the exported symbols of include/dem.h
 SIGNATURES = {
     "dem_create": (C.c_int, [C.POINTER(DemParams), C.POINTER(C.c_void_p)]),
@@ -88,6 +93,9 @@ SIGNATURES = {
     "dem_set_graphs": (C.c_int, [_V, C.c_int]),
     "dem_set_deterministic": (C.c_int, [_V, C.c_int]),
     "dem_autotune_bins": (C.c_int, [_V, C.c_int, _D, C.c_int, _D, _D]),
+    "dem_set_tiles": (C.c_int, [_V, C.POINTER(DemTiles)]),
+    "dem_get_tiles": (C.c_int, [_V, C.POINTER(DemTiles)]),
+    "dem_autotune_tiles": (C.c_int, [_V, C.c_int, C.c_int, C.POINTER(DemTiles)]),
     "dem_rebuild": (C.c_int, [_V]),
     "dem_eval_forces": (C.c_int, [_V]),
     "dem_get_forces": (C.c_int, [_V, _D, _D]),

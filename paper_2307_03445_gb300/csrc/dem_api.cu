@@ -68,13 +68,14 @@ struct dem_ctx {
   Buf b_grids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
   Buf b_flags, b_counters, b_totals, b_dstep;
   // detection scratch
-  Buf b_det, b_bin_size, b_wall_mask, b_wall_cnt, b_ids;
+  Buf b_det, b_bin_size, b_wall_mask, b_wall_cnt;
   Buf b_bin_start, b_pair_cnt, b_scan_scr, b_tmp;
   Buf b_rec, b_trho, b_upairs;
   unsigned long long ucap = 0;  // capacity of the unordered pair buffer
   double bin_factor = 1.0;      // bin edge multiplier chosen by dem_autotune_bins
-  long long n_entries = 0;       // bin registrations of the last rebuild (ids in b_ids,
-                                 // bins delimited by b_bin_start)
+  dem_tiles tiles = {8, 128, 8}; // launch shapes (dem_set_tiles / dem_autotune_tiles)
+  long long n_entries = 0;       // bin registrations of the last rebuild (records in
+                                 // b_rec, bins delimited by b_bin_start)
   long long n_entry_bins = 0;    // bins of that rebuild
   // contact lists (current, next) and an audit list
   struct ListBufs {
@@ -105,7 +106,7 @@ struct dem_ctx {
   std::vector<double> l_cand;
   long long n_occ = 0;
   Buf b_alast, b_chome, b_cmargin, b_bcnt, b_bvmax, b_bvsum, b_bamax, b_occ, b_nocc, b_binm, b_cand;
-  Buf b_feat, b_pred, b_dmax, b_T, b_tr_vox, b_tr_off, b_tr_pos, b_tr_q, b_tx, b_tt, b_tcount;
+  Buf b_feat, b_pred, b_dmax, b_T, b_tr_vox, b_tr_off, b_tr_pos, b_tr_q, b_tx, b_tt;
   Buf s_state, s_pb, s_u, s_ww, s_uw;
   long long snap_step = 0;
   // CUDA graphs of the steps between rebuilds (plain rule)
@@ -203,6 +204,8 @@ void set_det_pointers(dem_ctx* c) {
 
 void refresh_devstate(dem_ctx* c) {
   DevState& d = c->D;
+  d.pairs_bpsm = c->tiles.pairs_blocks_per_sm;
+  d.upd_block = c->tiles.update_block;
   d.prec = c->P.precision;
   d.ncl = c->ncl;
   d.ns = c->ns;
@@ -465,7 +468,10 @@ int finalize(dem_ctx* c) {
 
 // Detection into lists[li] with margin m (per clump from D.cmargin when set),
 // for a list that must last K steps (wall travel) -- also used by the audit.
-int detect_into(dem_ctx* c, int li, double m, int K) {
+// With an old list (old != NULL) the tangential history of the pairs both
+// lists hold is carried over as the rows are built.
+int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nullptr,
+                long long old_ns = 0) {
   const long long ns = c->ns;
   const double t = (double)c->step * c->P.dt;
   const double travel = c->P.dt * (double)std::max(1, K);
@@ -507,13 +513,12 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
     return fail(c, DEM_ERR_CAPACITY, "bin registrations exceed 2^32");
   c->n_entries = (long long)B;
   c->n_entry_bins = (long long)nb;
-  if (!grow(c, c->b_ids, 4 * (B + 1)) || !grow(c, c->b_rec, sizeof(EntryRec) * (B + 1)))
-    return fail(c, DEM_ERR_OOM, "bin buffers");
-  o.ids = ptr<uint32_t>(c->b_ids);
-  launch_bin_scatter(c->D, o, c->st);
+  if (!grow(c, c->b_rec, sizeof(EntryRec) * (B + 1))) return fail(c, DEM_ERR_OOM, "bin buffers");
   o.rec = ptr<EntryRec>(c->b_rec);
-  launch_gather_entries(c->D, o, (long long)B, c->st);
+  launch_bin_scatter(c->D, o, c->st);
   o.d_np = tot + 5;
+  o.next_bin = tot + 7;  // b_totals: 0 entries, 1 wall entries, 3 pairs, 4 audit, 5 d_np, 6 slot lists
+  o.chunk = c->tiles.narrow_chunk;
   // the find pass appends the kept pairs to an unordered buffer sized from
   // the last rebuild; if they did not fit it grows and the pass runs again
   unsigned long long NP = 0;
@@ -524,7 +529,8 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
     o.ucap = c->ucap;
     cudaMemsetAsync(o.pair_cnt, 0, 4 * (size_t)ns, c->st);
     cudaMemsetAsync(o.d_np, 0, sizeof(unsigned long long), c->st);
-    launch_narrow(c->D, o, false, nullptr, nullptr, c->st);
+    cudaMemsetAsync(o.next_bin, 0, sizeof(unsigned long long), c->st);
+    launch_narrow(c->D, o, c->st);
     exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
     cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "narrow phase");
@@ -571,7 +577,7 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
   cudaMemcpyAsync(L.dn, lens, sizeof(lens), cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(L.row + ns, &np32, 4, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(L.wrow + ns, &nw32, 4, cudaMemcpyHostToDevice, c->st);
-  launch_narrow(c->D, o, true, L.pa, L.pb, c->st);
+  launch_list_rows(c->D, o, L, old, old_ns, c->st);
   launch_wall_emit(c->D, o, L.ws, L.ww, c->st);
   cudaStreamSynchronize(c->st);  // the two host scalars above must outlive their copies
   return cuda_check(c, "detect_into");
@@ -582,10 +588,11 @@ int detect_into(dem_ctx* c, int li, double m, int K) {
 int rebuild(dem_ctx* c, double m, int K) {
   const int nxt = c->cur == 0 ? 1 : 0;
   if (c->timing) cudaEventRecord(c->ev[0], c->st);
-  int rc = detect_into(c, nxt, m, K);
+  const ContactList* old = c->have_list ? &curL(c) : nullptr;
+  int rc = detect_into(c, nxt, m, K, old, c->list_ns);
   if (rc) return rc;
   ContactList& N = c->lists[nxt].L;
-  if (c->have_list) launch_hist_map(curL(c), N, c->list_ns, c->st);
+  if (old) launch_hist_walls(*old, N, c->list_ns, c->st);
   c->cur = nxt;
   c->list_ns = c->ns;
   c->have_list = true;
@@ -1126,12 +1133,12 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_sb32, &c->b_grids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
                 &c->b_wpos, &c->b_wforce, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
                 &c->b_totals, &c->b_det, &c->b_bin_size, &c->b_wall_mask, &c->b_wall_cnt,
-                &c->b_ids, &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
+                &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
                 &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
                 &c->b_det_ids, &c->b_det_pair, &c->b_det_wall, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
                 &c->b_bcnt, &c->b_bvmax, &c->b_bvsum, &c->b_bamax, &c->b_occ, &c->b_nocc,
                 &c->b_binm, &c->b_cand, &c->b_feat, &c->b_pred, &c->b_dmax, &c->b_T, &c->b_tr_vox,
-                &c->b_tr_off, &c->b_tr_pos, &c->b_tr_q, &c->b_tx, &c->b_tt, &c->b_tcount,
+                &c->b_tr_off, &c->b_tr_pos, &c->b_tr_q, &c->b_tx, &c->b_tt,
                 &c->s_state, &c->s_pb, &c->s_u, &c->s_ww, &c->s_uw};
   for (Buf* b : all) dfree(c, b->p);
   for (auto& lb : c->lists) {
@@ -1234,7 +1241,8 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
   long long add_s = 0;
   for (int i = 0; i < n; ++i) add_s += c->tpl_off[tpl[i] + 1] - c->tpl_off[tpl[i]];
   const long long ncl = c->ncl + n, ns = c->ns + add_s;
-  if (ns >= (1ll << kIdBits)) return fail(c, DEM_ERR_INVALID_ARG, "more than 2^29 spheres");
+  // sphere ids share a 32-bit word with the history flag (bit 31)
+  if (ns >= (1ll << 31) - 1) return fail(c, DEM_ERR_INVALID_ARG, "2^31 - 1 spheres or more");
   const size_t k0 = (size_t)c->ncl, s0 = (size_t)c->ns;
   bool ok = grow(c, c->b_cinfo, 8 * ncl, 8 * k0) && grow(c, c->b_csph, 4 * (ncl + 1), 4 * k0) &&
             grow(c, c->b_cq, 32 * ncl, 32 * k0) && grow(c, c->b_cv, 32 * ncl, 32 * k0) &&
@@ -1501,17 +1509,18 @@ int dem_get_bins(dem_ctx* c, long long cap, unsigned int* keys, int* ids, long l
   if (!c || !n) return DEM_ERR_INVALID_ARG;
   *n = c->n_entries;
   const long long m = std::min(cap, c->n_entries);
-  if (m > 0 && keys && ids && c->b_ids.p) {
-    // the device holds the ids grouped by bin in slot order: restore the
-    // bin key of every entry and sort each bin by sphere id
+  if (m > 0 && keys && ids && c->b_rec.p) {
+    // the device holds the records grouped by bin in slot order: restore
+    // the bin key of every entry and sort each bin by sphere id
     const long long B = c->n_entries, nb = c->n_entry_bins;
+    if (!grow(c, c->b_tmp, 4 * (size_t)B)) return fail(c, DEM_ERR_OOM, "staging");
+    launch_rec_ids(ptr<EntryRec>(c->b_rec), B, ptr<uint32_t>(c->b_tmp), c->st);
     std::vector<uint32_t> start((size_t)nb + 1), v((size_t)B);
     cudaMemcpyAsync(start.data(), c->b_bin_start.p, 4 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, c->st);
-    cudaMemcpyAsync(v.data(), c->b_ids.p, 4 * (size_t)B, cudaMemcpyDeviceToHost, c->st);
+    cudaMemcpyAsync(v.data(), c->b_tmp.p, 4 * (size_t)B, cudaMemcpyDeviceToHost, c->st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "get_bins");
     for (long long k = 0; k < nb; ++k) {
       const uint32_t s0 = start[k], s1 = start[k + 1];
-      for (uint32_t i = s0; i < s1; ++i) v[i] &= kIdMask;  // drop the owning-bin mask
       std::sort(v.begin() + s0, v.begin() + s1);
       for (uint32_t i = s0; i < s1 && (long long)i < m; ++i) {
         keys[i] = (unsigned int)k;
@@ -1579,6 +1588,105 @@ int dem_autotune_bins(dem_ctx* c, int n, const double* factors, int reps, double
   return cuda_check(c, "autotune");
 }
 
+int dem_set_tiles(dem_ctx* c, const dem_tiles* t) {
+  if (!c || !t) return DEM_ERR_INVALID_ARG;
+  if (t->pairs_blocks_per_sm < 1 || t->pairs_blocks_per_sm > 32 ||
+      (t->update_block != 64 && t->update_block != 128 && t->update_block != 256) ||
+      t->narrow_chunk < 1 || t->narrow_chunk > 64)
+    return fail(c, DEM_ERR_INVALID_ARG, "launch shapes out of range");
+  c->tiles = *t;
+  drop_graphs(c);  // captured graphs hold the old launch shapes
+  refresh_devstate(c);
+  return DEM_OK;
+}
+
+int dem_get_tiles(dem_ctx* c, dem_tiles* t) {
+  if (!c || !t) return DEM_ERR_INVALID_ARG;
+  *t = c->tiles;
+  return DEM_OK;
+}
+
+int dem_autotune_tiles(dem_ctx* c, int steps, int reps, dem_tiles* best) {
+  if (!c || steps < 1 || reps < 1 || !best) return DEM_ERR_INVALID_ARG;
+  cudaSetDevice(c->P.device);
+  int rc = finalize(c);
+  if (rc) return rc;
+  const dem_stats saved = c->stats;
+  const float* cm = c->D.cmargin;
+  c->D.cmargin = nullptr;
+  StepRunner R(c, 0);
+  if ((rc = R.init())) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto elapsed = [&]() -> double {
+    cudaEventRecord(e1, c->st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    return (double)t;
+  };
+  // the narrow-phase chunk, timed on rebuilds (which change no state)
+  const int chunks[] = {2, 4, 8, 16, 32};
+  double best_ms = -1.0;
+  dem_tiles cur = c->tiles;
+  for (int ch : chunks) {
+    c->tiles.narrow_chunk = ch;
+    if ((rc = rebuild(c))) break;  // sizes the buffers
+    cudaEventRecord(e0, c->st);
+    for (int r = 0; r < reps && rc == DEM_OK; ++r) rc = rebuild(c);
+    const double ms = elapsed() / reps;
+    if (rc) break;
+    if (best_ms < 0.0 || ms < best_ms) { best_ms = ms; cur.narrow_chunk = ch; }
+  }
+  c->tiles = cur;
+  // the step kernels, timed on `steps` steps from a snapshot taken at a fresh
+  // list; the snapshot is restored before every trial and at the end
+  if (rc == DEM_OK && (rc = rebuild(c)) == DEM_OK && (rc = take_snapshot(c)) == DEM_OK) {
+    auto time_steps = [&](const dem_tiles& t) -> double {
+      c->tiles = t;
+      refresh_devstate(c);
+      if (restore_snapshot(c)) return -1.0;
+      c->since = 0;
+      R.step(c->margin, false, false);  // warm-up
+      cudaEventRecord(e0, c->st);
+      for (int i = 0; i < steps; ++i) R.step(c->margin, false, false);
+      return elapsed() / steps;
+    };
+    const int bpsm[] = {2, 4, 8, 16};
+    const int upd[] = {64, 128, 256};
+    best_ms = -1.0;
+    dem_tiles pick = cur;
+    for (int b : bpsm) {
+      dem_tiles t = pick;
+      t.pairs_blocks_per_sm = b;
+      const double ms = time_steps(t);
+      if (ms >= 0.0 && (best_ms < 0.0 || ms < best_ms)) { best_ms = ms; pick = t; }
+    }
+    best_ms = -1.0;
+    const dem_tiles base = pick;
+    for (int u : upd) {
+      dem_tiles t = base;
+      t.update_block = u;
+      const double ms = time_steps(t);
+      if (ms >= 0.0 && (best_ms < 0.0 || ms < best_ms)) { best_ms = ms; pick = t; }
+    }
+    c->tiles = pick;
+    refresh_devstate(c);
+    rc = restore_snapshot(c);
+    c->since = 0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->D.cmargin = cm;
+  drop_graphs(c);
+  // trial steps and rebuilds leave no trace in the counters
+  c->stats = saved;
+  if (rc) return rc;
+  *best = c->tiles;
+  return cuda_check(c, "autotune tiles");
+}
+
 int dem_set_deterministic(dem_ctx* c, int on) {
   if (!c) return DEM_ERR_INVALID_ARG;
   c->det = on ? 1 : 0;
@@ -1638,7 +1746,7 @@ int dem_trace(dem_ctx* c, int windows, int window, int n_candidates, const doubl
   const long long ncl = c->ncl;
   long long total = 0;
   const size_t capb = (size_t)std::max<long long>(cap, 1);
-  if (!grow(c, c->b_tx, 4 * capb * kMlpIn) || !grow(c, c->b_tt, 4 * capb) || !grow(c, c->b_tcount, 64) ||
+  if (!grow(c, c->b_tx, 4 * capb * kMlpIn) || !grow(c, c->b_tt, 4 * capb) ||
       !grow(c, c->b_tr_q, 16 * (ncl + 1)) || !grow(c, c->b_tr_vox, 16 * (ncl + 1)) ||
       !grow(c, c->b_tr_off, 16 * (ncl + 1)) || !grow(c, c->b_tr_pos, 32 * (ncl + 1)) ||
       !grow(c, c->b_dmax, 4 * ((size_t)c->nbins + 1))) {
@@ -1646,7 +1754,6 @@ int dem_trace(dem_ctx* c, int windows, int window, int n_candidates, const doubl
     c->l_cand = saved_cand;
     return fail(c, DEM_ERR_OOM, "trace buffers");
   }
-  cudaMemsetAsync(c->b_tcount.p, 0, 8, c->st);
   cudaMemsetAsync(c->b_dmax.p, 0, 4 * (size_t)c->nbins, c->st);
   TraceRef tr{ptr<int4>(c->b_tr_vox), ptr<float4>(c->b_tr_off), ptr<double4_32a>(c->b_tr_pos),
               ptr<float4>(c->b_tr_q)};
@@ -1666,7 +1773,7 @@ int dem_trace(dem_ctx* c, int windows, int window, int n_candidates, const doubl
                           ptr<int>(c->b_T), s, c->st);
       }
       launch_trace_emit(rows, ptr<float>(c->b_feat), ptr<int>(c->b_T), window, ptr<float>(c->b_tx),
-                        ptr<float>(c->b_tt), ptr<unsigned long long>(c->b_tcount), cap, c->st);
+                        ptr<float>(c->b_tt), total, cap, c->st);
       total += rows;
     }
   }

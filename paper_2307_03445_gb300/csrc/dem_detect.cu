@@ -97,6 +97,37 @@ __device__ __forceinline__ bool lattice_from_pose(const DevState& d, long long s
   return exact;
 }
 
+// The bins an enlarged box {q - rho, q + rho} touches (clamped to the grid),
+// walked with x fastest; mask() is the owning-bin mask of the current bin.
+struct BinWalk {
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  int x = 0, y = 0, z = 0;
+  long long n = 0;  // bins touched
+  uint32_t d0 = 0, d01 = 0, base = 0;
+  __device__ void init(const SceneGrid& g, const int4 q) {
+    const int qq[3] = {q.x, q.y, q.z};
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = clampi(floordiv_bin((long long)qq[k] - q.w, g.L, g.invL), g.dims[k] - 1);
+      hi[k] = clampi(floordiv_bin((long long)qq[k] + q.w, g.L, g.invL), g.dims[k] - 1);
+    }
+    x = lo[0]; y = lo[1]; z = lo[2];
+    n = (long long)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+    d0 = (uint32_t)g.dims[0];
+    d01 = d0 * (uint32_t)g.dims[1];
+    base = g.key_base;
+  }
+  __device__ uint32_t key() const { return base + (uint32_t)z * d01 + (uint32_t)y * d0 + (uint32_t)x; }
+  __device__ uint32_t mask() const {
+    return (x == lo[0] ? 1u : 0u) | (y == lo[1] ? 2u : 0u) | (z == lo[2] ? 4u : 0u);
+  }
+  __device__ void next() {
+    if (++x > hi[0]) {
+      x = lo[0];
+      if (++y > hi[1]) { y = lo[1]; ++z; }
+    }
+  }
+};
+
 // ceil((r + m) 2^24) + 1 with r + m rounded to double (the scaling by 2^24 is exact).
 __device__ __forceinline__ long long tpl_rho(double r, double m) {
   return ceil_pos_d2ll(__dmul_rn(__dadd_rn(r, m), kDetScale)) + 1;
@@ -107,6 +138,8 @@ __global__ void k_tpl_rho(DevState d, double margin, int n, int* __restrict__ tr
   if (i < n) trho[i] = (int)tpl_rho(d.tp64[i].w, margin);
 }
 
+// One thread per sphere: detection coordinates, wall candidates, and the
+// counting pass of the bin sort (one count per bin the enlarged box touches).
 __global__ void k_detect(DevState d, DetectOut o, double margin, const double* __restrict__ smargin,
                          double t, double travel_time) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,18 +180,20 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   const long long rho = o.trho ? (long long)o.trho[si.y] : tpl_rho(d.tp64[si.y].w, m);
   const float tf = d2f(t);
   const float rmf = d.tp32[si.y].w + d2f(m);  // r + m for the estimates
-  o.det[s] = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
-  // counting pass of the bin sort: one count per bin the enlarged box touches
-  int lo[3], hi[3];
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = clampi(floordiv_bin(qc[k] - rho, g.L, g.invL), g.dims[k] - 1);
-    hi[k] = clampi(floordiv_bin(qc[k] + rho, g.L, g.invL), g.dims[k] - 1);
+  const int4 dq = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
+  o.det[s] = dq;
+  {
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = clampi(floordiv_bin(qc[k] - rho, g.L, g.invL), g.dims[k] - 1);
+      hi[k] = clampi(floordiv_bin(qc[k] + rho, g.L, g.invL), g.dims[k] - 1);
+    }
+    const uint32_t d0 = (uint32_t)g.dims[0], d01 = d0 * (uint32_t)g.dims[1];
+    for (int bz = lo[2]; bz <= hi[2]; ++bz)
+      for (int by = lo[1]; by <= hi[1]; ++by)
+        for (int bx = lo[0]; bx <= hi[0]; ++bx)
+          atomicAdd(&o.bin_size[g.key_base + (uint32_t)bz * d01 + (uint32_t)by * d0 + (uint32_t)bx], 1u);
   }
-  const uint32_t d0 = (uint32_t)g.dims[0], d01 = d0 * (uint32_t)g.dims[1];
-  for (int bz = lo[2]; bz <= hi[2]; ++bz)
-    for (int by = lo[1]; by <= hi[1]; ++by)
-      for (int bx = lo[0]; bx <= hi[0]; ++bx)
-        atomicAdd(&o.bin_size[g.key_base + (uint32_t)bz * d01 + (uint32_t)by * d0 + (uint32_t)bx], 1u);
   // sphere-wall candidates: distance within radius + margin + wall travel
   uint32_t mask = 0;
   for (int i = 0; i < g.wall_count; ++i) {
@@ -185,51 +220,40 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
 }
 
 // Scatter pass of the bin sort: every registration takes a slot of its bin
-// (counting the bin's size down to zero) and stores the sphere id with the
-// owning-bin mask in the top bits.  The order inside a bin is whatever the
-// atomics give; nothing downstream depends on it.  A slot request past the
-// counted size (a broken invariant) is dropped and flagged.
+// (counting the bin's size down to zero) and stores there the record the
+// narrow phase tests (lattice centre, enlarged radius, owner, sphere id,
+// owning-bin mask).  The order inside a bin is whatever the atomics give;
+// nothing downstream depends on it.  A slot request past the counted size (a
+// broken invariant) is dropped and flagged.
 __global__ void k_bin_scatter(DevState d, DetectOut o) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= d.ns) return;
   const int4 q = o.det[s];
-  const SceneGrid g = d.grids[d.cinfo[d.sinfo[s].x].y];
-  int lo[3], hi[3];
-  const int qq[3] = {q.x, q.y, q.z};
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = clampi(floordiv_bin((long long)qq[k] - q.w, g.L, g.invL), g.dims[k] - 1);
-    hi[k] = clampi(floordiv_bin((long long)qq[k] + q.w, g.L, g.invL), g.dims[k] - 1);
+  const int owner = d.sinfo[s].x;
+  BinWalk w;
+  w.init(d.grids[d.cinfo[owner].y], q);
+  for (long long r = 0; r < w.n; ++r, w.next()) {
+    const uint32_t key = w.key();
+    const uint32_t left = atomicSub(&o.bin_size[key], 1u);
+    if (left == 0u) {  // more registrations than counted: a broken invariant
+      atomicAdd(&o.bin_size[key], 1u);
+      atomicOr(d.flags, kFlagBounds);
+      continue;
+    }
+    EntryRec rec;
+    rec.qx = q.x; rec.qy = q.y; rec.qz = q.z; rec.rho = q.w;
+    rec.owner = owner;
+    rec.id = (uint32_t)s;
+    rec.mask = w.mask();
+    rec.pad = 0u;
+    o.rec[o.bin_start[key] + left - 1u] = rec;
   }
-  const uint32_t d0 = (uint32_t)g.dims[0], d01 = d0 * (uint32_t)g.dims[1];
-  for (int z = lo[2]; z <= hi[2]; ++z)
-    for (int y = lo[1]; y <= hi[1]; ++y)
-      for (int x = lo[0]; x <= hi[0]; ++x) {
-        const uint32_t key = g.key_base + (uint32_t)z * d01 + (uint32_t)y * d0 + (uint32_t)x;
-        const uint32_t left = atomicSub(&o.bin_size[key], 1u);
-        if (left == 0u) {
-          atomicAdd(&o.bin_size[key], 1u);
-          atomicOr(d.flags, kFlagBounds);
-          continue;
-        }
-        const uint32_t mask = (x == lo[0] ? 1u : 0u) | (y == lo[1] ? 2u : 0u) | (z == lo[2] ? 4u : 0u);
-        o.ids[o.bin_start[key] + left - 1u] = (uint32_t)s | (mask << kIdBits);
-      }
 }
 
-// Gathers, in sorted order, the record of every registration.
-__global__ void k_gather_entries(DevState d, DetectOut o, long long n) {
+// The sphere id of every registration (inspection).
+__global__ void k_rec_ids(const EntryRec* __restrict__ rec, long long n, uint32_t* __restrict__ ids) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t v = o.ids[i];
-  const uint32_t s = v & kIdMask;
-  const int4 q = o.det[s];
-  EntryRec r;
-  r.qx = q.x; r.qy = q.y; r.qz = q.z; r.rho = q.w;
-  r.owner = d.sinfo[s].x;
-  r.id = s;
-  r.mask = v >> kIdBits;
-  r.pad = 0u;
-  o.rec[i] = r;
+  if (i < n) ids[i] = rec[i].id;
 }
 
 // Narrow phase, one warp per bin (persistent warps striding over the bins).
@@ -248,6 +272,7 @@ __global__ void k_gather_entries(DevState d, DetectOut o, long long n) {
 // grow the buffer and run the pass again.  o.pair_cnt[a] counts the partners
 // of every sphere a.
 constexpr int kNarrowWarps = 8;
+constexpr int kBinChunk = 8;  // bins a warp claims at a time, unless o.chunk says otherwise
 
 __device__ __forceinline__ void flush_pairs(const DetectOut& o, uint2* buf, int n, int lane) {
   unsigned long long base = 0;
@@ -340,9 +365,18 @@ __global__ void __launch_bounds__(32 * kNarrowWarps) k_narrow_bins(DetectOut o) 
     }
     __syncwarp();
   };
-  const long long nw = (long long)gridDim.x * kNarrowWarps;
-  for (long long bin = (long long)blockIdx.x * kNarrowWarps + wib; bin < (long long)o.nbins;
-       bin += nw) {
+  // every warp claims chunks of consecutive bins from a global counter until
+  // none are left, so bins of uneven size do not leave warps idle at the end
+  const unsigned long long chunk = (unsigned long long)(o.chunk > 0 ? o.chunk : kBinChunk);
+  unsigned long long bin = 0, b1 = 0;  // the warp's current chunk [bin, b1)
+  for (;; ++bin) {
+    if (bin >= b1) {
+      unsigned long long b0 = 0;
+      if (lane == 0) b0 = atomicAdd(o.next_bin, chunk);
+      bin = __shfl_sync(0xffffffffu, b0, 0);
+      if (bin >= (unsigned long long)o.nbins) break;
+      b1 = bin + chunk < o.nbins ? bin + chunk : o.nbins;
+    }
     const uint32_t s = o.bin_start[bin], e = o.bin_start[bin + 1];
     if (e <= s + 1u) continue;  // fewer than two registrations
     for (uint32_t i0 = s; i0 < e; i0 += 32u) {
@@ -401,13 +435,42 @@ __global__ void k_scatter_pairs(DetectOut o, long long np, uint32_t* __restrict_
   pb[o.pair_off[p.x] + left - 1u] = p.y;
 }
 
-// Sorts every row of the new list by b (insertion sort: rows are short) and
-// fills in the row owner a.
+// Sorts every row of the new list by b and fills in the row owner a.  A row
+// of up to kRowRegs partners (nearly all of them) is loaded at once into
+// registers and sorted there by odd-even transposition (kRowRegs rounds of
+// compare-exchanges with fixed indices); a longer row is insertion-sorted in
+// place.
+constexpr int kRowRegs = 8;
+
 __global__ void k_sort_rows(long long ns, const uint32_t* __restrict__ row, int* __restrict__ pa,
                             uint32_t* __restrict__ pb) {
   const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= ns) return;
   const uint32_t r0 = row[a], r1 = row[a + 1];
+  const uint32_t n = r1 - r0;
+  if (n == 0) return;
+  if (n <= (uint32_t)kRowRegs) {
+    uint32_t v[kRowRegs];
+#pragma unroll
+    for (int k = 0; k < kRowRegs; ++k) v[k] = (uint32_t)k < n ? pb[r0 + k] : 0xffffffffu;
+#pragma unroll
+    for (int p = 0; p < kRowRegs; ++p) {
+#pragma unroll
+      for (int k = p & 1; k + 1 < kRowRegs; k += 2) {
+        const uint32_t lo = min(v[k], v[k + 1]), hi = max(v[k], v[k + 1]);
+        v[k] = lo;
+        v[k + 1] = hi;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kRowRegs; ++k) {
+      if ((uint32_t)k < n) {
+        pb[r0 + k] = v[k];
+        pa[r0 + k] = (int)a;
+      }
+    }
+    return;
+  }
   for (uint32_t i = r0 + 1; i < r1; ++i) {
     const uint32_t v = pb[i];
     uint32_t j = i;
@@ -420,23 +483,8 @@ __global__ void k_sort_rows(long long ns, const uint32_t* __restrict__ row, int*
   for (uint32_t i = r0; i < r1; ++i) pa[i] = (int)a;
 }
 
-__global__ void k_wall_emit(DevState d, DetectOut o, int* __restrict__ ws, uint32_t* __restrict__ ww) {
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= d.ns) return;
-  uint32_t mask = o.wall_mask[s];
-  if (!mask) return;
-  const SceneGrid g = d.grids[d.cinfo[d.sinfo[s].x].y];
-  uint32_t off = o.wall_off[s];
-  while (mask) {
-    const int i = __ffs(mask) - 1;
-    mask &= mask - 1;
-    ws[off] = (int)s;
-    ww[off] = (uint32_t)d.wall_idx[g.wall_start + i];
-    ++off;
-  }
-}
-
-// Carry the tangential history of every (a, b) present in the old list.
+// Carries the tangential history of every (a, b) present in the old list
+// (binary search of b in the old row of a, which is sorted by b).
 __global__ void k_hist_pairs(ContactList oldl, ContactList newl, long long old_ns) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= newl.n) return;
@@ -456,6 +504,22 @@ __global__ void k_hist_pairs(ContactList oldl, ContactList newl, long long old_n
       newl.u[2 * newl.cap + i] = oldl.u[2 * oldl.cap + lo];
       newl.pb[i] = b | kHistFlag;
     }
+  }
+}
+
+__global__ void k_wall_emit(DevState d, DetectOut o, int* __restrict__ ws, uint32_t* __restrict__ ww) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns) return;
+  uint32_t mask = o.wall_mask[s];
+  if (!mask) return;
+  const SceneGrid g = d.grids[d.cinfo[d.sinfo[s].x].y];
+  uint32_t off = o.wall_off[s];
+  while (mask) {
+    const int i = __ffs(mask) - 1;
+    mask &= mask - 1;
+    ws[off] = (int)s;
+    ww[off] = (uint32_t)d.wall_idx[g.wall_start + i];
+    ++off;
   }
 }
 
@@ -556,9 +620,9 @@ void launch_detect(const DevState& d, const DetectOut& o, double margin, const d
   { k_detect<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, margin, smargin, t, travel_time); count_launch(); }
 }
 
-void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, cudaStream_t st) {
+void launch_rec_ids(const EntryRec* rec, long long n, uint32_t* ids, cudaStream_t st) {
   if (n == 0) return;
-  k_gather_entries<<<nblk(n, 256), 256, 0, st>>>(d, o, n);
+  k_rec_ids<<<nblk(n, 256), 256, 0, st>>>(rec, n, ids);
   count_launch();
 }
 
@@ -567,21 +631,36 @@ void launch_bin_scatter(const DevState& d, const DetectOut& o, cudaStream_t st) 
   { k_bin_scatter<<<nblk(d.ns, 128), 128, 0, st>>>(d, o); count_launch(); }
 }
 
-void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
-                   cudaStream_t st) {
+void launch_narrow(const DevState& d, const DetectOut& o, cudaStream_t st) {
   if (d.ns == 0 || o.nbins == 0) return;
-  if (write) {
-    if (o.np > 0) {
-      k_scatter_pairs<<<nblk(o.np, 256), 256, 0, st>>>(o, o.np, pb, d.flags);
-      count_launch();
+  // resident blocks only: the warps take their bins from the counter
+  static int occ = 0;
+  if (occ == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_narrow_bins, 32 * kNarrowWarps, 0) !=
+            cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 4;
     }
-    k_sort_rows<<<nblk(d.ns, 256), 256, 0, st>>>(d.ns, o.pair_off, pa, pb);
+  }
+  const long long per_block = (long long)kNarrowWarps * (o.chunk > 0 ? o.chunk : kBinChunk);
+  const long long want = ((long long)o.nbins + per_block - 1) / per_block;
+  const long long cap = (long long)device_sms() * occ;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  k_narrow_bins<<<grid, 32 * kNarrowWarps, 0, st>>>(o);
+  count_launch();
+}
+
+void launch_list_rows(const DevState& d, const DetectOut& o, const ContactList& newl,
+                      const ContactList* oldl, long long old_ns, cudaStream_t st) {
+  if (d.ns == 0) return;
+  if (o.np > 0) {
+    k_scatter_pairs<<<nblk(o.np, 256), 256, 0, st>>>(o, o.np, newl.pb, d.flags);
     count_launch();
-  } else {
-    const long long want = ((long long)o.nbins + kNarrowWarps - 1) / kNarrowWarps;
-    const long long cap = (long long)device_sms() * 8;
-    const unsigned grid = (unsigned)(want < cap ? want : cap);
-    k_narrow_bins<<<grid, 32 * kNarrowWarps, 0, st>>>(o);
+  }
+  k_sort_rows<<<nblk(d.ns, 256), 256, 0, st>>>(d.ns, newl.row, newl.pa, newl.pb);
+  count_launch();
+  if (oldl && oldl->n > 0 && o.np > 0) {
+    k_hist_pairs<<<nblk(o.np, 256), 256, 0, st>>>(*oldl, newl, old_ns);
     count_launch();
   }
 }
@@ -592,9 +671,8 @@ void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* 
   { k_wall_emit<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, ws, ww); count_launch(); }
 }
 
-void launch_hist_map(const ContactList& oldl, ContactList& newl, long long old_ns,
-                     cudaStream_t st) {
-  if (newl.n > 0) { k_hist_pairs<<<nblk(newl.n, 256), 256, 0, st>>>(oldl, newl, old_ns); count_launch(); }
+void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns,
+                       cudaStream_t st) {
   if (newl.nw > 0) { k_hist_walls<<<nblk(newl.nw, 256), 256, 0, st>>>(oldl, newl, old_ns); count_launch(); }
 }
 

@@ -76,6 +76,9 @@ struct DevState {
   long long* halt_at;       // learned rule, halt mode: the first step whose state failed
                             //   the displacement certificate (LLONG_MAX: none); every
                             //   per-step kernel of a later step returns at once.  NULL: off
+  // launch shapes (read by the host launchers; chosen by dem_autotune_tiles)
+  int pairs_bpsm;           // blocks of 256 threads per SM for the pair force kernels
+  int upd_block;            // clumps per block of the FP32_VOXEL update kernel: 64, 128, 256
 };
 
 // True when the kernels of the step that starts from state *d.dstep must not
@@ -101,23 +104,20 @@ struct alignas(32) EntryRec {
   uint32_t pad;
 };
 
-// Registrations carry the owning-bin mask in the top bits of the sphere id.
-constexpr int kIdBits = 29;
-constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
-
 struct DetectOut {
-  EntryRec* rec;            // per entry (bin order)
+  EntryRec* rec;            // per entry, grouped by bin (any order inside a bin)
   int4* det;                // per sphere {qx, qy, qz, rho}
   uint32_t* wall_mask;      // per sphere
   uint32_t* wall_cnt;       // per sphere
   uint32_t* wall_off;       // per sphere (scan)
-  uint32_t* ids;            // per entry, grouped by bin: sphere id | owning-bin mask << kIdBits
   uint32_t* bin_size;       // per bin (+1): registrations (counting pass)
   uint32_t* bin_start;      // per bin (+1): first entry; bin k is [start[k], start[k + 1])
   uint32_t nbins;
   uint2* upairs;            // narrow phase: kept pairs (a, b), unordered
   unsigned long long ucap;  //   capacity of upairs
   unsigned long long* d_np; //   pairs found (may exceed ucap)
+  unsigned long long* next_bin;  // next unclaimed bin (zeroed by the caller)
+  int chunk;                //   bins a warp claims at a time (a launch shape)
   long long np;             //   pairs found, on the host (write pass)
   uint32_t* pair_cnt;       // per sphere
   uint32_t* pair_off;       // per sphere (scan) -> row pointer (ns + 1 entries)
@@ -146,20 +146,24 @@ void launch_detect(const DevState& d, const DetectOut& o, double margin, const d
                    double t, double travel_time, cudaStream_t st);
 // Bin sort by counting: launch_detect adds every registration to o.bin_size
 // (zeroed by the caller); after the exclusive scan of bin_size into
-// o.bin_start (nbins + 1 entries), launch_bin_scatter places the ids and
-// leaves bin_size at zero.
+// o.bin_start (nbins + 1 entries), launch_bin_scatter writes the records
+// o.rec grouped by bin and leaves bin_size at zero.
 void launch_bin_scatter(const DevState& d, const DetectOut& o, cudaStream_t st);
-void launch_gather_entries(const DevState& d, const DetectOut& o, long long n, cudaStream_t st);
-// Narrow phase over the bins.  Find pass: the kept pairs go to o.upairs
-// (count in *o.d_np, zeroed by the caller) and o.pair_cnt[a] += partners
-// b > a (pair_cnt zeroed by the caller).  Write pass (after the scan of
-// pair_cnt into pair_off, o.np set): rows pa / pb, each sorted by b;
-// consumes pair_cnt.
-void launch_narrow(const DevState& d, const DetectOut& o, bool write, int* pa, uint32_t* pb,
-                   cudaStream_t st);
+// ids[i] = rec[i].id (inspection).
+void launch_rec_ids(const EntryRec* rec, long long n, uint32_t* ids, cudaStream_t st);
+// Narrow phase over the bins: the kept pairs go to o.upairs as (lower id,
+// higher id) (count in *o.d_np, zeroed by the caller) and o.pair_cnt[a] +=
+// partners b > a (pair_cnt zeroed by the caller).
+void launch_narrow(const DevState& d, const DetectOut& o, cudaStream_t st);
+// After the scan of pair_cnt into pair_off (= newl.row) with o.np set: rows
+// newl.pa / newl.pb, each sorted by b (consumes pair_cnt); with an old list
+// (oldl != NULL, its first old_ns spheres comparable) the tangential history
+// of every pair both lists hold is carried into newl.u.
+void launch_list_rows(const DevState& d, const DetectOut& o, const ContactList& newl,
+                      const ContactList* oldl, long long old_ns, cudaStream_t st);
 void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,
                       cudaStream_t st);
-void launch_hist_map(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
+void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
 void launch_copy_row(const uint32_t* off, long long n, uint32_t total, uint32_t* row,
                      cudaStream_t st);
 void launch_audit(const DevState& d, const DetectOut& o, const ContactList& cur, long long n_fresh,

@@ -157,14 +157,16 @@ __global__ void k_trace_bins(const uint32_t* __restrict__ occ, long long n_occ, 
   dmax[key] = 0;
 }
 
+// Row i of this window (occupied bin i / nc, candidate i % nc) goes to row
+// base + i of the output, so the candidates of one bin stay adjacent and in
+// order.
 __global__ void k_trace_emit(long long n_rows, const float* __restrict__ xw,
                              const int* __restrict__ T, int window, float* __restrict__ x,
-                             float* __restrict__ t, unsigned long long* __restrict__ count,
-                             long long cap) {
+                             float* __restrict__ t, long long base, long long cap) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_rows) return;
-  const unsigned long long k = atomicAdd(count, 1ull);
-  if ((long long)k >= cap) return;
+  const long long k = base + i;
+  if (k >= cap) return;
   for (int f = 0; f < kMlpIn; ++f) x[k * kMlpIn + f] = xw[i * kMlpIn + f];
   const int tt = T[i] > 0 ? T[i] : window;
   t[k] = logf((float)tt);
@@ -230,9 +232,9 @@ void launch_trace_step(const DevState& d, const TraceRef& tr, const uint32_t* ch
   count_launch(2);
 }
 void launch_trace_emit(long long n_rows, const float* xw, const int* T, int window, float* x,
-                       float* t, unsigned long long* count, long long cap, cudaStream_t st) {
-  if (n_rows == 0) return;
-  k_trace_emit<<<nblk(n_rows, 256), 256, 0, st>>>(n_rows, xw, T, window, x, t, count, cap);
+                       float* t, long long base, long long cap, cudaStream_t st) {
+  if (n_rows == 0 || base >= cap) return;
+  k_trace_emit<<<nblk(n_rows, 256), 256, 0, st>>>(n_rows, xw, T, window, x, t, base, cap);
   count_launch();
 }
 

@@ -40,7 +40,9 @@ void launch_trace_ref(const DevState& d, const TraceRef& tr, cudaStream_t st);
 void launch_trace_step(const DevState& d, const TraceRef& tr, const uint32_t* chome, int* dmax,
                        const uint32_t* occ, long long n_occ, int nc, const float* cand, int* T,
                        int step, cudaStream_t st);
+// Writes the window's rows (features, log lifetime) to rows base.. of x / t,
+// dropping those at or past cap.
 void launch_trace_emit(long long n_rows, const float* xw, const int* T, int window, float* x,
-                       float* t, unsigned long long* count, long long cap, cudaStream_t st);
+                       float* t, long long base, long long cap, cudaStream_t st);
 
 }  // namespace dem

@@ -484,16 +484,18 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
 }
 
 // FP32_VOXEL mode.
-// One block's batch of kUpd clumps starting at c0 (FP32_VOXEL mode).
+// One block's batch of B clumps starting at c0 (FP32_VOXEL mode).
+template <int B>
 struct UpdShared {
-  float Rh[kUpd][9];
-  float Rl[kUpd][9];
-  int4 vox[kUpd];
-  float4 off[kUpd];
+  float Rh[B][9];
+  float Rl[B][9];
+  int4 vox[B];
+  float4 off[B];
 };
 
+template <int B>
 __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, int integrate,
-                                               float margin, int check_cert, UpdShared& sh) {
+                                               float margin, int check_cert, UpdShared<B>& sh) {
   float (*sRh)[9] = sh.Rh;
   float (*sRl)[9] = sh.Rl;
   int4* sVox = sh.vox;
@@ -656,10 +658,10 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
     sOff[threadIdx.x] = off;
   }
   __syncthreads();
-  const long long c1 = c0 + kUpd < d.ncl ? c0 + kUpd : d.ncl;
+  const long long c1 = c0 + B < d.ncl ? c0 + B : d.ncl;
   if (c0 >= c1) return;
   const long long s0 = d.csph[c0], s1 = d.csph[c1];
-  for (long long s = s0 + threadIdx.x; s < s1; s += kUpd) {
+  for (long long s = s0 + threadIdx.x; s < s1; s += B) {
     const int2 si = d.sinfo[s];
     const int lc = (int)(si.x - c0);
     const float4 tp = d.tp32[si.y];
@@ -692,12 +694,14 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
   }
 }
 
-// One block per batch of kUpd clumps.
-__global__ void __launch_bounds__(kUpd) k_update32(DevState d, int integrate, float margin,
-                                                   int check_cert) {
+// One block per batch of B clumps (B = 64, 128 or 256: a launch shape the
+// tile autotuner picks).
+template <int B>
+__global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float margin,
+                                                int check_cert) {
   if (integrate && halted(d)) return;
-  __shared__ UpdShared sh;
-  update32_batch(d, (long long)blockIdx.x * kUpd, integrate, margin, check_cert, sh);
+  __shared__ UpdShared<B> sh;
+  update32_batch<B>(d, (long long)blockIdx.x * B, integrate, margin, check_cert, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -960,7 +964,7 @@ int sm_count() {
 // persistent grid of fixed size, so one launch (or one captured graph) serves
 // every list the buffers will hold.
 void launch_force_pairs(const DevState& d, ContactList& l, bool count_active, cudaStream_t st) {
-  const unsigned grid = (unsigned)sm_count() * 8;
+  const unsigned grid = (unsigned)sm_count() * (unsigned)(d.pairs_bpsm > 0 ? d.pairs_bpsm : 8);
   if (d.prec == 0)
     { k_pairs64<<<grid, 256, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
   else
@@ -988,10 +992,15 @@ void launch_update(const DevState& d, bool integrate, long long step, double mar
     if (d.prec == 0)
       { k_update64<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
                                                       check_cert ? 1 : 0); count_launch(); }
+    else if (d.upd_block == 64)
+      { k_update32<64><<<nblk(d.ncl, 64), 64, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
+                                                     check_cert ? 1 : 0); count_launch(); }
+    else if (d.upd_block == 256)
+      { k_update32<256><<<nblk(d.ncl, 256), 256, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
+                                                        check_cert ? 1 : 0); count_launch(); }
     else
-      { k_update32<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
-                                                      check_cert ? 1 : 0);
-        count_launch(); }
+      { k_update32<128><<<nblk(d.ncl, 128), 128, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
+                                                        check_cert ? 1 : 0); count_launch(); }
   }
   if (integrate) {
     k_walls_advance<<<1, 256, 0, st>>>(d);

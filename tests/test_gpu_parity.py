@@ -416,3 +416,48 @@ def test_deterministic_mode_is_bit_reproducible(dem, oracle_mod, prec):
     else:
         assert np.abs(vel - vo).max() / np.abs(vo - sc.vel).max() < 1e-5
         assert np.abs(pos - po).max() / np.abs(po - sc.pos).max() < 1e-5
+
+
+def test_launch_shapes_change_no_result(dem):
+    """Launch shapes (pair blocks per SM, update block, narrow chunk) change no
+    result: in deterministic mode the state after 45 steps with rebuilds is
+    bit-identical across shapes; the list and the bins are identical too.  The
+    tile autotuner picks shapes from its sets, leaves the state, step count
+    and counters as they were, and out-of-range shapes are refused."""
+    margin, K, nsteps = 2e-4, 10, 45
+    sc = _scene(8, 400, scenes.PREC_FP32, margin=margin, compress=1.0, jitter=0.05)
+    shapes = [None, dict(pairs_blocks_per_sm=2, update_block=64, narrow_chunk=3),
+              dict(pairs_blocks_per_sm=16, update_block=256, narrow_chunk=1)]
+    runs = []
+    for sh in shapes:
+        with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+            sim.set_deterministic(True)
+            if sh:
+                sim.set_tiles(**sh)
+                assert sim.tiles() == sh
+            sim.step(nsteps)
+            sim.rebuild()
+            a, b, _, ws, ww, _ = sim.contacts()
+            runs.append((sim.state(), sim.bins(), (a, b, ws, ww)))
+    for state, bins, lists in runs[1:]:
+        for x, y in zip(runs[0][0], state):
+            assert np.array_equal(x, y)
+        for x, y in zip(runs[0][1] + runs[0][2], bins + lists):
+            assert np.array_equal(x, y)
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        sim.step(7)
+        before, st0 = sim.state(), sim.stats()
+        best = sim.autotune_tiles(steps=3, reps=1)
+        assert best["pairs_blocks_per_sm"] in (2, 4, 8, 16)
+        assert best["update_block"] in (64, 128, 256)
+        assert best["narrow_chunk"] in (2, 4, 8, 16, 32)
+        assert sim.tiles() == best
+        for x, y in zip(before, sim.state()):
+            assert np.array_equal(x, y)
+        st1 = sim.stats()
+        assert st1["steps"] == st0["steps"] and st1["rebuilds"] == st0["rebuilds"]
+        for bad in (dict(update_block=100), dict(pairs_blocks_per_sm=0), dict(narrow_chunk=65)):
+            with pytest.raises(dem.DemError, match="INVALID"):
+                sim.set_tiles(**bad)
+        assert sim.tiles() == best
+        sim.step(5)  # still steps after tuning
