@@ -386,8 +386,10 @@ typedef struct {
 int dem_set_learned_policy(dem_ctx* ctx, dem_mlp* mlp, const dem_learned_params* params);
 
 /* Training traces from the plain rule.  Runs `windows` windows of `window`
- * steps; at the start of each window every occupied bin yields, for each
- * candidate margin m, the features
+ * steps; at the start of each window every occupied bin of the learned
+ * rule's grid (cells of the scene's base bin edge: its bin_size, else twice
+ * the largest enlarged radius, whatever edge dem_autotune_bins picks for
+ * detection) yields, for each candidate margin m, the features
  *   x = [ln(1 + clumps in bin), ln(h vmax / m), ln(h vmean / m),
  *        ln(h^2 amax / m), ln(m / r_mean), ln(h^2 |g| / m)]
  * (vmax, vmean: largest and mean clump speed bound |v| + |w| r_bound; amax:

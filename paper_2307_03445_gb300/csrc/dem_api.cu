@@ -56,6 +56,8 @@ struct dem_ctx {
   std::vector<int> wall_user, wall_scene;
   std::vector<SceneGrid> grids;
   uint32_t nbins = 0;
+  std::vector<SceneGrid> lgrids;  // the learned rule's feature grids (base bin edge)
+  uint32_t n_lbins = 0;
   // clumps (host bookkeeping)
   std::vector<int> h_ctpl, h_cscene;
   long long ncl = 0, ns = 0;
@@ -65,7 +67,7 @@ struct dem_ctx {
   Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cv, b_cw, b_mv64, b_mw64, b_mv32, b_mw32;
   Buf b_acc64, b_acc32, b_ref_pos, b_ref_vox, b_ref_off, b_ref_q;
   Buf b_sinfo, b_sa64, b_sb64, b_sa32, b_sb32;
-  Buf b_grids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
+  Buf b_grids, b_lgrids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
   Buf b_flags, b_counters, b_totals, b_dstep;
   // detection scratch
   Buf b_det, b_bin_size, b_wall_mask, b_wall_cnt;
@@ -348,13 +350,15 @@ double current_margin(const dem_ctx* c) {
 
 // Detection grids of all scenes (bin edge = the scene's base edge times
 // bin_factor); the wall ranges of existing grids are kept.
-int build_grids(dem_ctx* c) {
-  std::vector<SceneGrid> grids;
+// Per-scene grids with bin edge `factor` times the scene's base edge (its
+// bin_size, else twice the largest enlarged radius).
+int make_grids(dem_ctx* c, double factor, std::vector<SceneGrid>& grids, uint32_t& nbins) {
+  grids.clear();
   uint64_t base = 0;
   for (size_t s = 0; s < c->scenes.size(); ++s) {
     const SceneH& sh = c->scenes[s];
     SceneGrid g{};
-    const double bin = (sh.bin > 0.0 ? sh.bin : 2.0 * (c->r_max + c->margin)) * c->bin_factor;
+    const double bin = (sh.bin > 0.0 ? sh.bin : 2.0 * (c->r_max + c->margin)) * factor;
     long long L = (long long)std::ceil(bin * kDetScale);
     if (L < 1) L = 1;
     for (int k = 0; k < 3; ++k) {
@@ -372,14 +376,29 @@ int build_grids(dem_ctx* c) {
     g.key_base = (uint32_t)base;
     base += (uint64_t)g.dims[0] * g.dims[1] * g.dims[2];
     if (base >= (1ull << 32) - 1) return fail(c, DEM_ERR_INVALID_ARG, "too many bins (> 2^32)");
-    if (s < c->grids.size()) {
-      g.wall_start = c->grids[s].wall_start;
-      g.wall_count = c->grids[s].wall_count;
-    }
     grids.push_back(g);
   }
+  nbins = (uint32_t)base;
+  return DEM_OK;
+}
+
+// The detection grids (bin edge scaled by the tuned bin factor) and the
+// learned rule's feature grids (the base edge itself, so that the features
+// and the trained model do not depend on the detection tuning).
+int build_grids(dem_ctx* c) {
+  std::vector<SceneGrid> grids, lgrids;
+  uint32_t nb = 0, nlb = 0;
+  int rc = make_grids(c, c->bin_factor, grids, nb);
+  if (rc == DEM_OK) rc = make_grids(c, 1.0, lgrids, nlb);
+  if (rc) return rc;
+  for (size_t s = 0; s < grids.size() && s < c->grids.size(); ++s) {
+    grids[s].wall_start = c->grids[s].wall_start;
+    grids[s].wall_count = c->grids[s].wall_count;
+  }
   c->grids = grids;
-  c->nbins = (uint32_t)base;
+  c->nbins = nb;
+  c->lgrids = lgrids;
+  c->n_lbins = nlb;
   return DEM_OK;
 }
 
@@ -442,6 +461,7 @@ int finalize(dem_ctx* c) {
   }
   const size_t nw = std::max<size_t>(1, c->walls.size());
   if (!grow(c, c->b_grids, sizeof(SceneGrid) * c->grids.size()) ||
+      !grow(c, c->b_lgrids, sizeof(SceneGrid) * c->lgrids.size()) ||
       !grow(c, c->b_walls, sizeof(WallDev) * nw) || !grow(c, c->b_wall_idx, sizeof(int) * std::max<size_t>(1, idx.size())) ||
       !grow(c, c->b_wall_scene, sizeof(int) * nw) || !grow(c, c->b_wfix, 3 * sizeof(long long) * nw) ||
       !grow(c, c->b_wpos, 3 * sizeof(double) * nw) || !grow(c, c->b_wforce, 3 * sizeof(double) * nw) ||
@@ -449,6 +469,8 @@ int finalize(dem_ctx* c) {
       !grow(c, c->b_dstep, 64))
     return fail(c, DEM_ERR_OOM, "scene tables");
   cudaMemcpyAsync(c->b_grids.p, c->grids.data(), sizeof(SceneGrid) * c->grids.size(), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_lgrids.p, c->lgrids.data(), sizeof(SceneGrid) * c->lgrids.size(),
+                  cudaMemcpyHostToDevice, c->st);
   if (!c->walls.empty()) {
     cudaMemcpyAsync(c->b_walls.p, c->walls.data(), sizeof(WallDev) * c->walls.size(), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->b_wall_idx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c->st);
@@ -670,7 +692,7 @@ FeatureScales feature_scales(const dem_ctx* c) {
 
 // Per-clump margins from the regressor (sets D.cmargin).
 int predict_margins(dem_ctx* c) {
-  const long long ncl = c->ncl, nb = c->nbins;
+  const long long ncl = c->ncl, nb = c->n_lbins;  // bins of the feature grids
   const int nc = (int)c->l_cand.size();
   if (!grow(c, c->b_chome, 4 * (ncl + 1)) || !grow(c, c->b_cmargin, 4 * (ncl + 1)) ||
       !grow(c, c->b_bcnt, 4 * (nb + 1)) || !grow(c, c->b_bvmax, 4 * (nb + 1)) ||
@@ -688,7 +710,9 @@ int predict_margins(dem_ctx* c) {
   cudaMemsetAsync(bs.amax, 0, 4 * (size_t)nb, c->st);
   cudaMemsetAsync(c->b_nocc.p, 0, 4, c->st);
   c->D.cmargin = nullptr;
-  launch_clump_home(c->D, bs, c->st);
+  DevState dl = c->D;
+  dl.grids = ptr<SceneGrid>(c->b_lgrids);
+  launch_clump_home(dl, bs, c->st);
   launch_bin_compact(bs.cnt, nb, ptr<uint32_t>(c->b_occ), ptr<uint32_t>(c->b_nocc), c->st);
   uint32_t nocc = 0;
   cudaMemcpyAsync(&nocc, c->b_nocc.p, 4, cudaMemcpyDeviceToHost, c->st);
@@ -1130,7 +1154,7 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cv, &c->b_cw,
                 &c->b_tmassf, &c->b_tinertf, &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
                 &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_sa32,
-                &c->b_sb32, &c->b_grids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
+                &c->b_sb32, &c->b_grids, &c->b_lgrids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
                 &c->b_wpos, &c->b_wforce, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
                 &c->b_totals, &c->b_det, &c->b_bin_size, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
@@ -1749,12 +1773,12 @@ int dem_trace(dem_ctx* c, int windows, int window, int n_candidates, const doubl
   if (!grow(c, c->b_tx, 4 * capb * kMlpIn) || !grow(c, c->b_tt, 4 * capb) ||
       !grow(c, c->b_tr_q, 16 * (ncl + 1)) || !grow(c, c->b_tr_vox, 16 * (ncl + 1)) ||
       !grow(c, c->b_tr_off, 16 * (ncl + 1)) || !grow(c, c->b_tr_pos, 32 * (ncl + 1)) ||
-      !grow(c, c->b_dmax, 4 * ((size_t)c->nbins + 1))) {
+      !grow(c, c->b_dmax, 4 * ((size_t)c->n_lbins + 1))) {
     c->mlp = saved;
     c->l_cand = saved_cand;
     return fail(c, DEM_ERR_OOM, "trace buffers");
   }
-  cudaMemsetAsync(c->b_dmax.p, 0, 4 * (size_t)c->nbins, c->st);
+  cudaMemsetAsync(c->b_dmax.p, 0, 4 * (size_t)c->n_lbins, c->st);
   TraceRef tr{ptr<int4>(c->b_tr_vox), ptr<float4>(c->b_tr_off), ptr<double4_32a>(c->b_tr_pos),
               ptr<float4>(c->b_tr_q)};
   StepRunner R(c, windows * window);
