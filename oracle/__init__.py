@@ -223,13 +223,22 @@ class OracleModel:
                                    _p(mg, C.c_double), _p(qc, C.c_longlong), _p(rho, C.c_longlong))
         return qc, rho
 
+    def need_bins(self):
+        """The oracle takes the bin edge literally (a zero edge would be a grid
+        of one lattice unit per bin); the library's default edge depends on the
+        margin, which the model does not know, so binning needs an explicit one."""
+        if not self.m.bin_size > 0.0:
+            raise ValueError("the oracle needs an explicit bin edge (scene.bin_size > 0)")
+
     def grid_dims(self):
+        self.need_bins()
         dims = np.zeros(3, np.int64)
         L = np.zeros(1, np.int64)
         self.lib.orc_grid_dims(self.ptr, _p(dims, C.c_longlong), _p(L, C.c_longlong))
         return dims, int(L[0])
 
     def bin_entries(self, qc, rho):
+        self.need_bins()
         qc, rho = np.ascontiguousarray(qc, np.int64), np.ascontiguousarray(rho, np.int64)
         ns = len(rho)
         n = self.lib.orc_bin_entries(self.ptr, ns, _p(qc, C.c_longlong), _p(rho, C.c_longlong),
@@ -252,6 +261,7 @@ class OracleModel:
         return a, b
 
     def pairs_binned(self, owner, qc, rho):
+        self.need_bins()
         owner = _i32(owner)
         qc, rho = np.ascontiguousarray(qc, np.int64), np.ascontiguousarray(rho, np.int64)
         ns = len(rho)
@@ -341,6 +351,7 @@ class OracleSim:
 
     def __init__(self, scene, margin, rebuild_every, state=None):
         self.model = OracleModel(scene)
+        self.model.need_bins()
         self.lib = self.model.lib
         st = state if state is not None else scene
         self.tpl = _i32(st.tpl)

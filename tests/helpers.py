@@ -58,3 +58,30 @@ def triangle_clump_scene(r=1e-3, arm=1.2e-3, **kw):
     sc.tpl_mass = np.array([m])
     sc.tpl_inertia = np.array([np.diag(I)])
     return sc
+
+
+def settling_box_scene(n=400, seed=5, side=0.03, E=1e7, h=1e-5):
+    """Clumps of three overlapping spheres (the 1,000-clump workload's
+    templates, 20 of them) on a jittered lattice above the floor of a
+    side x side box, at rest; a soft material (E, CoR 0.3) so that a step of
+    h resolves the contacts and the bed settles within a few thousand steps.
+    Templates and positions are exact in the FP32 voxel layout, so every
+    precision mode starts from the same state."""
+    sc = scenes.config1(seed=seed, n_clumps=n, n_templates=20)
+    sc.E, sc.cor, sc.mu = np.array([E]), np.array([0.3]), np.array([0.5])
+    sc.h = h
+    rng = np.random.default_rng(seed + 1)
+    bound = sc.bounding_radius()[sc.tpl]
+    sp = 2.0 * float(bound.max()) + 2e-4
+    P = scenes.lattice_positions(n, sp, 0.0, side, 0.0, side, 0.0, rng, 0.1 * sp)
+    P[:, 2] += float(bound.max())
+    sc.pos = P
+    sc.quat = scenes.random_quaternions(rng, n)
+    sc.vel, sc.angvel = np.zeros((n, 3)), np.zeros((n, 3))
+    sc.walls = scenes.box_walls(0.0, side, 0.0, side, 0.0)
+    sc.lo = (-2.0 ** -9, -2.0 ** -9, -2.0 ** -9)  # on the FP32 offset grid
+    sc.hi = (side + 0.002, side + 0.002, float(P[:, 2].max()) + 0.01)
+    sc.tpl_pos = sc.tpl_pos.astype(np.float32).astype(np.float64)
+    sc.tpl_rad = sc.tpl_rad.astype(np.float32).astype(np.float64)
+    scenes.snap_to_voxel_grid(sc)
+    return sc
