@@ -34,6 +34,7 @@ METRIC = "sphere-steps/sec and contacts/sec at 1 GB300 (plain vs learned-margin/
 UNIT = "sphere-steps/s"
 MARGIN_VBOUND = 1.0   # m/s speed bound behind the fixed margin
 K_REBUILD = 20        # steps between list rebuilds
+N_CLUMPS_FULL = 11_000_000  # the paper-scale bed
 
 
 def workload_name(n_clumps, n_spheres):
@@ -288,7 +289,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--n-clumps", type=int, default=11_000_000)
+    ap.add_argument("--n-clumps", type=int, default=N_CLUMPS_FULL)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -370,7 +371,8 @@ def main():
     value = whole_job_rate(world, ns, args.steps, ms)
     contacts_ps = whole_job_rate(world, st["pair_steps"], 1, ms)
 
-    # dominant kernel: the sphere-sphere force kernel
+    # rooflines of the two step kernels; the update kernel takes the largest
+    # share of the step (the launch list in profiles/), so it is `roofline`
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -380,15 +382,31 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     n_pairs, n_active = st["n_pairs"], st["active_last"]
     pair_ms = st["ms_pairs"] / max(1, st["timed_steps"])
-    # algorithmic bytes per launch: ids of every listed pair (8 B), history
-    # read + write of each active contact (48 B), one read of every sphere's
-    # pose records (48 B), clump velocity mirrors (32 B) and accumulators
-    # (32 B read + 32 B write)
-    algo = 8 * n_pairs + 48 * n_active + 48 * ns + 96 * ncl
-    achieved = algo / (pair_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_pairs32",
-                "kernel_ms": pair_ms, "algorithmic_bytes": algo, "peak_source": peak_src}
+    upd_ms = st["ms_update"] / max(1, st["timed_steps"])
+    # DRAM read + write bytes per launch from one ncu capture of this command
+    # on the 11M-clump bed (profiles/dram_traffic_paper_bed_34M_spheres.md);
+    # they hold for that bed only
+    traffic = {"k_update32": 2.658e9 + 3.713e9, "k_pairs32": 3.824e9 + 1.189e9}
+    full_bed = ncl == N_CLUMPS_FULL
+
+    def roof(kernel, algo, ms):
+        achieved = algo / (ms / 1000.0) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic[kernel] if full_bed else None,
+                "kernel": kernel, "kernel_ms": ms, "algorithmic_bytes": algo,
+                "peak_source": peak_src}
+
+    # update kernel, algorithmic bytes per launch: per clump 216 B read (force
+    # and torque 32, template/scene 8, voxel + offset 32, orientation,
+    # velocity and angular velocity 96, certificate reference 48) and 192 B
+    # written (state 128, velocity mirrors 32, cleared accumulators 32); per
+    # sphere its {owner, template sphere} 8 B read and pose records 48 B written
+    roofline = roof("k_update32", 408 * ncl + 56 * ns, upd_ms)
+    # pair force kernel: ids of every listed pair (8 B), history read + write
+    # of each active contact (48 B), one read of every sphere's pose records
+    # (48 B), clump velocity mirrors (32 B) and accumulators (32 B read + 32 B
+    # write)
+    roofline_pairs = roof("k_pairs32", 8 * n_pairs + 48 * n_active + 48 * ns + 96 * ncl, pair_ms)
 
     e2e = None
     if not args.no_e2e:
@@ -449,6 +467,7 @@ def main():
                                 "rebuild_total": st["ms_detect"]}},
         "forms": forms,
         "roofline": roofline,
+        "roofline_pairs": roofline_pairs,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": st["launches"],
