@@ -386,7 +386,7 @@ def main():
     # DRAM read + write bytes per launch from one ncu capture of this command
     # on the 11M-clump bed (profiles/dram_traffic_paper_bed_34M_spheres.md);
     # they hold for that bed only
-    traffic = {"k_update32": 2.658e9 + 3.713e9, "k_pairs32": 3.824e9 + 1.189e9}
+    traffic = {"k_update32": 2.481e9 + 3.537e9, "k_pairs32": 3.821e9 + 1.188e9}
     full_bed = ncl == N_CLUMPS_FULL
 
     def roof(kernel, algo, ms):
@@ -396,12 +396,12 @@ def main():
                 "kernel": kernel, "kernel_ms": ms, "algorithmic_bytes": algo,
                 "peak_source": peak_src}
 
-    # update kernel, algorithmic bytes per launch: per clump 216 B read (force
-    # and torque 32, template/scene 8, voxel + offset 32, orientation,
-    # velocity and angular velocity 96, certificate reference 48) and 192 B
-    # written (state 128, velocity mirrors 32, cleared accumulators 32); per
+    # update kernel, algorithmic bytes per launch: per clump 200 B read (force
+    # and torque 32, template/scene 8, voxel + offset 32, orientation 32,
+    # velocity and angular velocity 48, certificate reference 48) and 176 B
+    # written (state 112, velocity mirrors 32, cleared accumulators 32); per
     # sphere its {owner, template sphere} 8 B read and pose records 48 B written
-    roofline = roof("k_update32", 408 * ncl + 56 * ns, upd_ms)
+    roofline = roof("k_update32", 376 * ncl + 56 * ns, upd_ms)
     # pair force kernel: ids of every listed pair (8 B), history read + write
     # of each active contact (48 B), one read of every sphere's pose records
     # (48 B), clump velocity mirrors (32 B) and accumulators (32 B read + 32 B

@@ -64,7 +64,7 @@ struct dem_ctx {
   // all device buffers
   std::vector<Buf*> owned;
   Buf b_tpl_off, b_tp64, b_tp32, b_tmat, b_tmass, b_tinert, b_tpbound, b_tmassf, b_tinertf;
-  Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cv, b_cw, b_mv64, b_mw64, b_mv32, b_mw32;
+  Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cvw, b_mv64, b_mw64, b_mv32, b_mw32;
   Buf b_acc64, b_acc32, b_ref_pos, b_ref_vox, b_ref_off, b_ref_q;
   Buf b_sinfo, b_sa64, b_sb64, b_sa32, b_sb32;
   Buf b_grids, b_lgrids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
@@ -234,8 +234,7 @@ void refresh_devstate(dem_ctx* c) {
   d.cvox = ptr<int4>(c->b_cvox);
   d.coff = ptr<float4>(c->b_coff);
   d.cq = ptr<double4_32a>(c->b_cq);
-  d.cv = ptr<double4_32a>(c->b_cv);
-  d.cw = ptr<double4_32a>(c->b_cw);
+  d.cvw = ptr<VelRec>(c->b_cvw);
   d.mv64 = ptr<double4_32a>(c->b_mv64);
   d.mw64 = ptr<double4_32a>(c->b_mw64);
   d.mv32 = ptr<float4>(c->b_mv32);
@@ -740,7 +739,8 @@ int take_snapshot(dem_ctx* c) {
   const size_t n = (size_t)c->ncl;
   const bool f64 = c->P.precision == DEM_FP64;
   ContactList& L = curL(c);
-  if (!grow(c, c->s_state, 128 * (n + 1)) || !grow(c, c->s_pb, 4 * (size_t)(L.n + 1)) ||
+  // position 32 | orientation 32 | velocity record 48 bytes per clump
+  if (!grow(c, c->s_state, 112 * (n + 1)) || !grow(c, c->s_pb, 4 * (size_t)(L.n + 1)) ||
       !grow(c, c->s_u, 24 * (size_t)(L.n + 1)) || !grow(c, c->s_ww, 4 * (size_t)(L.nw + 1)) ||
       !grow(c, c->s_uw, 24 * (size_t)(L.nw + 1)))
     return fail(c, DEM_ERR_OOM, "snapshot");
@@ -752,8 +752,7 @@ int take_snapshot(dem_ctx* c) {
     cudaMemcpyAsync(s + 16 * n, c->b_coff.p, 16 * n, cudaMemcpyDeviceToDevice, c->st);
   }
   cudaMemcpyAsync(s + 32 * n, c->b_cq.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(s + 64 * n, c->b_cv.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(s + 96 * n, c->b_cw.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(s + 64 * n, c->b_cvw.p, sizeof(VelRec) * n, cudaMemcpyDeviceToDevice, c->st);
   cudaMemcpyAsync(c->s_pb.p, L.pb, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, c->st);
   for (int k = 0; k < 3; ++k)
     cudaMemcpyAsync((double*)c->s_u.p + k * L.n, L.u + k * L.cap, 8 * (size_t)L.n,
@@ -778,8 +777,7 @@ int restore_snapshot(dem_ctx* c) {
     cudaMemcpyAsync(c->b_coff.p, s + 16 * n, 16 * n, cudaMemcpyDeviceToDevice, c->st);
   }
   cudaMemcpyAsync(c->b_cq.p, s + 32 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(c->b_cv.p, s + 64 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(c->b_cw.p, s + 96 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->b_cvw.p, s + 64 * n, sizeof(VelRec) * n, cudaMemcpyDeviceToDevice, c->st);
   cudaMemcpyAsync(L.pb, c->s_pb.p, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, c->st);
   for (int k = 0; k < 3; ++k)
     cudaMemcpyAsync(L.u + k * L.cap, (double*)c->s_u.p + k * L.n, 8 * (size_t)L.n,
@@ -1022,17 +1020,17 @@ struct StepRunner {
 int upload_clumps(dem_ctx* c, long long first, int n, const int* tpl, const double* pos,
                   const double* quat, const double* vel, const double* angvel) {
   const bool f64 = c->P.precision == DEM_FP64;
-  std::vector<double4_32a> vq(n), vv(n), vw(n), vp;
+  std::vector<double4_32a> vq(n), vp;
+  std::vector<VelRec> vr(n);
   std::vector<int4> vx;
   std::vector<float4> vo;
   if (f64) vp.resize(n); else { vx.resize(n); vo.resize(n); }
   for (int i = 0; i < n; ++i) {
     const double* q = quat + 4 * i;
     vq[i] = make_double4_32a(q[0], q[1], q[2], q[3]);
-    vv[i] = make_double4_32a(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0);
     double wb[3];
     qrot(q, angvel + 3 * i, wb, true);
-    vw[i] = make_double4_32a(wb[0], wb[1], wb[2], 0.0);
+    vr[i] = VelRec{vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], wb[0], wb[1], wb[2]};
     if (f64) {
       vp[i] = make_double4_32a(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], 0.0);
     } else {
@@ -1051,8 +1049,8 @@ int upload_clumps(dem_ctx* c, long long first, int n, const int* tpl, const doub
     }
   }
   cudaMemcpyAsync(ptr<double4_32a>(c->b_cq) + first, vq.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
-  cudaMemcpyAsync(ptr<double4_32a>(c->b_cv) + first, vv.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
-  cudaMemcpyAsync(ptr<double4_32a>(c->b_cw) + first, vw.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(ptr<VelRec>(c->b_cvw) + first, vr.data(), sizeof(VelRec) * (size_t)n,
+                  cudaMemcpyHostToDevice, c->st);
   if (f64) {
     cudaMemcpyAsync(ptr<double4_32a>(c->b_cpos) + first, vp.data(), 32 * (size_t)n, cudaMemcpyHostToDevice, c->st);
   } else {
@@ -1151,7 +1149,7 @@ void dem_destroy(dem_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->P.device);
   Buf* all[] = {&c->b_tpl_off, &c->b_tp64, &c->b_tp32, &c->b_tmat, &c->b_tmass, &c->b_tinert, &c->b_tpbound,
-                &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cv, &c->b_cw,
+                &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cvw,
                 &c->b_tmassf, &c->b_tinertf, &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
                 &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_sa32,
                 &c->b_sb32, &c->b_grids, &c->b_lgrids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
@@ -1269,8 +1267,8 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
   if (ns >= (1ll << 31) - 1) return fail(c, DEM_ERR_INVALID_ARG, "2^31 - 1 spheres or more");
   const size_t k0 = (size_t)c->ncl, s0 = (size_t)c->ns;
   bool ok = grow(c, c->b_cinfo, 8 * ncl, 8 * k0) && grow(c, c->b_csph, 4 * (ncl + 1), 4 * k0) &&
-            grow(c, c->b_cq, 32 * ncl, 32 * k0) && grow(c, c->b_cv, 32 * ncl, 32 * k0) &&
-            grow(c, c->b_cw, 32 * ncl, 32 * k0) && grow(c, c->b_ref_q, 16 * ncl) &&
+            grow(c, c->b_cq, 32 * ncl, 32 * k0) && grow(c, c->b_cvw, 48 * ncl, 48 * k0) &&
+            grow(c, c->b_ref_q, 16 * ncl) &&
             grow(c, c->b_alast, 4 * ncl, 4 * k0) &&
             grow(c, c->b_sinfo, 8 * ns, 8 * s0);
   if (c->P.precision == DEM_FP64) {

@@ -29,8 +29,7 @@ struct DevState {
   int4* cvox;               // FP32_VOXEL: voxel index (w unused)
   float4* coff;             // FP32_VOXEL: offset in the voxel (w unused)
   double4_32a* cq;              // orientation (both modes)
-  double4_32a* cv;              // velocity (both modes)
-  double4_32a* cw;              // angular velocity, body frame (both modes)
+  VelRec* cvw;              // velocity and body-frame angular velocity (both modes)
   double4_32a* mv64;            // FP64 mirrors for contacts: {v, mass}
   double4_32a* mw64;            //                            {omega world, 0}
   float4* mv32;             // FP32 mirrors: {v, mass}

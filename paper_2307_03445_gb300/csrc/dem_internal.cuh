@@ -26,6 +26,26 @@ constexpr float kFixToM = 5.684341886080802e-14f; // 2^-44
 constexpr float kMToFix = 17592186044416.0f;      // 2^44
 constexpr uint32_t kHistFlag = 0x80000000u;       // in pb / ww: history is non-zero
 
+// A clump's velocity and body-frame angular velocity (FP64, both precision
+// modes): 48 bytes, moved as three 16-byte vectors.
+struct alignas(16) VelRec {
+  double vx, vy, vz, wx, wy, wz;
+};
+
+__device__ __forceinline__ void load_vel(const VelRec* p, double4_32a& v, double4_32a& w) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = q[0], b = q[1], c = q[2];
+  v = make_double4_32a(a.x, a.y, b.x, 0.0);
+  w = make_double4_32a(b.y, c.x, c.y, 0.0);
+}
+
+__device__ __forceinline__ void store_vel(VelRec* p, const double4_32a& v, const double4_32a& w) {
+  double2* q = reinterpret_cast<double2*>(p);
+  q[0] = make_double2(v.x, v.y);
+  q[1] = make_double2(v.z, w.x);
+  q[2] = make_double2(w.y, w.z);
+}
+
 // Pair material coefficients (section 2.1: derived from E, nu, CoR and mu).
 // kn = 4/3 E*, kt = 8 G*, mu; the damping terms of Eq. (1a), (1b) are
 //   f gamma_n m = cn sqrt(f m),  f gamma_t m = ct sqrt(f m)

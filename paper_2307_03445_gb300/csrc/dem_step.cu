@@ -398,7 +398,8 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
   const long long c = c0 + threadIdx.x;
   if (c < d.ncl) {
     const int tpl = d.cinfo[c].x;
-    double4_32a X = d.cpos[c], q4 = d.cq[c], v = d.cv[c], w = d.cw[c];
+    double4_32a X = d.cpos[c], q4 = d.cq[c], v, w;
+    load_vel(d.cvw + c, v, w);
     const double mass = d.tmass[tpl];
     const double I[3] = {d.tinert[3 * tpl], d.tinert[3 * tpl + 1], d.tinert[3 * tpl + 2]};
     double q[4] = {q4.x, q4.y, q4.z, q4.w};
@@ -437,7 +438,8 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
       for (int k = 0; k < 4; ++k) q[k] = qn[k] / ql;
       q4 = make_double4_32a(q[0], q[1], q[2], q[3]);
       if (!(finite4(X) && finite4(v) && finite4(w) && finite4(q4))) atomicOr(d.flags, kFlagNonFinite);
-      d.cpos[c] = X; d.cq[c] = q4; d.cv[c] = v; d.cw[c] = w;
+      d.cpos[c] = X; d.cq[c] = q4;
+      store_vel(d.cvw + c, v, w);
       if (check_cert) {
         const double4_32a X0 = d.ref_pos[c];
         const float4 r0 = d.ref_q[c];
@@ -517,7 +519,8 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
     const int tpl = d.cinfo[c].x;
     int4 vox = d.cvox[c];
     float4 off = d.coff[c];
-    double4_32a q4 = d.cq[c], v = d.cv[c], w = d.cw[c];
+    double4_32a q4 = d.cq[c], v, w;
+    load_vel(d.cvw + c, v, w);
     const float mass = d.tmassf[tpl];
     // orientation as float-float; integrating needs only the high parts of
     // the old one (the rotation matrix is built from the new orientation)
@@ -602,7 +605,8 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
             finite_d(w.z) && finite_d(qd[0]) && finite_d(qd[1]) && finite_d(qd[2]) &&
             finite_d(qd[3]) && isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2])))
         atomicOr(d.flags, kFlagNonFinite);
-      d.cvox[c] = vox; d.coff[c] = off; d.cq[c] = q4; d.cv[c] = v; d.cw[c] = w;
+      d.cvox[c] = vox; d.coff[c] = off; d.cq[c] = q4;
+      store_vel(d.cvw + c, v, w);
       if (check_cert) {
         const int4 v0 = ref_v;
         const float4 o0 = ref_o;
@@ -858,14 +862,14 @@ __global__ void k_get_state(DevState d, double* pos, double* quat, double* vel, 
   if (quat) {
     quat[4 * c] = q.x; quat[4 * c + 1] = q.y; quat[4 * c + 2] = q.z; quat[4 * c + 3] = q.w;
   }
+  double4_32a v, w;
+  load_vel(d.cvw + c, v, w);
   if (vel) {
-    const double4_32a v = d.cv[c];
     vel[3 * c] = v.x; vel[3 * c + 1] = v.y; vel[3 * c + 2] = v.z;
   }
   if (angvel) {
     double R[9];
     quat_to_mat(q.x, q.y, q.z, q.w, R);
-    const double4_32a w = d.cw[c];
     const V3<double> ww = mat_mul(R, V3<double>{w.x, w.y, w.z});
     angvel[3 * c] = ww.x; angvel[3 * c + 1] = ww.y; angvel[3 * c + 2] = ww.z;
   }
@@ -910,11 +914,11 @@ __global__ void k_set_state(DevState d, const double* t) {
   const double* v = t + 7 * n + 3 * c;
   const double* w = t + 10 * n + 3 * c;
   d.cq[c] = make_double4_32a(q[0], q[1], q[2], q[3]);
-  d.cv[c] = make_double4_32a(v[0], v[1], v[2], 0.0);
   double R[9];
   quat_to_mat(q[0], q[1], q[2], q[3], R);
   const V3<double> wb = mat_tmul(R, V3<double>{w[0], w[1], w[2]});
-  d.cw[c] = make_double4_32a(wb.x, wb.y, wb.z, 0.0);
+  store_vel(d.cvw + c, make_double4_32a(v[0], v[1], v[2], 0.0),
+            make_double4_32a(wb.x, wb.y, wb.z, 0.0));
   if (d.prec == 0) {
     d.cpos[c] = make_double4_32a(p[0], p[1], p[2], 0.0);
   } else {
