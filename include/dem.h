@@ -281,6 +281,22 @@ int dem_get_forces(dem_ctx* ctx, double* force, double* torque);
 /* Net force on each wall from the last force evaluation (3 * n_walls). */
 int dem_get_wall_forces(dem_ctx* ctx, double* force);
 
+/* Co-simulation hook (boundaries driven by another solver, as the rover's
+ * multibody model drives the wheels in section 5.2).  Loads: the net
+ * force on each wall and its moment about the wall's reference point at the
+ * time of the last force evaluation (p + vel t), each contact force acting at
+ * its contact point (3 * n_walls doubles each, host buffers).  The sum over
+ * the clumps of X x F + T plus the sum over the walls of p(t) x F_w + T_w is
+ * zero up to rounding. */
+int dem_get_wall_loads(dem_ctx* ctx, double* force, double* torque);
+/* Motion: from the current time t on, wall `wall` (index in the walls given
+ * at creation) moves as point + vel (t' - t), i.e. its stored reference
+ * point becomes point - vel t.  The next step rebuilds the contact lists
+ * (the listed wall candidates assumed the old motion); the wall's tangential
+ * histories are kept for contacts that stay listed.  Errors:
+ * DEM_ERR_INVALID_ARG (index out of range), DEM_ERR_NONFINITE. */
+int dem_set_wall_motion(dem_ctx* ctx, int wall, const double* point, const double* vel);
+
 /* Sizes of the current lists. */
 int dem_num_contacts(dem_ctx* ctx, long long* n_pairs, long long* n_wall);
 

@@ -100,7 +100,7 @@ def _load():
                                           C.c_double, _D, _D, _D, _D]),
                 "orc_forces": (C.c_longlong, [_M, C.c_int, _I, _D, _D, _D, _D, C.c_double,
                                               C.c_longlong, _I, _I, _D, C.c_longlong, _I, _I, _D,
-                                              _D, _D, _D, _D]),
+                                              _D, _D, _D, _D, _D]),
                 "orc_integrate": (None, [_M, C.c_int, _I, _D, _D, _D, _D, _D, _D]),
                 "orc_sim_create": (C.c_void_p, [_M, C.c_int, _I, _D, _D, _D, _D, C.c_double, C.c_int]),
                 "orc_sim_step": (C.c_longlong, [C.c_void_p, C.c_int, C.c_int]),
@@ -312,9 +312,11 @@ class OracleModel:
         return bool(act), F, u, ca, cb
 
     def forces(self, tpl, pos, quat, vel, angvel, t, pa, pb, up, ws=None, ww=None, uw=None,
-               with_mag=False):
+               with_mag=False, wall_torque=False):
         """Clump forces/torques for one step; returns (F, T, Fwall, up_new, uw_new, n_active)
-        and, with ``with_mag``, the per-clump sums of |F| and |torque| over its contacts."""
+        and, with ``with_mag``, the per-clump sums of |F| and |torque| over its contacts;
+        with ``wall_torque``, also (last) the moment on each wall about its reference point
+        at time t."""
         tpl, pos, quat, vel, angvel = _i32(tpl), _f64(pos), _f64(quat), _f64(vel), _f64(angvel)
         pa, pb = _i32(pa), _i32(pb)
         up = _f64(up).reshape(-1, 3).copy()
@@ -325,16 +327,17 @@ class OracleModel:
         F = np.zeros((n, 3))
         T = np.zeros((n, 3))
         Fw = np.zeros((max(1, self.n_walls), 3))
+        Tw = np.zeros((max(1, self.n_walls), 3))
         mag = np.zeros((n, 2))
         act = self.lib.orc_forces(self.ptr, n, _p(tpl, C.c_int), _p(pos, C.c_double),
                                   _p(quat, C.c_double), _p(vel, C.c_double),
                                   _p(angvel, C.c_double), float(t), len(pa), _p(pa, C.c_int),
                                   _p(pb, C.c_int), _p(up, C.c_double), len(ws), _p(ws, C.c_int),
                                   _p(ww, C.c_int), _p(uw, C.c_double), _p(F, C.c_double),
-                                  _p(T, C.c_double), _p(Fw, C.c_double), _p(mag, C.c_double))
-        if with_mag:
-            return F, T, Fw[: self.n_walls], up, uw, int(act), mag
-        return F, T, Fw[: self.n_walls], up, uw, int(act)
+                                  _p(T, C.c_double), _p(Fw, C.c_double), _p(Tw, C.c_double),
+                                  _p(mag, C.c_double))
+        out = (F, T, Fw[: self.n_walls], up, uw, int(act)) + ((mag,) if with_mag else ())
+        return out + ((Tw[: self.n_walls],) if wall_torque else ())
 
     def integrate(self, tpl, pos, quat, vel, angvel, F, T):
         tpl = _i32(tpl)

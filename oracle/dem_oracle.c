@@ -443,7 +443,7 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
                      const double* quat, const double* vel, const double* angvel,
                      double t, long long np, const int* pa, const int* pb, double* up,
                      long long nw, const int* ws, const int* ww, double* uw, double* F,
-                     double* T, double* Fw, double* mag) {
+                     double* T, double* Fw, double* Tw, double* mag) {
     const long long ns = orc_num_spheres(m, n, tpl);
     double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)(ns + 1));
     int* owner = (int*)malloc(sizeof(int) * (size_t)(ns + 1));
@@ -451,6 +451,7 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
     orc_sphere_centres(m, n, tpl, pos, quat, xs, owner, tsph);
     for (long long i = 0; i < 3LL * n; ++i) { F[i] = 0.0; T[i] = 0.0; }
     if (Fw) for (int i = 0; i < 3 * m->n_walls; ++i) Fw[i] = 0.0;
+    if (Tw) for (int i = 0; i < 3 * m->n_walls; ++i) Tw[i] = 0.0;
     if (mag) for (long long i = 0; i < 2LL * n; ++i) mag[i] = 0.0;
     long long active = 0;
     for (long long c = 0; c < np; ++c) {
@@ -494,6 +495,14 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
             mag[2 * A + 1] += sqrt(dot3(ca, ca)) * sqrt(dot3(f, f));
         }
         if (Fw) for (int k = 0; k < 3; ++k) Fw[3 * k0 + k] += f[k];
+        if (Tw) {
+            /* moment of f about the wall's reference point at time t */
+            double arm[3], tw[3];
+            for (int k = 0; k < 3; ++k)
+                arm[k] = (pos[3 * A + k] + ca[k]) - (wl->p[k] + wl->vel[k] * t);
+            cross3(arm, f, tw);
+            for (int k = 0; k < 3; ++k) Tw[3 * k0 + k] += tw[k];
+        }
     }
     free(xs);
     free(owner);
@@ -679,7 +688,7 @@ long long orc_sim_step(orc_sim* s, int nsteps, int audit) {
         const double t = (double)s->step * s->m.h;
         s->active = orc_forces(&s->m, s->n, s->tpl, s->pos, s->quat, s->vel, s->angvel, t,
                                s->np, s->pa, s->pb, s->up, s->nw, s->ws, s->ww, s->uw, s->F,
-                               s->T, NULL, NULL);
+                               s->T, NULL, NULL, NULL);
         orc_integrate(&s->m, s->n, s->tpl, s->pos, s->quat, s->vel, s->angvel, s->F, s->T);
         s->step += 1;
         s->since += 1;

@@ -101,8 +101,10 @@ int orc_contact(const orc_model* m, int mat_a, int mat_b, const double xa[3],
                 double ca[3], double cb[3]);
 
 /* Forces and torques on every clump for one step (contacts given).  The
- * history arrays are updated in place.  F, T: 3 * n.  Fw: 3 * n_walls or NULL.
- * mag: 2 * n or NULL; receives, per clump, the sums over its contacts of |F|
+ * history arrays are updated in place.  F, T: 3 * n.  Fw: 3 * n_walls or NULL:
+ * the force on each wall.  Tw: 3 * n_walls or NULL: the moment of those forces
+ * about the wall's reference point at time t (p + vel t), each force acting
+ * at its contact point.  mag: 2 * n or NULL; receives, per clump, the sums over its contacts of |F|
  * and of |lever arm| * |F| (the scales that bound the rounding of the force
  * and torque totals, including the cancellation inside each cross product).
  * Returns the number of active contacts. */
@@ -110,7 +112,7 @@ long long orc_forces(const orc_model* m, int n, const int* tpl, const double* po
                      const double* quat, const double* vel, const double* angvel,
                      double t, long long np, const int* pa, const int* pb, double* up,
                      long long nw, const int* ws, const int* ww, double* uw, double* F,
-                     double* T, double* Fw, double* mag);
+                     double* T, double* Fw, double* Tw, double* mag);
 
 /* Explicit integration of Eq. (5) for every clump, in place. */
 void orc_integrate(const orc_model* m, int n, const int* tpl, double* pos, double* quat,

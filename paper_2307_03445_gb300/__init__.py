@@ -179,6 +179,21 @@ class Simulation:
         self._check(self.lib.dem_get_wall_forces(self.ctx, _pd(F)))
         return F[: self.n_walls]
 
+    def wall_loads(self):
+        """(force, moment about the wall's reference point) per wall, from the
+        last force evaluation."""
+        F = np.zeros((max(1, self.n_walls), 3))
+        T = np.zeros((max(1, self.n_walls), 3))
+        self._check(self.lib.dem_get_wall_loads(self.ctx, _pd(F), _pd(T)))
+        return F[: self.n_walls], T[: self.n_walls]
+
+    def set_wall_motion(self, wall, point, vel):
+        """From now on wall `wall` moves as point + vel * (t' - t_now)."""
+        p, v = _f64(point), _f64(vel)
+        if p.shape != (3,) or v.shape != (3,):
+            raise ValueError("point and vel are 3-vectors")
+        self._check(self.lib.dem_set_wall_motion(self.ctx, int(wall), _pd(p), _pd(v)))
+
     def contacts(self):
         npair, nw = C.c_longlong(), C.c_longlong()
         self._check(self.lib.dem_num_contacts(self.ctx, C.byref(npair), C.byref(nw)))

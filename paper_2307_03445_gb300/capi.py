@@ -100,6 +100,8 @@ SIGNATURES = {
     "dem_eval_forces": (C.c_int, [_V]),
     "dem_get_forces": (C.c_int, [_V, _D, _D]),
     "dem_get_wall_forces": (C.c_int, [_V, _D]),
+    "dem_get_wall_loads": (C.c_int, [_V, _D, _D]),
+    "dem_set_wall_motion": (C.c_int, [_V, C.c_int, _D, _D]),
     "dem_num_contacts": (C.c_int, [_V, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "dem_get_contacts": (C.c_int, [_V, _I, _I, _D, _I, _I, _D]),
     "dem_get_bins": (C.c_int, [_V, C.c_longlong, C.POINTER(C.c_uint), _I,

@@ -67,7 +67,7 @@ struct dem_ctx {
   Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cvw, b_mv64, b_mw64, b_mv32, b_mw32;
   Buf b_acc64, b_acc32, b_ref_pos, b_ref_vox, b_ref_off, b_ref_q;
   Buf b_sinfo, b_sa64, b_sb64, b_sa32, b_sb32;
-  Buf b_grids, b_lgrids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_pm64, b_pm32;
+  Buf b_grids, b_lgrids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_wtorque, b_pm64, b_pm32;
   Buf b_flags, b_counters, b_totals, b_dstep;
   // detection scratch
   Buf b_det, b_bin_size, b_wall_mask, b_wall_cnt;
@@ -259,6 +259,7 @@ void refresh_devstate(dem_ctx* c) {
   d.wfix = ptr<long long>(c->b_wfix);
   d.wpos = ptr<double>(c->b_wpos);
   d.wforce = ptr<double>(c->b_wforce);
+  d.wtorque = ptr<double>(c->b_wtorque);
   d.pm64 = ptr<PairMat<double>>(c->b_pm64);
   d.pm32 = ptr<PairMat<float>>(c->b_pm32);
   d.flags = ptr<int>(c->b_flags);
@@ -464,6 +465,7 @@ int finalize(dem_ctx* c) {
       !grow(c, c->b_walls, sizeof(WallDev) * nw) || !grow(c, c->b_wall_idx, sizeof(int) * std::max<size_t>(1, idx.size())) ||
       !grow(c, c->b_wall_scene, sizeof(int) * nw) || !grow(c, c->b_wfix, 3 * sizeof(long long) * nw) ||
       !grow(c, c->b_wpos, 3 * sizeof(double) * nw) || !grow(c, c->b_wforce, 3 * sizeof(double) * nw) ||
+      !grow(c, c->b_wtorque, 3 * sizeof(double) * nw) ||
       !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->b_totals, 64) ||
       !grow(c, c->b_dstep, 64))
     return fail(c, DEM_ERR_OOM, "scene tables");
@@ -476,6 +478,7 @@ int finalize(dem_ctx* c) {
     cudaMemcpyAsync(c->b_wall_scene.p, c->wall_scene.data(), sizeof(int) * c->wall_scene.size(), cudaMemcpyHostToDevice, c->st);
   }
   cudaMemsetAsync(c->b_wforce.p, 0, c->b_wforce.bytes, c->st);
+  cudaMemsetAsync(c->b_wtorque.p, 0, c->b_wtorque.bytes, c->st);
   cudaMemsetAsync(c->b_flags.p, 0, 64, c->st);
   cudaMemsetAsync(c->b_counters.p, 0, 64, c->st);
   c->stats.margin = c->margin;
@@ -649,7 +652,10 @@ void clear_acc(dem_ctx* c) {
 
 int force_pass(dem_ctx* c, bool count_active, cudaEvent_t mid = nullptr) {
   clear_acc(c);
-  if (!c->walls.empty()) cudaMemsetAsync(c->b_wforce.p, 0, 24 * c->walls.size(), c->st);
+  if (!c->walls.empty()) {
+    cudaMemsetAsync(c->b_wforce.p, 0, 24 * c->walls.size(), c->st);
+    cudaMemsetAsync(c->b_wtorque.p, 0, 24 * c->walls.size(), c->st);
+  }
   const double t = (double)c->step * c->P.dt;
   ContactList& L = curL(c);
   launch_force_pairs(c->D, L, count_active, c->st);
@@ -1153,7 +1159,7 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_tmassf, &c->b_tinertf, &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
                 &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_sa32,
                 &c->b_sb32, &c->b_grids, &c->b_lgrids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
-                &c->b_wpos, &c->b_wforce, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
+                &c->b_wpos, &c->b_wforce, &c->b_wtorque, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
                 &c->b_totals, &c->b_det, &c->b_bin_size, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
                 &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
@@ -1492,6 +1498,65 @@ int dem_get_wall_forces(dem_ctx* c, double* F) {
   for (size_t w = 0; w < c->walls.size(); ++w)
     for (int k = 0; k < 3; ++k) F[3 * c->wall_user[w] + k] += h[3 * w + k];
   return cuda_check(c, "get_wall_forces");
+}
+
+int dem_get_wall_loads(dem_ctx* c, double* F, double* T) {
+  if (!c || !F || !T) return DEM_ERR_INVALID_ARG;
+  const size_t nu = c->user_walls.size();
+  std::fill(F, F + 3 * nu, 0.0);
+  std::fill(T, T + 3 * nu, 0.0);
+  if (c->walls.empty()) return DEM_OK;
+  const size_t nw = c->walls.size();
+  std::vector<double> hf(3 * nw), ht(3 * nw);
+  cudaMemcpyAsync(hf.data(), c->b_wforce.p, 24 * nw, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(ht.data(), c->b_wtorque.p, 24 * nw, cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  // the copies of a wall in several scenes share its reference point
+  for (size_t w = 0; w < nw; ++w)
+    for (int k = 0; k < 3; ++k) {
+      F[3 * c->wall_user[w] + k] += hf[3 * w + k];
+      T[3 * c->wall_user[w] + k] += ht[3 * w + k];
+    }
+  return cuda_check(c, "get_wall_loads");
+}
+
+int dem_set_wall_motion(dem_ctx* c, int wall, const double* point, const double* vel) {
+  if (!c || !point || !vel || wall < 0 || wall >= (int)c->user_walls.size())
+    return DEM_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(point[k]) || !std::isfinite(vel[k]))
+      return fail(c, DEM_ERR_NONFINITE, "non-finite wall motion");
+  cudaSetDevice(c->P.device);
+  // a wall moves as p(t) = p + vel t: re-base it so that p(now) = point
+  const double t = (double)c->step * c->P.dt;
+  dem_wall& uw = c->user_walls[wall];
+  for (int k = 0; k < 3; ++k) {
+    uw.vel[k] = vel[k];
+    uw.p[k] = point[k] - vel[k] * t;
+  }
+  if (!c->finalized) return DEM_OK;  // the device tables are built from user_walls
+  const double speed = std::sqrt((vel[0] * vel[0] + vel[1] * vel[1]) + vel[2] * vel[2]);
+  for (size_t w = 0; w < c->walls.size(); ++w) {
+    if (c->wall_user[w] != wall) continue;
+    WallDev& d = c->walls[w];
+    for (int k = 0; k < 3; ++k) {
+      d.p[k] = uw.p[k];
+      d.vel[k] = uw.vel[k];
+      d.pf[k] = (float)uw.p[k];
+      d.vf[k] = (float)uw.vel[k];
+    }
+    d.speed_d = speed;
+    d.speed = (float)speed;
+  }
+  cudaMemcpyAsync(c->b_walls.p, c->walls.data(), sizeof(WallDev) * c->walls.size(),
+                  cudaMemcpyHostToDevice, c->st);
+  refresh_devstate(c);
+  launch_walls_at(c->D, c->step, c->st);  // wall positions of the current step
+  // the listed wall candidates assumed the old motion
+  c->need_rebuild = true;
+  drop_graphs(c);
+  cudaStreamSynchronize(c->st);  // the host table must outlive its copy
+  return cuda_check(c, "set_wall_motion");
 }
 
 int dem_num_contacts(dem_ctx* c, long long* n_pairs, long long* n_wall) {

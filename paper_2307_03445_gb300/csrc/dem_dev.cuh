@@ -58,6 +58,8 @@ struct DevState {
                             //   relative to its scene corner (3 per wall)
   double* wpos;             // wall reference point in world coordinates at the current time (3 per wall)
   double* wforce;           // 3 per wall (FP64 accumulation)
+  double* wtorque;          // 3 per wall: moment of those forces about the wall's
+                            //   reference point at the current time
   const PairMat<double>* pm64;
   const PairMat<float>* pm32;
   int* flags;

@@ -234,17 +234,21 @@ __global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int 
 // otherwise serialise on the same three addresses).
 constexpr int kMaxBlockWalls = 256;
 
-__device__ __forceinline__ void wall_force_flush(const DevState& d, float* s_wf) {
+__device__ __forceinline__ void wall_force_flush(const DevState& d, const float* s_wf,
+                                                 const float* s_wt) {
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * d.nwalls; i += blockDim.x)
+  for (int i = threadIdx.x; i < 3 * d.nwalls; i += blockDim.x) {
     if (s_wf[i] != 0.f) atomicAdd(d.wforce + i, (double)s_wf[i]);
+    if (s_wt[i] != 0.f) atomicAdd(d.wtorque + i, (double)s_wt[i]);
+  }
 }
 
 __global__ void k_walls32(DevState d, ContactList l, int count_active) {
   if (halted(d)) return;
-  __shared__ float s_wf[3 * kMaxBlockWalls];
+  __shared__ float s_wf[3 * kMaxBlockWalls];  // force on each wall
+  __shared__ float s_wt[3 * kMaxBlockWalls];  // its moment about the wall's reference point
   const bool shared_wf = d.nwalls <= kMaxBlockWalls;
-  for (int i = threadIdx.x; i < 3 * kMaxBlockWalls; i += blockDim.x) s_wf[i] = 0.f;
+  for (int i = threadIdx.x; i < 3 * kMaxBlockWalls; i += blockDim.x) s_wf[i] = s_wt[i] = 0.f;
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long lnw = l.dn[1];
@@ -296,18 +300,31 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     } else {
       add_clump32(d.acc32, S.owner, Fs, Ts);
     }
+    // moment about the wall's reference point (fixed point, like the sphere
+    // centre), the force acting at the contact point
+    const long long* wf = d.wfix + 3 * (long long)w;
+    const V3<float> rw = V3<float>{fix_to_float(S.x - wf[0]), fix_to_float(S.y - wf[1]),
+                                   fix_to_float(S.z - wf[2])} + (S.r - 0.5f * dn) * n;
+    const V3<float> tw = cross(rw, law.F);
     if (shared_wf) {
       atomicAdd(&s_wf[3 * w], law.F.x);
       atomicAdd(&s_wf[3 * w + 1], law.F.y);
       atomicAdd(&s_wf[3 * w + 2], law.F.z);
+      atomicAdd(&s_wt[3 * w], tw.x);
+      atomicAdd(&s_wt[3 * w + 1], tw.y);
+      atomicAdd(&s_wt[3 * w + 2], tw.z);
     } else {
       double* fw = d.wforce + 3 * (long long)w;
       atomicAdd(fw, (double)law.F.x);
       atomicAdd(fw + 1, (double)law.F.y);
       atomicAdd(fw + 2, (double)law.F.z);
+      double* mw = d.wtorque + 3 * (long long)w;
+      atomicAdd(mw, (double)tw.x);
+      atomicAdd(mw + 1, (double)tw.y);
+      atomicAdd(mw + 2, (double)tw.z);
     }
   }
-  if (shared_wf) wall_force_flush(d, s_wf);
+  if (shared_wf) wall_force_flush(d, s_wf, s_wt);
 }
 
 __global__ void k_walls64(DevState d, ContactList l, int count_active) {
@@ -363,6 +380,15 @@ __global__ void k_walls64(DevState d, ContactList l, int count_active) {
     atomicAdd(fw, law.F.x);
     atomicAdd(fw + 1, law.F.y);
     atomicAdd(fw + 2, law.F.z);
+    // moment about the wall's reference point p + v t, the force acting at
+    // the contact point
+    const V3<double> rw = V3<double>{x[0] - (W.p[0] + W.vel[0] * t), x[1] - (W.p[1] + W.vel[1] * t),
+                                     x[2] - (W.p[2] + W.vel[2] * t)} + (S.r - 0.5 * dn) * n;
+    const V3<double> tw = cross(rw, law.F);
+    double* mw = d.wtorque + 3 * (long long)w;
+    atomicAdd(mw, tw.x);
+    atomicAdd(mw + 1, tw.y);
+    atomicAdd(mw + 2, tw.z);
   }
 }
 

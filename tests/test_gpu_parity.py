@@ -237,16 +237,22 @@ def test_walls_plane_cylinder_cone(dem, oracle_mod, prec):
     with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
         F, T = sim.eval_forces()
         Fw = sim.wall_forces()
+        Fl, Tl = sim.wall_loads()
         a, b, u, ws, ww, uw = sim.contacts()
     om, _, _, ao, bo, wso, wwo = _oracle_lists(oracle_mod, sc, margin, K)
     assert np.array_equal(ws, wso) and np.array_equal(ww, wwo)
     assert set(np.unique(ww)) == {0, 1, 2, 3}
-    Fo, To, Fwo, _, _, act, mag = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, 0.0, ao,
-                                            bo, np.zeros((len(ao), 3)), wso, wwo,
-                                            np.zeros((len(wso), 3)), with_mag=True)
+    Fo, To, Fwo, _, _, act, mag, Two = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, 0.0,
+                                                 ao, bo, np.zeros((len(ao), 3)), wso, wwo,
+                                                 np.zeros((len(wso), 3)), with_mag=True,
+                                                 wall_torque=True)
     _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
+    assert np.array_equal(Fl, Fw)
+    extent = 0.07  # every lever arm about a wall's reference point is shorter
     for k in range(4):
         assert np.abs(Fw[k] - Fwo[k]).max() <= TOL[prec] * max(np.abs(Fwo).sum(), 1e-30)
+        assert np.abs(Tl[k] - Two[k]).max() <= TOL[prec] * extent * np.abs(Fwo).sum()
+        assert np.abs(Two[k]).max() > 0
 
 
 @pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
@@ -461,3 +467,51 @@ def test_launch_shapes_change_no_result(dem):
                 sim.set_tiles(**bad)
         assert sim.tiles() == best
         sim.step(5)  # still steps after tuning
+
+
+def test_wall_motion_import_matches_the_motion_given_from_the_start(dem, oracle_mod):
+    """Co-simulation hook: a plate held far above the clumps is moved, at step
+    20, to 2 um above them and driven down at 0.5 m/s (dem_set_wall_motion);
+    it reaches the bed and presses on it.  The run equals the oracle's run of
+    the same scene whose plate had that motion from t = 0 (out of reach of the
+    clumps until step 20 as well): the same trajectory to the FP64 trajectory
+    tolerances, and the same loads on the plate (force and moment about its
+    reference point) at the end."""
+    margin, K, t1, t2 = 2e-4, 10, 20, 60
+    sc = _scene(7, 250, scenes.PREC_FP64, margin=margin)
+    # the highest sphere surface of the generated bed
+    xs, _, tsph = oracle_mod.OracleModel(sc).sphere_centres(sc.tpl, sc.pos, sc.quat)
+    top = float((xs[:, 2] + sc.tpl_rad[tsph]).max())
+    v = np.array([0.0, 0.0, -0.5])
+    near = np.array([0.0, 0.0, top + 2e-6])  # reached a few steps after the import
+    sc_gpu = dataclasses.replace(sc, walls=list(sc.walls) + [scenes.plane((0, 0, top + 0.01), (0, 0, -1))],
+                                 hi=(sc.hi[0], sc.hi[1], top + 0.02))
+    p0 = near - v * (t1 * sc.h)
+    sc_orc = dataclasses.replace(sc_gpu, walls=list(sc.walls) + [scenes.plane(p0, (0, 0, -1), vel=v)])
+    plate = len(sc.walls)
+    with dem.Simulation(sc_gpu, margin=margin, rebuild_interval=K) as sim:
+        sim.step(t1)
+        sim.set_wall_motion(plate, near, v)
+        sim.step(t2 - t1)
+        pos, quat, vel, w = sim.state()
+        sim.eval_forces()
+        Fl, Tl = sim.wall_loads()
+        with pytest.raises(dem.DemError, match="INVALID"):
+            sim.set_wall_motion(plate + 1, near, v)
+    osim = oracle_mod.OracleSim(sc_orc, margin, K)
+    osim.step(t2)
+    po, qo, vo, wo = osim.state()
+    assert np.abs(pos - po).max() <= 1e-14 * (1 + np.abs(po).max())
+    assert np.abs(vel - vo).max() <= 1e-10 * np.abs(vo).max()
+    assert np.abs(w - wo).max() <= 1e-9 * np.abs(wo).max()
+    # the plate pushes on the bed by now: its loads with the oracle's own list
+    # and histories at the end of its run (the lists were rebuilt at the same
+    # steps; the histories agree to the trajectory tolerance)
+    ao, bo, uo, wso, wwo, uwo = osim.contacts()
+    om = oracle_mod.OracleModel(sc_orc)
+    _, _, Fwo, _, _, _, Two = om.forces(sc.tpl, po, qo, vo, wo, t2 * sc.h, ao, bo, uo, wso, wwo,
+                                        uwo, wall_torque=True)
+    assert Fwo[plate][2] > 0 and Fl[plate][2] > 0  # the bed pushes the plate up
+    scale = np.abs(Fwo[plate]).sum()
+    assert np.abs(Fl[plate] - Fwo[plate]).max() <= 1e-7 * scale
+    assert np.abs(Tl[plate] - Two[plate]).max() <= 1e-7 * scale * 0.1

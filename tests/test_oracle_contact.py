@@ -282,3 +282,37 @@ def test_tangential_history_update_and_cap(oracle_mod):
     # the normal component of a stored displacement is projected out (Eq. 3)
     act, F, u, *_ = om.contact(vb=[0, 0, 0], u=[3e-9, 2e-9, 0], **common)
     assert u[0] == 0.0 and u[1] == pytest.approx(2e-9, rel=1e-15)
+
+
+def test_wall_moments_balance(oracle_mod):
+    """Walls in the balance: for clumps pressed against moving box walls, the
+    total moment about the origin of every load vanishes, sum over clumps of
+    X x F + tau plus sum over walls of p_w(t) x F_w + tau_w, where tau_w is the
+    moment the oracle reports for wall w about its reference point p_w(t) =
+    p + v t; and the wall forces balance the clump forces."""
+    sc = scenes.packed_scene(12, 64, walls=True, compress=0.9)
+    rng = np.random.default_rng(3)
+    for w in sc.walls:
+        w["vel"] = tuple(rng.normal(scale=0.05, size=3))
+    t = 0.37
+    # the walls' positions at time t are where the packing put them at t = 0
+    for w in sc.walls:
+        w["p"] = tuple(np.asarray(w["p"]) - t * np.asarray(w["vel"]))
+    sc.bin_size = scenes.default_bin_size(sc, 1e-4)
+    om = oracle_mod.OracleModel(sc)
+    xs, owner, tsph = om.sphere_centres(sc.tpl, sc.pos, sc.quat)
+    qc, rho = om.detect_coords(xs, tsph, 1e-4)
+    a, b = om.pairs_binned(owner, qc, rho)
+    ws, ww = om.wall_candidates(xs, tsph, 1e-4, t, 0.0)
+    F, T, Fw, _, _, act, Tw = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, t, a, b,
+                                        np.zeros((len(a), 3)), ws, ww, np.zeros((len(ws), 3)),
+                                        wall_torque=True)
+    loaded = np.abs(Fw).sum(axis=1) > 0
+    assert loaded.sum() >= 3 and act > 30
+    scale = np.abs(F).sum() + np.abs(Fw).sum()
+    assert np.abs(F.sum(axis=0) + Fw.sum(axis=0)).max() < 1e-13 * scale
+    pw = np.array([np.asarray(w["p"]) + t * np.asarray(w["vel"]) for w in sc.walls])
+    L = (np.cross(sc.pos, F) + T).sum(axis=0) + (np.cross(pw, Fw) + Tw).sum(axis=0)
+    assert np.abs(L).max() < 1e-13 * scale * (np.abs(sc.pos).max() + np.abs(pw).max())
+    # and the wall moments are not trivially zero
+    assert np.abs(Tw).max() > 1e-6 * np.abs(Fw).max() * np.abs(sc.pos).max()
