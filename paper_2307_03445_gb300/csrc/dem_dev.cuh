@@ -89,7 +89,7 @@ __device__ __forceinline__ bool halted(const DevState& d) {
   return d.halt_at != nullptr && *d.dstep >= *d.halt_at;
 }
 
-// One bin registration after sorting, with everything the narrow phase tests:
+// One bin registration, in its bin's slot, with everything the narrow phase tests:
 // the lattice centre and enlarged radius, the owner clump, the sphere id and
 // the owning-bin mask: bit k is set when the clamped bin of the box's lower
 // corner equals this bin's coordinate on axis k.  A pair registered in a bin
