@@ -96,3 +96,32 @@ def bed_c5(n_clumps=11_000_000, lx=4.0, ly=2.0, patch=0.25, seed=1239, log=None,
     sc.walls = scenes.box_walls(0.0, lx, 0.0, ly, 0.0, top=plate, top_vel=(0.2, 0.0, 0.0))
     sc.hi = (lx, ly, plate + 0.01)
     return sc
+
+
+def compress(sim, plate_wall: dict, plate: int, speed: float, load: float, max_steps: int,
+             chunk: int = 10):
+    """Virtual compressor (section 4.1: the beds are compacted by a plate
+    before a test).  Drives the plane wall `plate` (its dict as given at
+    creation, `plate_wall`, whose normal points into the grains) into the bed
+    at `speed` m/s along its normal, checking the load on it every `chunk`
+    steps, until the grains push back with at least `load` newtons or
+    `max_steps` steps have run; then holds the plate where it is.  Returns
+    (steps run, final load, plate position).  Uses the library's wall loads
+    and wall motion calls (the co-simulation hook)."""
+    n = np.asarray(plate_wall["n"], float)
+    n = n / np.linalg.norm(n)
+    t0 = sim.stats()["time"]
+    p = np.asarray(plate_wall["p"], float) + np.asarray(plate_wall["vel"], float) * t0
+    sim.set_wall_motion(plate, p, speed * n)
+    steps, push = 0, 0.0
+    while steps < max_steps:
+        k = min(chunk, max_steps - steps)
+        sim.step(k)
+        steps += k
+        F, _ = sim.wall_loads()
+        push = -float(np.dot(F[plate], n))  # grains push the plate back along -n
+        if push >= load:
+            break
+    p = p + speed * n * (sim.stats()["time"] - t0)
+    sim.set_wall_motion(plate, p, np.zeros(3))
+    return steps, push, p
