@@ -544,13 +544,6 @@ __global__ void k_hist_walls(ContactList oldl, ContactList newl, long long old_n
 }
 
 // Row pointers of the wall list from the per-sphere offsets.
-__global__ void k_copy_row(const uint32_t* __restrict__ off, long long n, uint32_t total,
-                           uint32_t* __restrict__ row) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) row[i] = off[i];
-  if (i == n) row[n] = total;
-}
-
 // Exact missed-contact check: each touching pair of a fresh zero-margin list
 // must be present in the current list.
 __global__ void k_audit_pairs(DevState d, ContactList cur, long long nf, const int* __restrict__ fa,
@@ -674,11 +667,6 @@ void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* 
 void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns,
                        cudaStream_t st) {
   if (newl.nw > 0) { k_hist_walls<<<nblk(newl.nw, 256), 256, 0, st>>>(oldl, newl, old_ns); count_launch(); }
-}
-
-void launch_copy_row(const uint32_t* off, long long n, uint32_t total, uint32_t* row,
-                     cudaStream_t st) {
-  { k_copy_row<<<nblk(n + 1, 256), 256, 0, st>>>(off, n, total, row); count_launch(); }
 }
 
 void launch_audit(const DevState& d, const DetectOut& o, const ContactList& cur, long long n_fresh,

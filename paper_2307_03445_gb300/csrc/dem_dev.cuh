@@ -165,8 +165,6 @@ void launch_list_rows(const DevState& d, const DetectOut& o, const ContactList& 
 void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,
                       cudaStream_t st);
 void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
-void launch_copy_row(const uint32_t* off, long long n, uint32_t total, uint32_t* row,
-                     cudaStream_t st);
 void launch_audit(const DevState& d, const DetectOut& o, const ContactList& cur, long long n_fresh,
                   const int* fa, const uint32_t* fb, long long nw_fresh, const int* fws,
                   const uint32_t* fww, double t, unsigned long long* d_missed, cudaStream_t st);
