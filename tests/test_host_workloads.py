@@ -1,0 +1,61 @@
+"""Host logic of the sample-preparation compressor (no GPU): the loop that
+drives a plate through the co-simulation hook, checked against a stand-in
+simulation whose plate load grows once the plate has travelled a set
+distance.  The library calls it makes are the ones the GPU test exercises."""
+import numpy as np
+
+from paper_2307_03445_gb300 import scenes, workloads
+
+
+class FakeSim:
+    """Time advances by h per step; the plate's load is stiffness x travel
+    past `contact` once the plate has moved that far along its normal."""
+
+    def __init__(self, h, t0, contact, stiffness, plate):
+        self.h, self.t, self.contact, self.k, self.plate = h, t0, contact, stiffness, plate
+        self.motions = []  # (time, point, vel) of every set_wall_motion call
+        self.p = None
+        self.v = None
+
+    def stats(self):
+        return {"time": self.t}
+
+    def set_wall_motion(self, wall, point, vel):
+        assert wall == self.plate
+        self.motions.append((self.t, np.asarray(point, float).copy(), np.asarray(vel, float).copy()))
+        self.p, self.v, self.t_set = np.asarray(point, float), np.asarray(vel, float), self.t
+
+    def step(self, n):
+        self.t += n * self.h
+
+    def wall_loads(self):
+        pos = self.p + self.v * (self.t - self.t_set)
+        travel = float(np.dot(pos - self.motions[0][1], self.n))
+        F = np.zeros((self.plate + 1, 3))
+        F[self.plate] = -self.n * self.k * max(0.0, travel - self.contact)  # grains push back
+        return F, np.zeros_like(F)
+
+
+def test_compressor_drives_the_plate_until_the_load_then_holds_it():
+    plate_wall = scenes.plane((0.1, 0.2, 0.3), (0, 0, -2), vel=(0.0, 0.0, 0.0))
+    sim = FakeSim(h=1e-6, t0=5e-4, contact=3e-6, stiffness=1e5, plate=3)
+    sim.n = np.array([0.0, 0.0, -1.0])
+    steps, push, p = workloads.compress(sim, plate_wall, 3, speed=0.5, load=0.2, max_steps=1000,
+                                        chunk=4)
+    # travel to first contact 3 um, then 2 um more for 0.2 N at 1e5 N/m: 5 um at
+    # 0.5 um per step, checked every 4 steps -> stops at the first multiple of 4 >= 10
+    assert steps == 12 and push >= 0.2
+    assert np.allclose(p, [0.1, 0.2, 0.3 - 0.5 * steps * 1e-6], rtol=0, atol=1e-15)
+    (t0, p0, v0), (t1, p1, v1) = sim.motions
+    assert t0 == 5e-4 and np.allclose(p0, [0.1, 0.2, 0.3]) and np.allclose(v0, [0, 0, -0.5])
+    assert np.allclose(p1, p) and np.all(v1 == 0)  # held where it stopped
+
+
+def test_compressor_stops_at_the_step_budget():
+    plate_wall = scenes.plane((0.0, 0.0, 1.0), (0, 0, -1), vel=(0.0, 0.0, 0.1))
+    sim = FakeSim(h=1e-5, t0=0.0, contact=1.0, stiffness=1.0, plate=0)  # never reached
+    sim.n = np.array([0.0, 0.0, -1.0])
+    steps, push, p = workloads.compress(sim, plate_wall, 0, speed=0.2, load=1.0, max_steps=25,
+                                        chunk=10)
+    assert steps == 25 and push == 0.0
+    assert np.allclose(p, [0.0, 0.0, 1.0 - 0.2 * 25 * 1e-5], atol=1e-15)
