@@ -424,14 +424,15 @@ def test_deterministic_mode_is_bit_reproducible(dem, oracle_mod, prec):
         assert np.abs(pos - po).max() / np.abs(po - sc.pos).max() < 1e-5
 
 
-def test_launch_shapes_change_no_result(dem):
+@pytest.mark.parametrize("prec", [scenes.PREC_FP32, scenes.PREC_FP64])
+def test_launch_shapes_change_no_result(dem, prec):
     """Launch shapes (pair blocks per SM, update block, narrow chunk) change no
     result: in deterministic mode the state after 45 steps with rebuilds is
     bit-identical across shapes; the list and the bins are identical too.  The
     tile autotuner picks shapes from its sets, leaves the state, step count
     and counters as they were, and out-of-range shapes are refused."""
     margin, K, nsteps = 2e-4, 10, 45
-    sc = _scene(8, 400, scenes.PREC_FP32, margin=margin, compress=1.0, jitter=0.05)
+    sc = _scene(8, 400, prec, margin=margin, compress=1.0, jitter=0.05)
     shapes = [None, dict(pairs_blocks_per_sm=2, update_block=64, narrow_chunk=3),
               dict(pairs_blocks_per_sm=16, update_block=256, narrow_chunk=1)]
     runs = []
@@ -543,3 +544,32 @@ def test_virtual_compressor_reaches_its_load_and_holds(dem):
         assert F[k][2] > 0.0  # still loaded: the grains push the held plate up
         assert sim.stats()["guard_violations"] == 0
         assert sim.audit() == 0
+
+
+def test_set_state_uses_each_clumps_own_scene_corner(dem):
+    """Two scenes in one context, the second shifted by (0.5, 0.25, 0.125) m:
+    a state set on the device is split into voxel + offset against each
+    clump's own scene corner (restated here in numpy)."""
+    margin = 1e-4
+    sc = _scene(6, 300, scenes.PREC_FP32, margin=margin)
+    d = np.array([0.5, 0.25, 0.125])  # powers of two: the copy stays on the voxel grid
+    walls2 = [dict(w, p=tuple(np.asarray(w["p"]) + d)) for w in sc.walls]
+    sc2 = dataclasses.replace(sc, pos=sc.pos + d, lo=tuple(np.asarray(sc.lo) + d),
+                              hi=tuple(np.asarray(sc.hi) + d), walls=walls2)
+    rng = np.random.default_rng(23)
+    n = len(sc.tpl)
+    pos = np.concatenate([sc.pos, sc2.pos]) + rng.uniform(-2e-6, 2e-6, (2 * n, 3))
+    quat = scenes.random_quaternions(rng, 2 * n)
+    vel = rng.normal(scale=0.1, size=(2 * n, 3))
+    angvel = rng.normal(scale=30.0, size=(2 * n, 3))
+    with dem.Simulation(sc, margin=margin, rebuild_interval=10, extra_scenes=[sc2]) as sim:
+        sim.rebuild()
+        sim.set_state(pos, quat, vel, angvel)
+        P, Q, V, W = sim.state()
+        sim.step(3)  # and the scenes step
+    lo = np.concatenate([np.tile(sc.lo, (n, 1)), np.tile(sc2.lo, (n, 1))])
+    rel = pos - lo
+    m = np.rint(rel * 2.0**20)
+    off = (rel - m * 2.0**-20).astype(np.float32).astype(np.float64)
+    assert np.array_equal(P, lo + (m * 2.0**-20 + off))
+    assert np.array_equal(Q, quat) and np.array_equal(V, vel)
