@@ -44,7 +44,7 @@ extern "C" {
 
 /* ---- enumerations ------------------------------------------------------ */
 enum { DEM_FP64 = 0, DEM_FP32_VOXEL = 1 };
-enum { DEM_WALL_PLANE = 0, DEM_WALL_CYLINDER = 1, DEM_WALL_CONE = 2 };
+enum { DEM_WALL_PLANE = 0, DEM_WALL_CYLINDER = 1, DEM_WALL_CONE = 2, DEM_WALL_TRIANGLE = 3 };
 enum { DEM_MIX_MEAN = 0, DEM_MIX_MIN = 1, DEM_MIX_MAX = 2 };
 enum { DEM_MARGIN_FIXED = 0, DEM_MARGIN_LEARNED = 1 };
 enum { DEM_GUARD_OFF = 0, DEM_GUARD_COUNT = 1, DEM_GUARD_ROLLBACK = 2 };
@@ -55,6 +55,13 @@ enum { DEM_GUARD_OFF = 0, DEM_GUARD_COUNT = 1, DEM_GUARD_ROLLBACK = 2 };
  *   CYLINDER: p = a point on the axis, n = unit axis, radius; grains inside.
  *   CONE:     p = tip, n = unit axis from the tip towards the base,
  *             half_angle [rad], height (tip to base); grains outside the solid.
+ *   TRIANGLE: one facet of a triangle mesh (the paper's funnel, cone and wheel
+ *             boundaries, section 4): vertices p, b, c; n = the unit normal
+ *             (b - p) x (c - p) / |...| on the grains' side (checked to 1e-9).
+ *             Distance: the signed distance to the facet's plane where the
+ *             centre projects inside the facet, else the distance to the
+ *             nearest edge.  Every sphere-facet pair is its own contact (a
+ *             mesh is a list of facets; its load is the sum of theirs).
  * The surface moves with velocity vel: its reference point at time t is
  * p + vel * t.  material indexes the material table.  scene = -1 applies the
  * wall to every scene, otherwise to one scene. */
@@ -68,6 +75,7 @@ typedef struct {
     double height;
     double vel[3];
     int scene;
+    double b[3], c[3];  /* TRIANGLE: second and third vertex (else unused) */
 } dem_wall;
 
 /* Creation parameters.  Arrays are copied by dem_create. */

@@ -35,7 +35,7 @@ _LIB_PATH = os.path.join(_HERE, "libdem_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-WALL_PLANE, WALL_CYLINDER, WALL_CONE = 0, 1, 2
+WALL_PLANE, WALL_CYLINDER, WALL_CONE, WALL_TRIANGLE = 0, 1, 2, 3
 MIX_MEAN, MIX_MIN, MIX_MAX = 0, 1, 2
 
 
@@ -56,7 +56,8 @@ def build(force: bool = False) -> str:
 class Wall(C.Structure):
     _fields_ = [("type", C.c_int), ("material", C.c_int), ("p", C.c_double * 3),
                 ("n", C.c_double * 3), ("radius", C.c_double), ("half_angle", C.c_double),
-                ("height", C.c_double), ("vel", C.c_double * 3)]
+                ("height", C.c_double), ("vel", C.c_double * 3), ("b", C.c_double * 3),
+                ("c", C.c_double * 3)]
 
 
 class Model(C.Structure):
@@ -167,6 +168,8 @@ class OracleModel:
                 warr[i].p[j] = float(w["p"][j])
                 warr[i].n[j] = float(w["n"][j])
                 warr[i].vel[j] = float(w.get("vel", (0.0, 0.0, 0.0))[j])
+                warr[i].b[j] = float(w.get("b", (0.0, 0.0, 0.0))[j])
+                warr[i].c[j] = float(w.get("c", (0.0, 0.0, 0.0))[j])
             warr[i].radius = float(w.get("radius", 0.0))
             warr[i].half_angle = float(w.get("half_angle", 0.0))
             warr[i].height = float(w.get("height", 0.0))

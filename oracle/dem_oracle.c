@@ -26,6 +26,10 @@
  *   A11 multi-bin registration of the enlarged AABB, pair reported by the bin
  *       holding the per-axis max of the two lower corners; exact int64 test.
  *   A15 sphere-wall contacts: R = r_sphere, m = m_clump, wall material given.
+ *   A16 mesh facets (section 4 funnel, cone and wheel meshes): distance to
+ *       the closed triangle; the signed plane distance where the centre
+ *       projects inside it, else the unsigned distance to the nearest edge;
+ *       every sphere-facet pair is its own contact.
  */
 #include "dem_oracle.h"
 
@@ -263,6 +267,53 @@ long long orc_pairs_binned(const orc_model* m, long long ns, const int* owner,
 /* ------------------------------------------------------------------ */
 /* analytic boundaries                                                  */
 /* ------------------------------------------------------------------ */
+/* Mesh facet with vertices p, b, c (translating rigidly, so the edge
+ * vectors e1 = b - p, e2 = c - p do not depend on time) and d = x - p(t).
+ * Barycentric coordinates (u, v) of the projection of x on the facet's plane
+ * solve the normal equations [e1.e1 e1.e2; e1.e2 e2.e2] (u, v) = (d.e1, d.e2).
+ * Inside the facet (u, v >= 0, u + v <= 1) the closest point is the
+ * projection: signed distance d.n, normal n.  Outside it the closest point of
+ * the closed triangle lies on its boundary: the nearest of the three edges
+ * (p -> b, p -> c, b -> c), each the segment point at the clamped parameter
+ * of the perpendicular foot; normal from that point to x. */
+static double facet_distance(const orc_wall* w, const double d[3], double nw[3]) {
+    double e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = w->b[k] - w->p[k];
+        e2[k] = w->c[k] - w->p[k];
+    }
+    const double ax = dot3(d, w->n);
+    const double d00 = dot3(e1, e1), d01 = dot3(e1, e2), d11 = dot3(e2, e2);
+    const double b0 = dot3(d, e1), b1 = dot3(d, e2);
+    const double den = d00 * d11 - d01 * d01;
+    const double u = (d11 * b0 - d01 * b1) / den;
+    const double v = (d00 * b1 - d01 * b0) / den;
+    if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) {
+        for (int k = 0; k < 3; ++k) nw[k] = w->n[k];
+        return ax;
+    }
+    const double zero[3] = {0.0, 0.0, 0.0};
+    double e3[3];
+    for (int k = 0; k < 3; ++k) e3[k] = e2[k] - e1[k];
+    const double* org[3] = {zero, zero, e1};
+    const double* dir[3] = {e1, e2, e3};
+    double best = -1.0, qb[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < 3; ++j) {
+        double r[3], q[3];
+        for (int k = 0; k < 3; ++k) r[k] = d[k] - org[j][k];
+        double t = dot3(r, dir[j]) / dot3(dir[j], dir[j]);
+        t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+        for (int k = 0; k < 3; ++k) q[k] = r[k] - t * dir[j][k];
+        const double dist = sqrt(dot3(q, q));
+        if (best < 0.0 || dist < best) {
+            best = dist;
+            for (int k = 0; k < 3; ++k) qb[k] = q[k];
+        }
+    }
+    for (int k = 0; k < 3; ++k) nw[k] = best > 0.0 ? qb[k] / best : w->n[k];
+    return best;
+}
+
 /* Signed distance from x to the wall surface at time t (positive on the
  * grains' side) and the unit normal nw of the surface at the closest point,
  * pointing towards the grains. */
@@ -276,6 +327,7 @@ double orc_wall_distance(const orc_wall* w, double t, const double x[3], double 
         for (int k = 0; k < 3; ++k) nw[k] = w->n[k];
         return dot3(d, w->n);
     }
+    if (w->type == ORC_WALL_TRIANGLE) return facet_distance(w, d, nw);
     const double ax = dot3(d, w->n);
     double rv[3];
     for (int k = 0; k < 3; ++k) rv[k] = d[k] - ax * w->n[k];

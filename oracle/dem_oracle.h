@@ -28,7 +28,7 @@ extern "C" {
 /* Detection lattice: coordinates are quantised to 2^-ORC_EPS_LOG2 metres. */
 #define ORC_EPS_LOG2 24
 
-enum { ORC_WALL_PLANE = 0, ORC_WALL_CYLINDER = 1, ORC_WALL_CONE = 2 };
+enum { ORC_WALL_PLANE = 0, ORC_WALL_CYLINDER = 1, ORC_WALL_CONE = 2, ORC_WALL_TRIANGLE = 3 };
 enum { ORC_MIX_MEAN = 0, ORC_MIX_MIN = 1, ORC_MIX_MAX = 2 };
 
 typedef struct {
@@ -41,6 +41,8 @@ typedef struct {
     double half_angle;  /* cone half angle [rad] (grains outside the solid cone) */
     double height;      /* cone height, tip to base plane */
     double vel[3];      /* prescribed translation velocity [m/s] */
+    double b[3], c[3];  /* triangle: the other two vertices (p is the first);
+                           n is its unit normal on the grains' side */
 } orc_wall;
 
 typedef struct {

@@ -52,6 +52,8 @@ def walls_to_c(walls, scene_of=None):
             arr[i].p[k] = float(w["p"][k])
             arr[i].n[k] = float(w["n"][k])
             arr[i].vel[k] = float(w.get("vel", (0.0, 0.0, 0.0))[k])
+            arr[i].b[k] = float(w.get("b", (0.0, 0.0, 0.0))[k])
+            arr[i].c[k] = float(w.get("c", (0.0, 0.0, 0.0))[k])
         arr[i].radius = float(w.get("radius", 0.0))
         arr[i].half_angle = float(w.get("half_angle", 0.0))
         arr[i].height = float(w.get("height", 0.0))

@@ -29,7 +29,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class DemWall(C.Structure):
     _fields_ = [("type", C.c_int), ("material", C.c_int), ("p", C.c_double * 3),
                 ("n", C.c_double * 3), ("radius", C.c_double), ("half_angle", C.c_double),
-                ("height", C.c_double), ("vel", C.c_double * 3), ("scene", C.c_int)]
+                ("height", C.c_double), ("vel", C.c_double * 3), ("scene", C.c_int),
+                ("b", C.c_double * 3), ("c", C.c_double * 3)]
 
 
 class DemParams(C.Structure):

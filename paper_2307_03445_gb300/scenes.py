@@ -18,7 +18,7 @@ import math
 import numpy as np
 
 DENSITY = 2600.0  # kg/m^3; the paper gives no grain density
-WALL_PLANE, WALL_CYLINDER, WALL_CONE = 0, 1, 2
+WALL_PLANE, WALL_CYLINDER, WALL_CONE, WALL_TRIANGLE = 0, 1, 2, 3
 PREC_FP64, PREC_FP32 = 0, 1
 
 
@@ -178,6 +178,55 @@ def cone(tip, axis, half_angle, height, vel=(0.0, 0.0, 0.0), material=0):
     return {"type": WALL_CONE, "p": tuple(map(float, tip)), "n": tuple(a),
             "half_angle": float(half_angle), "height": float(height), "vel": tuple(vel),
             "material": material}
+
+
+def triangle(a, b, c, vel=(0.0, 0.0, 0.0), material=0):
+    """One mesh facet; the grains are on the side of (b - a) x (c - a)."""
+    a, b, c = (np.asarray(v, float) for v in (a, b, c))
+    n = np.cross(b - a, c - a)
+    n = n / np.linalg.norm(n)
+    return {"type": WALL_TRIANGLE, "p": tuple(map(float, a)), "b": tuple(map(float, b)),
+            "c": tuple(map(float, c)), "n": tuple(map(float, n)), "vel": tuple(vel),
+            "material": material}
+
+
+def mesh(vertices, faces, grains_at, vel=(0.0, 0.0, 0.0), material=0):
+    """Facets of a triangle mesh, each oriented so that its normal points to
+    the side of its plane where the point grains_at lies."""
+    v = np.asarray(vertices, float)
+    out = []
+    for i, j, k in faces:
+        a, b, c = v[i], v[j], v[k]
+        if np.dot(np.cross(b - a, c - a), np.asarray(grains_at, float) - a) < 0:
+            b, c = c, b
+        out.append(triangle(a, b, c, vel=vel, material=material))
+    return out
+
+
+def box_mesh(x0, x1, y0, y1, z0, z1, material=0):
+    """The six faces of a box as 12 facets, grains inside."""
+    v = [(x, y, z) for z in (z0, z1) for y in (y0, y1) for x in (x0, x1)]
+    quads = [(0, 1, 3, 2), (4, 5, 7, 6), (0, 1, 5, 4), (2, 3, 7, 6), (0, 2, 6, 4), (1, 3, 7, 5)]
+    faces = [f for q in quads for f in ((q[0], q[1], q[2]), (q[0], q[2], q[3]))]
+    centre = (0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (z0 + z1))
+    return mesh(v, faces, centre, material=material)
+
+
+def funnel_mesh(cx, cy, z0, z1, r0, r1, nseg, material=0):
+    """The side of a funnel (a frustum from radius r0 at height z0 to r1 at
+    z1, open at both ends) as 2 nseg facets, grains inside."""
+    ang = 2 * np.pi * np.arange(nseg) / nseg
+    v = [(cx + r * np.cos(t), cy + r * np.sin(t), z) for z, r in ((z0, r0), (z1, r1)) for t in ang]
+    faces = []
+    for i in range(nseg):
+        j = (i + 1) % nseg
+        faces += [(i, j, nseg + j), (i, nseg + j, nseg + i)]
+    out = []
+    for f in faces:
+        # orient towards the axis at the facet's own height
+        zc = np.mean([v[k][2] for k in f])
+        out.append(mesh(v, [f], (cx, cy, zc), material=material)[0])
+    return out
 
 
 def box_walls(x0, x1, y0, y1, z0, top=None, top_vel=(0.0, 0.0, 0.0)):

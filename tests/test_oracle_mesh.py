@@ -1,0 +1,130 @@
+"""Oracle pins for mesh facets (sphere-triangle contacts, the boundaries the
+paper builds from meshes in section 4): the distance is the distance to the
+closed triangle, checked against brute force over a dense sampling of the
+facet; in the facet's face region it is exactly the plane wall's; beyond a
+vertex it is the distance to that vertex."""
+import numpy as np
+
+from paper_2307_03445_gb300 import scenes
+from tests.helpers import set_clumps, single_sphere_scene
+
+A, B, Cv = np.array([0.01, -0.004, 0.002]), np.array([0.026, 0.001, -0.003]), np.array([0.004, 0.018, 0.006])
+
+
+def _model(oracle_mod, walls):
+    return oracle_mod.OracleModel(single_sphere_scene([1e-3], walls=walls))
+
+
+def _dense_facet(a, b, c, N=600):
+    i, j = np.meshgrid(np.arange(N + 1), np.arange(N + 1), indexing="ij")
+    keep = (i + j) <= N
+    u, v = i[keep] / N, j[keep] / N
+    return a + u[:, None] * (b - a) + v[:, None] * (c - a)
+
+
+def _barycentric(a, b, c, x):
+    e1, e2, d = b - a, c - a, x - a
+    M = np.array([[e1 @ e1, e1 @ e2], [e1 @ e2, e2 @ e2]])
+    return np.linalg.solve(M, [d @ e1, d @ e2])
+
+
+def test_facet_distance_is_the_distance_to_the_closed_triangle(oracle_mod):
+    tri = scenes.triangle(A, B, Cv)
+    om = _model(oracle_mod, [tri])
+    n = np.asarray(tri["n"])
+    pts = _dense_facet(A, B, Cv)
+    rng = np.random.default_rng(5)
+    centre = (A + B + Cv) / 3
+    regions = set()
+    for _ in range(150):
+        x = centre + rng.uniform(-0.02, 0.02, 3) + rng.choice([-1, 1]) * rng.uniform(5e-4, 4e-3) * n
+        d, nw = om.wall_distance(0, 0.0, x)
+        brute = np.sqrt(((pts - x) ** 2).sum(axis=1)).min()
+        assert abs(abs(d) - brute) <= 2e-7, (x, d, brute)
+        # the closest point x - |d| nw (face region: x - d n) lies on the facet
+        cp = x - d * nw
+        u, v = _barycentric(A, B, Cv, cp)
+        assert u >= -1e-9 and v >= -1e-9 and u + v <= 1 + 1e-9
+        assert abs(np.linalg.norm(nw) - 1.0) < 1e-12
+        inside = np.allclose(nw, n, rtol=0, atol=0)
+        regions.add(inside)
+        if inside:
+            assert np.isclose(d, (x - A) @ n, rtol=0, atol=1e-17)
+        else:
+            assert d >= 0  # edge or vertex region: unsigned
+    assert regions == {True, False}
+
+
+def test_facet_in_its_face_region_is_the_plane_wall_bit_for_bit(oracle_mod):
+    """Same point p and normal: a sphere that stays over the facet's interior
+    sees exactly the plane's distance, list and forces, through a whole
+    trajectory (sliding and rolling under gravity)."""
+    a, b, c = np.array([-0.04, -0.04, 0.0]), np.array([0.05, -0.03, 0.0]), np.array([-0.03, 0.05, 0.0])
+    runs = []
+    for wall in (scenes.triangle(a, b, c), scenes.plane(a, (0, 0, 1))):
+        sc = single_sphere_scene([1e-3], g=(0.3, 0.0, -9.81), walls=[wall], mu=0.4, cor=0.6)
+        # resting at about its static overlap, sliding along x
+        set_clumps(sc, [0], [[0.0, 0.0, 1e-3 - 1.2e-7]], vel=[[0.05, 0.0, 0.0]])
+        sim = oracle_mod.OracleSim(sc, margin=5e-5, rebuild_every=10)
+        sim.step(3000)
+        runs.append((sim.state(), sim.contacts()))
+    (s1, c1), (s2, c2) = runs
+    for x, y in zip(s1, s2):
+        assert np.array_equal(x, y)
+    assert np.array_equal(c1[3], c2[3]) and np.array_equal(c1[5], c2[5])
+    assert len(c1[3]) == 1 and np.abs(c1[5]).max() > 0  # it touched and slid
+
+
+def test_facet_vertex_and_edge_closed_forms(oracle_mod):
+    tri = scenes.triangle(A, B, Cv)
+    om = _model(oracle_mod, [tri])
+    n = np.asarray(tri["n"])
+    # beyond vertex B, away from both of its edges
+    out = (B - A) / np.linalg.norm(B - A) + (B - Cv) / np.linalg.norm(B - Cv)
+    x = B + 0.003 * out / np.linalg.norm(out) + 0.001 * n
+    d, nw = om.wall_distance(0, 0.0, x)
+    assert np.isclose(d, np.linalg.norm(x - B), rtol=1e-14)
+    assert np.allclose(nw, (x - B) / np.linalg.norm(x - B), atol=1e-13)
+    # off the middle of edge A-C, in the facet's plane, outwards
+    e = Cv - A
+    mid = A + 0.5 * e
+    perp = np.cross(n, e)
+    perp = perp / np.linalg.norm(perp)
+    if perp @ (B - A) > 0:
+        perp = -perp
+    x = mid + 0.002 * perp - 0.0005 * n  # behind the plane: still unsigned
+    d, nw = om.wall_distance(0, 0.0, x)
+    assert np.isclose(d, np.hypot(0.002, 0.0005), rtol=1e-13)
+
+
+def test_moving_facet_is_the_translated_facet(oracle_mod):
+    vel = np.array([0.01, -0.02, 0.03])
+    t = 0.25
+    om_m = _model(oracle_mod, [scenes.triangle(A, B, Cv, vel=tuple(vel))])
+    om_s = _model(oracle_mod, [scenes.triangle(A + vel * t, B + vel * t, Cv + vel * t)])
+    rng = np.random.default_rng(9)
+    for _ in range(40):
+        x = (A + B + Cv) / 3 + vel * t + rng.uniform(-0.02, 0.02, 3)
+        d1, n1 = om_m.wall_distance(0, t, x)
+        d2, n2 = om_s.wall_distance(0, 0.0, x)
+        assert abs(d1 - d2) <= 1e-15 and np.allclose(n1, n2, atol=1e-12)
+
+
+def test_mesh_helpers_orient_every_facet_towards_the_grains():
+    box = scenes.box_mesh(-0.01, 0.02, -0.015, 0.01, 0.0, 0.03)
+    assert len(box) == 12
+    centre = np.array([0.005, -0.0025, 0.015])
+    for f in box:
+        a, b, c, n = (np.asarray(f[k]) for k in ("p", "b", "c", "n"))
+        assert abs(np.linalg.norm(n) - 1) < 1e-15
+        assert abs(n @ (b - a)) < 1e-15 and abs(n @ (c - a)) < 1e-15
+        assert n @ (centre - a) > 0
+    # the 12 facets tile the six faces: total area = box surface
+    area = sum(0.5 * np.linalg.norm(np.cross(np.subtract(f["b"], f["p"]), np.subtract(f["c"], f["p"])))
+               for f in box)
+    assert np.isclose(area, 2 * (0.03 * 0.025 + 0.03 * 0.03 + 0.025 * 0.03), rtol=1e-13)
+    fun = scenes.funnel_mesh(0.0, 0.0, 0.0, 0.02, 0.005, 0.015, 8)
+    assert len(fun) == 16
+    for f in fun:
+        a, n = np.asarray(f["p"]), np.asarray(f["n"])
+        assert n[0] * -a[0] + n[1] * -a[1] > 0  # towards the axis
