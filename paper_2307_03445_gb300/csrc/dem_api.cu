@@ -450,6 +450,14 @@ int finalize(dem_ctx* c) {
       d.radf = (float)uw.radius;
       d.heightf = (float)uw.height;
       d.rbf = (float)d.rb;
+      if (uw.type == DEM_WALL_TRIANGLE) {
+        for (int k = 0; k < 3; ++k) {
+          d.e1[k] = uw.b[k] - uw.p[k];
+          d.e2[k] = uw.c[k] - uw.p[k];
+          split_ff(d.e1[k], d.e1h[k], d.e1l[k]);
+          split_ff(d.e2[k], d.e2h[k], d.e2l[k]);
+        }
+      }
       idx.push_back((int)c->walls.size());
       c->wall_user.push_back((int)w);
       c->wall_scene.push_back((int)s);
@@ -1102,12 +1110,25 @@ int dem_create(const dem_params* params, dem_ctx** out) {
       return bad("material out of range");
   for (int w = 0; w < p.n_walls; ++w) {
     const dem_wall& wl = p.walls[w];
-    if (wl.type < 0 || wl.type > 2) return bad("unknown wall type");
+    if (wl.type < 0 || wl.type > 3) return bad("unknown wall type");
     if (wl.material < 0 || wl.material >= p.n_materials) return bad("wall material out of range");
     const double nn = wl.n[0] * wl.n[0] + wl.n[1] * wl.n[1] + wl.n[2] * wl.n[2];
     if (!(std::fabs(nn - 1.0) < 1e-9)) return bad("wall normal / axis must be a unit vector");
     if (wl.type == DEM_WALL_CYLINDER && !(wl.radius > 0)) return bad("cylinder radius must be > 0");
     if (wl.type == DEM_WALL_CONE && !(wl.height > 0 && wl.half_angle > 0 && wl.half_angle < 1.5707963)) return bad("bad cone");
+    if (wl.type == DEM_WALL_TRIANGLE) {
+      double e1[3], e2[3];
+      for (int k = 0; k < 3; ++k) { e1[k] = wl.b[k] - wl.p[k]; e2[k] = wl.c[k] - wl.p[k]; }
+      const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+      const double l2 = std::sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
+      const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                   cz = e1[0] * e2[1] - e1[1] * e2[0];
+      const double area2 = std::sqrt(cx * cx + cy * cy + cz * cz);
+      if (!(area2 > 1e-9 * l1 * l2)) return bad("degenerate triangle");
+      // n must be the unit normal (b - p) x (c - p) / |...|
+      if (!(std::fabs(cx * wl.n[0] + cy * wl.n[1] + cz * wl.n[2] - area2) <= 1e-9 * area2))
+        return bad("triangle normal must be (b - p) x (c - p) normalised");
+    }
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1532,7 +1553,11 @@ int dem_set_wall_motion(dem_ctx* c, int wall, const double* point, const double*
   dem_wall& uw = c->user_walls[wall];
   for (int k = 0; k < 3; ++k) {
     uw.vel[k] = vel[k];
-    uw.p[k] = point[k] - vel[k] * t;
+    const double np = point[k] - vel[k] * t;
+    // a facet moves rigidly: its other vertices follow the first
+    uw.b[k] += np - uw.p[k];
+    uw.c[k] += np - uw.p[k];
+    uw.p[k] = np;
   }
   if (!c->finalized) return DEM_OK;  // the device tables are built from user_walls
   const double speed = std::sqrt((vel[0] * vel[0] + vel[1] * vel[1]) + vel[2] * vel[2]);

@@ -44,6 +44,31 @@ __device__ float wall_distance_est(const WallDev& w, float t, const float x[3]) 
   }
   const float ax = dd[0] * n[0] + dd[1] * n[1] + dd[2] * n[2];
   if (w.type == 0) return ax;
+  if (w.type == 3) {
+    const float* e1 = w.e1h;
+    const float* e2 = w.e2h;
+    const float d00 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    const float d01 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    const float d11 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    const float b0 = dd[0] * e1[0] + dd[1] * e1[1] + dd[2] * e1[2];
+    const float b1 = dd[0] * e2[0] + dd[1] * e2[1] + dd[2] * e2[2];
+    const float den = d00 * d11 - d01 * d01;
+    const float u = (d11 * b0 - d01 * b1) / den, v = (d00 * b1 - d01 * b0) / den;
+    if (u >= 0.f && v >= 0.f && u + v <= 1.f) return ax;
+    float best = 3.4e38f;
+    for (int j = 0; j < 3; ++j) {
+      float r[3], e[3];
+      for (int k = 0; k < 3; ++k) {
+        r[k] = j == 2 ? dd[k] - e1[k] : dd[k];
+        e[k] = j == 0 ? e1[k] : (j == 1 ? e2[k] : e2[k] - e1[k]);
+      }
+      float t = (r[0] * e[0] + r[1] * e[1] + r[2] * e[2]) / (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+      t = fminf(fmaxf(t, 0.f), 1.f);
+      const float q0 = r[0] - t * e[0], q1 = r[1] - t * e[1], q2 = r[2] - t * e[2];
+      best = fminf(best, sqrtf(q0 * q0 + q1 * q1 + q2 * q2));
+    }
+    return best;
+  }
   float rv[3] = {dd[0] - ax * n[0], dd[1] - ax * n[1], dd[2] - ax * n[2]};
   const float rho = sqrtf(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
   if (w.type == 1) return w.radf - rho;

@@ -83,6 +83,10 @@ struct WallDev {
   double speed_d;     // |vel| = sqrt((vx^2 + vy^2) + vz^2), evaluated on the host
   float pf[3], vf[3]; // reference point and velocity as float (estimates, wall speed)
   float radf, heightf, rbf;
+  // mesh facet: edge vectors from the first vertex p (translation invariant)
+  double e1[3], e2[3];      // b - p, c - p
+  float e1h[3], e1l[3];     // as float-float
+  float e2h[3], e2l[3];
 };
 
 // Sphere pose record used by the contact kernels (written every step).

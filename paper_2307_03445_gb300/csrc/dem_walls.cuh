@@ -8,6 +8,43 @@ __device__ __forceinline__ double dot3d(const double a[3], const double b[3]) {
   return __dadd_rn(__dadd_rn(__dmul_rn(a[0], b[0]), __dmul_rn(a[1], b[1])), __dmul_rn(a[2], b[2]));
 }
 
+// Mesh facet, FP64: dd = x - p(t) with p the first vertex.  Inside the face
+// region (barycentric coordinates of the projection from the normal
+// equations of the edge vectors all >= 0) the signed distance to the plane;
+// otherwise the unsigned distance to the nearest of the edges p->b, p->c,
+// b->c (first wins a tie), the foot at the clamped perpendicular parameter.
+__device__ __forceinline__ double facet_distance64(const WallDev& w, const double dd[3], double nw[3]) {
+  const double ax = dot3d(dd, w.n);
+  const double d00 = dot3d(w.e1, w.e1), d01 = dot3d(w.e1, w.e2), d11 = dot3d(w.e2, w.e2);
+  const double b0 = dot3d(dd, w.e1), b1 = dot3d(dd, w.e2);
+  const double den = __dsub_rn(__dmul_rn(d00, d11), __dmul_rn(d01, d01));
+  const double u = __ddiv_rn(__dsub_rn(__dmul_rn(d11, b0), __dmul_rn(d01, b1)), den);
+  const double v = __ddiv_rn(__dsub_rn(__dmul_rn(d00, b1), __dmul_rn(d01, b0)), den);
+  if (u >= 0.0 && v >= 0.0 && __dadd_rn(u, v) <= 1.0) {
+    for (int k = 0; k < 3; ++k) nw[k] = w.n[k];
+    return ax;
+  }
+  double best = -1.0, qb[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    double r[3], e[3], q[3];
+    for (int k = 0; k < 3; ++k) {
+      r[k] = j == 2 ? __dsub_rn(dd[k], w.e1[k]) : dd[k];
+      e[k] = j == 0 ? w.e1[k] : (j == 1 ? w.e2[k] : __dsub_rn(w.e2[k], w.e1[k]));
+    }
+    double t = __ddiv_rn(dot3d(r, e), dot3d(e, e));
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    for (int k = 0; k < 3; ++k) q[k] = __dsub_rn(r[k], __dmul_rn(t, e[k]));
+    const double dist = __dsqrt_rn(dot3d(q, q));
+    if (best < 0.0 || dist < best) {
+      best = dist;
+      for (int k = 0; k < 3; ++k) qb[k] = q[k];
+    }
+  }
+  for (int k = 0; k < 3; ++k) nw[k] = best > 0.0 ? __ddiv_rn(qb[k], best) : w.n[k];
+  return best;
+}
+
 // Signed distance from x to the wall at time t (positive on the grains' side),
 // with exactly the operation order of its definition; nw: unit normal of the
 // surface at the closest point, towards the grains.
@@ -21,6 +58,7 @@ __device__ __forceinline__ double wall_distance64(const WallDev& w, double t, co
     for (int k = 0; k < 3; ++k) nw[k] = w.n[k];
     return dot3d(dd, w.n);
   }
+  if (w.type == 3) return facet_distance64(w, dd, nw);
   const double ax = dot3d(dd, w.n);
   double rv[3];
   for (int k = 0; k < 3; ++k) rv[k] = __dsub_rn(dd[k], __dmul_rn(ax, w.n[k]));
@@ -86,6 +124,43 @@ __device__ __forceinline__ float wall_geom32(const WallDev& w, const long long w
   if (w.type == 0) {
     dist = ax;
     nw = {w.nh[0], w.nh[1], w.nh[2]};
+  } else if (w.type == 3) {
+    // mesh facet: the region is classified in float (the distance is
+    // continuous across the regions' borders), the distance in float-float
+    const V3<float> df = {d[0].h, d[1].h, d[2].h};
+    const V3<float> e1 = {w.e1h[0], w.e1h[1], w.e1h[2]}, e2 = {w.e2h[0], w.e2h[1], w.e2h[2]};
+    const float d00 = dot(e1, e1), d01 = dot(e1, e2), d11 = dot(e2, e2);
+    const float b0 = dot(df, e1), b1 = dot(df, e2);
+    const float den = d00 * d11 - d01 * d01;
+    const float u = (d11 * b0 - d01 * b1) / den, v = (d00 * b1 - d01 * b0) / den;
+    if (u >= 0.f && v >= 0.f && u + v <= 1.f) {
+      dist = ax;
+      nw = {w.nh[0], w.nh[1], w.nh[2]};
+    } else {
+      const ff E1[3] = {{w.e1h[0], w.e1l[0]}, {w.e1h[1], w.e1l[1]}, {w.e1h[2], w.e1l[2]}};
+      const ff E2[3] = {{w.e2h[0], w.e2l[0]}, {w.e2h[1], w.e2l[1]}, {w.e2h[2], w.e2l[2]}};
+      ff best = {-1.f, 0.f};
+      V3<float> qb = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        ff r[3], e[3];
+        for (int k = 0; k < 3; ++k) {
+          r[k] = j == 2 ? ff_sub(d[k], E1[k]) : d[k];
+          e[k] = j == 0 ? E1[k] : (j == 1 ? E2[k] : ff_sub(E2[k], E1[k]));
+        }
+        const V3<float> rh = {r[0].h, r[1].h, r[2].h}, eh = {e[0].h, e[1].h, e[2].h};
+        const float t = fminf(fmaxf(dot(rh, eh) / dot(eh, eh), 0.f), 1.f);
+        const ff q[3] = {ff_sub(r[0], ff_mulf(e[0], t)), ff_sub(r[1], ff_mulf(e[1], t)),
+                         ff_sub(r[2], ff_mulf(e[2], t))};
+        const ff dq = ff_sqrt(ff_add(ff_add(ff_mul(q[0], q[0]), ff_mul(q[1], q[1])), ff_mul(q[2], q[2])));
+        if (best.h < 0.f || dq.h < best.h) {
+          best = dq;
+          qb = {q[0].h, q[1].h, q[2].h};
+        }
+      }
+      dist = best;
+      nw = best.h > 0.f ? (1.f / best.h) * qb : V3<float>{w.nh[0], w.nh[1], w.nh[2]};
+    }
   } else {
     const ff rv[3] = {ff_sub(d[0], ff_mul(ax, a[0])), ff_sub(d[1], ff_mul(ax, a[1])),
                       ff_sub(d[2], ff_mul(ax, a[2]))};

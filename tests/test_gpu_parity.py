@@ -573,3 +573,92 @@ def test_set_state_uses_each_clumps_own_scene_corner(dem):
     off = (rel - m * 2.0**-20).astype(np.float32).astype(np.float64)
     assert np.array_equal(P, lo + (m * 2.0**-20 + off))
     assert np.array_equal(Q, quat) and np.array_equal(V, vel)
+
+
+def _mesh_scene(prec, seed=12):
+    """Clumps in a funnel built from 16 facets over a floor of 2 facets that
+    rises at 1 cm/s; 180 clumps are placed within reach of a facet, over its
+    face, beyond its edges or near its vertices (where neighbouring facets
+    share the contact), the rest inside the funnel."""
+    rng = np.random.default_rng(seed)
+    walls = scenes.funnel_mesh(0.03, 0.03, 0.0, 0.035, 0.015, 0.027, 8)
+    walls += scenes.mesh([(0.0, 0.0, 0.0), (0.06, 0.0, 0.0), (0.06, 0.06, 0.0), (0.0, 0.06, 0.0)],
+                         [(0, 1, 2), (0, 2, 3)], (0.03, 0.03, 1.0), vel=(0.0, 0.0, 0.01))
+    sc = scenes.packed_scene(seed, 400, precision=prec, compress=0.95, walls=False, vel_scale=0.02)
+    sc.walls = walls
+    n = len(sc.tpl)
+    bound = sc.bounding_radius()[sc.tpl]
+    z = 0.004 + 0.026 * rng.random(n)
+    rad = (0.9 * (0.015 + 0.012 * z / 0.035) - 1.5 * bound) * np.sqrt(rng.random(n))
+    th = 2 * math.pi * rng.random(n)
+    P = np.stack([0.03 + rad * np.cos(th), 0.03 + rad * np.sin(th), z], axis=1)
+    for i in range(180):
+        f = walls[i % len(walls)]
+        a, b, c, nf = (np.asarray(f[k]) for k in ("p", "b", "c", "n"))
+        u, v = rng.random(2)
+        if u + v > 1:
+            u, v = 1 - u, 1 - v
+        if i % 3 == 2:  # beyond an edge or a vertex
+            u, v = u * 1.25 - 0.1, v * 1.25 - 0.1
+        P[i] = a + u * (b - a) + v * (c - a) + rng.uniform(0.5, 1.1) * bound[i] * nf
+    sc.pos = P
+    sc.lo, sc.hi = (0.0, 0.0, -1.0 / 128), (0.06, 0.06, 0.07)
+    if prec == scenes.PREC_FP32:
+        sc.tpl_pos = sc.tpl_pos.astype(np.float32).astype(np.float64)
+        sc.tpl_rad = sc.tpl_rad.astype(np.float32).astype(np.float64)
+        scenes.snap_to_voxel_grid(sc)
+    sc.bin_size = scenes.default_bin_size(sc, 1e-4)
+    return sc
+
+
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+def test_mesh_facets_match_oracle(dem, oracle_mod, prec):
+    """Sphere-facet candidate lists bit-exact; clump forces, per-facet loads
+    and moments within the tolerance; a mesh's load is its facets' sum."""
+    margin, K = 1e-4, 10
+    sc = _mesh_scene(prec)
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        F, T = sim.eval_forces()
+        Fl, Tl = sim.wall_loads()
+        a, b, u, ws, ww, uw = sim.contacts()
+    om, _, _, ao, bo, wso, wwo = _oracle_lists(oracle_mod, sc, margin, K)
+    assert np.array_equal(ws, wso) and np.array_equal(ww, wwo)
+    assert len(np.unique(ww)) >= 16  # nearly every facet is reached
+    Fo, To, Fwo, _, _, act, mag, Two = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, 0.0,
+                                                 ao, bo, np.zeros((len(ao), 3)), wso, wwo,
+                                                 np.zeros((len(wso), 3)), with_mag=True,
+                                                 wall_torque=True)
+    _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
+    scale = np.abs(Fwo).sum()
+    extent = 0.07
+    assert np.abs(Fl - Fwo).max() <= TOL[prec] * scale
+    assert np.abs(Tl - Two).max() <= TOL[prec] * extent * scale
+    assert np.abs(Fl[:16].sum(axis=0) - Fwo[:16].sum(axis=0)).max() <= TOL[prec] * scale
+    assert (np.abs(Fwo).max(axis=1) > 0).sum() >= 14
+
+
+def test_fp64_trajectory_in_a_box_mesh_matches_oracle(dem, oracle_mod):
+    """A packed bed settling in a box made of 12 facets: 45 steps with a
+    rebuild every 10 against the oracle, as the FP64 trajectory test does
+    for analytic walls."""
+    margin, K, nsteps = 2e-4, 10, 45
+    sc = _scene(7, 250, scenes.PREC_FP64, margin=margin)
+    planes = sc.walls
+    lo, hi = np.array(sc.lo), np.array(sc.hi)
+    x0 = max(w["p"][0] for w in planes if w["n"][0] > 0.5)
+    x1 = min(w["p"][0] for w in planes if w["n"][0] < -0.5)
+    y0 = max(w["p"][1] for w in planes if w["n"][1] > 0.5)
+    y1 = min(w["p"][1] for w in planes if w["n"][1] < -0.5)
+    z0 = max(w["p"][2] for w in planes if w["n"][2] > 0.5)
+    sc.walls = scenes.box_mesh(x0, x1, y0, y1, z0, hi[2] - 1e-3)
+    sim, osim = _run_both(dem, oracle_mod, sc, margin, K, nsteps, scenes.PREC_FP64)
+    pos, quat, vel, w = sim.state()
+    po, qo, vo, wo = osim.state()
+    assert np.abs(pos - po).max() <= 1e-14 * (1 + np.abs(po).max())
+    assert np.abs(vel - vo).max() <= 1e-10 * np.abs(vo).max()
+    assert np.abs(w - wo).max() <= 1e-9 * np.abs(wo).max()
+    a, b, u, ws, ww, uw = sim.contacts()
+    ao, bo, uo, wso, wwo, uwo = osim.contacts()
+    assert np.array_equal(ws, wso) and np.array_equal(ww, wwo) and len(ws) > 10
+    assert np.abs(uw - uwo).max() <= 1e-8 * max(np.abs(uwo).max(), 1e-30)
+    sim.close()
