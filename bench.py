@@ -293,6 +293,8 @@ def main():
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--boundary", default="analytic", choices=["analytic", "mesh"],
+                    help="the box and plate as analytic planes or as 12 mesh facets")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned-margin and batched forms")
     args = ap.parse_args()
@@ -336,6 +338,8 @@ def main():
     log = (lambda m: print(f"[bench r{rank}] {m}", file=sys.stderr, flush=True))
     t0 = time.time()
     sc = workloads.bed_c5(n_clumps=args.n_clumps, log=log)
+    if args.boundary == "mesh":
+        sc.walls = workloads.facet_box(sc.walls)
     log(f"bed ready in {time.time() - t0:.1f} s: {sc.n_clumps} clumps, {sc.n_spheres} spheres")
     stream = torch.cuda.Stream()
     margin = MARGIN_VBOUND * sc.h * K_REBUILD
@@ -454,7 +458,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "contacts_per_sec": contacts_ps,
-        "config": {"workload": workload_name(ncl, ns), "n_clumps": ncl, "n_spheres": ns,
+        "config": {"workload": workload_name(ncl, ns) + (
+                       " (box and plate as 12 mesh facets)" if args.boundary == "mesh" else ""),
+                   "boundary": args.boundary, "n_clumps": ncl, "n_spheres": ns,
                    "listed_pairs": n_pairs, "active_contacts": n_active,
                    "wall_contacts": st["n_wall_contacts"], "margin_m": margin,
                    "rebuild_interval": K_REBUILD, "dt": sc.h, "rebuilds": st["rebuilds"],

@@ -125,3 +125,20 @@ def compress(sim, plate_wall: dict, plate: int, speed: float, load: float, max_s
     p = p + speed * n * (sim.stats()["time"] - t0)
     sim.set_wall_motion(plate, p, np.zeros(3))
     return steps, push, p
+
+
+def facet_box(walls):
+    """The same axis-aligned box as mesh facets: the floor, the four sides and
+    the top plate of `walls` (planes) become 12 facets; the two top facets
+    keep the plate's sliding velocity."""
+    def plane_at(axis, sign):
+        return next(w for w in walls if w["type"] == scenes.WALL_PLANE and w["n"][axis] * sign > 0.5)
+
+    x0, x1 = plane_at(0, 1)["p"][0], plane_at(0, -1)["p"][0]
+    y0, y1 = plane_at(1, 1)["p"][1], plane_at(1, -1)["p"][1]
+    top = plane_at(2, -1)
+    facets = scenes.box_mesh(x0, x1, y0, y1, plane_at(2, 1)["p"][2], top["p"][2])
+    for f in facets:
+        if f["n"][2] < -0.5:
+            f["vel"] = tuple(top["vel"])
+    return facets
