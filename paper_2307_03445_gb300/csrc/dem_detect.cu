@@ -36,7 +36,10 @@ __device__ __forceinline__ void clump_com(const DevState& d, int c, const SceneG
 }
 
 // Float estimate of the same distance; |error| is far below wall_slack().
-__device__ float wall_distance_est(const WallDev& w, float t, const float x[3]) {
+// A facet's distance is at least its plane distance, so once that exceeds
+// `cut` (the caller's threshold + slack: the pair is no candidate either way)
+// it is returned without the region and edge work.
+__device__ float wall_distance_est(const WallDev& w, float t, const float x[3], float cut) {
   float dd[3], n[3];
   for (int k = 0; k < 3; ++k) {
     dd[k] = x[k] - (w.pf[k] + w.vf[k] * t);
@@ -45,6 +48,7 @@ __device__ float wall_distance_est(const WallDev& w, float t, const float x[3]) 
   const float ax = dd[0] * n[0] + dd[1] * n[1] + dd[2] * n[2];
   if (w.type == 0) return ax;
   if (w.type == 3) {
+    if (ax > cut) return ax;
     const float* e1 = w.e1h;
     const float* e2 = w.e2h;
     const float d00 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
@@ -225,8 +229,8 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
     const WallDev& w = d.walls[d.wall_idx[g.wall_start + i]];
     // float threshold (r + m) + |v| travel_time; its error is far below slack
     const float thrf = rmf + w.speed * ttf;
-    const float est = wall_distance_est(w, tf, xf);
     const float slack = wall_slack(w, xf);
+    const float est = wall_distance_est(w, tf, xf, thrf + slack);
     bool in;
     if (est > thrf + slack) {
       in = false;
