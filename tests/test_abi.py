@@ -60,3 +60,48 @@ def test_create_rejects_bad_parameters_before_touching_a_device(lib):
     assert b"dt" in L.dem_last_error(None)
     assert not ctx.value
     assert L.dem_create(None, C.byref(ctx)) == -1
+
+
+def _params_with_walls(capi, walls, keep):
+    import numpy as np
+
+    from paper_2307_03445_gb300 import walls_to_c
+
+    p = capi.DemParams()
+    p.dt = 1e-6
+    for k in range(3):
+        p.domain_lo[k], p.domain_hi[k] = -0.1, 0.1
+    p.rebuild_interval, p.v_bound, p.guard = 10, 0.5, 1
+    mats = [np.array([v]) for v in (1e8, 0.3, 0.5, 0.5)]
+    keep += mats
+    p.n_materials = 1
+    p.E, p.nu, p.mu, p.cor = (m.ctypes.data_as(C.POINTER(C.c_double)) for m in mats)
+    warr = walls_to_c(walls)
+    keep.append(warr)
+    p.n_walls = len(walls)
+    p.walls = C.cast(warr, C.POINTER(capi.DemWall))
+    return p
+
+
+def test_create_checks_mesh_facets(lib):
+    """A facet must be a real triangle whose normal is (b - p) x (c - p)
+    normalised; a valid one passes to the device lookup."""
+    from paper_2307_03445_gb300 import capi, scenes
+
+    capi._lib = None
+    L = capi.load()
+    good = scenes.triangle((0, 0, 0), (0.01, 0, 0), (0, 0.01, 0))
+    flipped = dict(good, n=(0.0, 0.0, -1.0))
+    flat = dict(good, c=(0.02, 0.0, 0.0))
+    for wall, msg in ((flat, b"degenerate triangle"), (flipped, b"triangle normal")):
+        keep = []
+        ctx = C.c_void_p()
+        assert L.dem_create(C.byref(_params_with_walls(capi, [wall], keep)), C.byref(ctx)) == -1
+        assert msg in L.dem_last_error(None) and not ctx.value
+    keep = []
+    ctx = C.c_void_p()
+    rc = L.dem_create(C.byref(_params_with_walls(capi, [good], keep)), C.byref(ctx))
+    if rc == 0:  # a device is present: the context was made
+        L.dem_destroy(ctx)
+    else:
+        assert b"no CUDA device" in L.dem_last_error(None)
