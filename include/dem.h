@@ -295,7 +295,9 @@ int dem_get_wall_forces(dem_ctx* ctx, double* force);
  * time of the last force evaluation (p + vel t), each contact force acting at
  * its contact point (3 * n_walls doubles each, host buffers).  The sum over
  * the clumps of X x F + T plus the sum over the walls of p(t) x F_w + T_w is
- * zero up to rounding. */
+ * zero up to rounding.  A mesh's load is the sum over its facets: the force
+ * sum F_w, and about a point P (a wheel's hub) the sum of
+ * T_w + (p_w(t) - P) x F_w, with p_w(t) the facet's first vertex at that time. */
 int dem_get_wall_loads(dem_ctx* ctx, double* force, double* torque);
 /* Motion: from the current time t on, wall `wall` (index in the walls given
  * at creation) moves as point + vel (t' - t), i.e. its stored reference
