@@ -128,3 +128,22 @@ def test_mesh_helpers_orient_every_facet_towards_the_grains():
     for f in fun:
         a, n = np.asarray(f["p"]), np.asarray(f["n"])
         assert n[0] * -a[0] + n[1] * -a[1] > 0  # towards the axis
+
+
+def test_facet_box_is_the_workload_box():
+    """The benchmark's box and sliding plate as facets: the same six planes
+    (every facet lies in one of them, normal equal), 2 facets each, and only
+    the top facets carry the plate's velocity."""
+    from paper_2307_03445_gb300 import workloads
+
+    planes = scenes.config5(n_clumps=1).walls
+    facets = workloads.facet_box(planes)
+    assert len(facets) == 12
+    for pl in planes:
+        n, p = np.asarray(pl["n"]), np.asarray(pl["p"])
+        mine = [f for f in facets if np.allclose(f["n"], n, atol=1e-15)]
+        assert len(mine) == 2
+        for f in mine:
+            for k in ("p", "b", "c"):
+                assert abs((np.asarray(f[k]) - p) @ n) < 1e-15
+            assert tuple(f["vel"]) == tuple(pl["vel"])
