@@ -316,3 +316,39 @@ def test_wall_moments_balance(oracle_mod):
     assert np.abs(L).max() < 1e-13 * scale * (np.abs(sc.pos).max() + np.abs(pw).max())
     # and the wall moments are not trivially zero
     assert np.abs(Tw).max() > 1e-6 * np.abs(Fw).max() * np.abs(sc.pos).max()
+
+
+def test_facet_moments_balance(oracle_mod):
+    """The same balance with the box as 12 mesh facets, each translating with
+    its own velocity (every vertex moves with it): clumps touching a face's
+    two facets, edges and corners included."""
+    sc = scenes.packed_scene(12, 64, walls=True, compress=0.9)
+    pl = sc.walls
+    x0 = max(w["p"][0] for w in pl if w["n"][0] > 0.5)
+    x1 = min(w["p"][0] for w in pl if w["n"][0] < -0.5)
+    y0 = max(w["p"][1] for w in pl if w["n"][1] > 0.5)
+    y1 = min(w["p"][1] for w in pl if w["n"][1] < -0.5)
+    z0 = max(w["p"][2] for w in pl if w["n"][2] > 0.5)
+    rng = np.random.default_rng(4)
+    t = 0.37
+    sc.walls = []
+    for f in scenes.box_mesh(x0, x1, y0, y1, z0, sc.hi[2]):
+        v = rng.normal(scale=0.05, size=3)
+        g = {k: tuple(np.asarray(f[k]) - t * v) for k in ("p", "b", "c")}
+        sc.walls.append(dict(f, vel=tuple(v), **g))
+    sc.bin_size = scenes.default_bin_size(sc, 1e-4)
+    om = oracle_mod.OracleModel(sc)
+    xs, owner, tsph = om.sphere_centres(sc.tpl, sc.pos, sc.quat)
+    qc, rho = om.detect_coords(xs, tsph, 1e-4)
+    a, b = om.pairs_binned(owner, qc, rho)
+    ws, ww = om.wall_candidates(xs, tsph, 1e-4, t, 0.0)
+    F, T, Fw, _, _, act, Tw = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, t, a, b,
+                                        np.zeros((len(a), 3)), ws, ww, np.zeros((len(ws), 3)),
+                                        wall_torque=True)
+    assert (np.abs(Fw).sum(axis=1) > 0).sum() >= 5 and act > 30
+    scale = np.abs(F).sum() + np.abs(Fw).sum()
+    assert np.abs(F.sum(axis=0) + Fw.sum(axis=0)).max() < 1e-13 * scale
+    pw = np.array([np.asarray(w["p"]) + t * np.asarray(w["vel"]) for w in sc.walls])
+    L = (np.cross(sc.pos, F) + T).sum(axis=0) + (np.cross(pw, Fw) + Tw).sum(axis=0)
+    assert np.abs(L).max() < 1e-13 * scale * (np.abs(sc.pos).max() + np.abs(pw).max())
+    assert np.abs(Tw).max() > 1e-6 * np.abs(Fw).max() * np.abs(sc.pos).max()
