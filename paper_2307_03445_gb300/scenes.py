@@ -427,8 +427,8 @@ def config4(seed=1238, n_scenes=64, lo=5_000, hi=100_000):
 def merge_batch(parts):
     """Scenes with their own templates and materials -> (first, rest) for one
     context: `first` carries the concatenated template and material tables,
-    and the clumps of every scene refer to them through shifted ids.  All
-    scenes must share dt, g and precision."""
+    and the clumps and walls of every scene refer to them through shifted
+    ids.  All scenes must share dt, g and precision."""
     first = parts[0]
     for p in parts[1:]:
         if p.h != first.h or tuple(p.g) != tuple(first.g) or p.precision != first.precision:
@@ -447,6 +447,8 @@ def merge_batch(parts):
         E.append(p.E); nu.append(p.nu); mu.append(p.mu); cor.append(p.cor)
         q = Scene(**{**p.__dict__})
         q.tpl = np.asarray(p.tpl, np.int32) + t_base
+        # a wall's material is an index into its own scene's table too
+        q.walls = [dict(w, material=int(w.get("material", 0)) + m_base) for w in p.walls]
         out.append(q)
         t_base += len(p.tpl_mass)
         s_base += int(p.tpl_off[-1])

@@ -59,3 +59,24 @@ def test_compressor_stops_at_the_step_budget():
                                         chunk=10)
     assert steps == 25 and push == 0.0
     assert np.allclose(p, [0.0, 0.0, 1.0 - 0.2 * 25 * 1e-5], atol=1e-15)
+
+
+def test_merge_batch_shifts_template_material_and_wall_ids():
+    """One context of several scenes: through the merged tables every clump
+    keeps its own templates (spheres, radii, masses) and every sphere and wall
+    its own material values."""
+    parts = [scenes.packed_scene(s, n) for s, n in ((31, 40), (32, 70), (33, 25))]
+    first, rest = scenes.merge_batch(parts)
+    for q, p in zip([first] + rest, parts):
+        for t_new, t_old in zip(q.tpl, p.tpl):
+            a, b = q.tpl_off[t_new], q.tpl_off[t_new + 1]
+            c, d = p.tpl_off[t_old], p.tpl_off[t_old + 1]
+            assert np.array_equal(q.tpl_pos[a:b], p.tpl_pos[c:d])
+            assert np.array_equal(q.tpl_rad[a:b], p.tpl_rad[c:d])
+            assert q.tpl_mass[t_new] == p.tpl_mass[t_old]
+            for name in ("E", "nu", "mu", "cor"):
+                assert np.array_equal(getattr(q, name)[q.tpl_mat[a:b]], getattr(p, name)[p.tpl_mat[c:d]])
+        assert len(q.walls) == len(p.walls) > 0
+        for wq, wp in zip(q.walls, p.walls):
+            for name in ("E", "nu", "mu", "cor"):
+                assert getattr(q, name)[wq["material"]] == getattr(p, name)[wp.get("material", 0)]
