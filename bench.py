@@ -37,6 +37,63 @@ K_REBUILD = 20        # steps between list rebuilds
 N_CLUMPS_FULL = 11_000_000  # the paper-scale bed
 
 
+# ---------------------------------------------------------------------------
+# roofline bytes
+# ---------------------------------------------------------------------------
+# The method's algorithmic bytes per force step (FP32 voxel mode), the minimum
+# any implementation moves: per listed contact its pair ids (8 B) and FP64
+# tangential history read + write (48 B); per sphere its owner and component
+# id (8 B); per clump the pose and velocity read for the forces (64 B) and
+# the force/torque accumulation (24 B), and for the integration the force and
+# torque read (24 B), FP64 velocity and angular velocity read + write (96 B),
+# position read + write (48 B), orientation read + write (32 B) and FP32
+# mirrors written (40 B).  The update kernel is charged the integration part
+# (240 B per clump) and the sphere ids; the pair kernel the contacts, the
+# sphere ids and the force part (88 B per clump).
+def ALGO_UPDATE(ncl, ns):
+    return 240 * ncl + 8 * ns
+
+
+def ALGO_PAIRS(ncl, ns, n_pairs):
+    return 56 * n_pairs + 8 * ns + 88 * ncl
+
+
+# This implementation's own bytes per launch.  Update: per clump 204 B read
+# (force and torque 32, template and scene 8, voxel 16, offset 16,
+# orientation 32, velocity record 48, certificate reference 48, first-sphere
+# index 4) and 176 B written (voxel, offset, orientation, velocity record,
+# FP32 mirrors 32, cleared accumulators 32); per sphere its 16-byte pose
+# record written.  Pair forces: per listed pair its ids (8 B); per active
+# contact the FP64 history read + write (48 B); per sphere its {owner,
+# template sphere} (8 B) and pose record (16 B) read once; per clump voxel
+# and offset (32 B), velocity mirrors (32 B) and accumulators read + written
+# (64 B).
+def IMPL_UPDATE(ncl, ns):
+    return 380 * ncl + 16 * ns
+
+
+def IMPL_PAIRS(ncl, ns, n_pairs, n_active):
+    return 8 * n_pairs + 48 * n_active + 24 * ns + 128 * ncl
+
+
+# DRAM read + write bytes per launch of the current kernels, from one ncu
+# capture on the 11M-clump bed (the profile named beside each); None until
+# the current kernels have been captured.
+TRAFFIC = {"k_update32": None, "k_pairs32": None}
+TRAFFIC_SRC = {"k_update32": None, "k_pairs32": None}
+
+
+def roof(kernel, ms, algo, impl, peak, peak_src, full_bed):
+    achieved = algo / (ms / 1000.0) / 1e9
+    tr = TRAFFIC[kernel] if full_bed else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": tr,
+            "traffic_source": TRAFFIC_SRC[kernel] if tr is not None else None,
+            "kernel": kernel, "kernel_ms": ms, "algorithmic_bytes": algo,
+            "impl_bytes": impl, "impl_frac": impl / (ms / 1000.0) / 1e9 / peak,
+            "peak_source": peak_src}
+
+
 def workload_name(n_clumps, n_spheres):
     sph = f"{n_spheres:,}" if n_spheres else "~34,000,000"
     return (f"paper-scale bed: {n_clumps:,} clumps / {sph} spheres, 30 templates of 1-6 "
@@ -161,6 +218,39 @@ def time_oracle(budget_s=15.0, n_clumps=1500, max_steps=None):
                        f"{int(np.mean(pairs))} listed pairs at window ends; "
                        "single-threaded FP64 C"),
             "seconds": busy, "steps": steps, "ms_per_step": 1000.0 * busy / max(1, steps)}
+
+
+def _oracle_worker(args):
+    """One process of the all-cores oracle timing (spawned, so it shares no
+    state with a CUDA context of the parent)."""
+    budget_s, n_clumps, max_steps, warm = args
+    if warm:
+        time_oracle(1e9, n_clumps=n_clumps, max_steps=warm)
+    return time_oracle(budget_s, n_clumps=n_clumps, max_steps=max_steps)
+
+
+def time_oracle_all_cores(budget_s=15.0, n_clumps=1500, max_steps=None, warm=0, procs=None):
+    """The oracle on every host core: one independent copy of the sample per
+    process (the oracle is single-threaded), all running at once.  The rate
+    is the sum of the processes' own rates (sphere-steps over each one's
+    stepping time); the wall time of the pool is reported beside it."""
+    import multiprocessing as mp
+
+    n = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(n) as pool:
+        res = pool.map(_oracle_worker, [(budget_s, n_clumps, max_steps, warm)] * n)
+    wall = time.perf_counter() - t0
+    value = float(sum(r["value"] for r in res))
+    steps = res[0]["steps"]
+    return {"value": value, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": res[0]["sample"].replace("single-threaded FP64 C",
+                                               f"FP64 C, {n} independent single-threaded "
+                                               f"copies at once (one per host core)"),
+            "seconds": max(r["seconds"] for r in res), "pool_wall_s": wall, "steps": steps,
+            "ms_per_step": max(r["ms_per_step"] for r in res),
+            "per_process": [r["value"] for r in res]}
 
 
 # ---------------------------------------------------------------------------
@@ -308,9 +398,9 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # each step: one oracle step over a 20,000-clump sample of the workload
-        time_oracle(1e9, n_clumps=20000, max_steps=args.warmup)
-        cb = time_oracle(1e9, n_clumps=20000, max_steps=args.steps)
+        # each step: one oracle step over a 20,000-clump sample of the
+        # workload, in one independent copy per host core
+        cb = time_oracle_all_cores(1e9, n_clumps=20000, max_steps=args.steps, warm=args.warmup)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": cb["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -375,42 +465,27 @@ def main():
     value = whole_job_rate(world, ns, args.steps, ms)
     contacts_ps = whole_job_rate(world, st["pair_steps"], 1, ms)
 
-    # rooflines of the two step kernels; the update kernel takes the largest
-    # share of the step (the launch list in profiles/), so it is `roofline`
+    # rooflines of the two step kernels against the measured copy bandwidth
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak_src = "measured (burst copy)" if "hbm_gbs" in peaks else "fallback"
     n_pairs, n_active = st["n_pairs"], st["active_last"]
     pair_ms = st["ms_pairs"] / max(1, st["timed_steps"])
     upd_ms = st["ms_update"] / max(1, st["timed_steps"])
-    # DRAM read + write bytes per launch from one ncu capture of this command
-    # on the 11M-clump bed (profiles/dram_traffic_paper_bed_34M_spheres.md);
-    # they hold for that bed only
-    traffic = {"k_update32": 2.481e9 + 3.537e9, "k_pairs32": 3.821e9 + 1.188e9}
-    full_bed = ncl == N_CLUMPS_FULL
-
-    def roof(kernel, algo, ms):
-        achieved = algo / (ms / 1000.0) / 1e9
-        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic[kernel] if full_bed else None,
-                "kernel": kernel, "kernel_ms": ms, "algorithmic_bytes": algo,
-                "peak_source": peak_src}
-
-    # update kernel, algorithmic bytes per launch: per clump 200 B read (force
-    # and torque 32, template/scene 8, voxel + offset 32, orientation 32,
-    # velocity and angular velocity 48, certificate reference 48) and 176 B
-    # written (state 112, velocity mirrors 32, cleared accumulators 32); per
-    # sphere its {owner, template sphere} 8 B read and pose records 48 B written
-    roofline = roof("k_update32", 376 * ncl + 56 * ns, upd_ms)
-    # pair force kernel: ids of every listed pair (8 B), history read + write
-    # of each active contact (48 B), one read of every sphere's pose records
-    # (48 B), clump velocity mirrors (32 B) and accumulators (32 B read + 32 B
-    # write)
-    roofline_pairs = roof("k_pairs32", 8 * n_pairs + 48 * n_active + 48 * ns + 96 * ncl, pair_ms)
+    rooflines = {
+        "k_update32": roof("k_update32", upd_ms, algo=ALGO_UPDATE(ncl, ns),
+                           impl=IMPL_UPDATE(ncl, ns), peak=peak, peak_src=peak_src,
+                           full_bed=ncl == N_CLUMPS_FULL),
+        "k_pairs32": roof("k_pairs32", pair_ms, algo=ALGO_PAIRS(ncl, ns, n_pairs),
+                          impl=IMPL_PAIRS(ncl, ns, n_pairs, n_active), peak=peak,
+                          peak_src=peak_src, full_bed=ncl == N_CLUMPS_FULL),
+    }
+    # `roofline` is the kernel with the larger share of the step
+    roofline = max(rooflines.values(), key=lambda r: r["kernel_ms"])
 
     e2e = None
     if not args.no_e2e:
@@ -451,8 +526,11 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline:
-        cb = time_oracle(args.oracle_seconds)
+        # all host cores (one oracle copy per core), and one core alone
+        cb = time_oracle_all_cores(args.oracle_seconds)
+        one = time_oracle(args.oracle_seconds)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["single_core"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -473,7 +551,7 @@ def main():
                                 "rebuild_total": st["ms_detect"]}},
         "forms": forms,
         "roofline": roofline,
-        "roofline_pairs": roofline_pairs,
+        "rooflines": rooflines,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": st["launches"],

@@ -66,7 +66,7 @@ struct dem_ctx {
   Buf b_tpl_off, b_tp64, b_tp32, b_tmat, b_tmass, b_tinert, b_tpbound, b_tmassf, b_tinertf;
   Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cvw, b_mv64, b_mw64, b_mv32, b_mw32;
   Buf b_acc64, b_acc32, b_ref_pos, b_ref_vox, b_ref_off, b_ref_q;
-  Buf b_sinfo, b_sa64, b_sb64, b_sa32, b_sb32;
+  Buf b_sinfo, b_sa64, b_sb64, b_srec32;
   Buf b_grids, b_lgrids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_wtorque, b_pm64, b_pm32;
   Buf b_flags, b_counters, b_totals, b_dstep;
   // detection scratch
@@ -250,8 +250,7 @@ void refresh_devstate(dem_ctx* c) {
   d.sinfo = ptr<int2>(c->b_sinfo);
   d.sa64 = ptr<SphA64>(c->b_sa64);
   d.sb64 = ptr<double4_32a>(c->b_sb64);
-  d.sa32 = ptr<SphA32>(c->b_sa32);
-  d.sb32 = ptr<float4>(c->b_sb32);
+  d.srec32 = ptr<uint4>(c->b_srec32);
   d.grids = ptr<SceneGrid>(c->b_grids);
   d.walls = ptr<WallDev>(c->b_walls);
   d.wall_idx = ptr<int>(c->b_wall_idx);
@@ -1178,8 +1177,8 @@ void dem_destroy(dem_ctx* c) {
   Buf* all[] = {&c->b_tpl_off, &c->b_tp64, &c->b_tp32, &c->b_tmat, &c->b_tmass, &c->b_tinert, &c->b_tpbound,
                 &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cvw,
                 &c->b_tmassf, &c->b_tinertf, &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
-                &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_sa32,
-                &c->b_sb32, &c->b_grids, &c->b_lgrids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
+                &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_srec32,
+                &c->b_grids, &c->b_lgrids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
                 &c->b_wpos, &c->b_wforce, &c->b_wtorque, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
                 &c->b_totals, &c->b_det, &c->b_bin_size, &c->b_wall_mask, &c->b_wall_cnt,
                 &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
@@ -1222,6 +1221,13 @@ int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double
   for (int s = 0; s < S; ++s) {
     if (!(radius[s] > 0) || !std::isfinite(radius[s])) return fail(c, DEM_ERR_INVALID_ARG, "radius must be > 0");
     if (material[s] < 0 || material[s] >= c->P.n_materials) return fail(c, DEM_ERR_INVALID_ARG, "material out of range");
+    // FP32_VOXEL keeps a sphere's centre relative to its clump's voxel corner
+    // in 40-bit fixed point (2^-44 m): |p| + voxel must stay below 2^-5 m
+    const double* p = local_pos + 3 * s;
+    if (c->P.precision != DEM_FP64 &&
+        !(std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) < 0.03125 - 2.0 * kVoxel))
+      return fail(c, DEM_ERR_INVALID_ARG,
+                  "FP32_VOXEL: a template sphere centre lies 31 mm or more from the clump's centre of mass");
   }
   c->n_tpl = n_tpl;
   c->tpl_off.assign(off, off + n_tpl + 1);
@@ -1306,7 +1312,7 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
     ok = ok && grow(c, c->b_cvox, 16 * ncl, 16 * k0) && grow(c, c->b_coff, 16 * ncl, 16 * k0) &&
          grow(c, c->b_mv32, 16 * ncl) && grow(c, c->b_mw32, 16 * ncl) && grow(c, c->b_acc32, 32 * ncl) &&
          grow(c, c->b_ref_vox, 16 * ncl) && grow(c, c->b_ref_off, 16 * ncl) &&
-         grow(c, c->b_sa32, sizeof(SphA32) * ns) && grow(c, c->b_sb32, 16 * ns);
+         grow(c, c->b_srec32, 16 * ns);
   }
   if (!ok) return fail(c, DEM_ERR_OOM, "clump buffers");
   std::vector<int2> ci(n), si(add_s);
@@ -1465,6 +1471,13 @@ int dem_reset_stats(dem_ctx* c) {
 int dem_set_timing(dem_ctx* c, int timing) {
   if (!c) return DEM_ERR_INVALID_ARG;
   c->timing = timing ? 1 : 0;
+  if (c->timing) {
+    // the per-step event pool is created here, not inside a timed dem_step
+    // (creating thousands of events there leaves the device idle meanwhile)
+    cudaSetDevice(c->P.device);
+    StepRunner R(c, 0);
+    return R.init();
+  }
   return DEM_OK;
 }
 

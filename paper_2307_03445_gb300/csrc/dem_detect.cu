@@ -103,8 +103,8 @@ __device__ __forceinline__ bool lattice_from_pose(const DevState& d, long long s
                                                   long long qc[3], float xf[3]) {
   bool exact = true;
   if (d.prec == 1) {
-    const SphA32 A = d.sa32[s];
-    const long long P[3] = {A.x, A.y, A.z};
+    long long P[3];
+    sphere_fix(d, s, d.sinfo[s].x, P);
     for (int k = 0; k < 3; ++k) {
       const long long half = 1ll << (kFixBits - kDetBits - 1);
       const long long rem = P[k] & ((1ll << (kFixBits - kDetBits)) - 1);

@@ -47,8 +47,7 @@ struct DevState {
   const int2* sinfo;        // {owner, template sphere}
   SphA64* sa64;
   double4_32a* sb64;            // {rel = R p, bits(owner | mat << 32)}
-  SphA32* sa32;
-  float4* sb32;             // {rel = R p, int bits(mat)}
+  uint4* srec32;            // FP32_VOXEL pose record (pack_rel: centre from the voxel corner)
   // scenes, walls, materials
   const SceneGrid* grids;
   const WallDev* walls;
@@ -81,6 +80,17 @@ struct DevState {
   int pairs_bpsm;           // blocks of 256 threads per SM for the pair force kernels
   int upd_block;            // clumps per block of the FP32_VOXEL update kernel: 64, 128, 256
 };
+
+// Fixed-point centre (2^-44 m from the scene corner) of sphere s, owned by
+// clump c (FP32_VOXEL): the clump's voxel corner plus the pose record.
+__device__ __forceinline__ void sphere_fix(const DevState& d, long long s, int c, long long P[3]) {
+  const int4 v = d.cvox[c];
+  long long x, y, z;
+  unpack_rel(d.srec32[s], x, y, z);
+  P[0] = ((long long)v.x << (kFixBits - kVoxLog2)) + x;
+  P[1] = ((long long)v.y << (kFixBits - kVoxLog2)) + y;
+  P[2] = ((long long)v.z << (kFixBits - kVoxLog2)) + z;
+}
 
 // True when the kernels of the step that starts from state *d.dstep must not
 // run (its state failed the certificate).  Uniform across a launch: halt_at is

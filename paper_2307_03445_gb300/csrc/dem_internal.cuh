@@ -89,13 +89,31 @@ struct WallDev {
   float e2h[3], e2l[3];
 };
 
-// Sphere pose record used by the contact kernels (written every step).
-struct alignas(32) SphA32 {  // FP32_VOXEL
-  long long x, y, z;          // centre, fixed point 2^-44 m, relative to the scene corner
-  float r;                    // radius
-  int owner;                  // clump id
-};
-struct alignas(32) SphA64 {  // FP64
+// Sphere pose record of FP32_VOXEL (written every step by the update kernel,
+// 16 bytes): the sphere centre relative to its clump's voxel corner,
+// x_rel = off + R(q) p, in fixed point (2^-44 m), as three signed 40-bit
+// fields packed into a uint4 (x in bits 0-39, y in 40-79, z in 80-119; the
+// top 8 bits are zero).  The centre relative to the scene corner is
+// (voxel << 24) + x_rel.  40 bits hold |x_rel| < 2^39 units = 2^-5 m, so
+// template sphere centres must lie within 2^-5 m - 2^-20 m of the clump's
+// centre of mass (checked when the templates are loaded).  The radius,
+// material and owner come from the static per-sphere and template tables.
+constexpr long long kRelLimit = 1ll << 39;
+__device__ __forceinline__ uint4 pack_rel(long long x, long long y, long long z) {
+  const unsigned long long m = (1ull << 40) - 1ull;
+  const unsigned long long ux = (unsigned long long)x & m, uy = (unsigned long long)y & m,
+                           uz = (unsigned long long)z & m;
+  const unsigned long long lo = ux | (uy << 40), hi = (uy >> 24) | (uz << 16);
+  return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+}
+__device__ __forceinline__ void unpack_rel(uint4 r, long long& x, long long& y, long long& z) {
+  const unsigned long long lo = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+  const unsigned long long hi = (unsigned long long)r.z | ((unsigned long long)r.w << 32);
+  x = (long long)(lo << 24) >> 24;
+  y = (long long)(((lo >> 40) | (hi << 24)) << 24) >> 24;
+  z = (long long)(hi << 8) >> 24;
+}
+struct alignas(32) SphA64 {  // FP64 pose record: centre and radius
   double x, y, z, r;
 };
 
@@ -290,7 +308,11 @@ __device__ __forceinline__ ff ff_from_double(double d) {
   return {h, (b >> 63) ? -l : l};
 }
 __device__ __forceinline__ float ff_to_float(ff a) { return __fadd_rn(a.h, a.l); }
-// sqrt of a non-negative float-float to float-float accuracy (one Newton step)
+// sqrt of a non-negative float-float to float-float accuracy: Dekker's
+// double-length square root (T. J. Dekker, "A floating-point technique for
+// extending the available precision", Numer. Math. 18, 1971, procedure
+// sqrt2): s = sqrt(a.h), then one Newton correction (a - s^2) / (2 s) with
+// s^2 formed exactly by TwoProduct, added to s by FastTwoSum.
 __device__ __forceinline__ ff ff_sqrt(ff a) {
   if (!(a.h > 0.f)) return {0.f, 0.f};
   float s = sqrtf(a.h);

@@ -190,18 +190,44 @@ int sms() {
 
 }  // namespace
 
-void mlp_forward_dev(const __nv_bfloat16* w, const float* x, long long n, float* y, cudaStream_t st) {
-  if (n <= 0) return;
-  static bool attr = false;
-  const size_t smem = sizeof(float) * kMlpParams;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
+namespace {
+
+// The dynamic shared-memory limit of a kernel is a per-device setting: it is
+// raised once on every device the library launches the kernel on (a flag per
+// device and kernel, set only when the call succeeded).
+constexpr int kAttrMaxDevices = 64;
+std::mutex g_attr_mu;
+
+template <typename K>
+bool smem_attr_once(K kernel, int slot, size_t smem) {
+  static bool done[2][kAttrMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAttrMaxDevices) {
+    cudaGetLastError();
+    return false;
   }
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (done[slot][dev]) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  done[slot][dev] = true;
+  return true;
+}
+
+}  // namespace
+
+int mlp_forward_dev(const __nv_bfloat16* w, const float* x, long long n, float* y, cudaStream_t st) {
+  if (n <= 0) return DEM_OK;
+  const size_t smem = sizeof(float) * kMlpParams;
+  if (!smem_attr_once(k_mlp_forward, 0, smem)) return DEM_ERR_CUDA;
   const long long want = (n + 127) / 128;
   const long long cap = (long long)sms() * 4;
   k_mlp_forward<<<(unsigned)(want < cap ? want : cap), 128, smem, st>>>(w, x, n, y);
   count_launch();
+  return DEM_OK;
 }
 
 }  // namespace dem
@@ -250,12 +276,8 @@ void* stage(size_t bytes, cudaStream_t st) {
 int grad_pass(dem_mlp* M, long long n, const float* dx, const float* dt, double* loss_out) {
   cudaMemsetAsync(M->g, 0, sizeof(float) * kMlpParams, M->st);
   cudaMemsetAsync(M->loss, 0, sizeof(double), M->st);
-  static bool attr = false;
   const size_t smem = 2 * sizeof(float) * kMlpParams;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  if (!smem_attr_once(k_mlp_grad, 1, smem)) return mlp_fail(M, DEM_ERR_CUDA, "gradient kernel attribute");
   const long long want = (n + 63) / 64;
   const long long cap = (long long)sms() * 2;
   k_mlp_grad<<<(unsigned)(want < cap ? want : cap), 64, smem, M->st>>>(M->wq, dx, dt, n,
@@ -263,8 +285,11 @@ int grad_pass(dem_mlp* M, long long n, const float* dx, const float* dt, double*
   count_launch();
   if (loss_out) {
     double h = 0;
-    cudaMemcpyAsync(&h, M->loss, sizeof(double), cudaMemcpyDeviceToHost, M->st);
-    cudaStreamSynchronize(M->st);
+    if (cudaMemcpyAsync(&h, M->loss, sizeof(double), cudaMemcpyDeviceToHost, M->st) != cudaSuccess ||
+        cudaStreamSynchronize(M->st) != cudaSuccess) {
+      cudaGetLastError();
+      return mlp_fail(M, DEM_ERR_CUDA, "gradient pass");
+    }
     *loss_out = h / (double)n;
   }
   return cudaGetLastError() == cudaSuccess ? DEM_OK : DEM_ERR_CUDA;
@@ -357,7 +382,8 @@ int dem_mlp_forward(dem_mlp* M, long long n, const float* x, float* y) {
   float* dx = (float*)buf;
   float* dy = dx + (size_t)n * kIn;
   cudaMemcpyAsync(dx, x, sizeof(float) * (size_t)n * kIn, cudaMemcpyHostToDevice, M->st);
-  mlp_forward_dev(M->wq, dx, n, dy, M->st);
+  if (mlp_forward_dev(M->wq, dx, n, dy, M->st) != DEM_OK)
+    return mlp_fail(M, DEM_ERR_CUDA, "forward kernel attribute");
   cudaMemcpyAsync(y, dy, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, M->st);
   cudaStreamSynchronize(M->st);
   return cudaGetLastError() == cudaSuccess ? DEM_OK : DEM_ERR_CUDA;
@@ -490,7 +516,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mu;
 void* g_na_addr[kNaMaxDevices] = {};
-bool g_na_attr[kNaMaxDevices] = {};
 
 int noalloc_scratch(dem_mlp* M, unsigned char** out) {
   if (M->device < 0 || M->device >= kNaMaxDevices)
@@ -505,15 +530,8 @@ int noalloc_scratch(dem_mlp* M, unsigned char** out) {
     }
     g_na_addr[M->device] = p;
   }
-  if (!g_na_attr[M->device]) {
-    const size_t smem = 2 * sizeof(float) * kMlpParams;
-    if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return mlp_fail(M, DEM_ERR_CUDA, "gradient kernel attribute");
-    }
-    g_na_attr[M->device] = true;
-  }
+  if (!smem_attr_once(k_mlp_grad, 1, 2 * sizeof(float) * kMlpParams))
+    return mlp_fail(M, DEM_ERR_CUDA, "gradient kernel attribute");
   *out = (unsigned char*)g_na_addr[M->device];
   return DEM_OK;
 }
@@ -538,19 +556,28 @@ extern "C" int dem_mlp_loss_grad_noalloc(dem_mlp* M, long long n, const float* x
   float* d_t = (float*)(s + kNaTOff);
   // the two accumulators start at zero on every call; rows and targets are
   // overwritten up to n
-  cudaMemsetAsync(s, 0, kNaXOff, M->st);
-  cudaMemcpyAsync(d_x, x, sizeof(float) * (size_t)n * kIn, cudaMemcpyHostToDevice, M->st);
-  cudaMemcpyAsync(d_t, t, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, M->st);
+  if (cudaMemsetAsync(s, 0, kNaXOff, M->st) != cudaSuccess ||
+      cudaMemcpyAsync(d_x, x, sizeof(float) * (size_t)n * kIn, cudaMemcpyHostToDevice, M->st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(d_t, t, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, M->st) != cudaSuccess) {
+    cudaGetLastError();
+    return mlp_fail(M, DEM_ERR_CUDA, "staging the rows into the fixed scratch");
+  }
   const long long want = (n + 63) / 64;
   const long long cap = (long long)sms() * 2;
   k_mlp_grad<<<(unsigned)(want < cap ? want : cap), 64, 2 * sizeof(float) * kMlpParams, M->st>>>(
       M->wq, d_x, d_t, n, 1.f / (float)n, d_grad, d_loss);
   count_launch();
   double h = 0.0;
-  cudaMemcpyAsync(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost, M->st);
-  if (grad) cudaMemcpyAsync(grad, d_grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, M->st);
-  cudaStreamSynchronize(M->st);
-  if (cudaGetLastError() != cudaSuccess) return DEM_ERR_CUDA;
+  cudaError_t e = cudaMemcpyAsync(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost, M->st);
+  if (e == cudaSuccess && grad)
+    e = cudaMemcpyAsync(grad, d_grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, M->st);
+  // the host buffers must outlive their copies: wait even when one failed to enqueue
+  const cudaError_t es = cudaStreamSynchronize(M->st);
+  if (e != cudaSuccess || es != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return mlp_fail(M, DEM_ERR_CUDA, "gradient pass on the fixed scratch");
+  }
   if (loss) *loss = h / (double)n;
   return DEM_OK;
 }

@@ -13,7 +13,7 @@ constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + 2 * (kMlpHidden * 
                            kMlpHidden + 1;
 
 // y[k] = f(x[k * kMlpIn .. +kMlpIn]) for k < n (device pointers, BF16 weights).
-void mlp_forward_dev(const __nv_bfloat16* w, const float* x, long long n, float* y, cudaStream_t st);
+int mlp_forward_dev(const __nv_bfloat16* w, const float* x, long long n, float* y, cudaStream_t st);
 // The same on the tensor cores (tcgen05): every layer's input rounded to
 // bfloat16, FP32 accumulation.  A bounded wait that runs out ors
 // kFlagTimeout into *err (device, may be NULL).

@@ -11,7 +11,8 @@
 // Operand tiles are K-major with the 128-byte swizzle: a row of 64 bfloat16
 // values is 128 bytes, and its 16-byte chunk c is stored at chunk c ^ (row & 7).
 // Waits on the MMA-completion barrier are bounded; a wait that runs out sets
-// an error flag and the block stops.
+// an error flag and the block stops issuing work; it frees its tensor memory
+// only after a second bounded wait has seen the outstanding MMAs complete.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -73,9 +74,9 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
 }
 
-// Bounded wait for the barrier's phase with the given parity.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 20); ++i) {
+// Bounded wait (`tries` polls) for the barrier's phase with the given parity.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int tries = 1 << 20) {
+  for (int i = 0; i < tries; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -168,7 +169,10 @@ __global__ void __launch_bounds__(kRows) k_mlp_forward_tc(const __nv_bfloat16* _
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
             : "memory");
       }
-      ok = bar_wait(bar, parity) && ok;
+      // every thread waits; the block goes on only if all of them saw the
+      // phase complete, so that nothing is issued after a wait ran out
+      ok = __syncthreads_and(bar_wait(bar, parity) ? 1 : 0) != 0;
+      if (!ok) break;
       parity ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       uint32_t c[4][16];
@@ -195,12 +199,20 @@ __global__ void __launch_bounds__(kRows) k_mlp_forward_tc(const __nv_bfloat16* _
         if (r < n) y[r] = s;
       }
     }
-    if (!__syncthreads_and(ok ? 1 : 0)) break;  // a wait ran out: stop this block
+    if (!ok) break;  // a wait ran out: stop this block
   }
-  if (!ok && err) atomicOr(err, kFlagTimeout);
+  bool drained = true;
+  if (!ok) {
+    if (t == 0 && err) atomicOr(err, kFlagTimeout);
+    // the MMAs of the phase that did not complete may still write the
+    // accumulator: wait for that phase once more, 16 times longer, and give
+    // the tensor memory back only if it completed (freeing columns that an
+    // MMA still writes would hand them to the next block on this SM)
+    drained = __syncthreads_and(bar_wait(bar, parity, 1 << 24) ? 1 : 0) != 0;
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  if (warp == 0 && drained)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 

@@ -78,13 +78,50 @@ __device__ __forceinline__ void add_clump32(float* acc, int c, V3<float> F, V3<f
 // ---------------------------------------------------------------------------
 // sphere-sphere contacts
 // ---------------------------------------------------------------------------
+// One side of an FP32_VOXEL contact: the sphere's fixed-point centre, radius,
+// material, owner and the owner's voxel offset.
+struct Side32 {
+  long long P[3];
+  float r;
+  int owner, tsph;
+  float4 off;
+  long long rel[3];  // centre from the owner's voxel corner (the pose record)
+};
+
+// Loads of one side, in two dependent rounds: the static {owner, template
+// sphere} pair and the pose record, then the owner's voxel and offset and the
+// template sphere's radius.
+__device__ __forceinline__ Side32 load_side32(const DevState& d, uint32_t s) {
+  Side32 S;
+  const int2 si = d.sinfo[s];
+  const uint4 rec = d.srec32[s];
+  S.owner = si.x;
+  S.tsph = si.y;
+  const int4 v = d.cvox[si.x];
+  S.off = d.coff[si.x];
+  S.r = d.tp32[si.y].w;
+  unpack_rel(rec, S.rel[0], S.rel[1], S.rel[2]);
+  S.P[0] = ((long long)v.x << (kFixBits - kVoxLog2)) + S.rel[0];
+  S.P[1] = ((long long)v.y << (kFixBits - kVoxLog2)) + S.rel[1];
+  S.P[2] = ((long long)v.z << (kFixBits - kVoxLog2)) + S.rel[2];
+  return S;
+}
+
+// Lever arm R p of a side (float): its centre from the voxel corner minus the
+// clump's offset in the voxel.
+__device__ __forceinline__ V3<float> arm32(const Side32& S) {
+  return {fix_to_float(S.rel[0]) - S.off.x, fix_to_float(S.rel[1]) - S.off.y,
+          fix_to_float(S.rel[2]) - S.off.z};
+}
+
 __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int count_active) {
   if (halted(d)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long ln = l.dn[0];
   // software pipeline: the ids of the next pair are loaded one iteration
-  // ahead, and its two pose records are prefetched into L2 once those ids
-  // have arrived, so the dependent loads of an iteration start from L2
+  // ahead, and its two pose records and {owner, template sphere} pairs are
+  // prefetched into L2 once those ids have arrived, so the dependent loads
+  // of an iteration start from L2
   long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int a_n = 0;
   uint32_t bw_n = 0;
@@ -94,9 +131,9 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     const uint32_t bw = bw_n;
     const uint32_t b = bw & ~kHistFlag;
     if (i + stride < ln) { a_n = l.pa[i + stride]; bw_n = l.pb[i + stride]; }
-    const SphA32 A = d.sa32[a];
-    const SphA32 B = d.sa32[b];
-    const long long dxl = B.x - A.x, dyl = B.y - A.y, dzl = B.z - A.z;
+    const Side32 A = load_side32(d, (uint32_t)a);
+    const Side32 B = load_side32(d, b);
+    const long long dxl = B.P[0] - A.P[0], dyl = B.P[1] - A.P[1], dzl = B.P[2] - A.P[2];
     // cheap rejection of clear false positives
     const float fx = fix_to_float(dxl), fy = fix_to_float(dyl), fz = fix_to_float(dzl);
     const float s_est = fx * fx + fy * fy + fz * fz;
@@ -115,8 +152,10 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     const bool active = dn > 0.f;
     if (count_active) warp_count(active, d.counters);
     if (i + stride < ln) {
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.sa32 + a_n));
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.sa32 + (bw_n & ~kHistFlag)));
+      const uint32_t bn = bw_n & ~kHistFlag;
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.srec32 + a_n));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.srec32 + bn));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.sinfo + bn));
     }
     if (!active) {
       if (bw & kHistFlag) l.pb[i] = b;  // history reset (false positive)
@@ -127,21 +166,21 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
       continue;
     }
     const V3<float> n = {fx / dist, fy / dist, fz / dist};
-    const float4 RA = d.sb32[a], RB = d.sb32[b];
     const float4 va = d.mv32[A.owner], wa = d.mw32[A.owner];
     const float4 vb = d.mv32[B.owner], wb = d.mw32[B.owner];
-    const float sa = A.r - 0.5f * dn, sb = B.r - 0.5f * dn;
-    const V3<float> ca = V3<float>{RA.x, RA.y, RA.z} + sa * n;
-    const V3<float> cb = V3<float>{RB.x, RB.y, RB.z} - sb * n;
-    const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
-    const V3<float> vB = V3<float>{vb.x, vb.y, vb.z} + cross(V3<float>{wb.x, wb.y, wb.z}, cb);
+    const int ma = d.tmat[A.tsph], mb = d.tmat[B.tsph];
     double u0 = 0.0, u1 = 0.0, u2 = 0.0;
     if (bw & kHistFlag) {
       u0 = l.u[i];
       u1 = l.u[l.cap + i];
       u2 = l.u[2 * l.cap + i];
     }
-    const PairMat<float> pm = d.pm32[__float_as_int(RA.w) * d.nmat + __float_as_int(RB.w)];
+    const float sa = A.r - 0.5f * dn, sb = B.r - 0.5f * dn;
+    const V3<float> ca = arm32(A) + sa * n;
+    const V3<float> cb = arm32(B) - sb * n;
+    const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
+    const V3<float> vB = V3<float>{vb.x, vb.y, vb.z} + cross(V3<float>{wb.x, wb.y, wb.z}, cb);
+    const PairMat<float> pm = d.pm32[ma * d.nmat + mb];
     const float Rbar = A.r * B.r / (A.r + B.r);
     const float mbar = va.w * vb.w / (va.w + vb.w);
     const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vB - vA,
@@ -256,10 +295,10 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     const int s = l.ws[i];
     const uint32_t wwv = l.ww[i];
     const uint32_t w = wwv & ~kHistFlag;
-    const SphA32 S = d.sa32[s];
+    const Side32 S = load_side32(d, (uint32_t)s);
     const WallDev& W = d.walls[w];
     V3<float> n;
-    const float dn = wall_geom32(W, d.wfix + 3 * (long long)w, S.x, S.y, S.z, S.r, n);
+    const float dn = wall_geom32(W, d.wfix + 3 * (long long)w, S.P[0], S.P[1], S.P[2], S.r, n);
     const bool active = dn > 0.f;
     if (count_active) warp_count(active, d.counters);
     if (!active) {
@@ -270,9 +309,8 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
       }
       continue;
     }
-    const float4 RS = d.sb32[s];
     const float4 va = d.mv32[S.owner], wa = d.mw32[S.owner];
-    const V3<float> ca = V3<float>{RS.x, RS.y, RS.z} + (S.r - 0.5f * dn) * n;
+    const V3<float> ca = arm32(S) + (S.r - 0.5f * dn) * n;
     const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
     const V3<float> vW = {W.vf[0], W.vf[1], W.vf[2]};
     double u0 = 0.0, u1 = 0.0, u2 = 0.0;
@@ -281,7 +319,7 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
       u1 = l.uw[l.capw + i];
       u2 = l.uw[2 * l.capw + i];
     }
-    const PairMat<float> pm = d.pm32[__float_as_int(RS.w) * d.nmat + W.material];
+    const PairMat<float> pm = d.pm32[d.tmat[S.tsph] * d.nmat + W.material];
     const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vW - vA,
                                               V3<float>{d2f(u0), d2f(u1), d2f(u2)}, S.r, va.w);
     if (law.capped) {
@@ -303,8 +341,8 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     // moment about the wall's reference point (fixed point, like the sphere
     // centre), the force acting at the contact point
     const long long* wf = d.wfix + 3 * (long long)w;
-    const V3<float> rw = V3<float>{fix_to_float(S.x - wf[0]), fix_to_float(S.y - wf[1]),
-                                   fix_to_float(S.z - wf[2])} + (S.r - 0.5f * dn) * n;
+    const V3<float> rw = V3<float>{fix_to_float(S.P[0] - wf[0]), fix_to_float(S.P[1] - wf[1]),
+                                   fix_to_float(S.P[2] - wf[2])} + (S.r - 0.5f * dn) * n;
     const V3<float> tw = cross(rw, law.F);
     if (shared_wf) {
       atomicAdd(&s_wf[3 * w], law.F.x);
@@ -511,25 +549,18 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
   }
 }
 
-// FP32_VOXEL mode.
-// One block's batch of B clumps starting at c0 (FP32_VOXEL mode).
+// FP32_VOXEL mode: one thread per clump integrates Eq. (5) and then writes
+// the pose records of the clump's own spheres (consecutive in memory), from a
+// float-float rotation matrix held in registers.  No block barrier or shared
+// memory: every warp runs at its own pace.  B (64, 128 or 256 clumps per
+// block) is a launch shape the tile autotuner picks.
 template <int B>
-struct UpdShared {
-  float Rh[B][9];
-  float Rl[B][9];
-  int4 vox[B];
-  float4 off[B];
-};
-
-template <int B>
-__device__ __forceinline__ void update32_batch(const DevState& d, long long c0, int integrate,
-                                               float margin, int check_cert, UpdShared<B>& sh) {
-  float (*sRh)[9] = sh.Rh;
-  float (*sRl)[9] = sh.Rl;
-  int4* sVox = sh.vox;
-  float4* sOff = sh.off;
-  const long long c = c0 + threadIdx.x;
-  if (c < d.ncl) {
+__global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float margin,
+                                                int check_cert) {
+  if (integrate && halted(d)) return;
+  const long long c = (long long)blockIdx.x * B + threadIdx.x;
+  {
+    if (c >= d.ncl) return;
     // every global load of the clump is issued first (one memory round trip)
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, ref_o = a0, ref_qv = a0;
     int4 ref_v = make_int4(0, 0, 0, 0);
@@ -672,11 +703,7 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
     R[7] = ff_scale2(ff_add(yz, wx), 2.f);
     R[8] = ff_sub(one, ff_scale2(ff_add(xx, yy), 2.f));
     float Rf[9];
-    for (int k = 0; k < 9; ++k) {
-      sRh[threadIdx.x][k] = R[k].h;
-      sRl[threadIdx.x][k] = R[k].l;
-      Rf[k] = R[k].h;
-    }
+    for (int k = 0; k < 9; ++k) Rf[k] = R[k].h;
     if (!integrate) {
       wf_new = {d2f(w.x), d2f(w.y), d2f(w.z)};
       vf_new[0] = d2f(v.x); vf_new[1] = d2f(v.y); vf_new[2] = d2f(v.z);
@@ -684,54 +711,30 @@ __device__ __forceinline__ void update32_batch(const DevState& d, long long c0, 
     const V3<float> ww = mat_mul(Rf, wf_new);
     d.mv32[c] = make_float4(vf_new[0], vf_new[1], vf_new[2], mass);
     d.mw32[c] = make_float4(ww.x, ww.y, ww.z, 0.f);
-    sVox[threadIdx.x] = vox;
-    sOff[threadIdx.x] = off;
-  }
-  __syncthreads();
-  const long long c1 = c0 + B < d.ncl ? c0 + B : d.ncl;
-  if (c0 >= c1) return;
-  const long long s0 = d.csph[c0], s1 = d.csph[c1];
-  for (long long s = s0 + threadIdx.x; s < s1; s += B) {
-    const int2 si = d.sinfo[s];
-    const int lc = (int)(si.x - c0);
-    const float4 tp = d.tp32[si.y];
-    const float p[3] = {tp.x, tp.y, tp.z};
-    ff rel[3];
-    for (int i = 0; i < 3; ++i) {
-      ff acc = ff_mulf({sRh[lc][3 * i], sRl[lc][3 * i]}, p[0]);
-      acc = ff_add(acc, ff_mulf({sRh[lc][3 * i + 1], sRl[lc][3 * i + 1]}, p[1]));
-      acc = ff_add(acc, ff_mulf({sRh[lc][3 * i + 2], sRl[lc][3 * i + 2]}, p[2]));
-      rel[i] = acc;
-    }
-    const int4 vox = sVox[lc];
-    const float4 off = sOff[lc];
-    const int vv[3] = {vox.x, vox.y, vox.z};
-    const float oo[3] = {off.x, off.y, off.z};
-    long long P[3];
-    // fixed point = voxel + round(rel.h) + round(off) + round(rel.l), each term
-    // scaled to 2^-44 m units (|off| <= 2^-21 m and |rel.l| <= 2^-31 m fit a
+    // pose records: x_rel = round(R p .h) + round(off) + round(R p .l), each
+    // term in 2^-44 m units (|off| <= 2^-21 m and |R p .l| <= 2^-31 m fit a
     // 32-bit integer): three roundings of half a unit plus the float-float
-    // error of R p (a small fraction of a unit) keep the record within 2 units
-    // of the exact centre, the bound the detection relies on
-    for (int i = 0; i < 3; ++i)
-      P[i] = ((long long)vv[i] << (kFixBits - kVoxLog2)) + f2ll_rn(rel[i].h * kMToFix) +
-             (long long)__float2int_rn(oo[i] * kMToFix) +
-             (long long)__float2int_rn(rel[i].l * kMToFix);
-    SphA32 A;
-    A.x = P[0]; A.y = P[1]; A.z = P[2]; A.r = tp.w; A.owner = si.x;
-    d.sa32[s] = A;
-    d.sb32[s] = make_float4(rel[0].h, rel[1].h, rel[2].h, __int_as_float(d.tmat[si.y]));
+    // error of R p (a small fraction of a unit) keep the centre within 2
+    // units of the exact one, the bound the detection relies on
+    const int offx = __float2int_rn(off.x * kMToFix), offy = __float2int_rn(off.y * kMToFix),
+              offz = __float2int_rn(off.z * kMToFix);
+    const int s0 = d.csph[c], s1 = d.csph[c + 1];
+    const float4* tp = d.tp32 + d.tpl_off[tpl];
+    for (int s = s0; s < s1; ++s) {
+      const float4 t4 = tp[s - s0];
+      const float p[3] = {t4.x, t4.y, t4.z};
+      ff rel[3];
+      for (int i = 0; i < 3; ++i) {
+        ff acc = ff_mulf(R[3 * i], p[0]);
+        acc = ff_add(acc, ff_mulf(R[3 * i + 1], p[1]));
+        acc = ff_add(acc, ff_mulf(R[3 * i + 2], p[2]));
+        rel[i] = acc;
+      }
+      d.srec32[s] = pack_rel(f2ll_rn(rel[0].h * kMToFix) + offx + __float2int_rn(rel[0].l * kMToFix),
+                             f2ll_rn(rel[1].h * kMToFix) + offy + __float2int_rn(rel[1].l * kMToFix),
+                             f2ll_rn(rel[2].h * kMToFix) + offz + __float2int_rn(rel[2].l * kMToFix));
+    }
   }
-}
-
-// One block per batch of B clumps (B = 64, 128 or 256: a launch shape the
-// tile autotuner picks).
-template <int B>
-__global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float margin,
-                                                int check_cert) {
-  if (integrate && halted(d)) return;
-  __shared__ UpdShared<B> sh;
-  update32_batch<B>(d, (long long)blockIdx.x * B, integrate, margin, check_cert, sh);
 }
 
 // ---------------------------------------------------------------------------

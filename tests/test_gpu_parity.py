@@ -128,6 +128,38 @@ def test_forces_match_oracle(dem, oracle_mod, prec, seed, n):
         assert np.abs(Fw - Fwo).max() <= TOL[prec] * np.abs(Fwo).sum()
 
 
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+@pytest.mark.parametrize("mix", [1, 2])
+def test_forces_match_oracle_min_max_mixing(dem, oracle_mod, prec, mix):
+    """The min and max rules for mu and CoR (section 2.1: each sphere has its
+    own mu and CoR; reading A2 mixes them per contact): forces and torques
+    within the tolerance, on a bed where most listed pairs join spheres of
+    different materials (E, nu, mu and CoR all differ between the three)."""
+    margin, K = 1e-4, 10
+    sc = _scene(5, 600, prec, margin=margin)
+    sc.mix_rule = mix
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        F, T = sim.eval_forces()
+        st = sim.stats()
+    om, _, _, a, b, ws, ww = _oracle_lists(oracle_mod, sc, margin, K)
+    _, _, tsph = om.sphere_centres(sc.tpl, sc.pos, sc.quat)
+    mats = np.asarray(sc.tpl_mat)[tsph]
+    assert (mats[a] != mats[b]).sum() > 0.4 * len(a)
+    assert len(set(np.asarray(sc.mu))) == 3 and len(set(np.asarray(sc.cor))) == 3
+    Fo, To, _, _, _, act, mag = om.forces(sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, 0.0, a, b,
+                                          np.zeros((len(a), 3)), ws, ww, np.zeros((len(ws), 3)),
+                                          with_mag=True)
+    assert st["active_last"] == act
+    _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
+    # the rule matters on this bed: the mean rule moves some clump's force by
+    # far more than the tolerance
+    Fm = oracle_mod.OracleModel(dataclasses.replace(sc, mix_rule=0)).forces(
+        sc.tpl, sc.pos, sc.quat, sc.vel, sc.angvel, 0.0, a, b, np.zeros((len(a), 3)), ws, ww,
+        np.zeros((len(ws), 3)))[0]
+    touched = mag[:, 0] > 0
+    assert (np.abs(Fm - Fo).max(axis=1)[touched] / mag[touched, 0]).max() > 1e3 * TOL[prec]
+
+
 def _run_both(dem, oracle_mod, sc, margin, K, nsteps, prec, graphs=False):
     sim = dem.Simulation(sc, margin=margin, rebuild_interval=K, precision=prec)
     sim.set_graphs(graphs)
