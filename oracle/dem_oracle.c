@@ -269,13 +269,19 @@ long long orc_pairs_binned(const orc_model* m, long long ns, const int* owner,
 /* ------------------------------------------------------------------ */
 /* Mesh facet with vertices p, b, c (translating rigidly, so the edge
  * vectors e1 = b - p, e2 = c - p do not depend on time) and d = x - p(t).
- * Barycentric coordinates (u, v) of the projection of x on the facet's plane
+ * A facet is one-sided (reading A16): a centre behind its plane (d.n < 0)
+ * does not touch it, whatever its distance; the result is +infinity, which
+ * no candidate threshold reaches and which gives no overlap.  (Without this a
+ * sphere on the far side of a convex mesh, behind a far facet and inside that
+ * facet's prism, would be in deep contact with it.)  In front (d.n >= 0):
+ * barycentric coordinates (u, v) of the projection of x on the facet's plane
  * solve the normal equations [e1.e1 e1.e2; e1.e2 e2.e2] (u, v) = (d.e1, d.e2).
  * Inside the facet (u, v >= 0, u + v <= 1) the closest point is the
- * projection: signed distance d.n, normal n.  Outside it the closest point of
- * the closed triangle lies on its boundary: the nearest of the three edges
+ * projection: distance d.n, normal n.  Outside it the closest point of the
+ * closed triangle lies on its boundary: the nearest of the three edges
  * (p -> b, p -> c, b -> c), each the segment point at the clamped parameter
- * of the perpendicular foot; normal from that point to x. */
+ * of the perpendicular foot; normal from that point to x.  The distance is
+ * continuous across the regions' borders on the front side. */
 static double facet_distance(const orc_wall* w, const double d[3], double nw[3]) {
     double e1[3], e2[3];
     for (int k = 0; k < 3; ++k) {
@@ -283,6 +289,10 @@ static double facet_distance(const orc_wall* w, const double d[3], double nw[3])
         e2[k] = w->c[k] - w->p[k];
     }
     const double ax = dot3(d, w->n);
+    if (ax < 0.0) {
+        for (int k = 0; k < 3; ++k) nw[k] = w->n[k];
+        return HUGE_VAL;
+    }
     const double d00 = dot3(e1, e1), d01 = dot3(e1, e2), d11 = dot3(e2, e2);
     const double b0 = dot3(d, e1), b1 = dot3(d, e2);
     const double den = d00 * d11 - d01 * d01;

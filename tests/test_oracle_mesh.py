@@ -1,9 +1,13 @@
 """Oracle pins for mesh facets (sphere-triangle contacts, the boundaries the
-paper builds from meshes in section 4): the distance is the distance to the
-closed triangle, checked against brute force over a dense sampling of the
-facet; in the facet's face region it is exactly the plane wall's; beyond a
-vertex it is the distance to that vertex."""
+paper builds from meshes in section 4): in front of the facet's plane the
+distance is the distance to the closed triangle, checked against brute
+force over a dense sampling of the facet; in the facet's face region it is
+exactly the plane wall's; beyond a vertex it is the distance to that vertex.
+A facet is one-sided (reading A16): a centre behind its plane is at infinite
+distance, so a sphere that reaches a facet from behind passes through it."""
+import math
 import numpy as np
+import pytest
 
 from paper_2307_03445_gb300 import scenes
 from tests.helpers import set_clumps, single_sphere_scene
@@ -36,9 +40,14 @@ def test_facet_distance_is_the_distance_to_the_closed_triangle(oracle_mod):
     rng = np.random.default_rng(5)
     centre = (A + B + Cv) / 3
     regions = set()
+    behind = 0
     for _ in range(150):
         x = centre + rng.uniform(-0.02, 0.02, 3) + rng.choice([-1, 1]) * rng.uniform(5e-4, 4e-3) * n
         d, nw = om.wall_distance(0, 0.0, x)
+        if (x - A) @ n < 0:  # behind the plane: no contact, whatever the distance
+            assert d == math.inf and np.array_equal(nw, n)
+            behind += 1
+            continue
         brute = np.sqrt(((pts - x) ** 2).sum(axis=1)).min()
         assert abs(abs(d) - brute) <= 2e-7, (x, d, brute)
         # the closest point x - |d| nw (face region: x - d n) lies on the facet
@@ -48,11 +57,10 @@ def test_facet_distance_is_the_distance_to_the_closed_triangle(oracle_mod):
         assert abs(np.linalg.norm(nw) - 1.0) < 1e-12
         inside = np.allclose(nw, n, rtol=0, atol=0)
         regions.add(inside)
+        assert d >= 0
         if inside:
             assert np.isclose(d, (x - A) @ n, rtol=0, atol=1e-17)
-        else:
-            assert d >= 0  # edge or vertex region: unsigned
-    assert regions == {True, False}
+    assert regions == {True, False} and 40 < behind < 110
 
 
 def test_facet_in_its_face_region_is_the_plane_wall_bit_for_bit(oracle_mod):
@@ -92,9 +100,12 @@ def test_facet_vertex_and_edge_closed_forms(oracle_mod):
     perp = perp / np.linalg.norm(perp)
     if perp @ (B - A) > 0:
         perp = -perp
-    x = mid + 0.002 * perp - 0.0005 * n  # behind the plane: still unsigned
+    x = mid + 0.002 * perp + 0.0005 * n  # in front of the plane
     d, nw = om.wall_distance(0, 0.0, x)
     assert np.isclose(d, np.hypot(0.002, 0.0005), rtol=1e-13)
+    # the same point mirrored behind the plane touches nothing
+    d, nw = om.wall_distance(0, 0.0, x - 0.001 * n)
+    assert d == math.inf
 
 
 def test_moving_facet_is_the_translated_facet(oracle_mod):
@@ -107,7 +118,7 @@ def test_moving_facet_is_the_translated_facet(oracle_mod):
         x = (A + B + Cv) / 3 + vel * t + rng.uniform(-0.02, 0.02, 3)
         d1, n1 = om_m.wall_distance(0, t, x)
         d2, n2 = om_s.wall_distance(0, 0.0, x)
-        assert abs(d1 - d2) <= 1e-15 and np.allclose(n1, n2, atol=1e-12)
+        assert (d1 == d2 == math.inf or abs(d1 - d2) <= 1e-15) and np.allclose(n1, n2, atol=1e-12)
 
 
 def test_mesh_helpers_orient_every_facet_towards_the_grains():
@@ -147,3 +158,27 @@ def test_facet_box_is_the_workload_box():
             for k in ("p", "b", "c"):
                 assert abs((np.asarray(f[k]) - p) @ n) < 1e-15
             assert tuple(f["vel"]) == tuple(pl["vel"])
+
+
+def test_facet_is_one_sided(oracle_mod):
+    """A sphere thrown at a facet from its front rebounds exactly as from the
+    plane wall.  A sphere whose centre lies 0.5 mm behind the facet, gliding
+    along it, does not touch it: free flight, where the plane wall (which
+    has no back side) pushes it out with an overlap of r + 0.5 mm."""
+    a, b, c = np.array([-0.04, -0.04, 0.0]), np.array([0.05, -0.03, 0.0]), np.array([-0.03, 0.05, 0.0])
+    out = {}
+    for case, z0, v0 in (("front", 1.2e-3, (0.0, 0.0, -0.5)), ("behind", -0.5e-3, (0.05, 0.0, 0.0))):
+        for wall in (scenes.triangle(a, b, c), scenes.plane(a, (0, 0, 1))):
+            sc = single_sphere_scene([1e-3], walls=[wall], mu=0.3, cor=0.5)
+            sc.bin_size = 4e-3
+            set_clumps(sc, [0], [[0.0, 0.0, z0]], vel=[v0])
+            sim = oracle_mod.OracleSim(sc, margin=5e-5, rebuild_every=10)
+            sim.step(12000)
+            out[(case, wall["type"])] = (sim.state(), sim.contacts())
+    for x, y in zip(out[("front", scenes.WALL_TRIANGLE)][0], out[("front", scenes.WALL_PLANE)][0]):
+        assert np.array_equal(x, y)
+    assert out[("front", scenes.WALL_TRIANGLE)][0][2][0, 2] > 0  # bounced back up
+    (pos, quat, vel, angvel), lists = out[("behind", scenes.WALL_TRIANGLE)]
+    assert np.array_equal(vel[0], [0.05, 0.0, 0.0]) and len(lists[3]) == 0
+    assert pos[0, 0] == pytest.approx(0.05 * 12000 * 1e-6, rel=1e-12) and pos[0, 2] == -0.5e-3
+    assert out[("behind", scenes.WALL_PLANE)][0][2][0, 2] > 1.0  # the plane throws it out
