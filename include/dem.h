@@ -64,7 +64,12 @@ enum { DEM_GUARD_OFF = 0, DEM_GUARD_COUNT = 1, DEM_GUARD_ROLLBACK = 2 };
  *             mesh is a list of facets; its load is the sum of theirs).
  * The surface moves with velocity vel: its reference point at time t is
  * p + vel * t.  material indexes the material table.  scene = -1 applies the
- * wall to every scene, otherwise to one scene. */
+ * wall to every scene, otherwise to one scene.  A scene holds at most 32
+ * PLANE, CYLINDER and CONE walls (every sphere tests each of them at a
+ * rebuild); TRIANGLE facets have no such limit: at a rebuild each facet is
+ * registered in the detection bins its box (widened by its travel over the
+ * list's lifetime) touches, and only the spheres registered in the same bins
+ * are tested against it (section 2.2's binning, applied to the mesh). */
 typedef struct {
     int type;
     int material;
@@ -134,6 +139,7 @@ typedef struct {
                                 /*   displacement certificate (see below)           */
     double ms_predict;          /* device time of the learned rule's margin        */
                                 /*   predictions [ms], while timing is on           */
+    long long outer_rebuilds;   /* detections of the outer list (dem_set_outer_list) */
 } dem_stats;
 
 typedef struct dem_ctx dem_ctx;
@@ -213,6 +219,24 @@ int dem_get_state(dem_ctx* ctx, double* pos, double* quat, double* vel, double* 
  * its scene's corner; in both cases no clump record changes. */
 int dem_set_state(dem_ctx* ctx, const double* pos, const double* quat, const double* vel,
                   const double* angvel);
+
+/* Two-level contact list for the plain rule (no counterpart in the paper's
+ * text; an acceleration of section 2.2's rebuild that keeps its result).
+ * With n_inner >= 1 a rebuild detects an outer list with the wider margin
+ * factor * m (factor > 1), whose wall candidates also cover the walls' travel
+ * over n_inner rebuild intervals, and keeps the lattice point of every sphere
+ * at that time.  The next n_inner rebuilds (that one included) take their
+ * list from the outer one: each pair or wall candidate of the outer list is
+ * kept when it passes the exact test of a fresh detection at margin m, which
+ * gives exactly the fresh detection's list, in the same order, as long as no
+ * sphere's lattice point moved further from its outer-list point than the
+ * difference of its two enlarged radii; every rebuild checks this for every
+ * sphere and detects a new outer list when one moved further.  Adding clumps
+ * or changing a wall's motion also starts a new outer list; the learned rule
+ * and dem_rebuild use full detections.  n_inner = 0 turns it off (default).
+ * dem_get_bins then reports the outer list's bins.  Returns
+ * DEM_ERR_INVALID_ARG for factor <= 1 or n_inner < 0. */
+int dem_set_outer_list(dem_ctx* ctx, double factor, int n_inner);
 
 int dem_get_stats(dem_ctx* ctx, dem_stats* out);
 int dem_reset_stats(dem_ctx* ctx);

@@ -269,6 +269,11 @@ class Simulation:
         """Bit-reproducible force sums (per-contact slots summed in a fixed order)."""
         self._check(self.lib.dem_set_deterministic(self.ctx, 1 if on else 0))
 
+    def set_outer_list(self, factor=3.0, n_inner=4):
+        """Two-level contact list (see include/dem.h): an outer list at factor x
+        the margin serves the next n_inner rebuilds; n_inner=0 turns it off."""
+        self._check(self.lib.dem_set_outer_list(self.ctx, float(factor), int(n_inner)))
+
     def set_graphs(self, on=True):
         """Run the steps between rebuilds as one captured CUDA graph."""
         self._check(self.lib.dem_set_graphs(self.ctx, 1 if on else 0))

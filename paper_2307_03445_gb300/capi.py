@@ -56,7 +56,7 @@ class DemStats(C.Structure):
                 ("ms_detect", C.c_double), ("ms_pairs", C.c_double), ("ms_walls", C.c_double),
                 ("ms_update", C.c_double), ("timed_steps", C.c_longlong),
                 ("launches", C.c_longlong), ("early_rebuilds", C.c_longlong),
-                ("ms_predict", C.c_double)]
+                ("ms_predict", C.c_double), ("outer_rebuilds", C.c_longlong)]
 
 
 _D = C.POINTER(C.c_double)
@@ -93,6 +93,7 @@ SIGNATURES = {
     "dem_set_timing": (C.c_int, [_V, C.c_int]),
     "dem_set_graphs": (C.c_int, [_V, C.c_int]),
     "dem_set_deterministic": (C.c_int, [_V, C.c_int]),
+    "dem_set_outer_list": (C.c_int, [_V, C.c_double, C.c_int]),
     "dem_autotune_bins": (C.c_int, [_V, C.c_int, _D, C.c_int, _D, _D]),
     "dem_set_tiles": (C.c_int, [_V, C.POINTER(DemTiles)]),
     "dem_get_tiles": (C.c_int, [_V, C.POINTER(DemTiles)]),

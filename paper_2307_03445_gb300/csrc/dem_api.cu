@@ -73,6 +73,18 @@ struct dem_ctx {
   Buf b_det, b_bin_size, b_wall_mask, b_wall_cnt;
   Buf b_bin_start, b_pair_cnt, b_scan_scr, b_tmp;
   Buf b_rec, b_trho, b_upairs;
+  Buf b_facet_idx, b_fbin_size, b_fbin_start, b_frec, b_fcand, b_fcnt;
+  int n_facets = 0;
+  unsigned long long fcap = 0;  // capacity of the facet candidate buffer
+  // two-level list: an outer list at outer_factor x the margin serves
+  // outer_n rebuilds; b_q0 holds its lattice points and enlarged radii
+  double outer_factor = 0.0;
+  int outer_n = 0, outer_used = 0;
+  bool outer_valid = false;
+  long long outer_ns = 0;
+  double outer_m = 0.0;
+  int outer_K = 0;
+  Buf b_q0;
   unsigned long long ucap = 0;  // capacity of the unordered pair buffer
   double bin_factor = 1.0;      // bin edge multiplier chosen by dem_autotune_bins
   dem_tiles tiles = {8, 128, 8}; // launch shapes (dem_set_tiles / dem_autotune_tiles)
@@ -83,7 +95,7 @@ struct dem_ctx {
   struct ListBufs {
     Buf pa, pb, u, row, ws, ww, uw, wrow, dnb;
     ContactList L{};
-  } lists[3];
+  } lists[4];  // 0, 1: current and next; 2: audit; 3: outer list
   int cur = 0;
   long long list_ns = 0;  // spheres when the current list was built
   // state
@@ -217,6 +229,7 @@ void refresh_devstate(dem_ctx* c) {
   for (int k = 0; k < 3; ++k) {
     d.g[k] = c->P.g[k];
     d.hg[k] = c->P.dt * c->P.g[k];
+    d.hgf[k] = (float)d.hg[k];
   }
   d.tpl_off = ptr<int>(c->b_tpl_off);
   d.tp64 = ptr<double4_32a>(c->b_tp64);
@@ -255,6 +268,8 @@ void refresh_devstate(dem_ctx* c) {
   d.walls = ptr<WallDev>(c->b_walls);
   d.wall_idx = ptr<int>(c->b_wall_idx);
   d.wall_scene = ptr<int>(c->b_wall_scene);
+  d.facet_idx = ptr<int>(c->b_facet_idx);
+  d.nfacets = c->n_facets;
   d.wfix = ptr<long long>(c->b_wfix);
   d.wpos = ptr<double>(c->b_wpos);
   d.wforce = ptr<double>(c->b_wforce);
@@ -415,7 +430,7 @@ int finalize(dem_ctx* c) {
   c->walls.clear();
   c->wall_user.clear();
   c->wall_scene.clear();
-  std::vector<int> idx;
+  std::vector<int> idx, fidx;  // analytic walls per scene; mesh facets (found through the bins)
   for (size_t s = 0; s < c->scenes.size(); ++s) {
     c->grids[s].wall_start = (int)idx.size();
     int cnt = 0;
@@ -457,15 +472,22 @@ int finalize(dem_ctx* c) {
           split_ff(d.e2[k], d.e2h[k], d.e2l[k]);
         }
       }
-      idx.push_back((int)c->walls.size());
+      if (uw.type == DEM_WALL_TRIANGLE) {
+        fidx.push_back((int)c->walls.size());
+      } else {
+        idx.push_back((int)c->walls.size());
+        ++cnt;
+      }
       c->wall_user.push_back((int)w);
       c->wall_scene.push_back((int)s);
       c->walls.push_back(d);
-      ++cnt;
     }
-    if (cnt > 32) return fail(c, DEM_ERR_INVALID_ARG, "more than 32 walls in one scene");
+    // analytic walls are tested by every sphere of the scene (a bit mask per
+    // sphere); facets are registered in the bins and have no such limit
+    if (cnt > 32) return fail(c, DEM_ERR_INVALID_ARG, "more than 32 analytic walls in one scene");
     c->grids[s].wall_count = cnt;
   }
+  c->n_facets = (int)fidx.size();
   const size_t nw = std::max<size_t>(1, c->walls.size());
   if (!grow(c, c->b_grids, sizeof(SceneGrid) * c->grids.size()) ||
       !grow(c, c->b_lgrids, sizeof(SceneGrid) * c->lgrids.size()) ||
@@ -473,7 +495,8 @@ int finalize(dem_ctx* c) {
       !grow(c, c->b_wall_scene, sizeof(int) * nw) || !grow(c, c->b_wfix, 3 * sizeof(long long) * nw) ||
       !grow(c, c->b_wpos, 3 * sizeof(double) * nw) || !grow(c, c->b_wforce, 3 * sizeof(double) * nw) ||
       !grow(c, c->b_wtorque, 3 * sizeof(double) * nw) ||
-      !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->b_totals, 64) ||
+      !grow(c, c->b_facet_idx, sizeof(int) * std::max<size_t>(1, fidx.size())) ||
+      !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->b_totals, 128) ||
       !grow(c, c->b_dstep, 64))
     return fail(c, DEM_ERR_OOM, "scene tables");
   cudaMemcpyAsync(c->b_grids.p, c->grids.data(), sizeof(SceneGrid) * c->grids.size(), cudaMemcpyHostToDevice, c->st);
@@ -481,7 +504,10 @@ int finalize(dem_ctx* c) {
                   cudaMemcpyHostToDevice, c->st);
   if (!c->walls.empty()) {
     cudaMemcpyAsync(c->b_walls.p, c->walls.data(), sizeof(WallDev) * c->walls.size(), cudaMemcpyHostToDevice, c->st);
-    cudaMemcpyAsync(c->b_wall_idx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c->st);
+    if (!idx.empty())
+      cudaMemcpyAsync(c->b_wall_idx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c->st);
+    if (!fidx.empty())
+      cudaMemcpyAsync(c->b_facet_idx.p, fidx.data(), sizeof(int) * fidx.size(), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->b_wall_scene.p, c->wall_scene.data(), sizeof(int) * c->wall_scene.size(), cudaMemcpyHostToDevice, c->st);
   }
   cudaMemsetAsync(c->b_wforce.p, 0, c->b_wforce.bytes, c->st);
@@ -497,12 +523,49 @@ int finalize(dem_ctx* c) {
   return cuda_check(c, "finalize");
 }
 
+// Lists[li] sized for NP pairs and NW wall contacts (25 % headroom when it
+// grows) and its device view set; hist = false leaves out the tangential
+// history arrays (the outer list carries none).
+int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, bool hist) {
+  auto& LB = c->lists[li];
+  ContactList& L = LB.L;
+  if ((long long)NP > L.cap || !LB.pa.p) {
+    const long long cap = std::max<long long>((long long)(NP + NP / 4), 1024);
+    dfree(c, LB.pa.p); dfree(c, LB.pb.p); dfree(c, LB.u.p);
+    LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf();
+    if (!grow(c, LB.pa, 4 * cap) || !grow(c, LB.pb, 4 * cap) || (hist && !grow(c, LB.u, 24 * cap)))
+      return fail(c, DEM_ERR_OOM, "pair list");
+    L.cap = cap;
+  }
+  if ((long long)NW > L.capw || !LB.ws.p) {
+    const long long cap = std::max<long long>((long long)(NW + NW / 4), 1024);
+    dfree(c, LB.ws.p); dfree(c, LB.ww.p); dfree(c, LB.uw.p);
+    LB.ws = Buf(); LB.ww = Buf(); LB.uw = Buf();
+    if (!grow(c, LB.ws, 4 * cap) || !grow(c, LB.ww, 4 * cap) || (hist && !grow(c, LB.uw, 24 * cap)))
+      return fail(c, DEM_ERR_OOM, "wall list");
+    L.capw = cap;
+  }
+  L.pa = ptr<int>(LB.pa);
+  L.pb = ptr<uint32_t>(LB.pb);
+  L.u = ptr<double>(LB.u);
+  L.row = ptr<uint32_t>(LB.row);
+  L.ws = ptr<int>(LB.ws);
+  L.ww = ptr<uint32_t>(LB.ww);
+  L.uw = ptr<double>(LB.uw);
+  L.wrow = ptr<uint32_t>(LB.wrow);
+  if (!grow(c, LB.dnb, 16)) return fail(c, DEM_ERR_OOM, "list lengths");
+  L.dn = ptr<long long>(LB.dnb);
+  L.n = (long long)NP;
+  L.nw = (long long)NW;
+  return DEM_OK;
+}
+
 // Detection into lists[li] with margin m (per clump from D.cmargin when set),
 // for a list that must last K steps (wall travel) -- also used by the audit.
 // With an old list (old != NULL) the tangential history of the pairs both
 // lists hold is carried over as the rows are built.
 int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nullptr,
-                long long old_ns = 0) {
+                long long old_ns = 0, double wall_extra = 0.0) {
   const long long ns = c->ns;
   const double t = (double)c->step * c->P.dt;
   const double travel = c->P.dt * (double)std::max(1, K);
@@ -524,35 +587,61 @@ int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nu
   o.bin_size = ptr<uint32_t>(c->b_bin_size);
   o.bin_start = ptr<uint32_t>(c->b_bin_start);
   o.nbins = c->nbins;
+  o.wall_extra = wall_extra;
   if (!c->D.cmargin) {  // one margin for all clumps: radii from a per template sphere table
     o.n_tsph = (int)c->tpl_rad.size();
     if (!grow(c, c->b_trho, 4 * (size_t)(o.n_tsph + 1))) return fail(c, DEM_ERR_OOM, "detection buffers");
     o.trho = ptr<int>(c->b_trho);
   }
   unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
+  // b_totals: 0 entries, 1 analytic wall contacts, 3 pairs, 4 audit, 5 d_np,
+  // 6 slot lists, 7 next bin, 8 facet registrations, 9 facet candidates,
+  // 10 wall contacts with the facets
+  const bool facets = c->n_facets > 0;
+  if (facets && (!grow(c, c->b_fbin_size, 4 * (nb + 1)) || !grow(c, c->b_fbin_start, 4 * (nb + 1)) ||
+                 !grow(c, c->b_fcnt, 4 * (ns + 1))))
+    return fail(c, DEM_ERR_OOM, "facet bin buffers");
+  o.fbin_size = ptr<uint32_t>(c->b_fbin_size);
+  o.fbin_start = ptr<uint32_t>(c->b_fbin_start);
+  o.fcnt = ptr<uint32_t>(c->b_fcnt);
+  o.d_nf = tot + 9;
   // bin sort by counting: sizes (detection pass), starts (scan; the extra
-  // zero entry makes start[nbins] the total), then the scatter below
+  // zero entry makes start[nbins] the total), then the scatter below; the
+  // mesh facets' registrations the same way
   cudaMemsetAsync(o.bin_size, 0, 4 * (nb + 1), c->st);
   launch_detect(c->D, o, m, nullptr, t, travel, c->st);
   exclusive_scan_u32(o.bin_size, o.bin_start, (long long)nb + 1, c->b_scan_scr.p, tot + 0, c->st);
   exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 1, c->st);
-  unsigned long long h_tot[4] = {0, 0, 0, 0};
+  unsigned long long h_tot[12] = {};
+  if (facets) {
+    cudaMemsetAsync(o.fbin_size, 0, 4 * (nb + 1), c->st);
+    launch_facet_count(c->D, o, t, travel, c->st);
+    exclusive_scan_u32(o.fbin_size, o.fbin_start, (long long)nb + 1, c->b_scan_scr.p, tot + 8, c->st);
+    cudaMemcpyAsync(h_tot + 8, tot + 8, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+  }
   cudaMemcpyAsync(h_tot, tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "detect");
-  const unsigned long long B = h_tot[0], NW = h_tot[1];
-  if (B >= (1ull << 32) || NW >= (1ull << 31))
+  const unsigned long long B = h_tot[0], NWA = h_tot[1], NFR = h_tot[8];
+  if (B >= (1ull << 32) || NWA >= (1ull << 31) || NFR >= (1ull << 31))
     return fail(c, DEM_ERR_CAPACITY, "bin registrations exceed 2^32");
   c->n_entries = (long long)B;
   c->n_entry_bins = (long long)nb;
   if (!grow(c, c->b_rec, sizeof(EntryRec) * (B + 1))) return fail(c, DEM_ERR_OOM, "bin buffers");
   o.rec = ptr<EntryRec>(c->b_rec);
   launch_bin_scatter(c->D, o, c->st);
+  if (facets) {
+    if (!grow(c, c->b_frec, sizeof(uint4) * (NFR + 1))) return fail(c, DEM_ERR_OOM, "facet bin buffers");
+    o.frec = ptr<uint4>(c->b_frec);
+    o.nfreg = (long long)NFR;
+    launch_facet_scatter(c->D, o, t, travel, c->st);
+  }
   o.d_np = tot + 5;
-  o.next_bin = tot + 7;  // b_totals: 0 entries, 1 wall entries, 3 pairs, 4 audit, 5 d_np, 6 slot lists
+  o.next_bin = tot + 7;
   o.chunk = c->tiles.narrow_chunk;
-  // the find pass appends the kept pairs to an unordered buffer sized from
-  // the last rebuild; if they did not fit it grows and the pass runs again
-  unsigned long long NP = 0;
+  // the find passes append the kept pairs (and facet candidates) to
+  // unordered buffers sized from the last rebuild; if they did not fit they
+  // grow and the passes run again
+  unsigned long long NP = 0, NF = 0;
   for (int attempt = 0;; ++attempt) {
     if (c->ucap == 0) c->ucap = (unsigned long long)std::max<long long>(2 * ns, 1 << 16);
     if (!grow(c, c->b_upairs, 8 * (size_t)c->ucap)) return fail(c, DEM_ERR_OOM, "pair buffer");
@@ -564,45 +653,37 @@ int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nu
     launch_narrow(c->D, o, c->st);
     exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
     cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+    if (facets) {
+      if (c->fcap == 0) c->fcap = 1 << 16;
+      if (!grow(c, c->b_fcand, 8 * (size_t)c->fcap)) return fail(c, DEM_ERR_OOM, "facet candidates");
+      o.fcand = ptr<uint2>(c->b_fcand);
+      o.fcap = c->fcap;
+      cudaMemsetAsync(o.fcnt, 0, 4 * (size_t)ns, c->st);
+      cudaMemsetAsync(o.d_nf, 0, sizeof(unsigned long long), c->st);
+      launch_facet_narrow(c->D, o, m, nullptr, t, travel, c->st);
+      cudaMemcpyAsync(h_tot + 9, tot + 9, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+    }
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "narrow phase");
     NP = h_tot[3];
-    if (NP <= c->ucap) break;
+    NF = h_tot[9];
+    if (NP <= c->ucap && NF <= c->fcap) break;
     if (attempt > 0) return fail(c, DEM_ERR_STATE, "internal: pair buffer regrown twice");
-    c->ucap = NP + NP / 4 + 1024;
+    if (NP > c->ucap) c->ucap = NP + NP / 4 + 1024;
+    if (NF > c->fcap) c->fcap = NF + NF / 4 + 1024;
+  }
+  const unsigned long long NW = NWA + NF;
+  if (NW >= (1ull << 31)) return fail(c, DEM_ERR_CAPACITY, "wall list exceeds 2^31 entries");
+  if (NF > 0) {  // rows hold analytic walls and facets: counts and offsets again
+    launch_add_facet_counts(c->D, o, c->st);
+    exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 10, c->st);
   }
   o.np = (long long)NP;
   if (NP >= (1ull << 31)) return fail(c, DEM_ERR_CAPACITY, "pair list exceeds 2^31 entries");
-  if (c->P.max_contacts > 0 && (long long)NP > c->P.max_contacts)
+  if (li != 3 && c->P.max_contacts > 0 && (long long)NP > c->P.max_contacts)
     return fail(c, DEM_ERR_CAPACITY, "pair list exceeds max_contacts");
+  int rc = size_list(c, li, NP, NW, li != 3);
+  if (rc) return rc;
   ContactList& L = LB.L;
-  if ((long long)NP > L.cap || !LB.pa.p) {
-    const long long cap = std::max<long long>((long long)(NP + NP / 4), 1024);
-    dfree(c, LB.pa.p); dfree(c, LB.pb.p); dfree(c, LB.u.p);
-    LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf();
-    if (!grow(c, LB.pa, 4 * cap) || !grow(c, LB.pb, 4 * cap) || !grow(c, LB.u, 24 * cap))
-      return fail(c, DEM_ERR_OOM, "pair list");
-    L.cap = cap;
-  }
-  if ((long long)NW > L.capw || !LB.ws.p) {
-    const long long cap = std::max<long long>((long long)(NW + NW / 4), 1024);
-    dfree(c, LB.ws.p); dfree(c, LB.ww.p); dfree(c, LB.uw.p);
-    LB.ws = Buf(); LB.ww = Buf(); LB.uw = Buf();
-    if (!grow(c, LB.ws, 4 * cap) || !grow(c, LB.ww, 4 * cap) || !grow(c, LB.uw, 24 * cap))
-      return fail(c, DEM_ERR_OOM, "wall list");
-    L.capw = cap;
-  }
-  L.pa = ptr<int>(LB.pa);
-  L.pb = ptr<uint32_t>(LB.pb);
-  L.u = ptr<double>(LB.u);
-  L.row = ptr<uint32_t>(LB.row);
-  L.ws = ptr<int>(LB.ws);
-  L.ww = ptr<uint32_t>(LB.ww);
-  L.uw = ptr<double>(LB.uw);
-  L.wrow = ptr<uint32_t>(LB.wrow);
-  if (!grow(c, LB.dnb, 16)) return fail(c, DEM_ERR_OOM, "list lengths");
-  L.dn = ptr<long long>(LB.dnb);
-  L.n = (long long)NP;
-  L.nw = (long long)NW;
   const uint32_t np32 = (uint32_t)NP, nw32 = (uint32_t)NW;
   const long long lens[2] = {(long long)NP, (long long)NW};
   cudaMemcpyAsync(L.dn, lens, sizeof(lens), cudaMemcpyHostToDevice, c->st);
@@ -610,18 +691,107 @@ int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nu
   cudaMemcpyAsync(L.wrow + ns, &nw32, 4, cudaMemcpyHostToDevice, c->st);
   launch_list_rows(c->D, o, L, old, old_ns, c->st);
   launch_wall_emit(c->D, o, L.ws, L.ww, c->st);
+  launch_facet_finish(c->D, o, (long long)NF, L.ws, L.ww, c->st);
   cudaStreamSynchronize(c->st);  // the two host scalars above must outlive their copies
   return cuda_check(c, "detect_into");
 }
 
+// The list at margin m for K steps into lists[li], filtered from the outer
+// list (lists[3]); with an old list its tangential history is carried over.
+// *bad is set, and lists[li] left unused, when a sphere has left the
+// allowance around its outer-list lattice point.
+int filter_into(dem_ctx* c, int li, double m, int K, const ContactList* old, long long old_ns,
+                bool* bad) {
+  const long long ns = c->ns;
+  const double t = (double)c->step * c->P.dt;
+  const double travel = c->P.dt * (double)std::max(1, K);
+  auto& LB = c->lists[li];
+  const ContactList& O = c->lists[3].L;
+  if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_wall_cnt, 4 * (ns + 1)) ||
+      !grow(c, c->b_pair_cnt, 4 * (ns + 1)) || !grow(c, LB.row, 4 * (ns + 1)) ||
+      !grow(c, LB.wrow, 4 * (ns + 1)) || !grow(c, c->b_scan_scr, scan_scratch_bytes(ns + 1) + 256))
+    return fail(c, DEM_ERR_OOM, "detection buffers");
+  DetectOut o{};
+  o.det = ptr<int4>(c->b_det);
+  o.wall_cnt = ptr<uint32_t>(c->b_wall_cnt);
+  o.wall_off = ptr<uint32_t>(LB.wrow);
+  o.pair_cnt = ptr<uint32_t>(c->b_pair_cnt);
+  o.pair_off = ptr<uint32_t>(LB.row);
+  o.n_tsph = (int)c->tpl_rad.size();
+  if (!grow(c, c->b_trho, 4 * (size_t)(o.n_tsph + 1))) return fail(c, DEM_ERR_OOM, "detection buffers");
+  o.trho = ptr<int>(c->b_trho);
+  unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
+  cudaMemsetAsync(tot + 11, 0, sizeof(unsigned long long), c->st);
+  launch_lattice_check(c->D, o, m, ptr<int4>(c->b_q0), tot + 11, c->st);
+  launch_filter_count(c->D, o, O, m, t, travel, c->st);
+  exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
+  exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 1, c->st);
+  unsigned long long h_tot[12] = {};
+  cudaMemcpyAsync(h_tot, tot, 12 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "filter");
+  *bad = h_tot[11] != 0;
+  if (*bad) return DEM_OK;
+  const unsigned long long NP = h_tot[3], NW = h_tot[1];
+  if (c->P.max_contacts > 0 && (long long)NP > c->P.max_contacts)
+    return fail(c, DEM_ERR_CAPACITY, "pair list exceeds max_contacts");
+  int rc = size_list(c, li, NP, NW, true);
+  if (rc) return rc;
+  ContactList& L = LB.L;
+  const uint32_t np32 = (uint32_t)NP, nw32 = (uint32_t)NW;
+  const long long lens[2] = {(long long)NP, (long long)NW};
+  cudaMemcpyAsync(L.dn, lens, sizeof(lens), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(L.row + ns, &np32, 4, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(L.wrow + ns, &nw32, 4, cudaMemcpyHostToDevice, c->st);
+  launch_filter_emit(c->D, o, O, L, m, t, travel, c->st);
+  if (old) launch_hist_pairs(*old, L, old_ns, c->st);
+  cudaStreamSynchronize(c->st);  // the two host scalars above must outlive their copies
+  return cuda_check(c, "filter_into");
+}
+
+// A new outer list: a detection at outer_factor x m whose wall candidates
+// cover the walls' travel over outer_n intervals of K steps and 2^-21 m more
+// than the margins' difference; its lattice points and radii are kept.
+int build_outer(dem_ctx* c, double m, int K) {
+  const double mo = c->outer_factor * m;
+  int rc = detect_into(c, 3, mo, c->outer_n * std::max(1, K), nullptr, 0, 0x1p-21);
+  if (rc) return rc;
+  if (!grow(c, c->b_q0, sizeof(int4) * (c->ns + 1))) return fail(c, DEM_ERR_OOM, "outer list points");
+  cudaMemcpyAsync(c->b_q0.p, c->b_det.p, sizeof(int4) * c->ns, cudaMemcpyDeviceToDevice, c->st);
+  c->outer_valid = true;
+  c->outer_used = 0;
+  c->outer_ns = c->ns;
+  c->outer_m = m;
+  c->outer_K = K;
+  c->stats.outer_rebuilds++;
+  return DEM_OK;
+}
+
 // Rebuilds the current list with margin m (per clump when D.cmargin is set)
 // for a list meant to last K steps; history is carried from the old list.
-int rebuild(dem_ctx* c, double m, int K) {
+// With the two-level list on (and one margin for all clumps) the list is
+// filtered from the outer list, which is detected again when it has served
+// its rebuilds or a sphere has left its allowance.
+int rebuild(dem_ctx* c, double m, int K, bool allow_outer = true) {
   const int nxt = c->cur == 0 ? 1 : 0;
   if (c->timing) cudaEventRecord(c->ev[0], c->st);
   const ContactList* old = c->have_list ? &curL(c) : nullptr;
-  int rc = detect_into(c, nxt, m, K, old, c->list_ns);
-  if (rc) return rc;
+  int rc;
+  if (allow_outer && c->outer_n > 0 && !c->D.cmargin && m > 0.0) {
+    const bool stale = !c->outer_valid || c->outer_used >= c->outer_n || c->outer_ns != c->ns ||
+                       c->outer_m != m || c->outer_K != K;
+    if (stale && (rc = build_outer(c, m, K))) return rc;
+    bool bad = false;
+    if ((rc = filter_into(c, nxt, m, K, old, c->list_ns, &bad))) return rc;
+    if (bad) {  // a sphere moved past its allowance: a new outer list
+      if ((rc = build_outer(c, m, K)) || (rc = filter_into(c, nxt, m, K, old, c->list_ns, &bad)))
+        return rc;
+      if (bad) return fail(c, DEM_ERR_STATE, "internal: a fresh outer list fails its own check");
+    }
+    c->outer_used++;
+  } else {
+    rc = detect_into(c, nxt, m, K, old, c->list_ns);
+    if (rc) return rc;
+  }
   ContactList& N = c->lists[nxt].L;
   if (old) launch_hist_walls(*old, N, c->list_ns, c->st);
   c->cur = nxt;
@@ -644,7 +814,7 @@ int rebuild(dem_ctx* c, double m, int K) {
   }
   return cuda_check(c, "rebuild");
 }
-int rebuild(dem_ctx* c) { return rebuild(c, c->margin, c->P.rebuild_interval); }
+int rebuild(dem_ctx* c) { return rebuild(c, c->margin, c->P.rebuild_interval, false); }
 
 // Sphere-sphere then sphere-wall contact forces; `mid` (optional) is recorded
 // between the two kernels.
@@ -1181,6 +1351,7 @@ void dem_destroy(dem_ctx* c) {
                 &c->b_grids, &c->b_lgrids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
                 &c->b_wpos, &c->b_wforce, &c->b_wtorque, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
                 &c->b_totals, &c->b_det, &c->b_bin_size, &c->b_wall_mask, &c->b_wall_cnt,
+                &c->b_facet_idx, &c->b_fbin_size, &c->b_fbin_start, &c->b_frec, &c->b_fcand, &c->b_fcnt, &c->b_q0,
                 &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
                 &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
                 &c->b_det_ids, &c->b_det_pair, &c->b_det_wall, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
@@ -1249,8 +1420,8 @@ int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double
     }
   if (!grow(c, c->b_tpl_off, 4 * (n_tpl + 1)) || !grow(c, c->b_tp64, 32 * S) || !grow(c, c->b_tp32, 16 * S) ||
       !grow(c, c->b_tmat, 4 * S) || !grow(c, c->b_tmass, 8 * n_tpl) || !grow(c, c->b_tinert, 24 * n_tpl) ||
-      !grow(c, c->b_tpbound, 4 * n_tpl) || !grow(c, c->b_tmassf, 4 * n_tpl) ||
-      !grow(c, c->b_tinertf, 12 * n_tpl))
+      !grow(c, c->b_tpbound, 4 * n_tpl) || !grow(c, c->b_tmassf, 8 * n_tpl) ||
+      !grow(c, c->b_tinertf, 24 * n_tpl))
     return fail(c, DEM_ERR_OOM, "template tables");
   cudaMemcpyAsync(c->b_tpl_off.p, off, 4 * (n_tpl + 1), cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tp64.p, tp64.data(), 32 * (size_t)S, cudaMemcpyHostToDevice, c->st);
@@ -1258,9 +1429,18 @@ int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double
   cudaMemcpyAsync(c->b_tmat.p, material, 4 * (size_t)S, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tmass.p, mass, 8 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tinert.p, inertia, 24 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
-  std::vector<float> mf(mass, mass + n_tpl), inf(inertia, inertia + 3 * n_tpl);
-  cudaMemcpyAsync(c->b_tmassf.p, mf.data(), 4 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
-  cudaMemcpyAsync(c->b_tinertf.p, inf.data(), 12 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
+  // float tables of the FP32_VOXEL update: {m, 1/m} and {I0, I1, I2, 1/I0, 1/I1, 1/I2}
+  std::vector<float> mf(2 * n_tpl), inf(6 * n_tpl);
+  for (int t = 0; t < n_tpl; ++t) {
+    mf[2 * t] = (float)mass[t];
+    mf[2 * t + 1] = (float)(1.0 / mass[t]);
+    for (int k = 0; k < 3; ++k) {
+      inf[6 * t + k] = (float)inertia[3 * t + k];
+      inf[6 * t + 3 + k] = (float)(1.0 / inertia[3 * t + k]);
+    }
+  }
+  cudaMemcpyAsync(c->b_tmassf.p, mf.data(), 8 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_tinertf.p, inf.data(), 24 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tpbound.p, pb.data(), 4 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   cudaStreamSynchronize(c->st);
   return cuda_check(c, "load templates");
@@ -1347,6 +1527,7 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
     c->r_mean = c->r_sum / (double)ns;
   }
   c->need_rebuild = true;
+  c->outer_valid = false;
   c->acc_dirty = true;
   if (c->finalized) {
     refresh_devstate(c);
@@ -1592,6 +1773,7 @@ int dem_set_wall_motion(dem_ctx* c, int wall, const double* point, const double*
   launch_walls_at(c->D, c->step, c->st);  // wall positions of the current step
   // the listed wall candidates assumed the old motion
   c->need_rebuild = true;
+  c->outer_valid = false;
   drop_graphs(c);
   cudaStreamSynchronize(c->st);  // the host table must outlive its copy
   return cuda_check(c, "set_wall_motion");
@@ -1810,6 +1992,16 @@ int dem_autotune_tiles(dem_ctx* c, int steps, int reps, dem_tiles* best) {
   if (rc) return rc;
   *best = c->tiles;
   return cuda_check(c, "autotune tiles");
+}
+
+int dem_set_outer_list(dem_ctx* c, double factor, int n_inner) {
+  if (!c) return DEM_ERR_INVALID_ARG;
+  if (n_inner < 0 || (n_inner > 0 && !(factor > 1.0 && std::isfinite(factor))))
+    return fail(c, DEM_ERR_INVALID_ARG, "outer list: factor must be > 1 and n_inner >= 0");
+  c->outer_factor = factor;
+  c->outer_n = n_inner;
+  c->outer_valid = false;
+  return DEM_OK;
 }
 
 int dem_set_deterministic(dem_ctx* c, int on) {

@@ -167,34 +167,73 @@ __global__ void k_tpl_rho(DevState d, double margin, int n, int* __restrict__ tr
   if (i < n) trho[i] = (int)tpl_rho(d.tp64[i].w, margin);
 }
 
-// One thread per sphere: detection coordinates, wall candidates, and the
-// counting pass of the bin sort (one count per bin the enlarged box touches).
-__global__ void k_detect(DevState d, DetectOut o, double margin, const double* __restrict__ smargin,
-                         double t, double travel_time) {
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= d.ns) return;
-  const int2 si = d.sinfo[s];
-  const int2 ci = d.cinfo[si.x];
-  const float ttf = d2f(travel_time);
-  const SceneGrid g = d.grids[ci.y];
+// The exact detection centre of sphere s (owner c, template sphere ts) and
+// its float estimate, computed on first use.
+struct SphereCentre {
+  const DevState& d;
+  long long s;
+  int c, ts;
+  const SceneGrid& g;
   double x[3];
-  bool have_x = false;
-  auto exact_centre = [&]() {
-    if (have_x) return;
-    double X[3];
-    clump_com(d, si.x, g, X);
-    const double4_32a q4 = d.cq[si.x];
-    const double4_32a tp = d.tp64[si.y];
-    const double q[4] = {q4.x, q4.y, q4.z, q4.w};
-    const double p[3] = {tp.x, tp.y, tp.z};
-    det_centre(q, p, X, x);
-    have_x = true;
-  };
-  const double m = smargin ? smargin[s] : (d.cmargin ? f2d(d.cmargin[si.x]) : margin);
-  long long qc[3];
-  float xf[3];
+  bool have = false;
+  __device__ SphereCentre(const DevState& dd, long long ss, int cc, int tt, const SceneGrid& gg)
+      : d(dd), s(ss), c(cc), ts(tt), g(gg) {}
+  __device__ const double* exact() {
+    if (!have) {
+      double X[3];
+      clump_com(d, c, g, X);
+      const double4_32a q4 = d.cq[c];
+      const double4_32a tp = d.tp64[ts];
+      const double q[4] = {q4.x, q4.y, q4.z, q4.w};
+      const double p[3] = {tp.x, tp.y, tp.z};
+      det_centre(q, p, X, x);
+      have = true;
+    }
+    return x;
+  }
+};
+
+// Is wall w a candidate of the sphere (section 2.2's enlarged geometry: the
+// distance from its centre to the wall at time t within r + m plus the
+// wall's travel over the list's lifetime)?  A float estimate decides when it
+// is clear of the threshold by more than its error bound; otherwise the
+// double distance from the exact centre, as the oracle evaluates it.
+__device__ __forceinline__ bool wall_candidate(const WallDev& w, float tf, float ttf,
+                                               const float xf[3], float rmf, double t,
+                                               double travel_time, double r, double m,
+                                               SphereCentre& ctr) {
+  const float thrf = rmf + w.speed * ttf;
+  const float slack = wall_slack(w, xf);
+  bool exact = false;
+  if (w.type == 3) {
+    // a facet is one-sided: clearly behind its plane, no candidate; within
+    // the estimate's error of the plane, the side is decided exactly
+    float ax = 0.f;
+    for (int k = 0; k < 3; ++k) ax += (xf[k] - (w.pf[k] + w.vf[k] * tf)) * w.nh[k];
+    if (ax < -slack) return false;
+    exact = ax <= slack;
+  }
+  if (!exact) {
+    const float est = wall_distance_est(w, tf, xf, thrf + slack);
+    if (est > thrf + slack) return false;
+    if (est < thrf - slack) return true;
+  }
+  double nw[3];
+  const double thr = __dadd_rn(__dadd_rn(r, m), __dmul_rn(w.speed_d, travel_time));
+  return wall_distance64(w, t, ctr.exact(), nw) <= thr;
+}
+
+// One thread per sphere: detection coordinates, analytic wall candidates, and
+// the counting pass of the bin sort (one count per bin the enlarged box
+// touches).  Mesh facets are found through the bins (k_facet_narrow).
+// Lattice point of sphere s (clamped) and its enlarged lattice radius, with
+// the float estimate xf of its centre.
+__device__ __forceinline__ void sphere_lattice(const DevState& d, const DetectOut& o, long long s,
+                                               int2 si, const SceneGrid& g, double m,
+                                               SphereCentre& ctr, long long qc[3], float xf[3],
+                                               long long& rho) {
   if (!lattice_from_pose(d, s, g, qc, xf)) {
-    exact_centre();
+    const double* x = ctr.exact();
     for (int k = 0; k < 3; ++k) qc[k] = __double2ll_rn(__dmul_rn(__dsub_rn(x[k], g.lo[k]), kDetScale));
   }
   for (int k = 0; k < 3; ++k) {
@@ -206,9 +245,25 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
   }
   // enlarged lattice radius ceil((r + m) 2^24) + 1: from the per template
   // sphere table when every clump has the same margin
-  const long long rho = o.trho ? (long long)o.trho[si.y] : tpl_rho(d.tp64[si.y].w, m);
+  rho = o.trho ? (long long)o.trho[si.y] : tpl_rho(d.tp64[si.y].w, m);
+}
+
+__global__ void k_detect(DevState d, DetectOut o, double margin, const double* __restrict__ smargin,
+                         double t, double travel_time) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns) return;
+  const int2 si = d.sinfo[s];
+  const int2 ci = d.cinfo[si.x];
+  const float ttf = d2f(travel_time);
+  const SceneGrid g = d.grids[ci.y];
+  SphereCentre ctr(d, s, si.x, si.y, g);
+  const double m = smargin ? smargin[s] : (d.cmargin ? f2d(d.cmargin[si.x]) : margin);
+  long long qc[3], rho;
+  float xf[3];
+  sphere_lattice(d, o, s, si, g, m, ctr, qc, xf, rho);
   const float tf = d2f(t);
-  const float rmf = d.tp32[si.y].w + d2f(m);  // r + m for the estimates
+  const double mw = m + o.wall_extra;  // the wall candidates' margin
+  const float rmf = d.tp32[si.y].w + d2f(mw);  // r + m for the estimates
   const int4 dq = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
   o.det[s] = dq;
   {
@@ -223,26 +278,11 @@ __global__ void k_detect(DevState d, DetectOut o, double margin, const double* _
         for (int bx = lo[0]; bx <= hi[0]; ++bx)
           atomicAdd(&o.bin_size[g.key_base + (uint32_t)bz * d01 + (uint32_t)by * d0 + (uint32_t)bx], 1u);
   }
-  // sphere-wall candidates: distance within radius + margin + wall travel
+  // analytic wall candidates: distance within radius + margin + wall travel
   uint32_t mask = 0;
   for (int i = 0; i < g.wall_count; ++i) {
     const WallDev& w = d.walls[d.wall_idx[g.wall_start + i]];
-    // float threshold (r + m) + |v| travel_time; its error is far below slack
-    const float thrf = rmf + w.speed * ttf;
-    const float slack = wall_slack(w, xf);
-    const float est = wall_distance_est(w, tf, xf, thrf + slack);
-    bool in;
-    if (est > thrf + slack) {
-      in = false;
-    } else if (est < thrf - slack) {
-      in = true;
-    } else {
-      exact_centre();
-      double nw[3];
-      const double thr = __dadd_rn(__dadd_rn(d.tp64[si.y].w, m), __dmul_rn(w.speed_d, travel_time));
-      in = wall_distance64(w, t, x, nw) <= thr;
-    }
-    if (in) mask |= 1u << i;
+    if (wall_candidate(w, tf, ttf, xf, rmf, t, travel_time, d.tp64[si.y].w, mw, ctr)) mask |= 1u << i;
   }
   o.wall_mask[s] = mask;
   o.wall_cnt[s] = __popc(mask);
@@ -277,6 +317,262 @@ __global__ void k_bin_scatter(DevState d, DetectOut o) {
     rec.pad = 0u;
     o.rec[o.bin_start[key] + left - 1u] = rec;
   }
+}
+
+// ---------------------------------------------------------------------------
+// mesh facets in the bins
+// ---------------------------------------------------------------------------
+// A facet is registered, like a sphere, in every bin its enlarged box touches:
+// the box of its three vertices at time t, widened by the distance it
+// travels over the list's lifetime and by two lattice units for the
+// roundings.  A sphere within reach of the facet (centre within r + m + that
+// travel of a point of the facet) has an enlarged box [q - rho, q + rho]
+// that meets the facet's box, so the two share a bin; the pair is tested
+// only in the bin of the per-axis max of the two boxes' lower corners (the
+// owning-bin rule of the sphere pairs), so it is found once.
+__device__ __forceinline__ void facet_box(const DevState& d, const WallDev& w, const SceneGrid& g,
+                                          double t, double travel_time, long long lo[3],
+                                          long long hi[3]) {
+  const double reach = __dmul_rn(w.speed_d, travel_time);
+  for (int k = 0; k < 3; ++k) {
+    const double a = w.p[k] + w.vel[k] * t;
+    const double mn = fmin(a, fmin(a + w.e1[k], a + w.e2[k])) - reach;
+    const double mx = fmax(a, fmax(a + w.e1[k], a + w.e2[k])) + reach;
+    constexpr double kQ = (double)((1ll << 30) - 1);
+    const double l = fmin(fmax(floor((mn - g.lo[k]) * kDetScale) - 2.0, -kQ), kQ);
+    const double h = fmin(fmax(ceil((mx - g.lo[k]) * kDetScale) + 2.0, -kQ), kQ);
+    lo[k] = (long long)l;
+    hi[k] = (long long)h;
+  }
+}
+
+// The bins of a facet's enlarged box (clamped to its scene's grid).
+struct FacetBins {
+  int b0[3], b1[3];
+  uint32_t d0, d01, base;
+  long long n;
+  __device__ FacetBins(const DevState& d, const DetectOut& o, int f, double t, double travel_time) {
+    const int w = d.facet_idx[f];
+    const SceneGrid g = d.grids[d.wall_scene[w]];
+    long long lo[3], hi[3];
+    facet_box(d, d.walls[w], g, t, travel_time, lo, hi);
+    for (int k = 0; k < 3; ++k) {
+      b0[k] = clampi(floordiv_ll(lo[k], g.L), g.dims[k] - 1);
+      b1[k] = clampi(floordiv_ll(hi[k], g.L), g.dims[k] - 1);
+    }
+    d0 = (uint32_t)g.dims[0];
+    d01 = d0 * (uint32_t)g.dims[1];
+    base = g.key_base;
+    n = (long long)(b1[0] - b0[0] + 1) * (b1[1] - b0[1] + 1) * (b1[2] - b0[2] + 1);
+  }
+  // the j-th bin (x fastest): key and owning-bin mask
+  __device__ uint32_t key(long long j, uint32_t& mask) const {
+    const long long nx = b1[0] - b0[0] + 1, ny = b1[1] - b0[1] + 1;
+    const int bx = b0[0] + (int)(j % nx), by = b0[1] + (int)((j / nx) % ny),
+              bz = b0[2] + (int)(j / (nx * ny));
+    mask = (bx == b0[0] ? 1u : 0u) | (by == b0[1] ? 2u : 0u) | (bz == b0[2] ? 4u : 0u);
+    return base + (uint32_t)bz * d01 + (uint32_t)by * d0 + (uint32_t)bx;
+  }
+};
+
+// One block per facet, its threads over the facet's bins (a facet of a box
+// face spans a whole layer of bins): counts its registrations (o.fbin_size).
+__global__ void k_facet_count(DevState d, DetectOut o, double t, double travel_time) {
+  const FacetBins fb(d, o, blockIdx.x, t, travel_time);
+  for (long long j = threadIdx.x; j < fb.n; j += blockDim.x) {
+    uint32_t mask;
+    atomicAdd(&o.fbin_size[fb.key(j, mask)], 1u);
+  }
+}
+
+// Scatter pass: every facet registration takes a slot of its bin and stores
+// the bin key, the wall id and the facet's owning-bin mask in that bin.
+__global__ void k_facet_scatter(DevState d, DetectOut o, double t, double travel_time) {
+  const FacetBins fb(d, o, blockIdx.x, t, travel_time);
+  const uint32_t w = (uint32_t)d.facet_idx[blockIdx.x];
+  for (long long j = threadIdx.x; j < fb.n; j += blockDim.x) {
+    uint32_t mask;
+    const uint32_t key = fb.key(j, mask);
+    const uint32_t left = atomicSub(&o.fbin_size[key], 1u);
+    if (left == 0u) {  // more registrations than counted: a broken invariant
+      atomicAdd(&o.fbin_size[key], 1u);
+      atomicOr(d.flags, kFlagBounds);
+      continue;
+    }
+    o.frec[o.fbin_start[key] + left - 1u] = make_uint4(key, w, mask, 0u);
+  }
+}
+
+// Facet narrow phase: one warp per facet registration, its lanes over the
+// sphere registrations of the same bin.  A (sphere, facet) pair owned by the
+// bin is a candidate when the sphere is within reach (wall_candidate); it
+// goes to o.fcand and counts in o.fcnt[sphere].  Candidates past o.fcap are
+// counted but not written (the caller grows the buffer and runs again).
+__global__ void k_facet_narrow(DevState d, DetectOut o, double margin,
+                               const double* __restrict__ smargin, double t, double travel_time) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const float tf = d2f(t), ttf = d2f(travel_time);
+  for (long long e = warp; e < o.nfreg; e += nwarps) {
+    const uint4 fr = o.frec[e];
+    const uint32_t key = fr.x;
+    const WallDev& w = d.walls[fr.y];
+    const uint32_t b0 = o.bin_start[key], b1 = o.bin_start[key + 1];
+    for (uint32_t j = b0 + lane; j < b1; j += 32) {
+      const EntryRec r = o.rec[j];
+      if ((r.mask | fr.z) != 7u) continue;  // another bin owns the pair
+      const int2 si = d.sinfo[r.id];
+      const SceneGrid g = d.grids[d.cinfo[si.x].y];
+      const double m = (smargin ? smargin[r.id] : (d.cmargin ? f2d(d.cmargin[si.x]) : margin)) +
+                       o.wall_extra;
+      // float centre from the lattice point (within 2^-25 m, far below the slack)
+      const float xf[3] = {g.lof[0] + (float)r.qx * (1.f / 16777216.f),
+                           g.lof[1] + (float)r.qy * (1.f / 16777216.f),
+                           g.lof[2] + (float)r.qz * (1.f / 16777216.f)};
+      const float rmf = d.tp32[si.y].w + d2f(m);
+      SphereCentre ctr(d, r.id, si.x, si.y, g);
+      if (!wall_candidate(w, tf, ttf, xf, rmf, t, travel_time, d.tp64[si.y].w, m, ctr)) continue;
+      const unsigned long long slot = atomicAdd(o.d_nf, 1ull);
+      if (slot < o.fcap) o.fcand[slot] = make_uint2(r.id, fr.y);
+      atomicAdd(&o.fcnt[r.id], 1u);
+    }
+  }
+}
+
+// After k_wall_emit: each facet candidate takes a slot after its sphere's
+// analytic walls (o.fcnt, zeroed again, counts the slots taken), then every
+// row that got facets is sorted by wall id (rows are short: insertion sort).
+__global__ void k_facet_emit(DevState d, DetectOut o, long long nf, int* __restrict__ ws,
+                             uint32_t* __restrict__ ww) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const uint2 c = o.fcand[i];
+  const uint32_t k = atomicAdd(&o.fcnt[c.x], 1u);
+  const uint32_t at = o.wall_off[c.x] + __popc(o.wall_mask[c.x]) + k;
+  ws[at] = (int)c.x;
+  ww[at] = c.y;
+}
+
+__global__ void k_sort_wall_rows(DevState d, DetectOut o, uint32_t* __restrict__ ww) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns || o.fcnt[s] == 0u) return;
+  const uint32_t r0 = o.wall_off[s], r1 = o.wall_off[s + 1];
+  for (uint32_t i = r0 + 1; i < r1; ++i) {
+    const uint32_t v = ww[i];
+    uint32_t j = i;
+    while (j > r0 && ww[j - 1] > v) {
+      ww[j] = ww[j - 1];
+      --j;
+    }
+    ww[j] = v;
+  }
+}
+
+// wall_cnt[s] += fcnt[s] (analytic walls plus facets per sphere), and fcnt
+// cleared for k_facet_emit's slots; rows with facets are flagged in fcnt by
+// k_facet_emit again.
+__global__ void k_add_facet_counts(long long ns, DetectOut o) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  o.wall_cnt[s] += o.fcnt[s];
+  o.fcnt[s] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// inner lists filtered from an outer list
+// ---------------------------------------------------------------------------
+// An outer list holds the pairs and wall candidates of a detection with a
+// wider margin m_out, from the lattice points q0 and enlarged radii rho' of
+// its time.  While every sphere's lattice point stays within rho' - rho of
+// q0 (rho the enlarged radius at the list's own margin m), every pair that
+// meets the exact predicate |q_a - q_b|^2 <= (rho_a + rho_b)^2 now met the
+// wider one then (|q0_a - q0_b| <= |q_a - q_b| + |dq_a| + |dq_b| <= rho'_a +
+// rho'_b), so filtering the outer list with the predicate gives exactly the
+// list a fresh detection would give, in the same (a, b) order.  Wall
+// candidates likewise (the outer list's wall threshold covers the travel of
+// the walls over its lifetime and a little more than m_out - m of
+// displacement), each kept by the fresh detection's own test.
+
+// Lattice points and radii at the list's margin (o.det), and the count of
+// spheres that left their allowance around q0 (*bad).
+__global__ void k_lattice_check(DevState d, DetectOut o, double margin, const int4* __restrict__ q0,
+                                unsigned long long* bad) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns) return;
+  const int2 si = d.sinfo[s];
+  const SceneGrid g = d.grids[d.cinfo[si.x].y];
+  SphereCentre ctr(d, s, si.x, si.y, g);
+  long long qc[3], rho;
+  float xf[3];
+  sphere_lattice(d, o, s, si, g, margin, ctr, qc, xf, rho);
+  o.det[s] = make_int4((int)qc[0], (int)qc[1], (int)qc[2], (int)rho);
+  const int4 r0 = q0[s];
+  const long long lim = (long long)r0.w - rho;
+  const long long dx = qc[0] - r0.x, dy = qc[1] - r0.y, dz = qc[2] - r0.z;
+  if (lim < 0 || dx * dx + dy * dy + dz * dz > lim * lim) atomicAdd(bad, 1ull);
+}
+
+// The narrow phase's predicate on two lattice points (box test first, so
+// that the sum of the squares fits 63 bits).
+__device__ __forceinline__ bool lattice_pair(int4 qa, int4 qb) {
+  const long long rr = (long long)qa.w + qb.w;
+  const long long dx = (long long)qb.x - qa.x, dy = (long long)qb.y - qa.y, dz = (long long)qb.z - qa.z;
+  if (dx > rr || -dx > rr || dy > rr || -dy > rr || dz > rr || -dz > rr) return false;
+  return dx * dx + dy * dy + dz * dz <= rr * rr;
+}
+
+// EMIT = false: per sphere a, the partners of its outer row that pass (into
+// o.pair_cnt); EMIT = true: writes them into the inner rows (o.pair_off).
+template <bool EMIT>
+__global__ void k_filter_pairs(DevState d, DetectOut o, ContactList outer, ContactList inner) {
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.ns) return;
+  const int4 qa = o.det[a];
+  uint32_t k = EMIT ? o.pair_off[a] : 0u;
+  const uint32_t j1 = outer.row[a + 1];
+  for (uint32_t j = outer.row[a]; j < j1; ++j) {
+    const uint32_t b = outer.pb[j] & ~kHistFlag;
+    if (!lattice_pair(qa, o.det[b])) continue;
+    if (EMIT) {
+      inner.pa[k] = (int)a;
+      inner.pb[k] = b;
+    }
+    ++k;
+  }
+  if (!EMIT) o.pair_cnt[a] = k;
+}
+
+// The same for each sphere's wall candidates (into o.wall_cnt, then the
+// inner wall rows at o.wall_off).
+template <bool EMIT>
+__global__ void k_filter_walls(DevState d, DetectOut o, ContactList outer, ContactList inner,
+                               double margin, double t, double travel_time) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.ns) return;
+  const uint32_t j0 = outer.wrow[s], j1 = outer.wrow[s + 1];
+  uint32_t k = EMIT ? o.wall_off[s] : 0u;
+  if (j0 < j1) {
+    const int2 si = d.sinfo[s];
+    const SceneGrid g = d.grids[d.cinfo[si.x].y];
+    SphereCentre ctr(d, s, si.x, si.y, g);
+    long long qc[3];
+    float xf[3];
+    lattice_from_pose(d, s, g, qc, xf);
+    const float tf = d2f(t), ttf = d2f(travel_time);
+    const float rmf = d.tp32[si.y].w + d2f(margin);
+    for (uint32_t j = j0; j < j1; ++j) {
+      const uint32_t w = outer.ww[j] & ~kHistFlag;
+      if (!wall_candidate(d.walls[w], tf, ttf, xf, rmf, t, travel_time, d.tp64[si.y].w, margin, ctr))
+        continue;
+      if (EMIT) {
+        inner.ws[k] = (int)s;
+        inner.ww[k] = w;
+      }
+      ++k;
+    }
+  }
+  if (!EMIT) o.wall_cnt[s] = k;
 }
 
 // The sphere id of every registration (inspection).
@@ -691,6 +987,82 @@ void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* 
                       cudaStream_t st) {
   if (d.ns == 0) return;
   { k_wall_emit<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, ws, ww); count_launch(); }
+}
+
+void launch_facet_count(const DevState& d, const DetectOut& o, double t, double travel_time,
+                        cudaStream_t st) {
+  if (d.nfacets == 0) return;
+  k_facet_count<<<(unsigned)d.nfacets, 128, 0, st>>>(d, o, t, travel_time);
+  count_launch();
+}
+
+void launch_facet_scatter(const DevState& d, const DetectOut& o, double t, double travel_time,
+                          cudaStream_t st) {
+  if (d.nfacets == 0) return;
+  k_facet_scatter<<<(unsigned)d.nfacets, 128, 0, st>>>(d, o, t, travel_time);
+  count_launch();
+}
+
+void launch_facet_narrow(const DevState& d, const DetectOut& o, double margin, const double* smargin,
+                         double t, double travel_time, cudaStream_t st) {
+  if (o.nfreg == 0) return;
+  const long long warps = o.nfreg;
+  const long long cap = (long long)device_sms() * 8;  // 8 blocks of 8 warps per SM
+  const long long blocks = std::min((warps + 7) / 8, cap);
+  k_facet_narrow<<<(unsigned)blocks, 256, 0, st>>>(d, o, margin, smargin, t, travel_time);
+  count_launch();
+}
+
+void launch_facet_finish(const DevState& d, const DetectOut& o, long long nf, int* ws, uint32_t* ww,
+                         cudaStream_t st) {
+  if (nf == 0) return;
+  k_facet_emit<<<nblk(nf, 256), 256, 0, st>>>(d, o, nf, ws, ww);
+  count_launch();
+  k_sort_wall_rows<<<nblk(d.ns, 256), 256, 0, st>>>(d, o, ww);
+  count_launch();
+}
+
+void launch_add_facet_counts(const DevState& d, const DetectOut& o, cudaStream_t st) {
+  if (d.ns == 0) return;
+  k_add_facet_counts<<<nblk(d.ns, 256), 256, 0, st>>>(d.ns, o);
+  count_launch();
+}
+
+void launch_lattice_check(const DevState& d, const DetectOut& o, double margin, const int4* q0,
+                          unsigned long long* bad, cudaStream_t st) {
+  if (d.ns == 0) return;
+  if (o.trho) {
+    k_tpl_rho<<<(o.n_tsph + 127) / 128, 128, 0, st>>>(d, margin, o.n_tsph, o.trho);
+    count_launch();
+  }
+  k_lattice_check<<<nblk(d.ns, 128), 128, 0, st>>>(d, o, margin, q0, bad);
+  count_launch();
+}
+
+void launch_filter_count(const DevState& d, const DetectOut& o, const ContactList& outer,
+                         double margin, double t, double travel_time, cudaStream_t st) {
+  if (d.ns == 0) return;
+  k_filter_pairs<false><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, outer, outer);
+  count_launch();
+  k_filter_walls<false><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, outer, outer, margin, t, travel_time);
+  count_launch();
+}
+
+void launch_filter_emit(const DevState& d, const DetectOut& o, const ContactList& outer,
+                        const ContactList& inner, double margin, double t, double travel_time,
+                        cudaStream_t st) {
+  if (d.ns == 0) return;
+  k_filter_pairs<true><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, outer, inner);
+  count_launch();
+  k_filter_walls<true><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, outer, inner, margin, t, travel_time);
+  count_launch();
+}
+
+void launch_hist_pairs(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st) {
+  if (oldl.n > 0 && newl.n > 0) {
+    k_hist_pairs<<<nblk(newl.n, 256), 256, 0, st>>>(oldl, newl, old_ns);
+    count_launch();
+  }
 }
 
 void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns,

@@ -11,6 +11,7 @@ struct DevState {
   int nmat, nwalls;
   double h, g[3];
   double hg[3];             // h * g
+  float hgf[3];             // h * g as float
   float hf;                 // h as float
   // templates
   const int* tpl_off;
@@ -19,8 +20,8 @@ struct DevState {
   const int* tmat;          // per template sphere: material
   const double* tmass;      // per template
   const double* tinert;     // per template, 3 principal moments
-  const float* tmassf;      // the same two tables as float
-  const float* tinertf;
+  const float* tmassf;      // per template {mass, 1 / mass} (float)
+  const float* tinertf;     // per template {I0, I1, I2, 1/I0, 1/I1, 1/I2} (float)
   const float* tpbound;     // per template: max |p| over its spheres
   // clumps
   const int2* cinfo;        // {template, scene}
@@ -53,6 +54,8 @@ struct DevState {
   const WallDev* walls;
   const int* wall_idx;      // per scene wall lists (global wall ids)
   const int* wall_scene;    // scene of each (internal) wall
+  const int* facet_idx;     // the mesh facets (wall ids), registered in the bins at a rebuild
+  int nfacets;
   long long* wfix;          // FP32_VOXEL: wall reference point at the current time, fixed point
                             //   relative to its scene corner (3 per wall)
   double* wpos;             // wall reference point in world coordinates at the current time (3 per wall)
@@ -135,6 +138,16 @@ struct DetectOut {
   int* trho;                // per template sphere: enlarged lattice radius, when all
                             //   clumps share one margin (else NULL: per sphere)
   int n_tsph;               // template spheres
+  // mesh facets in the bins (when the scenes hold facets)
+  uint32_t* fbin_size;      // per bin (+1): facet registrations (counting pass)
+  uint32_t* fbin_start;     // per bin (+1): first facet registration (scan)
+  uint4* frec;              // per facet registration {bin key, wall id, owning-bin mask, 0}
+  long long nfreg;          //   facet registrations (host)
+  uint2* fcand;             // (sphere, facet) candidates, unordered
+  unsigned long long fcap;  //   capacity of fcand
+  unsigned long long* d_nf; //   candidates found (may exceed fcap)
+  uint32_t* fcnt;           // per sphere: facet candidates (then the slots taken)
+  double wall_extra;        // added to the margin in the wall candidates' threshold
 };
 
 struct ContactList {
@@ -174,7 +187,36 @@ void launch_list_rows(const DevState& d, const DetectOut& o, const ContactList& 
                       const ContactList* oldl, long long old_ns, cudaStream_t st);
 void launch_wall_emit(const DevState& d, const DetectOut& o, int* ws, uint32_t* ww,
                       cudaStream_t st);
+// Mesh facets: count (into o.fbin_size, zeroed by the caller) and, after the
+// scan into o.fbin_start, scatter the facets' bin registrations (o.frec);
+// after the sphere bin scatter, the facet narrow phase (candidates into
+// o.fcand, per-sphere counts into o.fcnt, both zeroed by the caller);
+// launch_add_facet_counts adds o.fcnt into o.wall_cnt (rescanned by the
+// caller into o.wall_off); after launch_wall_emit, launch_facet_finish puts
+// the nf candidates into their rows and sorts those rows by wall id.
+void launch_facet_count(const DevState& d, const DetectOut& o, double t, double travel_time,
+                        cudaStream_t st);
+void launch_facet_scatter(const DevState& d, const DetectOut& o, double t, double travel_time,
+                          cudaStream_t st);
+void launch_facet_narrow(const DevState& d, const DetectOut& o, double margin, const double* smargin,
+                         double t, double travel_time, cudaStream_t st);
+void launch_add_facet_counts(const DevState& d, const DetectOut& o, cudaStream_t st);
+void launch_facet_finish(const DevState& d, const DetectOut& o, long long nf, int* ws, uint32_t* ww,
+                         cudaStream_t st);
 void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
+void launch_hist_pairs(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
+// Inner list from an outer list (see dem_detect.cu): the lattice points at
+// margin m into o.det, with the count of spheres past their allowance around
+// q0 in *bad (zeroed by the caller); the per-sphere counts of kept pairs and
+// wall candidates (o.pair_cnt, o.wall_cnt), and after their scans into
+// o.pair_off / o.wall_off, the inner rows themselves.
+void launch_lattice_check(const DevState& d, const DetectOut& o, double margin, const int4* q0,
+                          unsigned long long* bad, cudaStream_t st);
+void launch_filter_count(const DevState& d, const DetectOut& o, const ContactList& outer,
+                         double margin, double t, double travel_time, cudaStream_t st);
+void launch_filter_emit(const DevState& d, const DetectOut& o, const ContactList& outer,
+                        const ContactList& inner, double margin, double t, double travel_time,
+                        cudaStream_t st);
 void launch_audit(const DevState& d, const DetectOut& o, const ContactList& cur, long long n_fresh,
                   const int* fa, const uint32_t* fb, long long nw_fresh, const int* fws,
                   const uint32_t* fww, double t, unsigned long long* d_missed, cudaStream_t st);

@@ -27,6 +27,15 @@ struct Law {
   bool capped;
 };
 
+// Division and square root inside the contact law.  FP64: IEEE.  FP32: the
+// hardware approximations (a reciprocal times the dividend; a square root as
+// x times its reciprocal square root), a few 1e-7 relative, far inside the
+// float path's 1e-5 bar, without the IEEE special-case code of '/' and sqrtf.
+__device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double csqrt_pos(double x) { return sqrt(x); }
+__device__ __forceinline__ float csqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+
 // Eq. (2b)-(4) for one active contact: n from a to b, dn > 0, vrel = velocity
 // of b minus velocity of a at the contact point, u the stored history.
 template <typename T>
@@ -38,15 +47,15 @@ __device__ __forceinline__ Law<T> contact_law(const PairMat<T>& pm, T h, V3<T> n
   const V3<T> up = u + h * vt;                      // Eq. (3)
   const T upn = dot(up, n);
   const V3<T> upt = up - upn * n;
-  const T f = sqrt(Rbar * dn);                      // Eq. (1c)
-  const T sfm = sqrt(f * mbar);
+  const T f = csqrt_pos(Rbar * dn);                 // Eq. (1c)
+  const T sfm = csqrt_pos(f * mbar);
   const T fns = f * pm.kn * dn - pm.cn * sfm * vns; // Eq. (1a) along n
   const V3<T> Ft = (-f * pm.kt) * upt - (pm.ct * sfm) * vt;  // Eq. (1b)
   const T fn = fabs(fns), ft = sqrt(dot(Ft, Ft));
   if (ft > pm.mu * fn) {                            // Eq. (4)
-    const T s = ft > T(0) ? pm.mu * fn / ft : T(0);
+    const T s = ft > T(0) ? cdiv(pm.mu * fn, ft) : T(0);
     const T ul = sqrt(dot(upt, upt));
-    const T us = ul > T(0) ? pm.mu * fn / (f * pm.kt) / ul : T(0);
+    const T us = ul > T(0) ? cdiv(cdiv(pm.mu * fn, f * pm.kt), ul) : T(0);
     r.F = fns * n + s * Ft;
     r.u = us * upt;
     r.capped = true;
@@ -114,6 +123,55 @@ __device__ __forceinline__ V3<float> arm32(const Side32& S) {
           fix_to_float(S.rel[2]) - S.off.z};
 }
 
+// Eq. (1)-(5) for one active sphere pair of the FP32_VOXEL list: forces, the
+// FP64 history update, and the force and moments added to both clumps.
+__device__ __forceinline__ void pair_force32(const DevState& d, ContactList& l, long long i,
+                                             uint32_t b, uint32_t bw, const Side32& A,
+                                             const Side32& B, float fx, float fy, float fz,
+                                             float dist, float dn) {
+    const float inv = __fdividef(1.f, dist);
+    const V3<float> n = {fx * inv, fy * inv, fz * inv};
+    const float4 va = d.mv32[A.owner], wa = d.mw32[A.owner];
+    const float4 vb = d.mv32[B.owner], wb = d.mw32[B.owner];
+    const int ma = d.tmat[A.tsph], mb = d.tmat[B.tsph];
+    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+    if (bw & kHistFlag) {
+      u0 = l.u[i];
+      u1 = l.u[l.cap + i];
+      u2 = l.u[2 * l.cap + i];
+    }
+    const float sa = A.r - 0.5f * dn, sb = B.r - 0.5f * dn;
+    const V3<float> ca = arm32(A) + sa * n;
+    const V3<float> cb = arm32(B) - sb * n;
+    const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
+    const V3<float> vB = V3<float>{vb.x, vb.y, vb.z} + cross(V3<float>{wb.x, wb.y, wb.z}, cb);
+    const PairMat<float> pm = d.pm32[ma * d.nmat + mb];
+    const float Rbar = __fdividef(A.r * B.r, A.r + B.r);
+    const float mbar = __fdividef(va.w * vb.w, va.w + vb.w);
+    const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vB - vA,
+                                              V3<float>{d2f(u0), d2f(u1), d2f(u2)}, Rbar, mbar);
+    // tangential history: FP64 accumulation of the float increment
+    if (law.capped) {
+      u0 = f2d(law.u.x); u1 = f2d(law.u.y); u2 = f2d(law.u.z);
+    } else {
+      u0 += f2d(law.u.x); u1 += f2d(law.u.y); u2 += f2d(law.u.z);
+    }
+    l.u[i] = u0;
+    l.u[l.cap + i] = u1;
+    l.u[2 * l.cap + i] = u2;
+    if (!(bw & kHistFlag)) l.pb[i] = b | kHistFlag;
+    const V3<float> F = law.F;
+    const V3<float> Ta = -1.f * cross(ca, F), Tb = cross(cb, F);
+    if (d.det_off) {
+      d.det_pair32[3 * i] = make_float4(F.x, F.y, F.z, 0.f);
+      d.det_pair32[3 * i + 1] = make_float4(Ta.x, Ta.y, Ta.z, 0.f);
+      d.det_pair32[3 * i + 2] = make_float4(Tb.x, Tb.y, Tb.z, 0.f);
+    } else {
+      add_clump32(d.acc32, B.owner, F, Tb);
+      add_clump32(d.acc32, A.owner, -1.f * F, Ta);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int count_active) {
   if (halted(d)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -146,8 +204,8 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
       const ff s = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
       const ff rho = two_sum(A.r, B.r);
       const ff diff = ff_sub(ff_mul(rho, rho), s);
-      dist = sqrtf(s.h);
-      dn = ff_to_float(diff) / (ff_to_float(rho) + dist);
+      dist = csqrt_pos(s.h);
+      dn = __fdividef(ff_to_float(diff), ff_to_float(rho) + dist);
     }
     const bool active = dn > 0.f;
     if (count_active) warp_count(active, d.counters);
@@ -163,48 +221,11 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         d.det_pair32[3 * i] = z; d.det_pair32[3 * i + 1] = z; d.det_pair32[3 * i + 2] = z;
       }
-      continue;
-    }
-    const V3<float> n = {fx / dist, fy / dist, fz / dist};
-    const float4 va = d.mv32[A.owner], wa = d.mw32[A.owner];
-    const float4 vb = d.mv32[B.owner], wb = d.mw32[B.owner];
-    const int ma = d.tmat[A.tsph], mb = d.tmat[B.tsph];
-    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
-    if (bw & kHistFlag) {
-      u0 = l.u[i];
-      u1 = l.u[l.cap + i];
-      u2 = l.u[2 * l.cap + i];
-    }
-    const float sa = A.r - 0.5f * dn, sb = B.r - 0.5f * dn;
-    const V3<float> ca = arm32(A) + sa * n;
-    const V3<float> cb = arm32(B) - sb * n;
-    const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
-    const V3<float> vB = V3<float>{vb.x, vb.y, vb.z} + cross(V3<float>{wb.x, wb.y, wb.z}, cb);
-    const PairMat<float> pm = d.pm32[ma * d.nmat + mb];
-    const float Rbar = A.r * B.r / (A.r + B.r);
-    const float mbar = va.w * vb.w / (va.w + vb.w);
-    const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vB - vA,
-                                              V3<float>{d2f(u0), d2f(u1), d2f(u2)}, Rbar, mbar);
-    // tangential history: FP64 accumulation of the float increment
-    if (law.capped) {
-      u0 = f2d(law.u.x); u1 = f2d(law.u.y); u2 = f2d(law.u.z);
     } else {
-      u0 += f2d(law.u.x); u1 += f2d(law.u.y); u2 += f2d(law.u.z);
+      pair_force32(d, l, i, b, bw, A, B, fx, fy, fz, dist, dn);
     }
-    l.u[i] = u0;
-    l.u[l.cap + i] = u1;
-    l.u[2 * l.cap + i] = u2;
-    if (!(bw & kHistFlag)) l.pb[i] = b | kHistFlag;
-    const V3<float> F = law.F;
-    const V3<float> Ta = -1.f * cross(ca, F), Tb = cross(cb, F);
-    if (d.det_off) {
-      d.det_pair32[3 * i] = make_float4(F.x, F.y, F.z, 0.f);
-      d.det_pair32[3 * i + 1] = make_float4(Ta.x, Ta.y, Ta.z, 0.f);
-      d.det_pair32[3 * i + 2] = make_float4(Tb.x, Tb.y, Tb.z, 0.f);
-    } else {
-      add_clump32(d.acc32, B.owner, F, Tb);
-      add_clump32(d.acc32, A.owner, -1.f * F, Ta);
-    }
+    // the lanes of a warp take the next pair together
+    __syncwarp();
   }
 }
 
@@ -270,13 +291,16 @@ __global__ void __launch_bounds__(256) k_pairs64(DevState d, ContactList l, int 
 // ---------------------------------------------------------------------------
 // Net force on each wall: summed per block in shared memory, then one global
 // double atomic per wall component per block (all contacts of a wall would
-// otherwise serialise on the same three addresses).
+// otherwise serialise on the same three addresses).  Walls past the first
+// kMaxBlockWalls (the facets of large meshes, each touched by few spheres)
+// add straight to global memory.
 constexpr int kMaxBlockWalls = 256;
 
 __device__ __forceinline__ void wall_force_flush(const DevState& d, const float* s_wf,
                                                  const float* s_wt) {
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * d.nwalls; i += blockDim.x) {
+  const int nw = d.nwalls < kMaxBlockWalls ? d.nwalls : kMaxBlockWalls;
+  for (int i = threadIdx.x; i < 3 * nw; i += blockDim.x) {
     if (s_wf[i] != 0.f) atomicAdd(d.wforce + i, (double)s_wf[i]);
     if (s_wt[i] != 0.f) atomicAdd(d.wtorque + i, (double)s_wt[i]);
   }
@@ -286,7 +310,6 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
   if (halted(d)) return;
   __shared__ float s_wf[3 * kMaxBlockWalls];  // force on each wall
   __shared__ float s_wt[3 * kMaxBlockWalls];  // its moment about the wall's reference point
-  const bool shared_wf = d.nwalls <= kMaxBlockWalls;
   for (int i = threadIdx.x; i < 3 * kMaxBlockWalls; i += blockDim.x) s_wf[i] = s_wt[i] = 0.f;
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -344,7 +367,7 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
     const V3<float> rw = V3<float>{fix_to_float(S.P[0] - wf[0]), fix_to_float(S.P[1] - wf[1]),
                                    fix_to_float(S.P[2] - wf[2])} + (S.r - 0.5f * dn) * n;
     const V3<float> tw = cross(rw, law.F);
-    if (shared_wf) {
+    if (w < (uint32_t)kMaxBlockWalls) {
       atomicAdd(&s_wf[3 * w], law.F.x);
       atomicAdd(&s_wf[3 * w + 1], law.F.y);
       atomicAdd(&s_wf[3 * w + 2], law.F.z);
@@ -362,7 +385,7 @@ __global__ void k_walls32(DevState d, ContactList l, int count_active) {
       atomicAdd(mw + 2, (double)tw.z);
     }
   }
-  if (shared_wf) wall_force_flush(d, s_wf, s_wt);
+  wall_force_flush(d, s_wf, s_wt);
 }
 
 __global__ void k_walls64(DevState d, ContactList l, int count_active) {
@@ -549,25 +572,41 @@ __global__ void __launch_bounds__(kUpd) k_update64(DevState d, int integrate, fl
   }
 }
 
-// FP32_VOXEL mode: one thread per clump integrates Eq. (5) and then writes
-// the pose records of the clump's own spheres (consecutive in memory), from a
-// float-float rotation matrix held in registers.  No block barrier or shared
-// memory: every warp runs at its own pace.  B (64, 128 or 256 clumps per
-// block) is a launch shape the tile autotuner picks.
-template <int B>
-__global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float margin,
-                                                int check_cert) {
-  if (integrate && halted(d)) return;
-  const long long c = (long long)blockIdx.x * B + threadIdx.x;
-  {
-    if (c >= d.ncl) return;
+// FP32_VOXEL mode, in two phases per warp of 32 clumps.  Phase 1: one thread
+// per clump integrates Eq. (5) and forms its float-float rotation matrix;
+// the matrix, the clump's offset in fixed point and its sphere range go to
+// the warp's slice of shared memory.  Phase 2: the warp's lanes take the
+// warp's spheres in order (consecutive records: coalesced 16-byte stores),
+// each finding its clump by a binary search of the sphere ranges, and write
+// the pose records.  Only __syncwarp between the phases; no block barrier.
+// INTEG = false recomputes poses and mirrors from the state; CERT adds the
+// displacement certificate.  B (64, 128 or 256 clumps per block) is a launch
+// shape the tile autotuner picks.
+struct WarpPoses {
+  float Rh[9][32], Rl[9][32];  // rotation matrix (float-float), [entry][lane]
+  int off[3][32];              // offset in the voxel, 2^-44 m units
+  int s0[33];                  // first sphere of each clump; s0[n] = end of the warp's spheres
+  int t0[32];                  // first template sphere of each clump's template
+};
+
+template <int B, bool INTEG, bool CERT>
+__global__ void __launch_bounds__(B) k_update32(DevState d, float margin) {
+  if (INTEG && halted(d)) return;
+  __shared__ WarpPoses sh[B / 32];
+  const int lane = threadIdx.x & 31;
+  WarpPoses& wp = sh[threadIdx.x >> 5];
+  const long long cw0 = (long long)blockIdx.x * B + (threadIdx.x & ~31);  // the warp's first clump
+  if (cw0 >= d.ncl) return;  // the whole warp
+  const int nw = (int)(d.ncl - cw0 < 32 ? d.ncl - cw0 : 32);
+  const long long c = cw0 + lane;
+  if (lane < nw) {
     // every global load of the clump is issued first (one memory round trip)
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, ref_o = a0, ref_qv = a0;
     int4 ref_v = make_int4(0, 0, 0, 0);
-    if (integrate) {
+    if (INTEG) {
       a0 = *reinterpret_cast<const float4*>(d.acc32 + 8 * c);
       a1 = *reinterpret_cast<const float4*>(d.acc32 + 8 * c + 4);
-      if (check_cert) {
+      if (CERT) {
         ref_v = d.ref_vox[c];
         ref_o = d.ref_off[c];
         ref_qv = d.ref_q[c];
@@ -578,29 +617,31 @@ __global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float
     float4 off = d.coff[c];
     double4_32a q4 = d.cq[c], v, w;
     load_vel(d.cvw + c, v, w);
-    const float mass = d.tmassf[tpl];
+    const float2 mim = *reinterpret_cast<const float2*>(d.tmassf + 2 * tpl);  // m, 1/m
+    const float mass = mim.x;
     // orientation as float-float; integrating needs only the high parts of
     // the old one (the rotation matrix is built from the new orientation)
     ff qw, qx, qy, qz;
     V3<float> wf_new;  // the new angular velocity as float (integrating)
     float vf_new[3];   // the new velocity as float (integrating)
-    if (integrate) {
+    if (INTEG) {
       qw = {d2f(q4.x), 0.f}; qx = {d2f(q4.y), 0.f}; qy = {d2f(q4.z), 0.f}; qz = {d2f(q4.w), 0.f};
     } else {
       qw = ff_from_double(q4.x); qx = ff_from_double(q4.y); qy = ff_from_double(q4.z);
       qz = ff_from_double(q4.w);
     }
-    if (integrate) {
+    if (INTEG) {
       float* acc = d.acc32 + 8 * c;
       *reinterpret_cast<float4*>(acc) = make_float4(0.f, 0.f, 0.f, 0.f);
       *reinterpret_cast<float4*>(acc + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
       const float hf = d.hf;
-      const float im = 1.f / mass;
+      const float im = mim.y;
       if (d.alast) d.alast[c] = sqrtf(a0.x * a0.x + a0.y * a0.y + a0.z * a0.z) * im;
-      // Eq. (5a): double velocity, accumulating h*F/m (float) and h*g (double)
-      v.x = (v.x + d.hg[0]) + f2d(hf * (a0.x * im));
-      v.y = (v.y + d.hg[1]) + f2d(hf * (a0.y * im));
-      v.z = (v.z + d.hg[2]) + f2d(hf * (a0.z * im));
+      // Eq. (5a): double velocity, accumulating the float increment
+      // h F/m + h g (one double addition per component)
+      v.x += f2d(fmaf(hf, a0.x * im, d.hgf[0]));
+      v.y += f2d(fmaf(hf, a0.y * im, d.hgf[1]));
+      v.z += f2d(fmaf(hf, a0.z * im, d.hgf[2]));
       // position: the offset increment h*v carries 1e-7 relative error, far
       // below the 2^-44 m resolution of the offset itself
       const float vx_f = d2f(v.x), vy_f = d2f(v.y), vz_f = d2f(v.z);
@@ -622,12 +663,11 @@ __global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float
       quat_to_mat(qw.h, qx.h, qy.h, qz.h, Rf);
       const V3<float> tb = mat_tmul(Rf, V3<float>{a0.w, a1.x, a1.y});
       const V3<float> wf = {d2f(w.x), d2f(w.y), d2f(w.z)};
-      const float I0 = d.tinertf[3 * tpl], I1 = d.tinertf[3 * tpl + 1],
-                  I2 = d.tinertf[3 * tpl + 2];
-      const V3<float> gy = cross(wf, V3<float>{I0 * wf.x, I1 * wf.y, I2 * wf.z});
-      w.x += f2d(hf * ((tb.x - gy.x) / I0));
-      w.y += f2d(hf * ((tb.y - gy.y) / I1));
-      w.z += f2d(hf * ((tb.z - gy.z) / I2));
+      const float* It = d.tinertf + 6 * tpl;  // I0, I1, I2 and their inverses
+      const V3<float> gy = cross(wf, V3<float>{It[0] * wf.x, It[1] * wf.y, It[2] * wf.z});
+      w.x += f2d(hf * ((tb.x - gy.x) * It[3]));
+      w.y += f2d(hf * ((tb.y - gy.y) * It[4]));
+      w.z += f2d(hf * ((tb.z - gy.z) * It[5]));
       // orientation: q <- q * exp(h w / 2); the increment q * (dq - 1) in
       // float, accumulated in double; then |q| is restored to one with a
       // first-order correction whose size is measured in float-float
@@ -664,7 +704,7 @@ __global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float
         atomicOr(d.flags, kFlagNonFinite);
       d.cvox[c] = vox; d.coff[c] = off; d.cq[c] = q4;
       store_vel(d.cvw + c, v, w);
-      if (check_cert) {
+      if (CERT) {
         const int4 v0 = ref_v;
         const float4 o0 = ref_o;
         const float dx = (float)(vox.x - v0.x) * kV + (off.x - o0.x);
@@ -704,36 +744,58 @@ __global__ void __launch_bounds__(B) k_update32(DevState d, int integrate, float
     R[8] = ff_sub(one, ff_scale2(ff_add(xx, yy), 2.f));
     float Rf[9];
     for (int k = 0; k < 9; ++k) Rf[k] = R[k].h;
-    if (!integrate) {
+    if (!INTEG) {
       wf_new = {d2f(w.x), d2f(w.y), d2f(w.z)};
       vf_new[0] = d2f(v.x); vf_new[1] = d2f(v.y); vf_new[2] = d2f(v.z);
     }
     const V3<float> ww = mat_mul(Rf, wf_new);
     d.mv32[c] = make_float4(vf_new[0], vf_new[1], vf_new[2], mass);
     d.mw32[c] = make_float4(ww.x, ww.y, ww.z, 0.f);
-    // pose records: x_rel = round(R p .h) + round(off) + round(R p .l), each
-    // term in 2^-44 m units (|off| <= 2^-21 m and |R p .l| <= 2^-31 m fit a
-    // 32-bit integer): three roundings of half a unit plus the float-float
-    // error of R p (a small fraction of a unit) keep the centre within 2
-    // units of the exact one, the bound the detection relies on
-    const int offx = __float2int_rn(off.x * kMToFix), offy = __float2int_rn(off.y * kMToFix),
-              offz = __float2int_rn(off.z * kMToFix);
-    const int s0 = d.csph[c], s1 = d.csph[c + 1];
-    const float4* tp = d.tp32 + d.tpl_off[tpl];
-    for (int s = s0; s < s1; ++s) {
-      const float4 t4 = tp[s - s0];
-      const float p[3] = {t4.x, t4.y, t4.z};
-      ff rel[3];
-      for (int i = 0; i < 3; ++i) {
-        ff acc = ff_mulf(R[3 * i], p[0]);
-        acc = ff_add(acc, ff_mulf(R[3 * i + 1], p[1]));
-        acc = ff_add(acc, ff_mulf(R[3 * i + 2], p[2]));
-        rel[i] = acc;
-      }
-      d.srec32[s] = pack_rel(f2ll_rn(rel[0].h * kMToFix) + offx + __float2int_rn(rel[0].l * kMToFix),
-                             f2ll_rn(rel[1].h * kMToFix) + offy + __float2int_rn(rel[1].l * kMToFix),
-                             f2ll_rn(rel[2].h * kMToFix) + offz + __float2int_rn(rel[2].l * kMToFix));
+    for (int k = 0; k < 9; ++k) {
+      wp.Rh[k][lane] = R[k].h;
+      wp.Rl[k][lane] = R[k].l;
     }
+    wp.off[0][lane] = __float2int_rn(off.x * kMToFix);
+    wp.off[1][lane] = __float2int_rn(off.y * kMToFix);
+    wp.off[2][lane] = __float2int_rn(off.z * kMToFix);
+    wp.s0[lane] = d.csph[c];
+    if (lane == nw - 1) wp.s0[nw] = d.csph[c + 1];
+    wp.t0[lane] = d.tpl_off[tpl];
+  }
+  __syncwarp();
+  // pose records: x_rel = round(R p .h) + round(off) + round(R p .l), each
+  // term in 2^-44 m units (|off| <= 2^-21 m and |R p .l| <= 2^-31 m fit a
+  // 32-bit integer): three roundings of half a unit plus the float-float
+  // error of R p (a small fraction of a unit) keep the centre within 2 units
+  // of the exact one, the bound the detection relies on
+  const int S0 = wp.s0[0], S1 = wp.s0[nw];
+  for (int j = S0 + lane; j < S1; j += 32) {
+    int lo = 0, hi = nw - 1;  // the clump k of sphere j: the last k with s0[k] <= j
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (wp.s0[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    const int k = lo;
+    const float4 t4 = d.tp32[wp.t0[k] + (j - wp.s0[k])];
+    const float p[3] = {t4.x, t4.y, t4.z};
+    long long X[3];
+    for (int i = 0; i < 3; ++i) {
+      // row i of R p in float-float: the three products of the high parts
+      // exactly (TwoProduct), summed with TwoSum; their errors, the rounding
+      // errors of the sums and the low parts' products, all below 2^-23 of
+      // the result, summed in float
+      const ff p0 = two_prod(wp.Rh[3 * i][k], p[0]);
+      const ff p1 = two_prod(wp.Rh[3 * i + 1][k], p[1]);
+      const ff p2 = two_prod(wp.Rh[3 * i + 2][k], p[2]);
+      const ff s01 = two_sum(p0.h, p1.h);
+      const ff s = two_sum(s01.h, p2.h);
+      float lo = fmaf(wp.Rl[3 * i][k], p[0], (p0.l + p1.l) + (p2.l + (s01.l + s.l)));
+      lo = fmaf(wp.Rl[3 * i + 1][k], p[1], lo);
+      lo = fmaf(wp.Rl[3 * i + 2][k], p[2], lo);
+      const ff acc = fast_two_sum(s.h, lo);
+      X[i] = f2ll_rn(acc.h * kMToFix) + wp.off[i][k] + __float2int_rn(acc.l * kMToFix);
+    }
+    d.srec32[j] = pack_rel(X[0], X[1], X[2]);
   }
 }
 
@@ -1015,6 +1077,15 @@ void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_
     { k_walls32<<<grid, 128, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
 }
 
+template <int B>
+void launch_update32(const DevState& d, bool integrate, bool cert, float margin, cudaStream_t st) {
+  const unsigned g = nblk(d.ncl, B);
+  if (!integrate) k_update32<B, false, false><<<g, B, 0, st>>>(d, margin);
+  else if (cert) k_update32<B, true, true><<<g, B, 0, st>>>(d, margin);
+  else k_update32<B, true, false><<<g, B, 0, st>>>(d, margin);
+  count_launch();
+}
+
 // integrate: one explicit step of every clump, then the device step counter
 // advances and the walls move to the new time.  Otherwise the sphere poses
 // and mirrors are recomputed from the state and the walls are placed at
@@ -1026,14 +1097,11 @@ void launch_update(const DevState& d, bool integrate, long long step, double mar
       { k_update64<<<nblk(d.ncl, kUpd), kUpd, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
                                                       check_cert ? 1 : 0); count_launch(); }
     else if (d.upd_block == 64)
-      { k_update32<64><<<nblk(d.ncl, 64), 64, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
-                                                     check_cert ? 1 : 0); count_launch(); }
+      launch_update32<64>(d, integrate, check_cert, (float)margin, st);
     else if (d.upd_block == 256)
-      { k_update32<256><<<nblk(d.ncl, 256), 256, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
-                                                        check_cert ? 1 : 0); count_launch(); }
+      launch_update32<256>(d, integrate, check_cert, (float)margin, st);
     else
-      { k_update32<128><<<nblk(d.ncl, 128), 128, 0, st>>>(d, integrate ? 1 : 0, (float)margin,
-                                                        check_cert ? 1 : 0); count_launch(); }
+      launch_update32<128>(d, integrate, check_cert, (float)margin, st);
   }
   if (integrate) {
     k_walls_advance<<<1, 256, 0, st>>>(d);

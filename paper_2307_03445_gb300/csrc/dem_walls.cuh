@@ -8,13 +8,19 @@ __device__ __forceinline__ double dot3d(const double a[3], const double b[3]) {
   return __dadd_rn(__dadd_rn(__dmul_rn(a[0], b[0]), __dmul_rn(a[1], b[1])), __dmul_rn(a[2], b[2]));
 }
 
-// Mesh facet, FP64: dd = x - p(t) with p the first vertex.  Inside the face
-// region (barycentric coordinates of the projection from the normal
-// equations of the edge vectors all >= 0) the signed distance to the plane;
-// otherwise the unsigned distance to the nearest of the edges p->b, p->c,
-// b->c (first wins a tie), the foot at the clamped perpendicular parameter.
+// Mesh facet, FP64: dd = x - p(t) with p the first vertex.  A facet is
+// one-sided: a centre behind its plane (dd.n < 0) does not touch it (+inf).
+// In front: inside the face region (barycentric coordinates of the
+// projection from the normal equations of the edge vectors all >= 0) the
+// distance to the plane; otherwise the distance to the nearest of the edges
+// p->b, p->c, b->c (first wins a tie), the foot at the clamped perpendicular
+// parameter.
 __device__ __forceinline__ double facet_distance64(const WallDev& w, const double dd[3], double nw[3]) {
   const double ax = dot3d(dd, w.n);
+  if (ax < 0.0) {
+    for (int k = 0; k < 3; ++k) nw[k] = w.n[k];
+    return __longlong_as_double(0x7ff0000000000000ll);  // +inf
+  }
   const double d00 = dot3d(w.e1, w.e1), d01 = dot3d(w.e1, w.e2), d11 = dot3d(w.e2, w.e2);
   const double b0 = dot3d(dd, w.e1), b1 = dot3d(dd, w.e2);
   const double den = __dsub_rn(__dmul_rn(d00, d11), __dmul_rn(d01, d01));
@@ -125,8 +131,14 @@ __device__ __forceinline__ float wall_geom32(const WallDev& w, const long long w
     dist = ax;
     nw = {w.nh[0], w.nh[1], w.nh[2]};
   } else if (w.type == 3) {
-    // mesh facet: the region is classified in float (the distance is
-    // continuous across the regions' borders), the distance in float-float
+    // mesh facet: one-sided (a centre behind its plane does not touch it);
+    // in front the region is classified in float (the distance is
+    // continuous across the regions' borders there), the distance in
+    // float-float
+    if (ax.h < 0.f || (ax.h == 0.f && ax.l < 0.f)) {
+      n = {-w.nh[0], -w.nh[1], -w.nh[2]};
+      return -1.f;
+    }
     const V3<float> df = {d[0].h, d[1].h, d[2].h};
     const V3<float> e1 = {w.e1h[0], w.e1h[1], w.e1h[2]}, e2 = {w.e2h[0], w.e2h[1], w.e2h[2]};
     const float d00 = dot(e1, e1), d01 = dot(e1, e2), d11 = dot(e2, e2);

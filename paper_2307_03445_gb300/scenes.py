@@ -229,6 +229,39 @@ def funnel_mesh(cx, cy, z0, z1, r0, r1, nseg, material=0):
     return out
 
 
+def cone_mesh(tip, half_angle, height, nseg, nrings, vel=(0.0, 0.0, 0.0), material=0, base=True):
+    """A cone with its tip at `tip`, its axis along +z and its flat base
+    (radius height * tan(half_angle)) at tip + height, as facets with the
+    grains outside: nseg around, nrings bands along the side (a fan at the
+    tip), and (base=True) a fan of nseg over the base; nseg (2 nrings - 1)
+    side facets plus nseg base facets."""
+    tx, ty, tz = (float(v) for v in tip)
+    rb = height * math.tan(half_angle)
+    ang = 2 * np.pi * np.arange(nseg) / nseg
+    ring = lambda k: [(tx + rb * k / nrings * np.cos(t), ty + rb * k / nrings * np.sin(t),
+                       tz + height * k / nrings) for t in ang]
+    v = [(tx, ty, tz)]
+    for k in range(1, nrings + 1):
+        v += ring(k)
+    base_c = len(v)
+    v.append((tx, ty, tz + height))
+    at = lambda k, i: 1 + (k - 1) * nseg + (i % nseg)  # vertex i of ring k >= 1
+    side = [(0, at(1, i), at(1, i + 1)) for i in range(nseg)]
+    for k in range(1, nrings):
+        for i in range(nseg):
+            side += [(at(k, i), at(k + 1, i), at(k + 1, i + 1)), (at(k, i), at(k + 1, i + 1), at(k, i + 1))]
+    out = []
+    vv = np.asarray(v, float)
+    for f in side:
+        c = vv[list(f)].mean(axis=0)
+        outward = c + np.array([c[0] - tx, c[1] - ty, 0.0])  # radially away from the axis
+        out.append(mesh(v, [f], outward, vel=vel, material=material)[0])
+    for i in range(nseg if base else 0):
+        out.append(mesh(v, [(base_c, at(nrings, i), at(nrings, i + 1))],
+                        (tx, ty, tz + 2.0 * height), vel=vel, material=material)[0])
+    return out
+
+
 def box_walls(x0, x1, y0, y1, z0, top=None, top_vel=(0.0, 0.0, 0.0)):
     w = [plane((0, 0, z0), (0, 0, 1)), plane((x0, 0, 0), (1, 0, 0)), plane((x1, 0, 0), (-1, 0, 0)),
          plane((0, y0, 0), (0, 1, 0)), plane((0, y1, 0), (0, -1, 0))]
