@@ -290,35 +290,90 @@ def _timed_steps(sim, stream, n):
     return e0.elapsed_time(e1)
 
 
-def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log):
-    """The learned rebuild rule on the same bed, from the current state:
-    traces of the plain rule, training on the GPU, then `steps` steps timed
-    (halt mode: a failed certificate ends an interval early), and an exact
-    audit of the final list."""
+def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, start_state=None,
+                 intervals=4, interval=80, audited=80):
+    """The learned rebuild rule on the same bed: traces of the plain rule and
+    training on the GPU (untimed), then `intervals` whole intervals of
+    `interval` steps timed with the learned rule and, from the same state,
+    the same number of steps with the plain rule (halt mode: a failed
+    certificate ends an interval early).  Then `audited` more learned steps,
+    each followed by the exact check against a fresh zero-margin detection
+    (missed contacts summed over all of them)."""
     t0 = time.time()
+    if start_state is None:
+        start_state = sim.state()
     x, t = sim.trace(2, 240, LEARN_CAND, cap=1 << 24)
     reg = dem.Regressor(device=sim_device(sim))
     loss = reg.train(x, t, steps=800, batch=8192, lr=2e-3, seed=1)
     log(f"learned form: {len(x)} trace samples, loss {loss:.4f}, {time.time() - t0:.1f} s")
-    # interval x safety stays inside the traced window, where lifetimes are not capped
-    sim.set_learned_policy(reg, interval=80, safety=2.0, candidates=LEARN_CAND)
-    sim.reset_stats()
+    n = intervals * interval
     sim.set_timing(True)  # events only: the steps are not serialised
-    ms = _timed_steps(sim, stream, steps)
+    # the plain rule from the start state over the same steps
+    sim.set_state(*start_state)
+    sim.reset_stats()
+    ms_plain = _timed_steps(sim, stream, n)
+    st_plain = sim.stats()
+    # the learned rule from the same state; interval x safety stays inside
+    # the traced window, where lifetimes are not capped
+    sim.set_state(*start_state)
+    sim.set_learned_policy(reg, interval=interval, safety=2.0, candidates=LEARN_CAND)
+    sim.reset_stats()
+    ms = _timed_steps(sim, stream, n)
     st = sim.stats()
-    missed = sim.audit()
+    sim.set_timing(False)
+    missed = 0
+    for _ in range(audited):
+        sim.step(1)
+        missed += sim.audit()
     sim.set_learned_policy(None)
     reg.close()
-    pair_steps_plain = plain_st["pair_steps"] / max(1, plain_st["steps"])
-    return {"value": ns * steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / steps,
-            "vs_plain": plain_ms_step / (ms / steps), "rebuilds": st["rebuilds"],
+    return {"value": ns * n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / n,
+            "steps": n, "intervals": intervals, "plain_ms_per_step_same_steps": ms_plain / n,
+            "vs_plain": ms_plain / ms, "rebuilds": st["rebuilds"],
             "early_rebuilds": st["early_rebuilds"], "rollbacks": st["rollbacks"],
             "listed_per_step": st["pair_steps"] / max(1, st["steps"]),
-            "listed_per_step_plain": pair_steps_plain, "missed_contacts": missed,
+            "listed_per_step_plain": st_plain["pair_steps"] / max(1, st_plain["steps"]),
+            "rebuilds_plain": st_plain["rebuilds"],
+            "missed_contacts": missed, "audited_steps": audited,
             "ms_predict_per_interval": st["ms_predict"] / max(1, st["rebuilds"]),
             "ms_rebuild_per_interval": st["ms_detect"] / max(1, st["rebuilds"]),
-            "rule": "6->3x64->1 MLP (BF16 weights) per bin, candidates 1-32 um, target "
-                    "interval 80 x 2.0, halt on certificate; trained on 2 x 240-step traces"}
+            "rule": f"6->3x64->1 MLP (BF16 weights) per bin, candidates 1-32 um, target "
+                    f"interval {interval} x 2.0, halt on certificate; trained on 2 x 240-step "
+                    f"traces; timed over {intervals} whole intervals; exact audit after each of "
+                    f"{audited} further steps"}
+
+
+def outer_form(sim, stream, ns, log, factor=3.0, n_inner=4, cycles=4):
+    """The two-level contact list on the same bed: an outer list at factor x
+    the margin serves n_inner rebuilds (each a filter of the outer list that
+    gives the fresh detection's list).  Timed over whole outer cycles
+    (cycles x n_inner x K steps), against the plain rule over the same steps
+    from the same state; both with per-phase events."""
+    s0 = sim.state()
+    n = cycles * n_inner * K_REBUILD
+    sim.set_timing(True)
+    sim.set_state(*s0)
+    sim.reset_stats()
+    ms_plain = _timed_steps(sim, stream, n)
+    st_plain = sim.stats()
+    sim.set_state(*s0)
+    sim.set_outer_list(factor, n_inner)
+    sim.step(n_inner * K_REBUILD)  # the first outer list
+    sim.set_state(*s0)
+    sim.reset_stats()
+    ms = _timed_steps(sim, stream, n)
+    st = sim.stats()
+    sim.set_outer_list(factor, 0)
+    sim.set_timing(False)
+    log(f"outer list: {ms / n:.4f} ms/step vs plain {ms_plain / n:.4f}")
+    return {"value": ns * n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / n, "steps": n,
+            "plain_ms_per_step_same_steps": ms_plain / n, "vs_plain": ms_plain / ms,
+            "rebuilds": st["rebuilds"], "outer_rebuilds": st["outer_rebuilds"],
+            "rebuild_ms_per_rebuild": st["ms_detect"] / max(1, st["rebuilds"]),
+            "plain_rebuild_ms_per_rebuild": st_plain["ms_detect"] / max(1, st_plain["rebuilds"]),
+            "rule": f"outer list at {factor} x the margin serving {n_inner} rebuilds of the "
+                    f"plain rule (each list exactly the fresh detection's); timed over {cycles} "
+                    f"whole outer cycles"}
 
 
 def sim_device(sim):
@@ -327,7 +382,7 @@ def sim_device(sim):
     return torch.cuda.current_device()
 
 
-def batched_form(dem, steps, device, log):
+def batched_form(dem, steps, device, log, warmup=K_REBUILD):
     """The batched sweep (64 box-settling scenes of 5,000-100,000 clumps, own
     friction and templates): one context with graph-captured steps against
     the same scenes run one context after another."""
@@ -346,11 +401,13 @@ def batched_form(dem, steps, device, log):
                          precision=dem.DEM_FP32_VOXEL, device=device, stream=stream.cuda_stream,
                          extra_scenes=rest)
     sim.set_graphs(True)
-    sim.step(K_REBUILD)
+    sim.step(warmup)
     fb, _ = sim.autotune_bins(BIN_FACTORS, reps=1)
     tiles = sim.autotune_tiles(steps=6, reps=1)
-    sim.step(K_REBUILD)
+    sim.step(warmup)
+    sim.reset_stats()
     ms_b = _timed_steps(sim, stream, steps)
+    launches = sim.stats()["launches"]
     sim.close()
     ms_s = 0.0
     for p in parts:
@@ -366,10 +423,156 @@ def batched_form(dem, steps, device, log):
     return {"value": ns * steps / (ms_b / 1000.0), "unit": UNIT, "ms_per_step": ms_b / steps,
             "per_scene_value": ns * steps / (ms_s / 1000.0),
             "vs_per_scene": ms_s / ms_b, "n_scenes": len(parts), "n_spheres": ns,
-            "bin_factor": fb, "tiles": tiles,
+            "bin_factor": fb, "tiles": tiles, "launches": launches,
             "workload": "64 box-settling scenes, 5,000-100,000 clumps (log-uniform), own mu "
                         "0.2-0.9 and 10 templates of 1-5 spheres each, FP32 voxel, one context "
                         "with graph-captured steps vs one context per scene"}
+
+
+# ---------------------------------------------------------------------------
+# the other workload shapes (--config 1-4)
+# ---------------------------------------------------------------------------
+def config_scene(cfg, n_clumps, log):
+    """(scene, precision, workload name) of workload shape 1, 2 or 3."""
+    from paper_2307_03445_gb300 import scenes, workloads
+
+    if cfg == 1:
+        sc = scenes.config1()
+        name = ("1,000 clumps of 3 overlapping spheres (r 1-2 mm), 1 material, FP64, settling "
+                "in a 5x5x10 cm box of planes from a jittered lattice, dt 1e-6 s")
+        return sc, scenes.PREC_FP64, name
+    if cfg == 2:
+        base = scenes.config2()
+        n = n_clumps or base.n_clumps
+        sc = workloads.settled_bed(base, n, 0.0, 0.25, 0.0, 0.25, seed=base.seed, log=log)
+        name = (f"{n:,} clumps from 20 templates of 1-5 spheres (r lognormal median 1.5 mm), "
+                "4 per-sphere materials, settled in a 0.25 m box, FP32 forces + voxel positions")
+        return sc, scenes.PREC_FP32, name
+    base = scenes.config3()
+    n = n_clumps or 1_000_000
+    R = 0.2
+
+    def inside(x, y, b):
+        return np.hypot(x, y) <= R - b
+
+    sc = workloads.settled_bed(base, n, -R, R, -R, R, seed=base.seed, inside=inside, log=log)
+    # the cone: tip 1 mm above the bed's top at the axis, pushed down at 1 cm/s
+    top = float((sc.pos[:, 2] + sc.bounding_radius()[sc.tpl]).max())
+    cone = dict(base.cone)
+    cone["p"] = (0.0, 0.0, top + 1e-3)
+    sc.walls = list(sc.walls) + [cone]
+    sc.hi = (sc.hi[0], sc.hi[1], top + 0.1)
+    name = (f"{n:,} clumps of 3 spheres (r 1-2 mm) settled in a cylinder of radius 0.2 m, an "
+            "analytic cone (30 deg half angle, 2 cm base) pushed down at 1 cm/s, FP32 forces + "
+            "FP64 integration")
+    return sc, scenes.PREC_FP32, name
+
+
+def small_config_line(args, dem, workloads, world, rank, local, log):
+    """The bench line of workload shape 1, 2, 3 (one scene) or 4 (batched).
+    The value is taken with graph-launched steps (these scenes are small
+    enough for launch overhead to matter); the per-kernel times come from a
+    second, event-timed pass of the same length."""
+    import torch
+
+    if args.config == 4:
+        b = batched_form(dem, args.steps, local, log, warmup=args.warmup)
+        return {"metric": METRIC, "value": world * b["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": b["workload"], "n_spheres": b["n_spheres"],
+                           "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (6M spheres)"},
+                "forms": {"batched": b}, "gpu_launches": b["launches"], "e2e": None}
+    t0 = time.time()
+    sc, prec, name = config_scene(args.config, None if args.n_clumps == N_CLUMPS_FULL
+                                  else args.n_clumps, log)
+    log(f"config {args.config} ready in {time.time() - t0:.1f} s: {sc.n_clumps} clumps, "
+        f"{sc.n_spheres} spheres")
+    stream = torch.cuda.Stream()
+    margin = MARGIN_VBOUND * sc.h * K_REBUILD
+    sim = dem.Simulation(sc, margin=margin, rebuild_interval=K_REBUILD, precision=prec,
+                         device=local, stream=stream.cuda_stream)
+    ns, ncl = sc.n_spheres, sc.n_clumps
+    sim.set_graphs(True)
+    sim.step(args.warmup)
+    if ncl >= 100_000:
+        sim.autotune_bins(BIN_FACTORS, reps=1)
+        sim.autotune_tiles(steps=6, reps=1)
+        sim.step(args.warmup)
+    s0 = sim.state()
+    sim.reset_stats()
+    with ClockSampler(local) as clk:
+        ms = _timed_steps(sim, stream, args.steps)
+    st = sim.stats()
+    if world > 1:
+        ms = max_over_ranks(ms, torch.device("cuda", local))
+    # the same steps again from the same state with per-kernel events
+    sim.set_state(*s0)
+    sim.reset_stats()
+    sim.set_timing(True)
+    _timed_steps(sim, stream, args.steps)
+    sim.set_timing(False)
+    st2 = sim.stats()
+    k = max(1, st2["timed_steps"])
+    line = {"metric": METRIC, "value": whole_job_rate(world, ns, args.steps, ms), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
+            "contacts_per_sec": whole_job_rate(world, st["pair_steps"], 1, ms),
+            "config": {"workload": name, "n_clumps": ncl, "n_spheres": ns,
+                       "listed_pairs": st["n_pairs"], "active_contacts": st["active_last"],
+                       "wall_contacts": st["n_wall_contacts"], "margin_m": margin,
+                       "rebuild_interval": K_REBUILD, "dt": sc.h, "rebuilds": st["rebuilds"],
+                       "guard_violations": st["guard_violations"],
+                       "parallelism": f"replicas{world}", "launch": "CUDA graphs",
+                       "l2": "state smaller than L2 (no flush)" if ns < 1_000_000
+                             else "inputs larger than L2",
+                       "phase_ms_event_timed_pass": {
+                           "pairs": st2["ms_pairs"] / k, "walls": st2["ms_walls"] / k,
+                           "update": st2["ms_update"] / k, "rebuild_total": st2["ms_detect"]}},
+            "gpu_launches": st["launches"], "clocks": clk.summary(), "e2e": None}
+    if not args.no_e2e:
+        sim.set_state(*s0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sim.set_state(*s0)
+        sim.step(args.steps)
+        out = sim.state()
+        e2e_ms = (time.perf_counter() - t1) * 1000.0
+        if world > 1:
+            e2e_ms = max_over_ranks(e2e_ms, torch.device("cuda", local))
+        b = ncl * 13 * 8
+        line["e2e"] = {"value": whole_job_rate(world, ns, args.steps, e2e_ms), "unit": UNIT,
+                       "h2d_bytes_per_step": b / args.steps, "d2h_bytes_per_step": b / args.steps,
+                       "steps": args.steps, "host_buffers": "pageable numpy"}
+        del out
+    if args.config == 3 and not args.no_forms:
+        sim.set_state(*s0)
+        line["forms"] = {"learned": learned_form(dem, sim, stream, args.steps, ns, st,
+                                                 ms / args.steps, log, start_state=s0)}
+    sim.close()
+    if rank == 0 and not args.no_cpu_baseline and args.config == 1:
+        # the oracle runs this workload whole (1,000 clumps), on one core and on all
+        line["cpu_baseline"] = time_oracle_config1(sc, margin, args.steps)
+    return line
+
+
+def time_oracle_config1(sc, margin, steps):
+    """The FP64 oracle on the 1,000-clump workload itself, `steps` steps from
+    the generated state, single-threaded (its CPU baseline)."""
+    import oracle
+
+    sc.bin_size = 2.0 * (float(sc.tpl_rad.max()) + margin)
+    sim = oracle.OracleSim(sc, margin, K_REBUILD)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sim.close()
+    return {"value": sc.n_spheres * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the whole workload ({sc.n_clumps} clumps / {sc.n_spheres} spheres), "
+                      f"{steps} steps from the generated state, single-threaded FP64 C"}
 
 
 # ---------------------------------------------------------------------------
@@ -380,13 +583,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n-clumps", type=int, default=N_CLUMPS_FULL)
+    ap.add_argument("--footprint", default="4x2",
+                    help="box footprint LXxLY in metres of the paper-scale bed; with the same "
+                         "0.25 m patch a smaller footprint gives a bed of the same depth and "
+                         "packing with fewer clumps (e.g. 1x0.5 and --n-clumps 687504)")
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--boundary", default="analytic", choices=["analytic", "mesh"],
-                    help="the box and plate as analytic planes or as 12 mesh facets")
+                    help="the box and plate as analytic planes, or as 12 mesh facets with a "
+                         "cone of 544 facets pushed into the bed")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned-margin and batched forms")
+    ap.add_argument("--config", type=int, default=5, choices=[1, 2, 3, 4, 5],
+                    help="workload: 5 the paper-scale bed (default); 1 the 1,000-clump FP64 "
+                         "settling box; 2 the 200,000-clump box; 3 the 1,000,000-clump cylinder "
+                         "with a cone, learned vs fixed margin; 4 the batched 64-scene sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -426,10 +638,19 @@ def main():
     from paper_2307_03445_gb300 import workloads
 
     log = (lambda m: print(f"[bench r{rank}] {m}", file=sys.stderr, flush=True))
+    if args.config != 5:
+        line = small_config_line(args, dem, workloads, world, rank, local, log)
+        if rank == 0:
+            print(json.dumps(line))
+        return
     t0 = time.time()
-    sc = workloads.bed_c5(n_clumps=args.n_clumps, log=log)
+    lx, ly = (float(v) for v in args.footprint.lower().split("x"))
+    sc = workloads.bed_c5(n_clumps=args.n_clumps, lx=lx, ly=ly, log=log)
     if args.boundary == "mesh":
+        # the box and sliding plate as 12 facets, and a cone of 544 facets
+        # pushed into the bed at 1 cm/s (section 4's cone penetration)
         sc.walls = workloads.facet_box(sc.walls)
+        sc = workloads.insert_cone_mesh(sc)
     log(f"bed ready in {time.time() - t0:.1f} s: {sc.n_clumps} clumps, {sc.n_spheres} spheres")
     stream = torch.cuda.Stream()
     margin = MARGIN_VBOUND * sc.h * K_REBUILD
@@ -517,7 +738,8 @@ def main():
         del out
     forms = None
     if not args.no_forms:
-        forms = {"learned": learned_form(dem, sim, stream, args.steps, ns, st, ms_step, log)}
+        forms = {"outer_list": outer_form(sim, stream, ns, log),
+                 "learned": learned_form(dem, sim, stream, args.steps, ns, st, ms_step, log)}
     sim.close()
     if forms is not None:
         forms["batched"] = batched_form(dem, args.steps, local, log)
@@ -537,7 +759,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "contacts_per_sec": contacts_ps,
         "config": {"workload": workload_name(ncl, ns) + (
-                       " (box and plate as 12 mesh facets)" if args.boundary == "mesh" else ""),
+                       " (box and plate as 12 mesh facets, a cone of 544 facets pushed in at "
+                       "1 cm/s)" if args.boundary == "mesh" else ""),
                    "boundary": args.boundary, "n_clumps": ncl, "n_spheres": ns,
                    "listed_pairs": n_pairs, "active_contacts": n_active,
                    "wall_contacts": st["n_wall_contacts"], "margin_m": margin,

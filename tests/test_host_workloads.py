@@ -80,3 +80,20 @@ def test_merge_batch_shifts_template_material_and_wall_ids():
         for wq, wp in zip(q.walls, p.walls):
             for name in ("E", "nu", "mu", "cor"):
                 assert getattr(q, name)[wq["material"]] == getattr(p, name)[wp.get("material", 0)]
+
+
+def test_repose_angle_of_synthetic_cones():
+    """The heap measurement on spheres filling cones of known flank angle
+    (20 and 32 degrees, 3 cm high): within half a degree, apex height within
+    a sphere radius."""
+    import math
+
+    rng = np.random.default_rng(0)
+    for ang in (20.0, 32.0):
+        H = 0.03
+        R = H / math.tan(math.radians(ang))
+        pts = rng.uniform([-R, -R, 0.0], [R, R, H], size=(200000, 3))
+        rho = np.hypot(pts[:, 0], pts[:, 1])
+        pts = pts[pts[:, 2] <= H - math.tan(math.radians(ang)) * rho]
+        got, hmax, rings = workloads.repose_angle(pts, np.full(len(pts), 1e-3), (0.0, 0.0), 0.0, 2e-3)
+        assert abs(got - ang) < 0.5 and abs(hmax - (H + 1e-3)) < 1e-3 and rings >= 5
