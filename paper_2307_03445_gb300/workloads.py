@@ -232,14 +232,16 @@ def insert_cone_mesh(sc: scenes.Scene, depth=0.005, nseg=32, nrings=9, speed=0.0
     return out
 
 
-def repose_angle(xs, radii, centre, z_floor, bin_width, lo_frac=0.2, hi_frac=0.8):
+def repose_angle(xs, radii, centre, z_floor, bin_width, lo_frac=0.2, hi_frac=0.8, min_count=5):
     """Angle of repose of a heap [degrees] (section 4's angle-of-repose test):
     the heap's top surface h(rho) is the highest sphere top above the floor
     in each ring of width `bin_width` around the vertical axis through
-    `centre`; a least-squares line h = a - b rho over the rings whose height
-    lies between lo_frac and hi_frac of the apex height (the flank, without
-    the rounded apex and the toe) gives the angle atan(b).  Returns (angle,
-    apex height, rings used)."""
+    `centre`, over the rings from the axis outwards up to the first one that
+    holds fewer than `min_count` spheres (grains scattered beyond the heap's
+    toe are not part of its flank); a least-squares line h = a - b rho over
+    those rings whose height lies between lo_frac and hi_frac of the apex
+    height (the flank, without the rounded apex and the toe) gives the angle
+    atan(b).  Returns (angle, apex height, rings used)."""
     xs = np.asarray(xs, float)
     top = xs[:, 2] + np.asarray(radii, float) - z_floor
     rho = np.hypot(xs[:, 0] - centre[0], xs[:, 1] - centre[1])
@@ -247,8 +249,14 @@ def repose_angle(xs, radii, centre, z_floor, bin_width, lo_frac=0.2, hi_frac=0.8
     nb = int(k.max()) + 1
     h = np.full(nb, -np.inf)
     np.maximum.at(h, k, top)
+    cnt = np.bincount(k, minlength=nb)
+    short = np.nonzero(cnt < min_count)[0]
+    end = int(short[0]) if len(short) else nb
     mid = (np.arange(nb) + 0.5) * bin_width
-    ok = np.isfinite(h)
+    ok = np.zeros(nb, bool)
+    ok[:end] = True
+    if not ok.any():
+        raise ValueError("no ring near the axis holds enough spheres")
     hmax = float(h[ok].max())
     sel = ok & (h >= lo_frac * hmax) & (h <= hi_frac * hmax)
     if sel.sum() < 3:

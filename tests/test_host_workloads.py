@@ -97,3 +97,10 @@ def test_repose_angle_of_synthetic_cones():
         pts = pts[pts[:, 2] <= H - math.tan(math.radians(ang)) * rho]
         got, hmax, rings = workloads.repose_angle(pts, np.full(len(pts), 1e-3), (0.0, 0.0), 0.0, 2e-3)
         assert abs(got - ang) < 0.5 and abs(hmax - (H + 1e-3)) < 1e-3 and rings >= 5
+        # grains scattered on the floor beyond the toe do not move the flank
+        far = np.column_stack([rng.uniform(R + 0.01, R + 0.1, 30) * np.cos(np.arange(30)),
+                               rng.uniform(R + 0.01, R + 0.1, 30) * np.sin(np.arange(30)),
+                               np.full(30, 1e-3)])
+        got2, _, _ = workloads.repose_angle(np.vstack([pts, far]), np.full(len(pts) + 30, 1e-3),
+                                            (0.0, 0.0), 0.0, 2e-3)
+        assert got2 == got
