@@ -79,13 +79,24 @@ def IMPL_PAIRS(ncl, ns, n_pairs, n_active):
 # DRAM read + write bytes per launch of the current kernels, from one ncu
 # capture on the 11M-clump bed (the profile named beside each); None until
 # the current kernels have been captured.
-TRAFFIC = {"k_update32": None, "k_pairs32": None}
-TRAFFIC_SRC = {"k_update32": None, "k_pairs32": None}
+# DRAM bytes (read + write) of one launch in an ncu capture of the same
+# kernel on the 687,504-clump bed of the same depth (--footprint 1x0.5), with
+# that launch's algorithmic bytes; a launch on a bed of this family is scaled
+# by its algorithmic bytes (both grow with the clumps, spheres and pairs in
+# the same proportions).  None once the kernel changes.
+TRAFFIC = {"k_update32": (140.312832e6 + 97.429504e6, 181879360),
+           "k_pairs32": (193.093120e6 + 42.739200e6, 202176992)}
+TRAFFIC_SRC = {k: "ncu dram__bytes_read.sum + dram__bytes_write.sum, 687,504-clump bed, scaled "
+                  "by algorithmic bytes (profiles/ncu_pairs_update_bed_2M_spheres.md)"
+               for k in TRAFFIC}
 
 
 def roof(kernel, ms, algo, impl, peak, peak_src, full_bed):
     achieved = algo / (ms / 1000.0) / 1e9
-    tr = TRAFFIC[kernel] if full_bed else None
+    tr = None
+    if full_bed and TRAFFIC[kernel] is not None:
+        meas, algo_meas = TRAFFIC[kernel]
+        tr = meas * algo / algo_meas
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": tr,
             "traffic_source": TRAFFIC_SRC[kernel] if tr is not None else None,
@@ -365,15 +376,33 @@ def outer_form(sim, stream, ns, log, factor=3.0, n_inner=4, cycles=4):
     st = sim.stats()
     sim.set_outer_list(factor, 0)
     sim.set_timing(False)
-    log(f"outer list: {ms / n:.4f} ms/step vs plain {ms_plain / n:.4f}")
+    # the same steps without per-phase events (graph-captured steps): plain,
+    # outer list, and outer list detected on a second stream while the
+    # interval's steps run
+    whole = {}
+    for name, args in (("plain", (factor, 0)), ("outer", (factor, n_inner)),
+                       ("outer_async", (factor, n_inner, True))):
+        sim.set_outer_list(*args)
+        sim.set_state(*s0)
+        sim.step(n_inner * K_REBUILD)  # the first outer list (and the first started on st2)
+        sim.set_state(*s0)
+        sim.reset_stats()
+        whole[name] = _timed_steps(sim, stream, n) / n
+        whole[name + "_outer_rebuilds"] = sim.stats()["outer_rebuilds"]
+    sim.set_outer_list(factor, 0)
+    log(f"outer list: {ms / n:.4f} ms/step vs plain {ms_plain / n:.4f} (per-phase events); "
+        f"without events plain {whole['plain']:.4f}, outer {whole['outer']:.4f}, "
+        f"outer on a second stream {whole['outer_async']:.4f}")
     return {"value": ns * n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / n, "steps": n,
             "plain_ms_per_step_same_steps": ms_plain / n, "vs_plain": ms_plain / ms,
             "rebuilds": st["rebuilds"], "outer_rebuilds": st["outer_rebuilds"],
             "rebuild_ms_per_rebuild": st["ms_detect"] / max(1, st["rebuilds"]),
             "plain_rebuild_ms_per_rebuild": st_plain["ms_detect"] / max(1, st_plain["rebuilds"]),
+            "ms_per_step_without_phase_events": whole,
             "rule": f"outer list at {factor} x the margin serving {n_inner} rebuilds of the "
                     f"plain rule (each list exactly the fresh detection's); timed over {cycles} "
-                    f"whole outer cycles"}
+                    f"whole outer cycles; outer_async: the next outer list detected on a second "
+                    f"stream during the interval before it is needed"}
 
 
 def sim_device(sim):
@@ -697,13 +726,14 @@ def main():
     n_pairs, n_active = st["n_pairs"], st["active_last"]
     pair_ms = st["ms_pairs"] / max(1, st["timed_steps"])
     upd_ms = st["ms_update"] / max(1, st["timed_steps"])
+    bed_family = args.boundary == "analytic"  # the beds the traffic capture scales to
     rooflines = {
         "k_update32": roof("k_update32", upd_ms, algo=ALGO_UPDATE(ncl, ns),
                            impl=IMPL_UPDATE(ncl, ns), peak=peak, peak_src=peak_src,
-                           full_bed=ncl == N_CLUMPS_FULL),
+                           full_bed=bed_family),
         "k_pairs32": roof("k_pairs32", pair_ms, algo=ALGO_PAIRS(ncl, ns, n_pairs),
                           impl=IMPL_PAIRS(ncl, ns, n_pairs, n_active), peak=peak,
-                          peak_src=peak_src, full_bed=ncl == N_CLUMPS_FULL),
+                          peak_src=peak_src, full_bed=bed_family),
     }
     # `roofline` is the kernel with the larger share of the step
     roofline = max(rooflines.values(), key=lambda r: r["kernel_ms"])

@@ -234,9 +234,26 @@ int dem_set_state(dem_ctx* ctx, const double* pos, const double* quat, const dou
  * sphere and detects a new outer list when one moved further.  Adding clumps
  * or changing a wall's motion also starts a new outer list; the learned rule
  * and dem_rebuild use full detections.  n_inner = 0 turns it off (default).
- * dem_get_bins then reports the outer list's bins.  Returns
- * DEM_ERR_INVALID_ARG for factor <= 1 or n_inner < 0. */
-int dem_set_outer_list(dem_ctx* ctx, double factor, int n_inner);
+ * dem_get_bins then reports the bins of the last outer list detected on the
+ * context stream.
+ *
+ * async_detect != 0 (section 2.2's kinematics thread building the next
+ * contact list while the dynamics thread steps, on one GPU with two streams):
+ * at the last rebuild an outer list serves, the next one is started from
+ * that rebuild's state; the part that reads the state (lattice points, bin
+ * counts, wall candidates) runs on the context stream in order with the
+ * steps, the rest (bin scatter, narrow phase, the list's rows and the host's
+ * waits for its sizes) on a second stream of the context while the
+ * interval's steps run; the next rebuild adopts it.  Its wall candidates
+ * cover n_inner + 1 intervals, since it is adopted one interval after its
+ * state; the lists filtered from it are still exactly those of a fresh
+ * detection (the allowance check holds them to that).  Off while the scene
+ * has mesh facets (their registration reads the state in the second part).
+ * dem_step returns with the second stream idle.  Needs the library's
+ * stream-ordered allocator (not a dem_params.alloc).  Returns
+ * DEM_ERR_INVALID_ARG for factor <= 1, n_inner < 0, or async_detect with a
+ * custom allocator. */
+int dem_set_outer_list(dem_ctx* ctx, double factor, int n_inner, int async_detect);
 
 int dem_get_stats(dem_ctx* ctx, dem_stats* out);
 int dem_reset_stats(dem_ctx* ctx);

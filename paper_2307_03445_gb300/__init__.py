@@ -269,10 +269,13 @@ class Simulation:
         """Bit-reproducible force sums (per-contact slots summed in a fixed order)."""
         self._check(self.lib.dem_set_deterministic(self.ctx, 1 if on else 0))
 
-    def set_outer_list(self, factor=3.0, n_inner=4):
+    def set_outer_list(self, factor=3.0, n_inner=4, async_detect=False):
         """Two-level contact list (see include/dem.h): an outer list at factor x
-        the margin serves the next n_inner rebuilds; n_inner=0 turns it off."""
-        self._check(self.lib.dem_set_outer_list(self.ctx, float(factor), int(n_inner)))
+        the margin serves the next n_inner rebuilds; n_inner=0 turns it off.
+        async_detect builds the next outer list on a second stream while the
+        steps run."""
+        self._check(self.lib.dem_set_outer_list(self.ctx, float(factor), int(n_inner),
+                                                1 if async_detect else 0))
 
     def set_graphs(self, on=True):
         """Run the steps between rebuilds as one captured CUDA graph."""

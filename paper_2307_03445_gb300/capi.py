@@ -93,7 +93,7 @@ SIGNATURES = {
     "dem_set_timing": (C.c_int, [_V, C.c_int]),
     "dem_set_graphs": (C.c_int, [_V, C.c_int]),
     "dem_set_deterministic": (C.c_int, [_V, C.c_int]),
-    "dem_set_outer_list": (C.c_int, [_V, C.c_double, C.c_int]),
+    "dem_set_outer_list": (C.c_int, [_V, C.c_double, C.c_int, C.c_int]),
     "dem_autotune_bins": (C.c_int, [_V, C.c_int, _D, C.c_int, _D, _D]),
     "dem_set_tiles": (C.c_int, [_V, C.POINTER(DemTiles)]),
     "dem_get_tiles": (C.c_int, [_V, C.POINTER(DemTiles)]),

@@ -35,6 +35,29 @@ struct SceneH {
   double lo[3], hi[3], bin;
 };
 
+// Scratch of one detection (the main one on the context stream; a second
+// set for the outer list detected on the second stream, see
+// dem_set_outer_list).
+struct DetScratch {
+  Buf det, wall_mask, wall_cnt, pair_cnt, bin_size, bin_start, scan_scr, trho, totals;
+  Buf rec, upairs, fbin_size, fbin_start, fcnt, frec, fcand;
+  unsigned long long ucap = 0;  // capacity of the unordered pair buffer
+  unsigned long long fcap = 0;  // capacity of the facet candidate buffer
+};
+
+// A detection in two parts.  detect_prepare reads the clump state (the
+// lattice points, the bin counts, the analytic wall candidates) on stream
+// st; detect_finish does the rest (scans, bin scatter, facets, narrow phase,
+// the list's rows) on stream st2, which may be another stream once it waits
+// for the first part, since nothing there reads the state again except the
+// facet passes (a detection with facets finishes on the same stream at once).
+struct DetJob {
+  DetectOut o{};
+  int li = 0, si = 0, K = 1;
+  double m = 0.0, t = 0.0, travel = 0.0;
+};
+
+
 }  // namespace
 
 struct dem_ctx {
@@ -70,12 +93,9 @@ struct dem_ctx {
   Buf b_grids, b_lgrids, b_walls, b_wall_idx, b_wall_scene, b_wfix, b_wpos, b_wforce, b_wtorque, b_pm64, b_pm32;
   Buf b_flags, b_counters, b_totals, b_dstep;
   // detection scratch
-  Buf b_det, b_bin_size, b_wall_mask, b_wall_cnt;
-  Buf b_bin_start, b_pair_cnt, b_scan_scr, b_tmp;
-  Buf b_rec, b_trho, b_upairs;
-  Buf b_facet_idx, b_fbin_size, b_fbin_start, b_frec, b_fcand, b_fcnt;
+  DetScratch ds[2];  // 0: detections on the context stream; 1: the outer list on st2
+  Buf b_tmp, b_facet_idx;
   int n_facets = 0;
-  unsigned long long fcap = 0;  // capacity of the facet candidate buffer
   // two-level list: an outer list at outer_factor x the margin serves
   // outer_n rebuilds; b_q0 holds its lattice points and enlarged radii
   double outer_factor = 0.0;
@@ -84,8 +104,20 @@ struct dem_ctx {
   long long outer_ns = 0;
   double outer_m = 0.0;
   int outer_K = 0;
+  long long outer_until = 0;  // its wall candidates cover the steps before this one
   Buf b_q0;
-  unsigned long long ucap = 0;  // capacity of the unordered pair buffer
+  // the next outer list detected on a second stream while the steps run
+  // (async_state 0: none; 1: its state-reading part is queued on st, the
+  // rest still to be queued on st2; 2: queued in full, ev_ready marks its end)
+  bool outer_async = false;
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_snap = nullptr, ev_ready = nullptr;
+  int async_state = 0;
+  DetJob async_job;
+  double async_m = 0.0;
+  int async_K = 0;
+  long long async_ns = 0, async_until = 0;
+  Buf b_q1;
   double bin_factor = 1.0;      // bin edge multiplier chosen by dem_autotune_bins
   dem_tiles tiles = {8, 128, 8}; // launch shapes (dem_set_tiles / dem_autotune_tiles)
   long long n_entries = 0;       // bin registrations of the last rebuild (records in
@@ -95,7 +127,7 @@ struct dem_ctx {
   struct ListBufs {
     Buf pa, pb, u, row, ws, ww, uw, wrow, dnb;
     ContactList L{};
-  } lists[4];  // 0, 1: current and next; 2: audit; 3: outer list
+  } lists[5];  // 0, 1: current and next; 2: audit; 3: outer list; 4: the next outer list
   int cur = 0;
   long long list_ns = 0;  // spheres when the current list was built
   // state
@@ -143,33 +175,36 @@ int fail(dem_ctx* c, int code, const std::string& msg) {
   return code;
 }
 
-void* dalloc(dem_ctx* c, size_t bytes) {
+// Device memory, stream-ordered on `st` (the context stream unless given).
+void* dalloc(dem_ctx* c, size_t bytes, cudaStream_t st = nullptr) {
   if (bytes == 0) bytes = 16;
   void* p = nullptr;
   if (c->P.alloc) {
     p = c->P.alloc(bytes, c->P.alloc_user);
-  } else if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+  } else if (cudaMallocAsync(&p, bytes, st ? st : c->st) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
   }
   return p;
 }
-void dfree(dem_ctx* c, void* p) {
+void dfree(dem_ctx* c, void* p, cudaStream_t st = nullptr) {
   if (!p) return;
   if (c->P.free) c->P.free(p, c->P.alloc_user);
-  else cudaFreeAsync(p, c->st);
+  else cudaFreeAsync(p, st ? st : c->st);
 }
 
-// Grows b to at least `bytes`, preserving the first `keep` bytes.
-bool grow(dem_ctx* c, Buf& b, size_t bytes, size_t keep = 0) {
+// Grows b to at least `bytes`, preserving the first `keep` bytes; the new
+// block is allocated and the old one freed in the order of stream `st`.
+bool grow(dem_ctx* c, Buf& b, size_t bytes, size_t keep = 0, cudaStream_t st = nullptr) {
   if (b.bytes >= bytes && b.p) return true;
+  if (!st) st = c->st;
   size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
   nb = (nb + 255) & ~(size_t)255;
-  void* p = dalloc(c, nb);
+  void* p = dalloc(c, nb, st);
   if (!p) return false;
   c->layout++;
-  if (keep && b.p) cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->st);
-  dfree(c, b.p);
+  if (keep && b.p) cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, st);
+  dfree(c, b.p, st);
   b.p = p;
   b.bytes = nb;
   return true;
@@ -305,8 +340,8 @@ int build_det_lists(dem_ctx* c) {
   cudaMemsetAsync(c->b_det_cnt.p, 0, 4 * (size_t)(ncl + 1), c->st);
   cudaMemsetAsync(c->b_det_fill.p, 0, 4 * (size_t)(ncl + 1), c->st);
   launch_det_lists(c->D, L, n, nw, ptr<uint32_t>(c->b_det_cnt), ptr<uint32_t>(c->b_det_fill),
-                   ptr<uint32_t>(c->b_det_off), ptr<uint32_t>(c->b_det_ids), c->b_scan_scr.p,
-                   ptr<unsigned long long>(c->b_totals) + 6, c->st);
+                   ptr<uint32_t>(c->b_det_off), ptr<uint32_t>(c->b_det_ids), c->ds[0].scan_scr.p,
+                   ptr<unsigned long long>(c->ds[0].totals) + 6, c->st);
   c->det_ready = true;
   set_det_pointers(c);
   return cuda_check(c, "deterministic lists");
@@ -496,7 +531,7 @@ int finalize(dem_ctx* c) {
       !grow(c, c->b_wpos, 3 * sizeof(double) * nw) || !grow(c, c->b_wforce, 3 * sizeof(double) * nw) ||
       !grow(c, c->b_wtorque, 3 * sizeof(double) * nw) ||
       !grow(c, c->b_facet_idx, sizeof(int) * std::max<size_t>(1, fidx.size())) ||
-      !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->b_totals, 128) ||
+      !grow(c, c->b_flags, 64) || !grow(c, c->b_counters, 64) || !grow(c, c->ds[0].totals, 128) ||
       !grow(c, c->b_dstep, 64))
     return fail(c, DEM_ERR_OOM, "scene tables");
   cudaMemcpyAsync(c->b_grids.p, c->grids.data(), sizeof(SceneGrid) * c->grids.size(), cudaMemcpyHostToDevice, c->st);
@@ -526,22 +561,23 @@ int finalize(dem_ctx* c) {
 // Lists[li] sized for NP pairs and NW wall contacts (25 % headroom when it
 // grows) and its device view set; hist = false leaves out the tangential
 // history arrays (the outer list carries none).
-int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, bool hist) {
+int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, bool hist,
+              cudaStream_t st = nullptr) {
   auto& LB = c->lists[li];
   ContactList& L = LB.L;
   if ((long long)NP > L.cap || !LB.pa.p) {
     const long long cap = std::max<long long>((long long)(NP + NP / 4), 1024);
-    dfree(c, LB.pa.p); dfree(c, LB.pb.p); dfree(c, LB.u.p);
+    dfree(c, LB.pa.p, st); dfree(c, LB.pb.p, st); dfree(c, LB.u.p, st);
     LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf();
-    if (!grow(c, LB.pa, 4 * cap) || !grow(c, LB.pb, 4 * cap) || (hist && !grow(c, LB.u, 24 * cap)))
+    if (!grow(c, LB.pa, 4 * cap, 0, st) || !grow(c, LB.pb, 4 * cap, 0, st) || (hist && !grow(c, LB.u, 24 * cap, 0, st)))
       return fail(c, DEM_ERR_OOM, "pair list");
     L.cap = cap;
   }
   if ((long long)NW > L.capw || !LB.ws.p) {
     const long long cap = std::max<long long>((long long)(NW + NW / 4), 1024);
-    dfree(c, LB.ws.p); dfree(c, LB.ww.p); dfree(c, LB.uw.p);
+    dfree(c, LB.ws.p, st); dfree(c, LB.ww.p, st); dfree(c, LB.uw.p, st);
     LB.ws = Buf(); LB.ww = Buf(); LB.uw = Buf();
-    if (!grow(c, LB.ws, 4 * cap) || !grow(c, LB.ww, 4 * cap) || (hist && !grow(c, LB.uw, 24 * cap)))
+    if (!grow(c, LB.ws, 4 * cap, 0, st) || !grow(c, LB.ww, 4 * cap, 0, st) || (hist && !grow(c, LB.uw, 24 * cap, 0, st)))
       return fail(c, DEM_ERR_OOM, "wall list");
     L.capw = cap;
   }
@@ -553,87 +589,107 @@ int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, 
   L.ww = ptr<uint32_t>(LB.ww);
   L.uw = ptr<double>(LB.uw);
   L.wrow = ptr<uint32_t>(LB.wrow);
-  if (!grow(c, LB.dnb, 16)) return fail(c, DEM_ERR_OOM, "list lengths");
+  if (!grow(c, LB.dnb, 16, 0, st)) return fail(c, DEM_ERR_OOM, "list lengths");
   L.dn = ptr<long long>(LB.dnb);
   L.n = (long long)NP;
   L.nw = (long long)NW;
   return DEM_OK;
 }
 
-// Detection into lists[li] with margin m (per clump from D.cmargin when set),
-// for a list that must last K steps (wall travel) -- also used by the audit.
-// With an old list (old != NULL) the tangential history of the pairs both
-// lists hold is carried over as the rows are built.
-int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nullptr,
-                long long old_ns = 0, double wall_extra = 0.0) {
+int detect_prepare(dem_ctx* c, int li, double m, int K, double wall_extra, int si, cudaStream_t st,
+                   DetJob& J) {
+  DetScratch& S = c->ds[si];
   const long long ns = c->ns;
   const double t = (double)c->step * c->P.dt;
   const double travel = c->P.dt * (double)std::max(1, K);
   auto& LB = c->lists[li];
   const size_t nb = (size_t)c->nbins;
-  if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_wall_mask, 4 * (ns + 1)) ||
-      !grow(c, c->b_wall_cnt, 4 * (ns + 1)) || !grow(c, c->b_pair_cnt, 4 * (ns + 1)) ||
-      !grow(c, c->b_bin_size, 4 * (nb + 1)) || !grow(c, c->b_bin_start, 4 * (nb + 1)) ||
-      !grow(c, LB.row, 4 * (ns + 1)) || !grow(c, LB.wrow, 4 * (ns + 1)) ||
-      !grow(c, c->b_scan_scr, scan_scratch_bytes(std::max<size_t>(ns, nb) + 1) + 256))
+  if (!grow(c, S.det, sizeof(int4) * (ns + 1), 0, st) || !grow(c, S.wall_mask, 4 * (ns + 1), 0, st) ||
+      !grow(c, S.wall_cnt, 4 * (ns + 1), 0, st) || !grow(c, S.pair_cnt, 4 * (ns + 1), 0, st) ||
+      !grow(c, S.bin_size, 4 * (nb + 1), 0, st) || !grow(c, S.bin_start, 4 * (nb + 1), 0, st) ||
+      !grow(c, LB.row, 4 * (ns + 1), 0, st) || !grow(c, LB.wrow, 4 * (ns + 1), 0, st) ||
+      !grow(c, S.scan_scr, scan_scratch_bytes(std::max<size_t>(ns, nb) + 1) + 256, 0, st) ||
+      !grow(c, S.totals, 128, 0, st))
     return fail(c, DEM_ERR_OOM, "detection buffers");
-  DetectOut o{};
-  o.det = ptr<int4>(c->b_det);
-  o.wall_mask = ptr<uint32_t>(c->b_wall_mask);
-  o.wall_cnt = ptr<uint32_t>(c->b_wall_cnt);
+  DetectOut& o = J.o;
+  o = DetectOut{};
+  J.li = li;
+  J.si = si;
+  J.K = K;
+  J.m = m;
+  J.t = t;
+  J.travel = travel;
+  o.det = ptr<int4>(S.det);
+  o.wall_mask = ptr<uint32_t>(S.wall_mask);
+  o.wall_cnt = ptr<uint32_t>(S.wall_cnt);
   o.wall_off = ptr<uint32_t>(LB.wrow);
-  o.pair_cnt = ptr<uint32_t>(c->b_pair_cnt);
+  o.pair_cnt = ptr<uint32_t>(S.pair_cnt);
   o.pair_off = ptr<uint32_t>(LB.row);
-  o.bin_size = ptr<uint32_t>(c->b_bin_size);
-  o.bin_start = ptr<uint32_t>(c->b_bin_start);
+  o.bin_size = ptr<uint32_t>(S.bin_size);
+  o.bin_start = ptr<uint32_t>(S.bin_start);
   o.nbins = c->nbins;
   o.wall_extra = wall_extra;
   if (!c->D.cmargin) {  // one margin for all clumps: radii from a per template sphere table
     o.n_tsph = (int)c->tpl_rad.size();
-    if (!grow(c, c->b_trho, 4 * (size_t)(o.n_tsph + 1))) return fail(c, DEM_ERR_OOM, "detection buffers");
-    o.trho = ptr<int>(c->b_trho);
+    if (!grow(c, S.trho, 4 * (size_t)(o.n_tsph + 1), 0, st)) return fail(c, DEM_ERR_OOM, "detection buffers");
+    o.trho = ptr<int>(S.trho);
   }
-  unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
+  unsigned long long* tot = ptr<unsigned long long>(S.totals);
   // b_totals: 0 entries, 1 analytic wall contacts, 3 pairs, 4 audit, 5 d_np,
   // 6 slot lists, 7 next bin, 8 facet registrations, 9 facet candidates,
   // 10 wall contacts with the facets
   const bool facets = c->n_facets > 0;
-  if (facets && (!grow(c, c->b_fbin_size, 4 * (nb + 1)) || !grow(c, c->b_fbin_start, 4 * (nb + 1)) ||
-                 !grow(c, c->b_fcnt, 4 * (ns + 1))))
+  if (facets && (!grow(c, S.fbin_size, 4 * (nb + 1), 0, st) || !grow(c, S.fbin_start, 4 * (nb + 1), 0, st) ||
+                 !grow(c, S.fcnt, 4 * (ns + 1), 0, st)))
     return fail(c, DEM_ERR_OOM, "facet bin buffers");
-  o.fbin_size = ptr<uint32_t>(c->b_fbin_size);
-  o.fbin_start = ptr<uint32_t>(c->b_fbin_start);
-  o.fcnt = ptr<uint32_t>(c->b_fcnt);
+  o.fbin_size = ptr<uint32_t>(S.fbin_size);
+  o.fbin_start = ptr<uint32_t>(S.fbin_start);
+  o.fcnt = ptr<uint32_t>(S.fcnt);
   o.d_nf = tot + 9;
   // bin sort by counting: sizes (detection pass), starts (scan; the extra
   // zero entry makes start[nbins] the total), then the scatter below; the
   // mesh facets' registrations the same way
-  cudaMemsetAsync(o.bin_size, 0, 4 * (nb + 1), c->st);
-  launch_detect(c->D, o, m, nullptr, t, travel, c->st);
-  exclusive_scan_u32(o.bin_size, o.bin_start, (long long)nb + 1, c->b_scan_scr.p, tot + 0, c->st);
-  exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 1, c->st);
+  cudaMemsetAsync(o.bin_size, 0, 4 * (nb + 1), st);
+  launch_detect(c->D, o, m, nullptr, t, travel, st);
+  return cuda_check(c, "detect_prepare");
+}
+
+int detect_finish(dem_ctx* c, DetJob& J, const ContactList* old, long long old_ns, cudaStream_t st) {
+  DetScratch& S = c->ds[J.si];
+  DetectOut& o = J.o;
+  const int li = J.li;
+  const double m = J.m, t = J.t, travel = J.travel;
+  const long long ns = c->ns;
+  auto& LB = c->lists[li];
+  const size_t nb = (size_t)c->nbins;
+  unsigned long long* tot = ptr<unsigned long long>(S.totals);
+  const bool facets = c->n_facets > 0;
+  exclusive_scan_u32(o.bin_size, o.bin_start, (long long)nb + 1, S.scan_scr.p, tot + 0, st);
+  exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, S.scan_scr.p, tot + 1, st);
   unsigned long long h_tot[12] = {};
   if (facets) {
-    cudaMemsetAsync(o.fbin_size, 0, 4 * (nb + 1), c->st);
-    launch_facet_count(c->D, o, t, travel, c->st);
-    exclusive_scan_u32(o.fbin_size, o.fbin_start, (long long)nb + 1, c->b_scan_scr.p, tot + 8, c->st);
-    cudaMemcpyAsync(h_tot + 8, tot + 8, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+    cudaMemsetAsync(o.fbin_size, 0, 4 * (nb + 1), st);
+    launch_facet_count(c->D, o, t, travel, st);
+    exclusive_scan_u32(o.fbin_size, o.fbin_start, (long long)nb + 1, S.scan_scr.p, tot + 8, st);
+    cudaMemcpyAsync(h_tot + 8, tot + 8, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
   }
-  cudaMemcpyAsync(h_tot, tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
-  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "detect");
+  cudaMemcpyAsync(h_tot, tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "detect");
   const unsigned long long B = h_tot[0], NWA = h_tot[1], NFR = h_tot[8];
   if (B >= (1ull << 32) || NWA >= (1ull << 31) || NFR >= (1ull << 31))
     return fail(c, DEM_ERR_CAPACITY, "bin registrations exceed 2^32");
-  c->n_entries = (long long)B;
-  c->n_entry_bins = (long long)nb;
-  if (!grow(c, c->b_rec, sizeof(EntryRec) * (B + 1))) return fail(c, DEM_ERR_OOM, "bin buffers");
-  o.rec = ptr<EntryRec>(c->b_rec);
-  launch_bin_scatter(c->D, o, c->st);
+  if (J.si == 0) {
+    c->n_entries = (long long)B;
+    c->n_entry_bins = (long long)nb;
+  }
+  if (!grow(c, S.rec, sizeof(EntryRec) * (B + 1), 0, st)) return fail(c, DEM_ERR_OOM, "bin buffers");
+  o.rec = ptr<EntryRec>(S.rec);
+  launch_bin_scatter(c->D, o, st);
   if (facets) {
-    if (!grow(c, c->b_frec, sizeof(uint4) * (NFR + 1))) return fail(c, DEM_ERR_OOM, "facet bin buffers");
-    o.frec = ptr<uint4>(c->b_frec);
+    if (!grow(c, S.frec, sizeof(uint4) * (NFR + 1), 0, st)) return fail(c, DEM_ERR_OOM, "facet bin buffers");
+    o.frec = ptr<uint4>(S.frec);
     o.nfreg = (long long)NFR;
-    launch_facet_scatter(c->D, o, t, travel, c->st);
+    launch_facet_scatter(c->D, o, t, travel, st);
   }
   o.d_np = tot + 5;
   o.next_bin = tot + 7;
@@ -643,57 +699,71 @@ int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nu
   // grow and the passes run again
   unsigned long long NP = 0, NF = 0;
   for (int attempt = 0;; ++attempt) {
-    if (c->ucap == 0) c->ucap = (unsigned long long)std::max<long long>(2 * ns, 1 << 16);
-    if (!grow(c, c->b_upairs, 8 * (size_t)c->ucap)) return fail(c, DEM_ERR_OOM, "pair buffer");
-    o.upairs = ptr<uint2>(c->b_upairs);
-    o.ucap = c->ucap;
-    cudaMemsetAsync(o.pair_cnt, 0, 4 * (size_t)ns, c->st);
-    cudaMemsetAsync(o.d_np, 0, sizeof(unsigned long long), c->st);
-    cudaMemsetAsync(o.next_bin, 0, sizeof(unsigned long long), c->st);
-    launch_narrow(c->D, o, c->st);
-    exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
-    cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+    if (S.ucap == 0) S.ucap = (unsigned long long)std::max<long long>(2 * ns, 1 << 16);
+    if (!grow(c, S.upairs, 8 * (size_t)S.ucap, 0, st)) return fail(c, DEM_ERR_OOM, "pair buffer");
+    o.upairs = ptr<uint2>(S.upairs);
+    o.ucap = S.ucap;
+    cudaMemsetAsync(o.pair_cnt, 0, 4 * (size_t)ns, st);
+    cudaMemsetAsync(o.d_np, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(o.next_bin, 0, sizeof(unsigned long long), st);
+    launch_narrow(c->D, o, st);
+    exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, S.scan_scr.p, tot + 3, st);
+    cudaMemcpyAsync(h_tot + 3, tot + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (facets) {
-      if (c->fcap == 0) c->fcap = 1 << 16;
-      if (!grow(c, c->b_fcand, 8 * (size_t)c->fcap)) return fail(c, DEM_ERR_OOM, "facet candidates");
-      o.fcand = ptr<uint2>(c->b_fcand);
-      o.fcap = c->fcap;
-      cudaMemsetAsync(o.fcnt, 0, 4 * (size_t)ns, c->st);
-      cudaMemsetAsync(o.d_nf, 0, sizeof(unsigned long long), c->st);
-      launch_facet_narrow(c->D, o, m, nullptr, t, travel, c->st);
-      cudaMemcpyAsync(h_tot + 9, tot + 9, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
+      if (S.fcap == 0) S.fcap = 1 << 16;
+      if (!grow(c, S.fcand, 8 * (size_t)S.fcap, 0, st)) return fail(c, DEM_ERR_OOM, "facet candidates");
+      o.fcand = ptr<uint2>(S.fcand);
+      o.fcap = S.fcap;
+      cudaMemsetAsync(o.fcnt, 0, 4 * (size_t)ns, st);
+      cudaMemsetAsync(o.d_nf, 0, sizeof(unsigned long long), st);
+      launch_facet_narrow(c->D, o, m, nullptr, t, travel, st);
+      cudaMemcpyAsync(h_tot + 9, tot + 9, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     }
-    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "narrow phase");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "narrow phase");
     NP = h_tot[3];
     NF = h_tot[9];
-    if (NP <= c->ucap && NF <= c->fcap) break;
+    if (NP <= S.ucap && NF <= S.fcap) break;
     if (attempt > 0) return fail(c, DEM_ERR_STATE, "internal: pair buffer regrown twice");
-    if (NP > c->ucap) c->ucap = NP + NP / 4 + 1024;
-    if (NF > c->fcap) c->fcap = NF + NF / 4 + 1024;
+    if (NP > S.ucap) S.ucap = NP + NP / 4 + 1024;
+    if (NF > S.fcap) S.fcap = NF + NF / 4 + 1024;
   }
   const unsigned long long NW = NWA + NF;
   if (NW >= (1ull << 31)) return fail(c, DEM_ERR_CAPACITY, "wall list exceeds 2^31 entries");
   if (NF > 0) {  // rows hold analytic walls and facets: counts and offsets again
-    launch_add_facet_counts(c->D, o, c->st);
-    exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 10, c->st);
+    launch_add_facet_counts(c->D, o, st);
+    exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, S.scan_scr.p, tot + 10, st);
   }
   o.np = (long long)NP;
   if (NP >= (1ull << 31)) return fail(c, DEM_ERR_CAPACITY, "pair list exceeds 2^31 entries");
-  if (li != 3 && c->P.max_contacts > 0 && (long long)NP > c->P.max_contacts)
+  if (li < 3 && c->P.max_contacts > 0 && (long long)NP > c->P.max_contacts)
     return fail(c, DEM_ERR_CAPACITY, "pair list exceeds max_contacts");
-  int rc = size_list(c, li, NP, NW, li != 3);
+  int rc = size_list(c, li, NP, NW, li < 3, st);
   if (rc) return rc;
   ContactList& L = LB.L;
   const uint32_t np32 = (uint32_t)NP, nw32 = (uint32_t)NW;
   const long long lens[2] = {(long long)NP, (long long)NW};
-  cudaMemcpyAsync(L.dn, lens, sizeof(lens), cudaMemcpyHostToDevice, c->st);
-  cudaMemcpyAsync(L.row + ns, &np32, 4, cudaMemcpyHostToDevice, c->st);
-  cudaMemcpyAsync(L.wrow + ns, &nw32, 4, cudaMemcpyHostToDevice, c->st);
-  launch_list_rows(c->D, o, L, old, old_ns, c->st);
-  launch_wall_emit(c->D, o, L.ws, L.ww, c->st);
-  launch_facet_finish(c->D, o, (long long)NF, L.ws, L.ww, c->st);
-  cudaStreamSynchronize(c->st);  // the two host scalars above must outlive their copies
+  cudaMemcpyAsync(L.dn, lens, sizeof(lens), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.row + ns, &np32, 4, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.wrow + ns, &nw32, 4, cudaMemcpyHostToDevice, st);
+  launch_list_rows(c->D, o, L, old, old_ns, st);
+  launch_wall_emit(c->D, o, L.ws, L.ww, st);
+  launch_facet_finish(c->D, o, (long long)NF, L.ws, L.ww, st);
+  cudaStreamSynchronize(st);  // the two host scalars above must outlive their copies
   return cuda_check(c, "detect_into");
+}
+
+// Detection into lists[li] with margin m (per clump from D.cmargin when set),
+// for a list that must last K steps (wall travel) -- also used by the audit.
+// With an old list (old != NULL) the tangential history of the pairs both
+// lists hold is carried over as the rows are built.  wall_extra widens the
+// wall candidates' threshold; si picks the scratch set, st the stream.
+int detect_into(dem_ctx* c, int li, double m, int K, const ContactList* old = nullptr,
+                long long old_ns = 0, double wall_extra = 0.0, int si = 0, cudaStream_t st = nullptr) {
+  if (!st) st = c->st;
+  DetJob J;
+  int rc = detect_prepare(c, li, m, K, wall_extra, si, st, J);
+  if (rc) return rc;
+  return detect_finish(c, J, old, old_ns, st);
 }
 
 // The list at margin m for K steps into lists[li], filtered from the outer
@@ -707,25 +777,25 @@ int filter_into(dem_ctx* c, int li, double m, int K, const ContactList* old, lon
   const double travel = c->P.dt * (double)std::max(1, K);
   auto& LB = c->lists[li];
   const ContactList& O = c->lists[3].L;
-  if (!grow(c, c->b_det, sizeof(int4) * (ns + 1)) || !grow(c, c->b_wall_cnt, 4 * (ns + 1)) ||
-      !grow(c, c->b_pair_cnt, 4 * (ns + 1)) || !grow(c, LB.row, 4 * (ns + 1)) ||
-      !grow(c, LB.wrow, 4 * (ns + 1)) || !grow(c, c->b_scan_scr, scan_scratch_bytes(ns + 1) + 256))
+  if (!grow(c, c->ds[0].det, sizeof(int4) * (ns + 1)) || !grow(c, c->ds[0].wall_cnt, 4 * (ns + 1)) ||
+      !grow(c, c->ds[0].pair_cnt, 4 * (ns + 1)) || !grow(c, LB.row, 4 * (ns + 1)) ||
+      !grow(c, LB.wrow, 4 * (ns + 1)) || !grow(c, c->ds[0].scan_scr, scan_scratch_bytes(ns + 1) + 256))
     return fail(c, DEM_ERR_OOM, "detection buffers");
   DetectOut o{};
-  o.det = ptr<int4>(c->b_det);
-  o.wall_cnt = ptr<uint32_t>(c->b_wall_cnt);
+  o.det = ptr<int4>(c->ds[0].det);
+  o.wall_cnt = ptr<uint32_t>(c->ds[0].wall_cnt);
   o.wall_off = ptr<uint32_t>(LB.wrow);
-  o.pair_cnt = ptr<uint32_t>(c->b_pair_cnt);
+  o.pair_cnt = ptr<uint32_t>(c->ds[0].pair_cnt);
   o.pair_off = ptr<uint32_t>(LB.row);
   o.n_tsph = (int)c->tpl_rad.size();
-  if (!grow(c, c->b_trho, 4 * (size_t)(o.n_tsph + 1))) return fail(c, DEM_ERR_OOM, "detection buffers");
-  o.trho = ptr<int>(c->b_trho);
-  unsigned long long* tot = ptr<unsigned long long>(c->b_totals);
+  if (!grow(c, c->ds[0].trho, 4 * (size_t)(o.n_tsph + 1))) return fail(c, DEM_ERR_OOM, "detection buffers");
+  o.trho = ptr<int>(c->ds[0].trho);
+  unsigned long long* tot = ptr<unsigned long long>(c->ds[0].totals);
   cudaMemsetAsync(tot + 11, 0, sizeof(unsigned long long), c->st);
   launch_lattice_check(c->D, o, m, ptr<int4>(c->b_q0), tot + 11, c->st);
   launch_filter_count(c->D, o, O, m, t, travel, c->st);
-  exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->b_scan_scr.p, tot + 3, c->st);
-  exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->b_scan_scr.p, tot + 1, c->st);
+  exclusive_scan_u32(o.pair_cnt, o.pair_off, ns, c->ds[0].scan_scr.p, tot + 3, c->st);
+  exclusive_scan_u32(o.wall_cnt, o.wall_off, ns, c->ds[0].scan_scr.p, tot + 1, c->st);
   unsigned long long h_tot[12] = {};
   cudaMemcpyAsync(h_tot, tot, 12 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "filter");
@@ -756,14 +826,93 @@ int build_outer(dem_ctx* c, double m, int K) {
   int rc = detect_into(c, 3, mo, c->outer_n * std::max(1, K), nullptr, 0, 0x1p-21);
   if (rc) return rc;
   if (!grow(c, c->b_q0, sizeof(int4) * (c->ns + 1))) return fail(c, DEM_ERR_OOM, "outer list points");
-  cudaMemcpyAsync(c->b_q0.p, c->b_det.p, sizeof(int4) * c->ns, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->b_q0.p, c->ds[0].det.p, sizeof(int4) * c->ns, cudaMemcpyDeviceToDevice, c->st);
   c->outer_valid = true;
   c->outer_used = 0;
   c->outer_ns = c->ns;
   c->outer_m = m;
   c->outer_K = K;
+  c->outer_until = c->step + (long long)c->outer_n * std::max(1, K);
   c->stats.outer_rebuilds++;
   return DEM_OK;
+}
+
+// The next outer list on the second stream (the paper's kinematics thread
+// computing the contact list while the dynamics thread steps, section 2.2,
+// on one GPU): its state-reading part is queued on the context stream now,
+// in order with the steps, and ev_snap marks it; outer_async_finish queues
+// the rest on st2 after the interval's steps have been queued, so that the
+// host's waits for its sizes overlap them; outer_async_adopt makes it the
+// outer list once the context stream has waited for ev_ready.  Its lattice
+// points are those of the time it was started, so every rebuild's
+// allowance check covers the steps since then.  st2 is idle whenever a call
+// returns to the user (dem_step waits for it), so nothing the user changes
+// between calls can be in use there.
+int outer_async_start(dem_ctx* c, double m, int K) {
+  if (!c->st2) {
+    if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_check(c, "second stream");
+  }
+  const long long layout = c->layout;
+  // it is adopted at the next rebuild, at most K steps later, and serves
+  // outer_n rebuilds from there: its wall candidates cover (outer_n + 1) K steps
+  int rc = detect_prepare(c, 4, c->outer_factor * m, (c->outer_n + 1) * std::max(1, K), 0x1p-21, 1,
+                          c->st, c->async_job);
+  c->layout = layout;  // no captured graph refers to the second outer list's buffers
+  if (rc) return rc;
+  cudaEventRecord(c->ev_snap, c->st);
+  c->async_state = 1;
+  c->async_m = m;
+  c->async_K = K;
+  c->async_ns = c->ns;
+  c->async_until = c->step + (long long)(c->outer_n + 1) * std::max(1, K);
+  return cuda_check(c, "outer list start");
+}
+
+int outer_async_finish(dem_ctx* c) {
+  if (c->async_state != 1) return DEM_OK;
+  const long long layout = c->layout;
+  cudaStreamWaitEvent(c->st2, c->ev_snap, 0);
+  int rc = detect_finish(c, c->async_job, nullptr, 0, c->st2);
+  if (rc == DEM_OK && !grow(c, c->b_q1, sizeof(int4) * (c->ns + 1), 0, c->st2))
+    rc = fail(c, DEM_ERR_OOM, "outer list points");
+  c->layout = layout;
+  if (rc) return rc;
+  cudaMemcpyAsync(c->b_q1.p, c->ds[1].det.p, sizeof(int4) * c->ns, cudaMemcpyDeviceToDevice, c->st2);
+  cudaEventRecord(c->ev_ready, c->st2);
+  c->async_state = 2;
+  return cuda_check(c, "outer list finish");
+}
+
+void outer_async_adopt(dem_ctx* c) {
+  cudaStreamWaitEvent(c->st, c->ev_ready, 0);
+  std::swap(c->lists[3], c->lists[4]);
+  std::swap(c->b_q0, c->b_q1);
+  c->outer_valid = true;
+  c->outer_used = 0;
+  c->outer_ns = c->async_ns;
+  c->outer_m = c->async_m;
+  c->outer_K = c->async_K;
+  c->outer_until = c->async_until;
+  c->async_state = 0;
+  c->stats.outer_rebuilds++;
+}
+
+// Drops an outer list in progress (its buffers are reused only after st2 is idle).
+int outer_async_drop(dem_ctx* c) {
+  int rc = DEM_OK;
+  if (c->async_state == 1) rc = outer_async_finish(c);
+  if (c->st2) cudaStreamSynchronize(c->st2);
+  c->async_state = 0;
+  return rc;
+}
+
+// The outer lists no longer hold (new clumps, a new wall motion).
+int invalidate_outer(dem_ctx* c) {
+  c->outer_valid = false;
+  return outer_async_drop(c);
 }
 
 // Rebuilds the current list with margin m (per clump when D.cmargin is set)
@@ -777,17 +926,31 @@ int rebuild(dem_ctx* c, double m, int K, bool allow_outer = true) {
   const ContactList* old = c->have_list ? &curL(c) : nullptr;
   int rc;
   if (allow_outer && c->outer_n > 0 && !c->D.cmargin && m > 0.0) {
+    if (c->async_state == 1 && (rc = outer_async_finish(c))) return rc;
+    // (a list whose wall candidates no longer cover this list's K steps, as
+    // after steps of the learned rule in between, is not used)
+    const long long until = c->step + std::max(1, K);
+    if (c->async_state == 2 && (!c->outer_valid || c->outer_used >= c->outer_n) &&
+        c->async_ns == c->ns && c->async_m == m && c->async_K == K && until <= c->async_until)
+      outer_async_adopt(c);
     const bool stale = !c->outer_valid || c->outer_used >= c->outer_n || c->outer_ns != c->ns ||
-                       c->outer_m != m || c->outer_K != K;
+                       c->outer_m != m || c->outer_K != K || until > c->outer_until;
+    if (stale && (rc = outer_async_drop(c))) return rc;
     if (stale && (rc = build_outer(c, m, K))) return rc;
     bool bad = false;
     if ((rc = filter_into(c, nxt, m, K, old, c->list_ns, &bad))) return rc;
     if (bad) {  // a sphere moved past its allowance: a new outer list
-      if ((rc = build_outer(c, m, K)) || (rc = filter_into(c, nxt, m, K, old, c->list_ns, &bad)))
+      if ((rc = outer_async_drop(c)) || (rc = build_outer(c, m, K)) ||
+          (rc = filter_into(c, nxt, m, K, old, c->list_ns, &bad)))
         return rc;
       if (bad) return fail(c, DEM_ERR_STATE, "internal: a fresh outer list fails its own check");
     }
     c->outer_used++;
+    // the next outer list, started while this one serves its last interval;
+    // the next rebuild finishes it (with the interval's steps already queued)
+    if (c->outer_async && c->n_facets == 0 && c->async_state == 0 &&
+        c->outer_used >= c->outer_n && (rc = outer_async_start(c, m, K)))
+      return rc;
   } else {
     rc = detect_into(c, nxt, m, K, old, c->list_ns);
     if (rc) return rc;
@@ -1344,22 +1507,29 @@ int dem_create(const dem_params* params, dem_ctx** out) {
 void dem_destroy(dem_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->P.device);
+  if (c->st2) cudaStreamSynchronize(c->st2);
   Buf* all[] = {&c->b_tpl_off, &c->b_tp64, &c->b_tp32, &c->b_tmat, &c->b_tmass, &c->b_tinert, &c->b_tpbound,
                 &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cvw,
                 &c->b_tmassf, &c->b_tinertf, &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
                 &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_srec32,
                 &c->b_grids, &c->b_lgrids, &c->b_walls, &c->b_wall_idx, &c->b_wall_scene, &c->b_wfix,
                 &c->b_wpos, &c->b_wforce, &c->b_wtorque, &c->b_pm64, &c->b_pm32, &c->b_flags, &c->b_counters,
-                &c->b_totals, &c->b_det, &c->b_bin_size, &c->b_wall_mask, &c->b_wall_cnt,
-                &c->b_facet_idx, &c->b_fbin_size, &c->b_fbin_start, &c->b_frec, &c->b_fcand, &c->b_fcnt, &c->b_q0,
-                &c->b_bin_start, &c->b_pair_cnt, &c->b_scan_scr, &c->b_tmp,
-                &c->b_rec, &c->b_trho, &c->b_upairs, &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
+                &c->b_facet_idx, &c->b_q0,
+                &c->b_tmp,
+                &c->b_det_cnt, &c->b_det_fill, &c->b_det_off,
                 &c->b_det_ids, &c->b_det_pair, &c->b_det_wall, &c->b_dstep, &c->b_alast, &c->b_chome, &c->b_cmargin,
                 &c->b_bcnt, &c->b_bvmax, &c->b_bvsum, &c->b_bamax, &c->b_occ, &c->b_nocc,
                 &c->b_binm, &c->b_cand, &c->b_feat, &c->b_pred, &c->b_dmax, &c->b_T, &c->b_tr_vox,
                 &c->b_tr_off, &c->b_tr_pos, &c->b_tr_q, &c->b_tx, &c->b_tt,
                 &c->s_state, &c->s_pb, &c->s_u, &c->s_ww, &c->s_uw};
   for (Buf* b : all) dfree(c, b->p);
+  for (auto& S : c->ds) {
+    Buf* sb[] = {&S.det, &S.wall_mask, &S.wall_cnt, &S.pair_cnt, &S.bin_size, &S.bin_start,
+                 &S.scan_scr, &S.trho, &S.totals, &S.rec, &S.upairs, &S.fbin_size,
+                 &S.fbin_start, &S.fcnt, &S.frec, &S.fcand};
+    for (Buf* b : sb) dfree(c, b->p);
+  }
+  dfree(c, c->b_q1.p);
   for (auto& lb : c->lists) {
     Buf* lbs[] = {&lb.pa, &lb.pb, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow, &lb.dnb};
     for (Buf* b : lbs) dfree(c, b->p);
@@ -1368,6 +1538,9 @@ void dem_destroy(dem_ctx* c) {
   drop_graphs(c);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->ev_snap) cudaEventDestroy(c->ev_snap);
+  if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+  if (c->st2) cudaStreamDestroy(c->st2);
   if (c->own_stream) cudaStreamDestroy(c->st);
   delete c;
 }
@@ -1527,7 +1700,7 @@ int dem_add_clumps(dem_ctx* c, int n, const int* tpl, const double* pos, const d
     c->r_mean = c->r_sum / (double)ns;
   }
   c->need_rebuild = true;
-  c->outer_valid = false;
+  if ((rc = invalidate_outer(c))) return rc;
   c->acc_dirty = true;
   if (c->finalized) {
     refresh_devstate(c);
@@ -1554,6 +1727,8 @@ int dem_step(dem_ctx* c, int n_steps) {
     rc = R.run_guarded(n_steps);
   }
   if (rc) return rc;
+  if (c->async_state == 1 && (rc = outer_async_finish(c))) return rc;
+  if (c->st2) cudaStreamSynchronize(c->st2);
   c->stats.time = (double)c->step * c->P.dt;
   rc = read_flags(c);
   R.finish();
@@ -1773,9 +1948,10 @@ int dem_set_wall_motion(dem_ctx* c, int wall, const double* point, const double*
   launch_walls_at(c->D, c->step, c->st);  // wall positions of the current step
   // the listed wall candidates assumed the old motion
   c->need_rebuild = true;
-  c->outer_valid = false;
+  int rc = invalidate_outer(c);
   drop_graphs(c);
   cudaStreamSynchronize(c->st);  // the host table must outlive its copy
+  if (rc) return rc;
   return cuda_check(c, "set_wall_motion");
 }
 
@@ -1816,14 +1992,14 @@ int dem_get_bins(dem_ctx* c, long long cap, unsigned int* keys, int* ids, long l
   if (!c || !n) return DEM_ERR_INVALID_ARG;
   *n = c->n_entries;
   const long long m = std::min(cap, c->n_entries);
-  if (m > 0 && keys && ids && c->b_rec.p) {
+  if (m > 0 && keys && ids && c->ds[0].rec.p) {
     // the device holds the records grouped by bin in slot order: restore
     // the bin key of every entry and sort each bin by sphere id
     const long long B = c->n_entries, nb = c->n_entry_bins;
     if (!grow(c, c->b_tmp, 4 * (size_t)B)) return fail(c, DEM_ERR_OOM, "staging");
-    launch_rec_ids(ptr<EntryRec>(c->b_rec), B, ptr<uint32_t>(c->b_tmp), c->st);
+    launch_rec_ids(ptr<EntryRec>(c->ds[0].rec), B, ptr<uint32_t>(c->b_tmp), c->st);
     std::vector<uint32_t> start((size_t)nb + 1), v((size_t)B);
-    cudaMemcpyAsync(start.data(), c->b_bin_start.p, 4 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, c->st);
+    cudaMemcpyAsync(start.data(), c->ds[0].bin_start.p, 4 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, c->st);
     cudaMemcpyAsync(v.data(), c->b_tmp.p, 4 * (size_t)B, cudaMemcpyDeviceToHost, c->st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "get_bins");
     for (long long k = 0; k < nb; ++k) {
@@ -1994,12 +2170,19 @@ int dem_autotune_tiles(dem_ctx* c, int steps, int reps, dem_tiles* best) {
   return cuda_check(c, "autotune tiles");
 }
 
-int dem_set_outer_list(dem_ctx* c, double factor, int n_inner) {
+int dem_set_outer_list(dem_ctx* c, double factor, int n_inner, int async_detect) {
   if (!c) return DEM_ERR_INVALID_ARG;
   if (n_inner < 0 || (n_inner > 0 && !(factor > 1.0 && std::isfinite(factor))))
     return fail(c, DEM_ERR_INVALID_ARG, "outer list: factor must be > 1 and n_inner >= 0");
+  if (async_detect && c->P.alloc)
+    return fail(c, DEM_ERR_INVALID_ARG,
+                "outer list on a second stream: needs the library's stream-ordered allocator");
+  cudaSetDevice(c->P.device);
+  int rc = outer_async_drop(c);
+  if (rc) return rc;
   c->outer_factor = factor;
   c->outer_n = n_inner;
+  c->outer_async = async_detect != 0;
   c->outer_valid = false;
   return DEM_OK;
 }
@@ -2138,7 +2321,7 @@ int audit_now(dem_ctx* c, long long* missed) {
   c->D.cmargin = saved_cm;
   if (rc) return rc;
   const ContactList& F = c->lists[2].L;
-  unsigned long long* d_m = ptr<unsigned long long>(c->b_totals) + 4;
+  unsigned long long* d_m = ptr<unsigned long long>(c->ds[0].totals) + 4;
   cudaMemsetAsync(d_m, 0, 8, c->st);
   DetectOut o{};
   launch_audit(c->D, o, curL(c), F.n, F.pa, F.pb, F.nw, F.ws, F.ww, (double)c->step * c->P.dt, d_m, c->st);

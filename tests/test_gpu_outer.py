@@ -83,6 +83,70 @@ def test_filtered_lists_are_the_fresh_detection(dem, prec):
             sim.close()
 
 
+@pytest.mark.parametrize("graphs", [False, True])
+@pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
+def test_outer_list_on_a_second_stream_is_the_fresh_detection(dem, prec, graphs):
+    """The next outer list detected on a second stream while the steps run
+    (async_detect): 12 rebuilds 5 steps apart against a context detecting
+    every list afresh, both deterministic; lists and states bit-identical
+    after every rebuild, and an outer list adopted every fourth rebuild."""
+    margin, K = 2e-4, 5
+    sc = _scene(prec, margin=margin)
+    sims = [dem.Simulation(sc, margin=margin, rebuild_interval=K) for _ in range(2)]
+    try:
+        for sim in sims:
+            sim.set_deterministic(True)
+            sim.set_graphs(graphs)
+        sims[1].set_outer_list(3.0, 4, async_detect=True)
+        for sim in sims:
+            sim.step(1)
+        for block in range(11):
+            lists = []
+            for sim in sims:
+                sim.step(K)
+                lists.append(sim.contacts())
+            for x, y in zip(lists[0], lists[1]):
+                assert np.array_equal(x, y), block
+            for x, y in zip(sims[0].state(), sims[1].state()):
+                assert np.array_equal(x, y), block
+        st = sims[1].stats()
+        # built at rebuild 1, then started at rebuilds 4 and 8 and adopted at 5 and 9
+        assert st["rebuilds"] == 12 and st["outer_rebuilds"] == 3
+        # the same steps in one call (the detection overlaps them inside the call)
+        for sim in sims:
+            sim.step(4 * K + 3)
+        for x, y in zip(sims[0].contacts(), sims[1].contacts()):
+            assert np.array_equal(x, y)
+        for x, y in zip(sims[0].state(), sims[1].state()):
+            assert np.array_equal(x, y)
+        assert sims[1].stats()["outer_rebuilds"] == 4
+    finally:
+        for sim in sims:
+            sim.close()
+
+
+def test_outer_list_on_a_second_stream_after_a_jump(dem, oracle_mod):
+    """A state set from outside while an outer list detected on the second
+    stream waits to be adopted: the allowance check rejects it, a new outer
+    list is detected, and the list is the oracle's detection of that state."""
+    margin, K = 1e-4, 5
+    sc = _scene(scenes.PREC_FP64, seed=23)
+    pos = sc.pos.copy()
+    pos[::7, 0] += 1e-3
+    with dem.Simulation(sc, margin=margin, rebuild_interval=K) as sim:
+        sim.set_outer_list(3.0, 2, async_detect=True)
+        sim.step(K + 1)  # rebuilds at steps 0 and 5: the one at 5 started the next list
+        n_outer = sim.stats()["outer_rebuilds"]
+        t = sim.stats()["time"]
+        sim.set_state(pos, sc.quat, sc.vel, sc.angvel)
+        sim.step(1)
+        a, b, u, ws, ww, uw = sim.contacts()
+        assert sim.stats()["outer_rebuilds"] == n_outer + 2  # adopted, rejected, detected
+    ao, bo, wso, wwo = _fresh(oracle_mod, sc, pos, sc.quat, margin, K, t)
+    assert np.array_equal(a, ao) and np.array_equal(b, bo)
+    assert np.array_equal(ws, wso) and np.array_equal(ww, wwo)
+
+
 def test_outer_list_fp64_trajectory_matches_oracle(dem, oracle_mod):
     """45 steps with a rebuild every 5, the lists filtered from outer lists:
     trajectory, lists and histories against the oracle's own run of the

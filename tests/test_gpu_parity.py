@@ -109,6 +109,20 @@ def _compare_forces(sc, F, T, Fo, To, mag, tol):
     return errF[touched].max(), errT[touched].max()
 
 
+def _net_force_error(sc, F, Fo, mag):
+    """Each clump's force error relative to its net force |F_ref|, floored
+    at 1e-3 m |g| (a clump at rest under balanced contacts has a net force
+    near zero whatever the precision), and the ratio of the contributions'
+    sum to that net force (the cancellation that separates the two bounds)."""
+    m = sc.tpl_mass[sc.tpl]
+    g = float(np.linalg.norm(sc.g))
+    net = np.maximum(np.linalg.norm(Fo, axis=1), 1e-3 * m * g)
+    touched = mag[:, 0] > 0
+    err = np.linalg.norm(F - Fo, axis=1)[touched] / net[touched]
+    cancel = mag[touched, 0] / net[touched]
+    return err, cancel
+
+
 @pytest.mark.parametrize("prec", [scenes.PREC_FP64, scenes.PREC_FP32])
 @pytest.mark.parametrize("seed,n", [(4, 300), (5, 777)])
 def test_forces_match_oracle(dem, oracle_mod, prec, seed, n):
@@ -124,6 +138,13 @@ def test_forces_match_oracle(dem, oracle_mod, prec, seed, n):
                                             with_mag=True)
     assert st["active_last"] == act
     _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
+    # the error against the net force: within TOL x the cancellation ratio
+    # (bound of the per-contact error summed), and reported
+    err, cancel = _net_force_error(sc, F, Fo, mag)
+    assert np.all(err <= 2.0 * TOL[prec] * cancel)
+    print(f"net-force error prec={prec} n={n}: median {np.median(err):.2e} p99 "
+          f"{np.percentile(err, 99):.2e} max {err.max():.2e}; cancellation median "
+          f"{np.median(cancel):.1f} max {cancel.max():.1f}")
     if len(ws):
         assert np.abs(Fw - Fwo).max() <= TOL[prec] * np.abs(Fwo).sum()
 
