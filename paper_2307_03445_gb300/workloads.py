@@ -10,6 +10,7 @@ materials and dt = 1e-6 s from that settled, copied bed.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 import time
 
@@ -186,7 +187,7 @@ def settled_bed(base: scenes.Scene, n_clumps: int, x0: float, x1: float, y0: flo
     soft.pos, soft.quat, soft.vel, soft.angvel = pos, quat, vel, angvel
     pos, quat, vel, angvel = settle(soft, stiffen_time, v_bound=2.0, K=20, log=log)
     perm = scenes.morton_order(pos, base.lo, 2.0 * float(bound_t.max()))
-    out = scenes.Scene(**{**base.__dict__})
+    out = dataclasses.replace(base)  # the dataclass fields (not attributes set on base)
     out.tpl, out.pos, out.quat = tpl[perm], pos[perm], quat[perm]
     out.vel, out.angvel = vel[perm], angvel[perm]
     out.hi = (base.hi[0], base.hi[1], max(base.hi[2], float(pos[:, 2].max()) + 0.05))
