@@ -26,7 +26,7 @@
  *   A11 multi-bin registration of the enlarged AABB, pair reported by the bin
  *       holding the per-axis max of the two lower corners; exact int64 test.
  *   A15 sphere-wall contacts: R = r_sphere, m = m_clump, wall material given.
- *   A16 mesh facets (section 4 funnel, cone and wheel meshes): distance to
+ *   B1 mesh facets (section 4 funnel, cone and wheel meshes): distance to
  *       the closed triangle; the signed plane distance where the centre
  *       projects inside it, else the unsigned distance to the nearest edge;
  *       every sphere-facet pair is its own contact.
@@ -269,7 +269,7 @@ long long orc_pairs_binned(const orc_model* m, long long ns, const int* owner,
 /* ------------------------------------------------------------------ */
 /* Mesh facet with vertices p, b, c (translating rigidly, so the edge
  * vectors e1 = b - p, e2 = c - p do not depend on time) and d = x - p(t).
- * A facet is one-sided (reading A16): a centre behind its plane (d.n < 0)
+ * A facet is one-sided (reading B1): a centre behind its plane (d.n < 0)
  * does not touch it, whatever its distance; the result is +infinity, which
  * no candidate threshold reaches and which gives no overlap.  (Without this a
  * sphere on the far side of a convex mesh, behind a far facet and inside that

@@ -3,7 +3,7 @@ paper builds from meshes in section 4): in front of the facet's plane the
 distance is the distance to the closed triangle, checked against brute
 force over a dense sampling of the facet; in the facet's face region it is
 exactly the plane wall's; beyond a vertex it is the distance to that vertex.
-A facet is one-sided (reading A16): a centre behind its plane is at infinite
+A facet is one-sided (reading B1): a centre behind its plane is at infinite
 distance, so a sphere that reaches a facet from behind passes through it."""
 import math
 import numpy as np
