@@ -302,7 +302,7 @@ def _timed_steps(sim, stream, n):
 
 
 def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, start_state=None,
-                 intervals=4, interval=80, audited=80):
+                 intervals=4, interval=80, audited=80, cand=None):
     """The learned rebuild rule on the same bed: traces of the plain rule and
     training on the GPU (untimed), then `intervals` whole intervals of
     `interval` steps timed with the learned rule and, from the same state,
@@ -313,7 +313,8 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
     t0 = time.time()
     if start_state is None:
         start_state = sim.state()
-    x, t = sim.trace(2, 240, LEARN_CAND, cap=1 << 24)
+    cand = LEARN_CAND if cand is None else cand
+    x, t = sim.trace(2, 240, cand, cap=1 << 24)
     reg = dem.Regressor(device=sim_device(sim))
     loss = reg.train(x, t, steps=800, batch=8192, lr=2e-3, seed=1)
     log(f"learned form: {len(x)} trace samples, loss {loss:.4f}, {time.time() - t0:.1f} s")
@@ -327,7 +328,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
     # the learned rule from the same state; interval x safety stays inside
     # the traced window, where lifetimes are not capped
     sim.set_state(*start_state)
-    sim.set_learned_policy(reg, interval=interval, safety=2.0, candidates=LEARN_CAND)
+    sim.set_learned_policy(reg, interval=interval, safety=2.0, candidates=cand)
     sim.reset_stats()
     ms = _timed_steps(sim, stream, n)
     st = sim.stats()
@@ -348,7 +349,8 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
             "missed_contacts": missed, "audited_steps": audited,
             "ms_predict_per_interval": st["ms_predict"] / max(1, st["rebuilds"]),
             "ms_rebuild_per_interval": st["ms_detect"] / max(1, st["rebuilds"]),
-            "rule": f"6->3x64->1 MLP (BF16 weights) per bin, candidates 1-32 um, target "
+            "rule": f"6->3x64->1 MLP (BF16 weights) per bin, candidates {cand[0] * 1e6:g}-"
+                    f"{cand[-1] * 1e6:g} um, target "
                     f"interval {interval} x 2.0, halt on certificate; trained on 2 x 240-step "
                     f"traces; timed over {intervals} whole intervals; exact audit after each of "
                     f"{audited} further steps"}
@@ -583,8 +585,11 @@ def small_config_line(args, dem, workloads, world, rank, local, log):
         del out
     if args.config == 3 and not args.no_forms:
         sim.set_state(*s0)
+        # the settled cylinder still holds rattling clumps: candidates up to
+        # 128 um so that their bins can be given a margin for a whole interval
         line["forms"] = {"learned": learned_form(dem, sim, stream, args.steps, ns, st,
-                                                 ms / args.steps, log, start_state=s0)}
+                                                 ms / args.steps, log, start_state=s0,
+                                                 cand=LEARN_CAND + [6.4e-5, 1.28e-4])}
     sim.close()
     if rank == 0 and not args.no_cpu_baseline and args.config == 1:
         # the oracle runs this workload whole (1,000 clumps), on one core and on all
@@ -626,6 +631,10 @@ def main():
     ap.add_argument("--boundary", default="analytic", choices=["analytic", "mesh"],
                     help="the box and plate as analytic planes, or as 12 mesh facets with a "
                          "cone of 544 facets pushed into the bed")
+    ap.add_argument("--outer-list", type=int, default=4,
+                    help="rebuilds one outer list (3 x the margin) serves in the timed run; every "
+                         "list filtered from it is exactly the fresh detection's (0: every "
+                         "rebuild detects afresh)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned-margin and batched forms")
     ap.add_argument("--config", type=int, default=5, choices=[1, 2, 3, 4, 5],
@@ -690,6 +699,8 @@ def main():
     sim = dem.Simulation(sc, margin=margin, rebuild_interval=K_REBUILD,
                          precision=dem.DEM_FP32_VOXEL, device=local, stream=stream.cuda_stream)
     ns, ncl = sc.n_spheres, sc.n_clumps
+    if args.outer_list > 0:
+        sim.set_outer_list(3.0, args.outer_list)
     sim.step(args.warmup)
     bin_factor, bin_ms = sim.autotune_bins(BIN_FACTORS, reps=1)
     log(f"bin autotune: factor {bin_factor} ({bin_ms})")
@@ -799,6 +810,12 @@ def main():
                    "listed_pairs": n_pairs, "active_contacts": n_active,
                    "wall_contacts": st["n_wall_contacts"], "margin_m": margin,
                    "rebuild_interval": K_REBUILD, "dt": sc.h, "rebuilds": st["rebuilds"],
+                   "contact_list": (f"two-level: an outer list at 3 x the margin serves "
+                                    f"{args.outer_list} rebuilds, each list filtered from it "
+                                    f"with the exact test (equal to a fresh detection); "
+                                    f"{st['outer_rebuilds']} outer detections in the timed "
+                                    f"steps" if args.outer_list > 0 else
+                                    "a fresh detection at every rebuild"),
                    "bin_factor": bin_factor, "bin_autotune_ms": bin_ms, "tiles": tiles,
                    "guard_violations": st["guard_violations"],
                    "l2": "inputs larger than L2 (state ~GBs)", "parallelism": f"replicas{world}",

@@ -12,6 +12,8 @@
 // The update kernel integrates Eq. (5) for a block of clumps, then, with the
 // new orientation held as a float-float rotation matrix in shared memory,
 // recomputes the pose records of all spheres of those clumps.
+#include <algorithm>
+
 #include "dem_dev.cuh"
 #include "dem_prims.cuh"
 #include "dem_walls.cuh"
@@ -1070,7 +1072,12 @@ void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_
                         cudaStream_t st) {
   (void)t;
   if (d.nwalls == 0) return;
-  const unsigned grid = (unsigned)sm_count() * 2;
+  // about one wall contact per thread (the list's length at its rebuild; the
+  // kernel strides over the length on the device), at most the blocks that
+  // fit at once (80 registers x 128 threads: 6 per SM)
+  const long long want = (l.nw + 127) / 128;
+  const long long cap = (long long)sm_count() * 6;
+  const unsigned grid = (unsigned)std::max(1LL, std::min(want, cap));
   if (d.prec == 0)
     { k_walls64<<<grid, 128, 0, st>>>(d, l, count_active ? 1 : 0); count_launch(); }
   else
