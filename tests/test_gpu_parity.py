@@ -138,10 +138,11 @@ def test_forces_match_oracle(dem, oracle_mod, prec, seed, n):
                                             with_mag=True)
     assert st["active_last"] == act
     _compare_forces(sc, F, T, Fo, To, mag, TOL[prec])
-    # the error against the net force: within TOL x the cancellation ratio
-    # (bound of the per-contact error summed), and reported
+    # the error against the net force floored at 1e-3 m |g| (reading A17):
+    # within TOL itself, on these cases where the contributions cancel by up
+    # to 21x (reported)
     err, cancel = _net_force_error(sc, F, Fo, mag)
-    assert np.all(err <= 2.0 * TOL[prec] * cancel)
+    assert err.max() <= TOL[prec], (err.max(), cancel.max())
     print(f"net-force error prec={prec} n={n}: median {np.median(err):.2e} p99 "
           f"{np.percentile(err, 99):.2e} max {err.max():.2e}; cancellation median "
           f"{np.median(cancel):.1f} max {cancel.max():.1f}")
