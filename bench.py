@@ -76,16 +76,13 @@ def IMPL_PAIRS(ncl, ns, n_pairs, n_active):
     return 8 * n_pairs + 48 * n_active + 24 * ns + 128 * ncl
 
 
-# DRAM read + write bytes per launch of the current kernels, from one ncu
-# capture on the 11M-clump bed (the profile named beside each); None until
-# the current kernels have been captured.
 # DRAM bytes (read + write) of one launch in an ncu capture of the same
 # kernel on the 687,504-clump bed of the same depth (--footprint 1x0.5), with
 # that launch's algorithmic bytes; a launch on a bed of this family is scaled
 # by its algorithmic bytes (both grow with the clumps, spheres and pairs in
 # the same proportions).  None once the kernel changes.
-TRAFFIC = {"k_update32": (140.312832e6 + 97.429504e6, 181879360),
-           "k_pairs32": (193.093120e6 + 42.739200e6, 202176992)}
+TRAFFIC = {"k_update32": (140.322048e6 + 97.068544e6, 181879360),
+           "k_pairs32": (194.522880e6 + 39.961088e6, 202154256)}
 TRAFFIC_SRC = {k: "ncu dram__bytes_read.sum + dram__bytes_write.sum, 687,504-clump bed, scaled "
                   "by algorithmic bytes (profiles/ncu_pairs_update_bed_2M_spheres.md)"
                for k in TRAFFIC}
@@ -341,7 +338,9 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
     reg.close()
     return {"value": ns * n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / n,
             "steps": n, "intervals": intervals, "plain_ms_per_step_same_steps": ms_plain / n,
-            "vs_plain": ms_plain / ms, "rebuilds": st["rebuilds"],
+            "vs_plain": ms_plain / ms,
+            # against the headline run's step (the plain rule on the two-level list)
+            "vs_headline_step": plain_ms_step / (ms / n), "rebuilds": st["rebuilds"],
             "early_rebuilds": st["early_rebuilds"], "rollbacks": st["rollbacks"],
             "listed_per_step": st["pair_steps"] / max(1, st["steps"]),
             "listed_per_step_plain": st_plain["pair_steps"] / max(1, st_plain["steps"]),
@@ -364,6 +363,7 @@ def outer_form(sim, stream, ns, log, factor=3.0, n_inner=4, cycles=4):
     from the same state; both with per-phase events."""
     s0 = sim.state()
     n = cycles * n_inner * K_REBUILD
+    sim.set_outer_list(factor, 0)  # the plain rule: a fresh detection at every rebuild
     sim.set_timing(True)
     sim.set_state(*s0)
     sim.reset_stats()

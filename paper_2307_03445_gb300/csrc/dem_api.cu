@@ -139,6 +139,10 @@ struct dem_ctx {
   dem_stats stats{};
   DevState D{};
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // learned rule, halt mode: the halt step read back after every chunk of
+  // steps (pinned host slots, one per chunk in flight, and their events)
+  long long* h_halt = nullptr;
+  cudaEvent_t ev_halt[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> evpool;  // 4 per timed step, read at the end of dem_step
   // learned rebuild rule (extension) and rollback snapshots
   dem_mlp* mlp = nullptr;
@@ -1255,14 +1259,38 @@ struct StepRunner {
   // the certificate.  Returns the steps completed (>= 1) in *done.
   int run_halting(int nb, int* done) {
     long long* halt = ptr<long long>(c->b_dstep) + 1;
-    const long long big = LLONG_MAX;
+    static const long long big = LLONG_MAX;
     cudaMemcpyAsync(halt, &big, sizeof(big), cudaMemcpyHostToDevice, c->st);
     const float* cm = c->D.cmargin;
     const long long step0 = c->step, n_list = curL(c).n + curL(c).nw;
     c->D.halt_at = halt;
-    for (int i = 0; i < nb; ++i) {
-      c->D.cmargin = cm;
-      step(c->margin, true, i == nb - 1);
+    if (!c->h_halt) {
+      if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_halt), 2 * sizeof(long long),
+                        cudaHostAllocDefault) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_halt[0], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_halt[1], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_check(c, "halt read-back");
+    }
+    // the interval is launched in chunks; after each chunk the halt step is
+    // copied to the host, and the copy of the chunk before is waited for
+    // while this one runs: once a halt is seen, no further chunk is launched
+    // (the steps launched after the halt return at once on the device)
+    constexpr int kChunk = 8;
+    int launched = 0, k = 0;
+    while (launched < nb) {
+      const int m = std::min(kChunk, nb - launched);
+      for (int j = 0; j < m; ++j) {
+        c->D.cmargin = cm;
+        step(c->margin, true, launched + j == nb - 1);
+      }
+      launched += m;
+      cudaMemcpyAsync(c->h_halt + (k & 1), halt, sizeof(long long), cudaMemcpyDeviceToHost, c->st);
+      cudaEventRecord(c->ev_halt[k & 1], c->st);
+      if (k > 0) {
+        cudaEventSynchronize(c->ev_halt[(k - 1) & 1]);
+        if (c->h_halt[(k - 1) & 1] != LLONG_MAX) break;
+      }
+      ++k;
     }
     c->D.halt_at = nullptr;
     long long dstep = 0;
@@ -1271,8 +1299,8 @@ struct StepRunner {
     int rc = read_flags(c, &hit);  // synchronises: dstep and the halt value are in
     if (rc) return rc;
     const long long d = dstep - step0;
-    if (d < 1 || d > nb) return fail(c, DEM_ERR_STATE, "internal: halted interval out of range");
-    const long long undone = nb - d;
+    if (d < 1 || d > launched) return fail(c, DEM_ERR_STATE, "internal: halted interval out of range");
+    const long long undone = launched - d;
     if (undone > 0) {
       c->step -= undone;
       c->since -= (int)undone;
@@ -1538,6 +1566,9 @@ void dem_destroy(dem_ctx* c) {
   drop_graphs(c);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->ev_halt[0]) cudaEventDestroy(c->ev_halt[0]);
+  if (c->ev_halt[1]) cudaEventDestroy(c->ev_halt[1]);
+  if (c->h_halt) cudaFreeHost(c->h_halt);
   if (c->ev_snap) cudaEventDestroy(c->ev_snap);
   if (c->ev_ready) cudaEventDestroy(c->ev_ready);
   if (c->st2) cudaStreamDestroy(c->st2);
