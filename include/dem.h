@@ -434,7 +434,9 @@ int dem_mlp_train(dem_mlp* mlp, long long n, const float* x, const float* t, int
  *     every later step of the interval is skipped on the device before it
  *     computes a force (its kernels see the halt step and return); the list
  *     is rebuilt at once and stepping continues.  Nothing is rolled back; no
- *     force is ever computed with a list that lacks a contact.
+ *     force is ever computed with a list that lacks a contact.  The interval
+ *     is launched in chunks of 8 steps and the host reads the halt step back
+ *     one chunk behind, so at most about two chunks are launched past a halt.
  *   DEM_LEARNED_ROLLBACK (1): the interval runs to its end; it is then judged
  *     by the certificate and by the exact check against a fresh zero-margin
  *     detection (as dem_audit); on a failure or a missing contact the state
