@@ -299,7 +299,7 @@ def _timed_steps(sim, stream, n):
 
 
 def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, start_state=None,
-                 intervals=4, interval=80, audited=80, cand=None):
+                 intervals=4, interval=80, audited=80, cand=None, safety=2.0):
     """The learned rebuild rule on the same bed: traces of the plain rule and
     training on the GPU (untimed), then `intervals` whole intervals of
     `interval` steps timed with the learned rule and, from the same state,
@@ -325,7 +325,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
     # the learned rule from the same state; interval x safety stays inside
     # the traced window, where lifetimes are not capped
     sim.set_state(*start_state)
-    sim.set_learned_policy(reg, interval=interval, safety=2.0, candidates=cand)
+    sim.set_learned_policy(reg, interval=interval, safety=safety, candidates=cand)
     sim.reset_stats()
     ms = _timed_steps(sim, stream, n)
     st = sim.stats()
@@ -350,7 +350,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
             "ms_rebuild_per_interval": st["ms_detect"] / max(1, st["rebuilds"]),
             "rule": f"6->3x64->1 MLP (BF16 weights) per bin, candidates {cand[0] * 1e6:g}-"
                     f"{cand[-1] * 1e6:g} um, target "
-                    f"interval {interval} x 2.0, halt on certificate; trained on 2 x 240-step "
+                    f"interval {interval} x {safety:g}, halt on certificate; trained on 2 x 240-step "
                     f"traces; timed over {intervals} whole intervals; exact audit after each of "
                     f"{audited} further steps"}
 
