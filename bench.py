@@ -704,7 +704,7 @@ def main():
     sim.step(args.warmup)
     bin_factor, bin_ms = sim.autotune_bins(BIN_FACTORS, reps=1)
     log(f"bin autotune: factor {bin_factor} ({bin_ms})")
-    tiles = sim.autotune_tiles(steps=6, reps=1)
+    tiles = sim.autotune_tiles(steps=6, reps=2)
     log(f"tile autotune: {tiles}")
     sim.step(args.warmup)
     sim.reset_stats()
