@@ -299,7 +299,7 @@ def _timed_steps(sim, stream, n):
 
 
 def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, start_state=None,
-                 intervals=4, interval=80, audited=80, cand=None, safety=2.0):
+                 intervals=4, interval=80, audited=80, cand=None, safety=2.0, speed_floor=0.0):
     """The learned rebuild rule on the same bed: traces of the plain rule and
     training on the GPU (untimed), then `intervals` whole intervals of
     `interval` steps timed with the learned rule and, from the same state,
@@ -325,7 +325,8 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
     # the learned rule from the same state; interval x safety stays inside
     # the traced window, where lifetimes are not capped
     sim.set_state(*start_state)
-    sim.set_learned_policy(reg, interval=interval, safety=safety, candidates=cand)
+    sim.set_learned_policy(reg, interval=interval, safety=safety, candidates=cand,
+                           speed_floor=speed_floor)
     sim.reset_stats()
     ms = _timed_steps(sim, stream, n)
     st = sim.stats()
@@ -350,7 +351,10 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
             "ms_rebuild_per_interval": st["ms_detect"] / max(1, st["rebuilds"]),
             "rule": f"6->3x64->1 MLP (BF16 weights) per bin, candidates {cand[0] * 1e6:g}-"
                     f"{cand[-1] * 1e6:g} um, target "
-                    f"interval {interval} x {safety:g}, halt on certificate; trained on 2 x 240-step "
+                    f"interval {interval} x {safety:g}, "
+                    + (f"margins at least {speed_floor:g} x h x interval x speed per clump, "
+                       if speed_floor > 0 else "")
+                    + f"halt on certificate; trained on 2 x 240-step "
                     f"traces; timed over {intervals} whole intervals; exact audit after each of "
                     f"{audited} further steps"}
 
@@ -589,7 +593,8 @@ def small_config_line(args, dem, workloads, world, rank, local, log):
         # 128 um so that their bins can be given a margin for a whole interval
         line["forms"] = {"learned": learned_form(dem, sim, stream, args.steps, ns, st,
                                                  ms / args.steps, log, start_state=s0,
-                                                 cand=LEARN_CAND + [6.4e-5, 1.28e-4])}
+                                                 cand=LEARN_CAND + [6.4e-5, 1.28e-4],
+                                                 speed_floor=1.5)}
     sim.close()
     if rank == 0 and not args.no_cpu_baseline and args.config == 1:
         # the oracle runs this workload whole (1,000 clumps), on one core and on all
@@ -784,7 +789,8 @@ def main():
     forms = None
     if not args.no_forms:
         forms = {"outer_list": outer_form(sim, stream, ns, log),
-                 "learned": learned_form(dem, sim, stream, args.steps, ns, st, ms_step, log)}
+                 "learned": learned_form(dem, sim, stream, args.steps, ns, st, ms_step, log,
+                                         speed_floor=1.5)}
     sim.close()
     if forms is not None:
         forms["batched"] = batched_form(dem, args.steps, local, log)

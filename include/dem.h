@@ -443,6 +443,12 @@ int dem_mlp_train(dem_mlp* mlp, long long n, const float* x, const float* t, int
  *     and tangential history are rolled back to the rebuild and the interval
  *     is replayed with the plain rule (margin and rebuild_interval of
  *     dem_params), and with a rebuild every step if that fails too.
+ * speed_floor (>= 0; 0 turns it off) keeps every clump's margin at least
+ * speed_floor * h * interval * (|v| + |omega| b), b the template's largest
+ * sphere-centre distance from its centre of mass, at the clump's speed when
+ * the margins are chosen: the distance it covers in the interval at that
+ * speed.  The regressor judges bins; a fast clump in a bin of slow ones would
+ * otherwise end the interval early on the certificate.
  * mlp = NULL restores the plain rule.  The regressor must outlive its use. */
 enum { DEM_LEARNED_HALT = 0, DEM_LEARNED_ROLLBACK = 1 };
 typedef struct {
@@ -451,6 +457,7 @@ typedef struct {
     int n_candidates;
     const double* candidates;
     int mode;                 /* DEM_LEARNED_HALT or DEM_LEARNED_ROLLBACK */
+    double speed_floor;       /* 0: off; else the margin floor's factor (see above) */
 } dem_learned_params;
 int dem_set_learned_policy(dem_ctx* ctx, dem_mlp* mlp, const dem_learned_params* params);
 

@@ -282,7 +282,7 @@ class Simulation:
         self._check(self.lib.dem_set_graphs(self.ctx, 1 if on else 0))
 
     def set_learned_policy(self, regressor, interval=40, safety=1.5, candidates=None,
-                           mode=capi.DEM_LEARNED_HALT):
+                           mode=capi.DEM_LEARNED_HALT, speed_floor=0.0):
         """Learned rebuild rule (see include/dem.h); regressor=None restores the plain rule."""
         if regressor is None:
             self._check(self.lib.dem_set_learned_policy(self.ctx, None, None))
@@ -290,7 +290,8 @@ class Simulation:
             return
         cand = _f64(candidates)
         self._cand = cand
-        lp = capi.DemLearnedParams(int(interval), float(safety), len(cand), _pd(cand), int(mode))
+        lp = capi.DemLearnedParams(int(interval), float(safety), len(cand), _pd(cand), int(mode),
+                                   float(speed_floor))
         self._check(self.lib.dem_set_learned_policy(self.ctx, regressor.h, C.byref(lp)))
         self._regressor = regressor  # keep it alive while in use
 

@@ -67,7 +67,8 @@ _V = C.c_void_p
 
 class DemLearnedParams(C.Structure):
     _fields_ = [("interval", C.c_int), ("safety", C.c_double), ("n_candidates", C.c_int),
-                ("candidates", C.POINTER(C.c_double)), ("mode", C.c_int)]
+                ("candidates", C.POINTER(C.c_double)), ("mode", C.c_int),
+                ("speed_floor", C.c_double)]
 
 
 DEM_LEARNED_HALT, DEM_LEARNED_ROLLBACK = 0, 1

@@ -149,6 +149,7 @@ struct dem_ctx {
   int l_interval = 0;
   double l_safety = 1.0;
   int l_mode = 0;
+  double l_floor = 0.0;  // speed floor factor of the learned margins (0: off)
   // deterministic reduction: slot buffers and per-clump slot lists of the current list
   int det = 0;
   bool det_ready = false;
@@ -1078,7 +1079,9 @@ int predict_margins(dem_ctx* c) {
     const float ln_need = (float)std::log(std::max(1.0, c->l_interval * c->l_safety));
     launch_choose_margin(ptr<uint32_t>(c->b_occ), nocc, nc, ptr<float>(c->b_cand),
                          ptr<float>(c->b_pred), ln_need, ptr<float>(c->b_binm), c->st);
-    launch_clump_margin(ncl, bs.chome, ptr<float>(c->b_binm), ptr<float>(c->b_cmargin), c->st);
+    const float floor_scale = (float)(c->l_floor * c->P.dt * c->l_interval);
+    launch_clump_margin(c->D, bs.chome, ptr<float>(c->b_binm), floor_scale,
+                        ptr<float>(c->b_cmargin), c->st);
     c->D.cmargin = ptr<float>(c->b_cmargin);
   }
   return cuda_check(c, "predict margins");
@@ -2252,9 +2255,12 @@ int dem_set_learned_policy(dem_ctx* c, dem_mlp* mlp, const dem_learned_params* l
   c->mlp = mlp;
   if (lp->mode != DEM_LEARNED_HALT && lp->mode != DEM_LEARNED_ROLLBACK)
     return fail(c, DEM_ERR_INVALID_ARG, "learned policy mode");
+  if (!(lp->speed_floor >= 0.0) || !std::isfinite(lp->speed_floor))
+    return fail(c, DEM_ERR_INVALID_ARG, "learned policy speed floor must be finite and >= 0");
   c->l_interval = lp->interval;
   c->l_safety = lp->safety;
   c->l_mode = lp->mode;
+  c->l_floor = lp->speed_floor;
   c->l_cand.assign(lp->candidates, lp->candidates + lp->n_candidates);
   c->need_rebuild = true;
   return DEM_OK;

@@ -108,10 +108,16 @@ __global__ void k_choose_margin(const uint32_t* __restrict__ occ, long long n_oc
   bin_margin[occ[b]] = m;
 }
 
-__global__ void k_clump_margin(long long ncl, const uint32_t* __restrict__ chome,
-                               const float* __restrict__ bin_margin, float* __restrict__ cmargin) {
+// The clump's margin: its home bin's, at least floor_scale times its speed
+// bound (the distance it covers in the interval at its current speed).
+__global__ void k_clump_margin(DevState d, const uint32_t* __restrict__ chome,
+                               const float* __restrict__ bin_margin, float floor_scale,
+                               float* __restrict__ cmargin) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < ncl) cmargin[c] = bin_margin[chome[c]];
+  if (c >= d.ncl) return;
+  float m = bin_margin[chome[c]];
+  if (floor_scale > 0.f) m = fmaxf(m, floor_scale * clump_speed_bound(d, c, d.cinfo[c].x));
+  cmargin[c] = m;
 }
 
 // Displacement bound of every clump since the trace reference, maxed per home bin.
@@ -212,10 +218,10 @@ void launch_choose_margin(const uint32_t* occ, long long n_occ, int nc, const fl
   k_choose_margin<<<nblk(n_occ, 256), 256, 0, st>>>(occ, n_occ, nc, cand, y, ln_need, bin_margin);
   count_launch();
 }
-void launch_clump_margin(long long ncl, const uint32_t* chome, const float* bin_margin,
-                         float* cmargin, cudaStream_t st) {
-  if (ncl == 0) return;
-  k_clump_margin<<<nblk(ncl, 256), 256, 0, st>>>(ncl, chome, bin_margin, cmargin);
+void launch_clump_margin(const DevState& d, const uint32_t* chome, const float* bin_margin,
+                         float floor_scale, float* cmargin, cudaStream_t st) {
+  if (d.ncl == 0) return;
+  k_clump_margin<<<nblk(d.ncl, 256), 256, 0, st>>>(d, chome, bin_margin, floor_scale, cmargin);
   count_launch();
 }
 void launch_trace_ref(const DevState& d, const TraceRef& tr, cudaStream_t st) {

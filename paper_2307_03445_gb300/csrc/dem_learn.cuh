@@ -34,8 +34,8 @@ void launch_bin_features(const BinStats& bs, const uint32_t* occ, long long n_oc
                          const float* cand, const FeatureScales& fs, float* x, cudaStream_t st);
 void launch_choose_margin(const uint32_t* occ, long long n_occ, int nc, const float* cand,
                           const float* y, float ln_need, float* bin_margin, cudaStream_t st);
-void launch_clump_margin(long long ncl, const uint32_t* chome, const float* bin_margin,
-                         float* cmargin, cudaStream_t st);
+void launch_clump_margin(const DevState& d, const uint32_t* chome, const float* bin_margin,
+                         float floor_scale, float* cmargin, cudaStream_t st);
 void launch_trace_ref(const DevState& d, const TraceRef& tr, cudaStream_t st);
 void launch_trace_step(const DevState& d, const TraceRef& tr, const uint32_t* chome, int* dmax,
                        const uint32_t* occ, long long n_occ, int nc, const float* cand, int* T,

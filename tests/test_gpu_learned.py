@@ -142,6 +142,32 @@ def test_bad_predictions_never_miss_a_contact(dem, bed, mode):
     assert np.abs(pos_l - pos_p).max() <= 1e-3 * moved
 
 
+def test_speed_floor_keeps_fast_clumps_listed(dem, bed):
+    """A regressor that promises every bin an everlasting list gives every
+    clump the smallest candidate (1 um), and the clumps the plate drags end
+    intervals early; with the speed floor each clump's margin covers at least
+    its own travel over the interval at its speed, so fewer intervals end
+    early.  No contact is missed either way, and a negative or non-finite
+    floor is refused."""
+    sc = bed
+    reg = _everlasting(dem)
+    early = []
+    for floor in (0.0, 1.5):
+        with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
+            sim.set_learned_policy(reg, interval=40, safety=1.0, candidates=CAND,
+                                   speed_floor=floor)
+            sim.step(400)
+            st = sim.stats()
+            assert st["steps"] == 400 and sim.audit() == 0
+            early.append(st["early_rebuilds"])
+    assert early[0] >= 1 and early[1] < early[0], early
+    with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
+        for bad in (-1.0, float("nan"), float("inf")):
+            with pytest.raises(dem.DemError, match="INVALID"):
+                sim.set_learned_policy(reg, interval=40, safety=1.0, candidates=CAND,
+                                       speed_floor=bad)
+
+
 def test_trained_rule_beats_the_plain_rule(dem, bed):
     """Trained on traces of the plain rule, the learned rule lists fewer pairs
     and rebuilds less often than the plain rule, with zero missed contacts."""
