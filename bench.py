@@ -359,7 +359,7 @@ def learned_form(dem, sim, stream, steps, ns, plain_st, plain_ms_step, log, star
                     f"{audited} further steps"}
 
 
-def outer_form(sim, stream, ns, log, factor=3.0, n_inner=4, cycles=4):
+def outer_form(sim, stream, ns, log, factor=4.0, n_inner=10, cycles=2):
     """The two-level contact list on the same bed: an outer list at factor x
     the margin serves n_inner rebuilds (each a filter of the outer list that
     gives the fresh detection's list).  Timed over whole outer cycles
@@ -636,8 +636,10 @@ def main():
     ap.add_argument("--boundary", default="analytic", choices=["analytic", "mesh"],
                     help="the box and plate as analytic planes, or as 12 mesh facets with a "
                          "cone of 544 facets pushed into the bed")
-    ap.add_argument("--outer-list", type=int, default=4,
-                    help="rebuilds one outer list (3 x the margin) serves in the timed run; every "
+    ap.add_argument("--outer-factor", type=float, default=4.0,
+                    help="the outer list's margin over the plain margin")
+    ap.add_argument("--outer-list", type=int, default=10,
+                    help="rebuilds one outer list serves in the timed run; every "
                          "list filtered from it is exactly the fresh detection's (0: every "
                          "rebuild detects afresh)")
     ap.add_argument("--no-forms", action="store_true",
@@ -705,7 +707,7 @@ def main():
                          precision=dem.DEM_FP32_VOXEL, device=local, stream=stream.cuda_stream)
     ns, ncl = sc.n_spheres, sc.n_clumps
     if args.outer_list > 0:
-        sim.set_outer_list(3.0, args.outer_list)
+        sim.set_outer_list(args.outer_factor, args.outer_list)
     sim.step(args.warmup)
     bin_factor, bin_ms = sim.autotune_bins(BIN_FACTORS, reps=1)
     log(f"bin autotune: factor {bin_factor} ({bin_ms})")
@@ -788,7 +790,8 @@ def main():
         del out
     forms = None
     if not args.no_forms:
-        forms = {"outer_list": outer_form(sim, stream, ns, log),
+        forms = {"outer_list": outer_form(sim, stream, ns, log, factor=args.outer_factor,
+                                          n_inner=max(1, args.outer_list)),
                  "learned": learned_form(dem, sim, stream, args.steps, ns, st, ms_step, log,
                                          speed_floor=1.5)}
     sim.close()
@@ -816,7 +819,8 @@ def main():
                    "listed_pairs": n_pairs, "active_contacts": n_active,
                    "wall_contacts": st["n_wall_contacts"], "margin_m": margin,
                    "rebuild_interval": K_REBUILD, "dt": sc.h, "rebuilds": st["rebuilds"],
-                   "contact_list": (f"two-level: an outer list at 3 x the margin serves "
+                   "contact_list": (f"two-level: an outer list at {args.outer_factor:g} x the "
+                                    f"margin serves "
                                     f"{args.outer_list} rebuilds, each list filtered from it "
                                     f"with the exact test (equal to a fresh detection); "
                                     f"{st['outer_rebuilds']} outer detections in the timed "

@@ -144,8 +144,8 @@ def test_bad_predictions_never_miss_a_contact(dem, bed, mode):
 
 def test_speed_floor_keeps_fast_clumps_listed(dem, bed):
     """A regressor that promises every bin an everlasting list gives every
-    clump the smallest candidate (1 um), and the clumps the plate drags end
-    intervals early; with the speed floor each clump's margin covers at least
+    clump the smallest candidate (1 um), and over intervals of 200 steps the
+    clumps the plate drags end them early; with the speed floor each clump's margin covers at least
     its own travel over the interval at its speed, so fewer intervals end
     early.  No contact is missed either way, and a negative or non-finite
     floor is refused."""
@@ -154,7 +154,7 @@ def test_speed_floor_keeps_fast_clumps_listed(dem, bed):
     early = []
     for floor in (0.0, 1.5):
         with dem.Simulation(sc, margin=2e-5, rebuild_interval=20) as sim:
-            sim.set_learned_policy(reg, interval=40, safety=1.0, candidates=CAND,
+            sim.set_learned_policy(reg, interval=200, safety=1.0, candidates=CAND,
                                    speed_floor=floor)
             sim.step(400)
             st = sim.stats()
