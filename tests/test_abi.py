@@ -105,3 +105,35 @@ def test_create_checks_mesh_facets(lib):
         L.dem_destroy(ctx)
     else:
         assert b"no CUDA device" in L.dem_last_error(None)
+
+
+def test_binding_structures_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    the C compiler gives the header's struct (a C program built with gcc
+    prints them; nothing runs on a device)."""
+    import shutil
+    import subprocess
+
+    from paper_2307_03445_gb300 import capi
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"dem_wall": capi.DemWall, "dem_params": capi.DemParams, "dem_stats": capi.DemStats,
+             "dem_learned_params": capi.DemLearnedParams, "dem_tiles": capi.DemTiles}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dem.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
