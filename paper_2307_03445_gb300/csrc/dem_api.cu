@@ -41,6 +41,7 @@ struct SceneH {
 struct DetScratch {
   Buf det, wall_mask, wall_cnt, pair_cnt, bin_size, bin_start, scan_scr, trho, totals;
   Buf rec, upairs, fbin_size, fbin_start, fcnt, frec, fcand;
+  Buf fkeep, wkeep;  // the filter's decisions (lists filtered from the outer list)
   unsigned long long ucap = 0;  // capacity of the unordered pair buffer
   unsigned long long fcap = 0;  // capacity of the facet candidate buffer
 };
@@ -784,10 +785,13 @@ int filter_into(dem_ctx* c, int li, double m, int K, const ContactList* old, lon
   const ContactList& O = c->lists[3].L;
   if (!grow(c, c->ds[0].det, sizeof(int4) * (ns + 1)) || !grow(c, c->ds[0].wall_cnt, 4 * (ns + 1)) ||
       !grow(c, c->ds[0].pair_cnt, 4 * (ns + 1)) || !grow(c, LB.row, 4 * (ns + 1)) ||
-      !grow(c, LB.wrow, 4 * (ns + 1)) || !grow(c, c->ds[0].scan_scr, scan_scratch_bytes(ns + 1) + 256))
+      !grow(c, LB.wrow, 4 * (ns + 1)) || !grow(c, c->ds[0].scan_scr, scan_scratch_bytes(ns + 1) + 256) ||
+      !grow(c, c->ds[0].fkeep, (size_t)O.n + 16) || !grow(c, c->ds[0].wkeep, 4 * (ns + 1)))
     return fail(c, DEM_ERR_OOM, "detection buffers");
   DetectOut o{};
   o.det = ptr<int4>(c->ds[0].det);
+  o.fkeep = ptr<uint8_t>(c->ds[0].fkeep);
+  o.wkeep = ptr<uint32_t>(c->ds[0].wkeep);
   o.wall_cnt = ptr<uint32_t>(c->ds[0].wall_cnt);
   o.wall_off = ptr<uint32_t>(LB.wrow);
   o.pair_cnt = ptr<uint32_t>(c->ds[0].pair_cnt);
@@ -1557,7 +1561,7 @@ void dem_destroy(dem_ctx* c) {
   for (auto& S : c->ds) {
     Buf* sb[] = {&S.det, &S.wall_mask, &S.wall_cnt, &S.pair_cnt, &S.bin_size, &S.bin_start,
                  &S.scan_scr, &S.trho, &S.totals, &S.rec, &S.upairs, &S.fbin_size,
-                 &S.fbin_start, &S.fcnt, &S.frec, &S.fcand};
+                 &S.fbin_start, &S.fcnt, &S.frec, &S.fcand, &S.fkeep, &S.wkeep};
     for (Buf* b : sb) dfree(c, b->p);
   }
   dfree(c, c->b_q1.p);

@@ -523,24 +523,35 @@ __device__ __forceinline__ bool lattice_pair(int4 qa, int4 qb) {
 }
 
 // EMIT = false: per sphere a, the partners of its outer row that pass (into
-// o.pair_cnt); EMIT = true: writes them into the inner rows (o.pair_off).
+// o.pair_cnt, each decision into o.fkeep); EMIT = true: writes the kept ones
+// into the inner rows (o.pair_off), from the recorded decisions.
 template <bool EMIT>
 __global__ void k_filter_pairs(DevState d, DetectOut o, ContactList outer, ContactList inner) {
   const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= d.ns) return;
-  const int4 qa = o.det[a];
   uint32_t k = EMIT ? o.pair_off[a] : 0u;
-  const uint32_t j1 = outer.row[a + 1];
-  for (uint32_t j = outer.row[a]; j < j1; ++j) {
-    const uint32_t b = outer.pb[j] & ~kHistFlag;
-    if (!lattice_pair(qa, o.det[b])) continue;
-    if (EMIT) {
+  const uint32_t j0 = outer.row[a], j1 = outer.row[a + 1];
+  if (EMIT) {
+    for (uint32_t j = j0; j < j1; ++j) {
+      if (!o.fkeep[j]) continue;
       inner.pa[k] = (int)a;
-      inner.pb[k] = b;
+      inner.pb[k] = outer.pb[j] & ~kHistFlag;
+      ++k;
     }
-    ++k;
+    return;
   }
-  if (!EMIT) o.pair_cnt[a] = k;
+  if (j0 == j1) {
+    o.pair_cnt[a] = 0u;
+    return;
+  }
+  const int4 qa = o.det[a];
+  for (uint32_t j = j0; j < j1; ++j) {
+    const uint32_t b = outer.pb[j] & ~kHistFlag;
+    const bool keep = lattice_pair(qa, o.det[b]);
+    o.fkeep[j] = keep ? 1 : 0;
+    k += keep ? 1u : 0u;
+  }
+  o.pair_cnt[a] = k;
 }
 
 // The same for each sphere's wall candidates (into o.wall_cnt, then the
@@ -552,6 +563,17 @@ __global__ void k_filter_walls(DevState d, DetectOut o, ContactList outer, Conta
   if (s >= d.ns) return;
   const uint32_t j0 = outer.wrow[s], j1 = outer.wrow[s + 1];
   uint32_t k = EMIT ? o.wall_off[s] : 0u;
+  if (EMIT && j1 - j0 <= 32u) {  // the decisions recorded by the count pass
+    const uint32_t keep = j0 < j1 ? o.wkeep[s] : 0u;
+    for (uint32_t j = j0; j < j1; ++j) {
+      if (!((keep >> (j - j0)) & 1u)) continue;
+      inner.ws[k] = (int)s;
+      inner.ww[k] = outer.ww[j] & ~kHistFlag;
+      ++k;
+    }
+    return;
+  }
+  uint32_t keep = 0u;
   if (j0 < j1) {
     const int2 si = d.sinfo[s];
     const SceneGrid g = d.grids[d.cinfo[si.x].y];
@@ -565,6 +587,7 @@ __global__ void k_filter_walls(DevState d, DetectOut o, ContactList outer, Conta
       const uint32_t w = outer.ww[j] & ~kHistFlag;
       if (!wall_candidate(d.walls[w], tf, ttf, xf, rmf, t, travel_time, d.tp64[si.y].w, margin, ctr))
         continue;
+      if (j - j0 < 32u) keep |= 1u << (j - j0);
       if (EMIT) {
         inner.ws[k] = (int)s;
         inner.ww[k] = w;
@@ -572,7 +595,10 @@ __global__ void k_filter_walls(DevState d, DetectOut o, ContactList outer, Conta
       ++k;
     }
   }
-  if (!EMIT) o.wall_cnt[s] = k;
+  if (!EMIT) {
+    o.wall_cnt[s] = k;
+    if (j0 < j1) o.wkeep[s] = keep;
+  }
 }
 
 // The sphere id of every registration (inspection).

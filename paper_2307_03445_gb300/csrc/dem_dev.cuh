@@ -148,6 +148,11 @@ struct DetectOut {
   unsigned long long* d_nf; //   candidates found (may exceed fcap)
   uint32_t* fcnt;           // per sphere: facet candidates (then the slots taken)
   double wall_extra;        // added to the margin in the wall candidates' threshold
+  // filtering a list from the outer list: the count pass records each outer
+  // pair's decision and each sphere's wall decisions (bit j: its j-th outer
+  // wall candidate, j < 32), which the emit pass then copies
+  uint8_t* fkeep;           // per outer pair
+  uint32_t* wkeep;          // per sphere
 };
 
 struct ContactList {
