@@ -58,18 +58,19 @@ def ALGO_PAIRS(ncl, ns, n_pairs):
     return 56 * n_pairs + 8 * ns + 88 * ncl
 
 
-# This implementation's own bytes per launch.  Update: per clump 204 B read
+# This implementation's own bytes per launch.  Update: per clump 156 B read
 # (force and torque 32, template and scene 8, voxel 16, offset 16,
-# orientation 32, velocity record 48, certificate reference 48, first-sphere
-# index 4) and 176 B written (voxel, offset, orientation, velocity record,
-# FP32 mirrors 32, cleared accumulators 32); per sphere its 16-byte pose
-# record written.  Pair forces: per listed pair its ids (8 B); per active
+# orientation 32, velocity record 48, first-sphere index 4; the 48-byte
+# certificate reference only for the clumps whose motion bound reaches their
+# margin, none in this workload) and 160 B written (offset, orientation,
+# velocity record, FP32 mirrors 32, cleared accumulators 32; the voxel only
+# when it changes); per sphere its 16-byte pose record written.  Pair forces: per listed pair its ids (8 B); per active
 # contact the FP64 history read + write (48 B); per sphere its {owner,
 # template sphere} (8 B) and pose record (16 B) read once; per clump voxel
 # and offset (32 B), velocity mirrors (32 B) and accumulators read + written
 # (64 B).
 def IMPL_UPDATE(ncl, ns):
-    return 380 * ncl + 16 * ns
+    return 316 * ncl + 16 * ns
 
 
 def IMPL_PAIRS(ncl, ns, n_pairs, n_active):
@@ -81,8 +82,7 @@ def IMPL_PAIRS(ncl, ns, n_pairs, n_active):
 # that launch's algorithmic bytes; a launch on a bed of this family is scaled
 # by its algorithmic bytes (both grow with the clumps, spheres and pairs in
 # the same proportions).  None once the kernel changes.
-TRAFFIC = {"k_update32": (140.322048e6 + 97.068544e6, 181879360),
-           "k_pairs32": (194.522880e6 + 39.961088e6, 202154256)}
+TRAFFIC = {"k_update32": None, "k_pairs32": None}
 TRAFFIC_SRC = {k: "ncu dram__bytes_read.sum + dram__bytes_write.sum, 687,504-clump bed, scaled "
                   "by algorithmic bytes (profiles/ncu_pairs_update_bed_2M_spheres.md)"
                for k in TRAFFIC}

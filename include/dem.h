@@ -353,7 +353,9 @@ int dem_num_contacts(dem_ctx* ctx, long long* n_pairs, long long* n_wall);
 
 /* Copies the current lists (host buffers sized by dem_num_contacts): pairs
  * (a < b, sphere ids, sorted by (a, b)) with their tangential history u
- * (3 doubles each), and sphere-wall contacts (sphere, wall) with history. */
+ * (3 doubles each), and sphere-wall contacts (sphere, wall) with history.
+ * In DEM_FP32_VOXEL the device keeps a pair's history components as
+ * float-float (about 48 significant bits); u receives their sums. */
 int dem_get_contacts(dem_ctx* ctx, int* a, int* b, double* u, int* wall_sphere, int* wall_id,
                      double* wall_u);
 

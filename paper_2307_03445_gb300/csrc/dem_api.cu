@@ -2013,10 +2013,24 @@ int dem_get_contacts(dem_ctx* c, int* a, int* b, double* u, int* wall_sphere, in
   if (L.nw) cudaMemcpyAsync(ww.data(), L.ww, 4 * L.nw, cudaMemcpyDeviceToHost, c->st);
   if (wall_u && L.nw) cudaMemcpyAsync(uw.data(), L.uw, 24 * L.capw, cudaMemcpyDeviceToHost, c->st);
   cudaStreamSynchronize(c->st);
+  // FP32_VOXEL keeps each pair history component as a float-float {high,
+  // low} in its 8-byte slot; FP64 as a double
+  const bool ffh = c->P.precision != DEM_FP64;
   for (long long i = 0; i < L.n; ++i) {
     if (b) b[i] = (int)(pb[i] & ~kHistFlag);
     if (u)
-      for (int k = 0; k < 3; ++k) u[3 * i + k] = (pb[i] & kHistFlag) ? uu[k * L.cap + i] : 0.0;
+      for (int k = 0; k < 3; ++k) {
+        double v = 0.0;
+        if (pb[i] & kHistFlag) {
+          v = uu[k * L.cap + i];
+          if (ffh) {
+            float hl[2];
+            std::memcpy(hl, &uu[k * L.cap + i], sizeof hl);
+            v = (double)hl[0] + (double)hl[1];
+          }
+        }
+        u[3 * i + k] = v;
+      }
   }
   for (long long i = 0; i < L.nw; ++i) {
     if (wall_id) wall_id[i] = c->wall_user[ww[i] & ~kHistFlag];

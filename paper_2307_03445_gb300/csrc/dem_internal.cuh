@@ -225,6 +225,17 @@ __device__ __forceinline__ long long f2ll_rn(float x) {
   return (u >> 31) ? -v : v;
 }
 
+// float -> nearest int64 (ties to even) for |x| < 2^43, without branches: with
+// a = x / 2^22 rounded to an integer, b = x - a 2^22 is exact (|b| <= 2^21 and
+// a multiple of x's last place), and the rounding of b decides the rounding of
+// x (a 2^22 is even).  Equal to f2ll_rn on that range.
+__device__ __forceinline__ long long f2ll_rn_near(float x) {
+  const float t = fmaf(x, 2.38418579101562500e-7f, 12582912.0f);  // x / 2^22 + 1.5 2^23
+  const int a = __float_as_int(t) - 0x4B400000;
+  const float b = fmaf(t - 12582912.0f, -4194304.0f, x);
+  return (long long)a * 4194304ll + (long long)small_f2i(b);
+}
+
 // ceil(d) for finite 0 <= d < 2^62, integer pipe.
 __device__ __forceinline__ long long ceil_pos_d2ll(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
@@ -329,6 +340,15 @@ __device__ __forceinline__ ff fix_to_ff(long long v) {
   const float c2 = small_i2f((int)(v1 >> 22)) * 17592186044416.0f;      // 2^44
   ff s = two_sum(c2, c1);
   s = ff_add(s, {c0, 0.f});
+  return {s.h * kFixToM, s.l * kFixToM};
+}
+// The same for |v| < 2^44 (neighbour differences): v = h 2^22 + l with both
+// pieces exact floats, so TwoSum of them is the exact float-float of v (the
+// same pair as fix_to_ff, whose high part is fix_to_float(v)).
+__device__ __forceinline__ ff fix_to_ff_near(long long v) {
+  const float h = small_i2f((int)(v >> 22)) * 4194304.0f;  // exact: |v >> 22| <= 2^22
+  const float l = small_i2f((int)(v & 0x3fffff));
+  const ff s = two_sum(h, l);
   return {s.h * kFixToM, s.l * kFixToM};
 }
 // Float estimate of a fixed-point value with |v| < 2^44 (neighbour differences).

@@ -53,9 +53,21 @@ __device__ __forceinline__ Law<T> contact_law(const PairMat<T>& pm, T h, V3<T> n
   const T sfm = csqrt_pos(f * mbar);
   const T fns = f * pm.kn * dn - pm.cn * sfm * vns; // Eq. (1a) along n
   const V3<T> Ft = (-f * pm.kt) * upt - (pm.ct * sfm) * vt;  // Eq. (1b)
-  const T fn = fabs(fns), ft = sqrt(dot(Ft, Ft));
-  if (ft > pm.mu * fn) {                            // Eq. (4)
-    const T s = ft > T(0) ? cdiv(pm.mu * fn, ft) : T(0);
+  const T fn = fabs(fns), ft2 = dot(Ft, Ft);
+  // Eq. (4): FP64 compares |F_t| itself (the oracle's order); float compares
+  // the squares and scales with a reciprocal square root
+  bool cap;
+  T s;
+  if constexpr (sizeof(T) == 4) {
+    const T lim = pm.mu * fn;
+    cap = ft2 > lim * lim;
+    s = cap ? lim * rsqrtf(ft2) : T(1);
+  } else {
+    const T ft = sqrt(ft2);
+    cap = ft > pm.mu * fn;
+    s = cap && ft > T(0) ? cdiv(pm.mu * fn, ft) : T(0);
+  }
+  if (cap) {
     const T ul = sqrt(dot(upt, upt));
     const T us = ul > T(0) ? cdiv(cdiv(pm.mu * fn, f * pm.kt), ul) : T(0);
     r.F = fns * n + s * Ft;
@@ -89,8 +101,8 @@ __device__ __forceinline__ void add_clump32(float* acc, int c, V3<float> F, V3<f
 // ---------------------------------------------------------------------------
 // sphere-sphere contacts
 // ---------------------------------------------------------------------------
-// One side of an FP32_VOXEL contact: the sphere's fixed-point centre, radius,
-// material, owner and the owner's voxel offset.
+// One side of an FP32_VOXEL sphere-wall contact: the sphere's fixed-point
+// centre, radius, material, owner and the owner's voxel offset.
 struct Side32 {
   long long P[3];
   float r;
@@ -125,22 +137,68 @@ __device__ __forceinline__ V3<float> arm32(const Side32& S) {
           fix_to_float(S.rel[2]) - S.off.z};
 }
 
+// One side of an FP32_VOXEL sphere pair, as the pair kernel uses it: the
+// owner's voxel, the centre from that voxel's corner (the pose record), the
+// owner's offset in the voxel, the radius and the ids.  The centre difference
+// of two sides is ((voxel_b - voxel_a) << 24) + (rel_b - rel_a), in 2^-44 m.
+struct PairSide32 {
+  int vx, vy, vz;
+  int owner, tsph;
+  float r;
+  float4 off;
+  long long rel[3];
+};
+
+__device__ __forceinline__ PairSide32 load_pair_side32(const DevState& d, uint32_t s) {
+  PairSide32 S;
+  const int2 si = d.sinfo[s];
+  const uint4 rec = d.srec32[s];
+  S.owner = si.x;
+  S.tsph = si.y;
+  const int4 v = d.cvox[si.x];
+  S.vx = v.x; S.vy = v.y; S.vz = v.z;
+  S.off = d.coff[si.x];
+  S.r = d.tp32[si.y].w;
+  unpack_rel(rec, S.rel[0], S.rel[1], S.rel[2]);
+  return S;
+}
+
+__device__ __forceinline__ long long fix_diff(int va, int vb, long long ra, long long rb) {
+  return (long long)(vb - va) * (1ll << (kFixBits - kVoxLog2)) + (rb - ra);
+}
+
+__device__ __forceinline__ V3<float> arm32(const PairSide32& S) {
+  return {fix_to_float(S.rel[0]) - S.off.x, fix_to_float(S.rel[1]) - S.off.y,
+          fix_to_float(S.rel[2]) - S.off.z};
+}
+
+// Tangential history of an FP32_VOXEL pair contact: each component a
+// float-float (high, low) in the 8 bytes of its slot, the high part the
+// component rounded to float.  The float increment of Eq. (3) is added
+// without rounding away its low bits (TwoSum), as a double sum would.
+__device__ __forceinline__ float2 hist_add(float2 u, float inc) {
+  const ff s = two_sum(u.x, inc);
+  const ff r = fast_two_sum(s.h, __fadd_rn(s.l, u.y));
+  return make_float2(r.h, r.l);
+}
+
 // Eq. (1)-(5) for one active sphere pair of the FP32_VOXEL list: forces, the
-// FP64 history update, and the force and moments added to both clumps.
+// history update, and the force and moments added to both clumps.
 __device__ __forceinline__ void pair_force32(const DevState& d, ContactList& l, long long i,
-                                             uint32_t b, uint32_t bw, const Side32& A,
-                                             const Side32& B, float fx, float fy, float fz,
+                                             uint32_t b, uint32_t bw, const PairSide32& A,
+                                             const PairSide32& B, float fx, float fy, float fz,
                                              float dist, float dn) {
     const float inv = __fdividef(1.f, dist);
     const V3<float> n = {fx * inv, fy * inv, fz * inv};
     const float4 va = d.mv32[A.owner], wa = d.mw32[A.owner];
     const float4 vb = d.mv32[B.owner], wb = d.mw32[B.owner];
     const int ma = d.tmat[A.tsph], mb = d.tmat[B.tsph];
-    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+    float2* uf = reinterpret_cast<float2*>(l.u);
+    float2 u0 = make_float2(0.f, 0.f), u1 = u0, u2 = u0;
     if (bw & kHistFlag) {
-      u0 = l.u[i];
-      u1 = l.u[l.cap + i];
-      u2 = l.u[2 * l.cap + i];
+      u0 = uf[i];
+      u1 = uf[l.cap + i];
+      u2 = uf[2 * l.cap + i];
     }
     const float sa = A.r - 0.5f * dn, sb = B.r - 0.5f * dn;
     const V3<float> ca = arm32(A) + sa * n;
@@ -151,16 +209,16 @@ __device__ __forceinline__ void pair_force32(const DevState& d, ContactList& l, 
     const float Rbar = __fdividef(A.r * B.r, A.r + B.r);
     const float mbar = __fdividef(va.w * vb.w, va.w + vb.w);
     const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vB - vA,
-                                              V3<float>{d2f(u0), d2f(u1), d2f(u2)}, Rbar, mbar);
-    // tangential history: FP64 accumulation of the float increment
+                                              V3<float>{u0.x, u1.x, u2.x}, Rbar, mbar);
     if (law.capped) {
-      u0 = f2d(law.u.x); u1 = f2d(law.u.y); u2 = f2d(law.u.z);
+      u0 = make_float2(law.u.x, 0.f); u1 = make_float2(law.u.y, 0.f);
+      u2 = make_float2(law.u.z, 0.f);
     } else {
-      u0 += f2d(law.u.x); u1 += f2d(law.u.y); u2 += f2d(law.u.z);
+      u0 = hist_add(u0, law.u.x); u1 = hist_add(u1, law.u.y); u2 = hist_add(u2, law.u.z);
     }
-    l.u[i] = u0;
-    l.u[l.cap + i] = u1;
-    l.u[2 * l.cap + i] = u2;
+    uf[i] = u0;
+    uf[l.cap + i] = u1;
+    uf[2 * l.cap + i] = u2;
     if (!(bw & kHistFlag)) l.pb[i] = b | kHistFlag;
     const V3<float> F = law.F;
     const V3<float> Ta = -1.f * cross(ca, F), Tb = cross(cb, F);
@@ -191,18 +249,21 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     const uint32_t bw = bw_n;
     const uint32_t b = bw & ~kHistFlag;
     if (i + stride < ln) { a_n = l.pa[i + stride]; bw_n = l.pb[i + stride]; }
-    const Side32 A = load_side32(d, (uint32_t)a);
-    const Side32 B = load_side32(d, b);
-    const long long dxl = B.P[0] - A.P[0], dyl = B.P[1] - A.P[1], dzl = B.P[2] - A.P[2];
+    const PairSide32 A = load_pair_side32(d, (uint32_t)a);
+    const PairSide32 B = load_pair_side32(d, b);
+    // the centre difference b - a as exact float-float metres; its high
+    // parts are the float estimate used for the cheap rejection
+    const ff dx = fix_to_ff_near(fix_diff(A.vx, B.vx, A.rel[0], B.rel[0]));
+    const ff dy = fix_to_ff_near(fix_diff(A.vy, B.vy, A.rel[1], B.rel[1]));
+    const ff dz = fix_to_ff_near(fix_diff(A.vz, B.vz, A.rel[2], B.rel[2]));
+    const float fx = dx.h, fy = dy.h, fz = dz.h;
     // cheap rejection of clear false positives
-    const float fx = fix_to_float(dxl), fy = fix_to_float(dyl), fz = fix_to_float(dzl);
     const float s_est = fx * fx + fy * fy + fz * fz;
     const float rs = A.r + B.r;
     float dn = -1.f;
     float dist = 0.f;
     if (s_est <= rs * rs * 1.0001f) {
       // overlap rho - |d| = (rho^2 - |d|^2) / (rho + |d|), numerator in float-float
-      const ff dx = fix_to_ff(dxl), dy = fix_to_ff(dyl), dz = fix_to_ff(dzl);
       const ff s = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
       const ff rho = two_sum(A.r, B.r);
       const ff diff = ff_sub(ff_mul(rho, rho), s);
@@ -605,16 +666,10 @@ __global__ void __launch_bounds__(B, 896 / B) k_update32(DevState d, float margi
   const long long c = cw0 + lane;
   if (lane < nw) {
     // every global load of the clump is issued first (one memory round trip)
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, ref_o = a0, ref_qv = a0;
-    int4 ref_v = make_int4(0, 0, 0, 0);
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
     if (INTEG) {
       a0 = *reinterpret_cast<const float4*>(d.acc32 + 8 * c);
       a1 = *reinterpret_cast<const float4*>(d.acc32 + 8 * c + 4);
-      if (CERT) {
-        ref_v = d.ref_vox[c];
-        ref_o = d.ref_off[c];
-        ref_qv = d.ref_q[c];
-      }
     }
     const int tpl = d.cinfo[c].x;
     int4 vox = d.cvox[c];
@@ -653,15 +708,16 @@ __global__ void __launch_bounds__(B, 896 / B) k_update32(DevState d, float margi
       float o[3] = {off.x + hf * vx_f, off.y + hf * vy_f, off.z + hf * vz_f};
       int vi[3] = {vox.x, vox.y, vox.z};
       const float kV = (float)kVoxel;
+      bool carried = false;
       for (int k = 0; k < 3; ++k) {
         if (fabsf(o[k]) > 0.5f * kV) {
           const float m = rintf(o[k] * (1.f / kV));
           vi[k] += (int)m;
           o[k] -= m * kV;  // exact: m * 2^-20 and the difference are representable
+          carried = true;
         }
       }
       vox = make_int4(vi[0], vi[1], vi[2], vox.w);
-      off = make_float4(o[0], o[1], o[2], 0.f);
       // Eq. (5b): body frame, float angular acceleration, double accumulation
       float Rf[9];
       quat_to_mat(qw.h, qx.h, qy.h, qz.h, Rf);
@@ -706,15 +762,40 @@ __global__ void __launch_bounds__(B, 896 / B) k_update32(DevState d, float margi
       qw = ff_add(a[0], ff_mulf(a[0], hs)); qx = ff_add(a[1], ff_mulf(a[1], hs));
       qy = ff_add(a[2], ff_mulf(a[2], hs)); qz = ff_add(a[3], ff_mulf(a[3], hs));
       q4 = make_double4_32a(qd[0], qd[1], qd[2], qd[3]);
+      // motion bound since the last rebuild, in the offset record's fourth
+      // word (+inf when unknown): a sphere at most b from the centre of mass
+      // moved at most h |v| + b h |omega| this step, plus the rounding of the
+      // offset update (below 2^-43 m); summed with upward rounding.  The
+      // square roots are x rsqrt(x) (within 2^-21 of the root), which the
+      // factor 1 + 2^-18 covers together with the float rounding of v
+      const float bnd = d.tpbound[tpl];
+      const float v2 = __fmaf_ru(vx_f, vx_f, __fmaf_ru(vy_f, vy_f, __fmaf_ru(vz_f, vz_f, 1e-30f)));
+      const float w2 = __fmaf_ru(wn.x, wn.x, __fmaf_ru(wn.y, wn.y, __fmaf_ru(wn.z, wn.z, 1e-30f)));
+      const float sv = __fmul_ru(v2, rsqrtf(v2)), sw = __fmul_ru(w2, rsqrtf(w2));
+      const float step_b = __fmaf_ru(__fmul_ru(hf, __fmaf_ru(bnd, sw, sv)), 1.000003814697265625f,
+                                     1.1368683772161603e-13f);  // (1 + 2^-18), 2^-43 m
+      const float motion = __fadd_ru(off.w, step_b);
+      off = make_float4(o[0], o[1], o[2], motion);
       if (!(finite_d(v.x) && finite_d(v.y) && finite_d(v.z) && finite_d(w.x) && finite_d(w.y) &&
             finite_d(w.z) && finite_d(qd[0]) && finite_d(qd[1]) && finite_d(qd[2]) &&
             finite_d(qd[3]) && isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2])))
         atomicOr(d.flags, kFlagNonFinite);
-      d.cvox[c] = vox; d.coff[c] = off; d.cq[c] = q4;
+      if (carried) d.cvox[c] = vox;
+      d.coff[c] = off; d.cq[c] = q4;
       store_vel(d.cvw + c, v, w);
-      if (CERT) {
-        const int4 v0 = ref_v;
-        const float4 o0 = ref_o;
+      const float mlim = CERT ? (d.cmargin ? d.cmargin[c] : margin) : 0.f;
+      // The exact certificate (below) reads the 48-byte state of the last
+      // rebuild.  Its computed displacement is at most the motion bound times
+      // (1 + 2^-12) plus 2^-40 m plus b 2^-18 (the roundings of the offsets'
+      // differences, of the float reference orientation and of the quaternion
+      // product), and its test is monotone in the displacement: when that
+      // bound passes the same test the exact certificate passes too.
+      const float mb = __fmaf_ru(off.w, 1.000244140625f,
+                                 __fmaf_ru(bnd, 3.814697265625e-6f, 9.094947017729282e-13f));
+      if (CERT && mb * 1.00001f + 1e-12f > mlim) {
+        const int4 v0 = d.ref_vox[c];
+        const float4 o0 = d.ref_off[c];
+        const float4 ref_qv = d.ref_q[c];
         const float dx = (float)(vox.x - v0.x) * kV + (off.x - o0.x);
         const float dy = (float)(vox.y - v0.y) * kV + (off.y - o0.y);
         const float dz = (float)(vox.z - v0.z) * kV + (off.z - o0.z);
@@ -724,8 +805,7 @@ __global__ void __launch_bounds__(B, 896 / B) k_update32(DevState d, float margi
         float e[4];
         quat_mulf(a, b, e);
         const float disp = sqrtf(dx * dx + dy * dy + dz * dz) +
-                           2.f * d.tpbound[tpl] * sqrtf(e[1] * e[1] + e[2] * e[2] + e[3] * e[3]);
-        const float mlim = d.cmargin ? d.cmargin[c] : margin;
+                           2.f * bnd * sqrtf(e[1] * e[1] + e[2] * e[2] + e[3] * e[3]);
         if (disp * 1.00001f + 1e-12f > mlim) {
           atomicOr(d.flags, kFlagGuard);
           atomicAdd(d.counters + 1, 1ull);
@@ -755,6 +835,8 @@ __global__ void __launch_bounds__(B, 896 / B) k_update32(DevState d, float margi
     if (!INTEG) {
       wf_new = {d2f(w.x), d2f(w.y), d2f(w.z)};
       vf_new[0] = d2f(v.x); vf_new[1] = d2f(v.y); vf_new[2] = d2f(v.z);
+      // a state set from outside: its motion since the last rebuild is unknown
+      d.coff[c] = make_float4(off.x, off.y, off.z, __int_as_float(0x7f800000));
     }
     const V3<float> ww = mat_mul(Rf, wf_new);
     d.mv32[c] = make_float4(vf_new[0], vf_new[1], vf_new[2], mass);
@@ -801,7 +883,7 @@ __global__ void __launch_bounds__(B, 896 / B) k_update32(DevState d, float margi
       lo = fmaf(wp.Rl[3 * i + 1][k], p[1], lo);
       lo = fmaf(wp.Rl[3 * i + 2][k], p[2], lo);
       const ff acc = fast_two_sum(s.h, lo);
-      X[i] = f2ll_rn(acc.h * kMToFix) + wp.off[i][k] + __float2int_rn(acc.l * kMToFix);
+      X[i] = f2ll_rn_near(acc.h * kMToFix) + wp.off[i][k] + __float2int_rn(acc.l * kMToFix);
     }
     d.srec32[j] = pack_rel(X[0], X[1], X[2]);
   }
@@ -937,7 +1019,9 @@ __global__ void k_set_ref(DevState d) {
     d.ref_pos[c] = d.cpos[c];
   } else {
     d.ref_vox[c] = d.cvox[c];
-    d.ref_off[c] = d.coff[c];
+    const float4 o = d.coff[c];
+    d.ref_off[c] = o;
+    d.coff[c] = make_float4(o.x, o.y, o.z, 0.f);  // no motion since this state
   }
 }
 
