@@ -87,7 +87,7 @@ struct dem_ctx {
   long long ncl = 0, ns = 0;
   // all device buffers
   std::vector<Buf*> owned;
-  Buf b_tpl_off, b_tp64, b_tp32, b_tmat, b_tmass, b_tinert, b_tpbound, b_tmassf, b_tinertf;
+  Buf b_tpl_off, b_tp64, b_tp32, b_trm, b_tmat, b_tmass, b_tinert, b_tpbound, b_tmassf, b_tinertf;
   Buf b_cinfo, b_csph, b_cpos, b_cvox, b_coff, b_cq, b_cvw, b_mv64, b_mw64, b_mv32, b_mw32;
   Buf b_acc64, b_acc32, b_ref_pos, b_ref_vox, b_ref_off, b_ref_q;
   Buf b_sinfo, b_sa64, b_sb64, b_srec32;
@@ -126,7 +126,7 @@ struct dem_ctx {
   long long n_entry_bins = 0;    // bins of that rebuild
   // contact lists (current, next) and an audit list
   struct ListBufs {
-    Buf pa, pb, u, row, ws, ww, uw, wrow, dnb;
+    Buf pa, pb, pown, u, row, ws, ww, uw, wrow, dnb;
     ContactList L{};
   } lists[5];  // 0, 1: current and next; 2: audit; 3: outer list; 4: the next outer list
   int cur = 0;
@@ -276,6 +276,7 @@ void refresh_devstate(dem_ctx* c) {
   d.tp64 = ptr<double4_32a>(c->b_tp64);
   d.tp32 = ptr<float4>(c->b_tp32);
   d.tmat = ptr<int>(c->b_tmat);
+  d.trm = ptr<float2>(c->b_trm);
   d.tmass = ptr<double>(c->b_tmass);
   d.tinert = ptr<double>(c->b_tinert);
   d.tmassf = ptr<float>(c->b_tmassf);
@@ -573,9 +574,11 @@ int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, 
   ContactList& L = LB.L;
   if ((long long)NP > L.cap || !LB.pa.p) {
     const long long cap = std::max<long long>((long long)(NP + NP / 4), 1024);
-    dfree(c, LB.pa.p, st); dfree(c, LB.pb.p, st); dfree(c, LB.u.p, st);
-    LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf();
-    if (!grow(c, LB.pa, 4 * cap, 0, st) || !grow(c, LB.pb, 4 * cap, 0, st) || (hist && !grow(c, LB.u, 24 * cap, 0, st)))
+    dfree(c, LB.pa.p, st); dfree(c, LB.pb.p, st); dfree(c, LB.u.p, st); dfree(c, LB.pown.p, st);
+    LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf(); LB.pown = Buf();
+    const bool own = hist && c->P.precision != DEM_FP64;
+    if (!grow(c, LB.pa, 4 * cap, 0, st) || !grow(c, LB.pb, 4 * cap, 0, st) ||
+        (hist && !grow(c, LB.u, 24 * cap, 0, st)) || (own && !grow(c, LB.pown, 16 * cap, 0, st)))
       return fail(c, DEM_ERR_OOM, "pair list");
     L.cap = cap;
   }
@@ -589,6 +592,7 @@ int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, 
   }
   L.pa = ptr<int>(LB.pa);
   L.pb = ptr<uint32_t>(LB.pb);
+  L.pown = ptr<int4>(LB.pown);
   L.u = ptr<double>(LB.u);
   L.row = ptr<uint32_t>(LB.row);
   L.ws = ptr<int>(LB.ws);
@@ -966,6 +970,7 @@ int rebuild(dem_ctx* c, double m, int K, bool allow_outer = true) {
   }
   ContactList& N = c->lists[nxt].L;
   if (old) launch_hist_walls(*old, N, c->list_ns, c->st);
+  if (c->P.precision != DEM_FP64) launch_pair_owners(c->D, N, c->st);
   c->cur = nxt;
   c->list_ns = c->ns;
   c->have_list = true;
@@ -1543,7 +1548,7 @@ void dem_destroy(dem_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->P.device);
   if (c->st2) cudaStreamSynchronize(c->st2);
-  Buf* all[] = {&c->b_tpl_off, &c->b_tp64, &c->b_tp32, &c->b_tmat, &c->b_tmass, &c->b_tinert, &c->b_tpbound,
+  Buf* all[] = {&c->b_tpl_off, &c->b_tp64, &c->b_tp32, &c->b_trm, &c->b_tmat, &c->b_tmass, &c->b_tinert, &c->b_tpbound,
                 &c->b_cinfo, &c->b_csph, &c->b_cpos, &c->b_cvox, &c->b_coff, &c->b_cq, &c->b_cvw,
                 &c->b_tmassf, &c->b_tinertf, &c->b_mv64, &c->b_mw64, &c->b_mv32, &c->b_mw32, &c->b_acc64, &c->b_acc32, &c->b_ref_pos,
                 &c->b_ref_vox, &c->b_ref_off, &c->b_ref_q, &c->b_sinfo, &c->b_sa64, &c->b_sb64, &c->b_srec32,
@@ -1566,7 +1571,7 @@ void dem_destroy(dem_ctx* c) {
   }
   dfree(c, c->b_q1.p);
   for (auto& lb : c->lists) {
-    Buf* lbs[] = {&lb.pa, &lb.pb, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow, &lb.dnb};
+    Buf* lbs[] = {&lb.pa, &lb.pb, &lb.pown, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow, &lb.dnb};
     for (Buf* b : lbs) dfree(c, b->p);
   }
   cudaStreamSynchronize(c->st);
@@ -1621,16 +1626,20 @@ int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double
   c->r_max = *std::max_element(radius, radius + S);
   std::vector<double4_32a> tp64(S);
   std::vector<float4> tp32(S);
+  std::vector<float2> trm(S);
   std::vector<float> pb(n_tpl, 0.f);
   for (int t = 0; t < n_tpl; ++t)
     for (int s = off[t]; s < off[t + 1]; ++s) {
       const double* p = local_pos + 3 * s;
       tp64[s] = make_double4_32a(p[0], p[1], p[2], radius[s]);
       tp32[s] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)radius[s]);
+      float mat_bits;
+      std::memcpy(&mat_bits, &material[s], sizeof mat_bits);
+      trm[s] = make_float2((float)radius[s], mat_bits);
       pb[t] = std::max(pb[t], (float)std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) * 1.000001f);
     }
   if (!grow(c, c->b_tpl_off, 4 * (n_tpl + 1)) || !grow(c, c->b_tp64, 32 * S) || !grow(c, c->b_tp32, 16 * S) ||
-      !grow(c, c->b_tmat, 4 * S) || !grow(c, c->b_tmass, 8 * n_tpl) || !grow(c, c->b_tinert, 24 * n_tpl) ||
+      !grow(c, c->b_trm, 8 * S) || !grow(c, c->b_tmat, 4 * S) || !grow(c, c->b_tmass, 8 * n_tpl) || !grow(c, c->b_tinert, 24 * n_tpl) ||
       !grow(c, c->b_tpbound, 4 * n_tpl) || !grow(c, c->b_tmassf, 8 * n_tpl) ||
       !grow(c, c->b_tinertf, 24 * n_tpl))
     return fail(c, DEM_ERR_OOM, "template tables");
@@ -1638,6 +1647,7 @@ int dem_load_clump_templates(dem_ctx* c, int n_tpl, const int* off, const double
   cudaMemcpyAsync(c->b_tp64.p, tp64.data(), 32 * (size_t)S, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tp32.p, tp32.data(), 16 * (size_t)S, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tmat.p, material, 4 * (size_t)S, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->b_trm.p, trm.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tmass.p, mass, 8 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->b_tinert.p, inertia, 24 * (size_t)n_tpl, cudaMemcpyHostToDevice, c->st);
   // float tables of the FP32_VOXEL update: {m, 1/m} and {I0, I1, I2, 1/I0, 1/I1, 1/I2}

@@ -834,6 +834,17 @@ __global__ void k_sort_rows(long long ns, const uint32_t* __restrict__ row, int*
   for (uint32_t i = r0; i < r1; ++i) pa[i] = (int)a;
 }
 
+// The owner clumps and template spheres of both sides of every pair, so that
+// the force kernel issues all of a pair's pose loads at once.
+__global__ void k_pair_owners(DevState d, ContactList l) {
+  const long long n = l.dn[0];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int2 sa = d.sinfo[l.pa[i]], sb = d.sinfo[l.pb[i] & ~kHistFlag];
+    l.pown[i] = make_int4(sa.x, sb.x, sa.y, sb.y);
+  }
+}
+
 // Carries the tangential history of every (a, b) present in the old list
 // (binary search of b in the old row of a, which is sorted by b).
 __global__ void k_hist_pairs(ContactList oldl, ContactList newl, long long old_ns) {
@@ -1082,6 +1093,13 @@ void launch_filter_emit(const DevState& d, const DetectOut& o, const ContactList
   count_launch();
   k_filter_walls<true><<<nblk(d.ns, 128), 128, 0, st>>>(d, o, outer, inner, margin, t, travel_time);
   count_launch();
+}
+
+void launch_pair_owners(const DevState& d, const ContactList& l, cudaStream_t st) {
+  if (l.n > 0 && l.pown) {
+    k_pair_owners<<<nblk(l.n, 256), 256, 0, st>>>(d, l);
+    count_launch();
+  }
 }
 
 void launch_hist_pairs(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st) {

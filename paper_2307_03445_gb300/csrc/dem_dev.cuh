@@ -18,6 +18,7 @@ struct DevState {
   const double4_32a* tp64;      // per template sphere: p (FP64), r
   const float4* tp32;       // per template sphere: p, r (float)
   const int* tmat;          // per template sphere: material
+  const float2* trm;        // per template sphere: {radius (float), material (int bits)}
   const double* tmass;      // per template
   const double* tinert;     // per template, 3 principal moments
   const float* tmassf;      // per template {mass, 1 / mass} (float)
@@ -158,6 +159,8 @@ struct DetectOut {
 struct ContactList {
   int* pa;                  // sphere a (pairs)
   uint32_t* pb;             // sphere b | kHistFlag
+  int4* pown;               // FP32_VOXEL lists the force kernel reads: per pair {owner of a,
+                            //   owner of b, template sphere of a, of b} (written at the rebuild)
   double* u;                // 3 * capacity (SoA: ux | uy | uz)
   uint32_t* row;            // ns + 1 row pointer by sphere a
   long long n, cap;
@@ -210,6 +213,8 @@ void launch_facet_finish(const DevState& d, const DetectOut& o, long long nf, in
                          cudaStream_t st);
 void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
 void launch_hist_pairs(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
+// The per-pair owner records l.pown of a finished FP32_VOXEL list.
+void launch_pair_owners(const DevState& d, const ContactList& l, cudaStream_t st);
 // Inner list from an outer list (see dem_detect.cu): the lattice points at
 // margin m into o.det, with the count of spheres past their allowance around
 // q0 in *bad (zeroed by the caller); the per-sphere counts of kept pairs and

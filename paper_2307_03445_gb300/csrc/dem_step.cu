@@ -139,26 +139,27 @@ __device__ __forceinline__ V3<float> arm32(const Side32& S) {
 
 // One side of an FP32_VOXEL sphere pair, as the pair kernel uses it: the
 // owner's voxel, the centre from that voxel's corner (the pose record), the
-// owner's offset in the voxel, the radius and the ids.  The centre difference
-// of two sides is ((voxel_b - voxel_a) << 24) + (rel_b - rel_a), in 2^-44 m.
+// radius, material and owner.  The centre difference of two sides is
+// ((voxel_b - voxel_a) << 24) + (rel_b - rel_a), in 2^-44 m.  With the owner
+// and template sphere taken from the list's per-pair record, all of these
+// loads depend on the pair alone and issue together.
 struct PairSide32 {
   int vx, vy, vz;
-  int owner, tsph;
+  int owner, mat;
   float r;
-  float4 off;
   long long rel[3];
 };
 
-__device__ __forceinline__ PairSide32 load_pair_side32(const DevState& d, uint32_t s) {
+__device__ __forceinline__ PairSide32 load_pair_side32(const DevState& d, uint32_t s, int owner,
+                                                       int tsph) {
   PairSide32 S;
-  const int2 si = d.sinfo[s];
   const uint4 rec = d.srec32[s];
-  S.owner = si.x;
-  S.tsph = si.y;
-  const int4 v = d.cvox[si.x];
+  S.owner = owner;
+  const int4 v = d.cvox[owner];
   S.vx = v.x; S.vy = v.y; S.vz = v.z;
-  S.off = d.coff[si.x];
-  S.r = d.tp32[si.y].w;
+  const float2 rm = d.trm[tsph];
+  S.r = rm.x;
+  S.mat = __float_as_int(rm.y);
   unpack_rel(rec, S.rel[0], S.rel[1], S.rel[2]);
   return S;
 }
@@ -167,9 +168,11 @@ __device__ __forceinline__ long long fix_diff(int va, int vb, long long ra, long
   return (long long)(vb - va) * (1ll << (kFixBits - kVoxLog2)) + (rb - ra);
 }
 
-__device__ __forceinline__ V3<float> arm32(const PairSide32& S) {
-  return {fix_to_float(S.rel[0]) - S.off.x, fix_to_float(S.rel[1]) - S.off.y,
-          fix_to_float(S.rel[2]) - S.off.z};
+// Lever arm R p of a pair side: its centre from the voxel corner minus the
+// owner's offset in the voxel.
+__device__ __forceinline__ V3<float> arm32(const PairSide32& S, float4 off) {
+  return {fix_to_float(S.rel[0]) - off.x, fix_to_float(S.rel[1]) - off.y,
+          fix_to_float(S.rel[2]) - off.z};
 }
 
 // Tangential history of an FP32_VOXEL pair contact: each component a
@@ -192,7 +195,8 @@ __device__ __forceinline__ void pair_force32(const DevState& d, ContactList& l, 
     const V3<float> n = {fx * inv, fy * inv, fz * inv};
     const float4 va = d.mv32[A.owner], wa = d.mw32[A.owner];
     const float4 vb = d.mv32[B.owner], wb = d.mw32[B.owner];
-    const int ma = d.tmat[A.tsph], mb = d.tmat[B.tsph];
+    const float4 offa = d.coff[A.owner], offb = d.coff[B.owner];
+    const int ma = A.mat, mb = B.mat;
     float2* uf = reinterpret_cast<float2*>(l.u);
     float2 u0 = make_float2(0.f, 0.f), u1 = u0, u2 = u0;
     if (bw & kHistFlag) {
@@ -201,8 +205,8 @@ __device__ __forceinline__ void pair_force32(const DevState& d, ContactList& l, 
       u2 = uf[2 * l.cap + i];
     }
     const float sa = A.r - 0.5f * dn, sb = B.r - 0.5f * dn;
-    const V3<float> ca = arm32(A) + sa * n;
-    const V3<float> cb = arm32(B) - sb * n;
+    const V3<float> ca = arm32(A, offa) + sa * n;
+    const V3<float> cb = arm32(B, offb) - sb * n;
     const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
     const V3<float> vB = V3<float>{vb.x, vb.y, vb.z} + cross(V3<float>{wb.x, wb.y, wb.z}, cb);
     const PairMat<float> pm = d.pm32[ma * d.nmat + mb];
@@ -236,21 +240,23 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
   if (halted(d)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long ln = l.dn[0];
-  // software pipeline: the ids of the next pair are loaded one iteration
-  // ahead, and its two pose records and {owner, template sphere} pairs are
-  // prefetched into L2 once those ids have arrived, so the dependent loads
-  // of an iteration start from L2
+  // software pipeline: the ids and owner record of the next pair are loaded
+  // one iteration ahead, and its two pose records and its b owner's voxel
+  // are prefetched into L2 once those have arrived, so the loads of an
+  // iteration (one round: pose records, voxels, radii) start from L2
   long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int a_n = 0;
   uint32_t bw_n = 0;
-  if (i0 < ln) { a_n = l.pa[i0]; bw_n = l.pb[i0]; }
+  int4 own_n = make_int4(0, 0, 0, 0);
+  if (i0 < ln) { a_n = l.pa[i0]; bw_n = l.pb[i0]; own_n = l.pown[i0]; }
   for (long long i = i0; i < ln; i += stride) {
     const int a = a_n;
     const uint32_t bw = bw_n;
     const uint32_t b = bw & ~kHistFlag;
-    if (i + stride < ln) { a_n = l.pa[i + stride]; bw_n = l.pb[i + stride]; }
-    const PairSide32 A = load_pair_side32(d, (uint32_t)a);
-    const PairSide32 B = load_pair_side32(d, b);
+    const int4 own = own_n;
+    if (i + stride < ln) { a_n = l.pa[i + stride]; bw_n = l.pb[i + stride]; own_n = l.pown[i + stride]; }
+    const PairSide32 A = load_pair_side32(d, (uint32_t)a, own.x, own.z);
+    const PairSide32 B = load_pair_side32(d, b, own.y, own.w);
     // the centre difference b - a as exact float-float metres; its high
     // parts are the float estimate used for the cheap rejection
     const ff dx = fix_to_ff_near(fix_diff(A.vx, B.vx, A.rel[0], B.rel[0]));
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
       const uint32_t bn = bw_n & ~kHistFlag;
       asm volatile("prefetch.global.L2 [%0];" :: "l"(d.srec32 + a_n));
       asm volatile("prefetch.global.L2 [%0];" :: "l"(d.srec32 + bn));
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.sinfo + bn));
+      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cvox + own_n.y));
     }
     if (!active) {
       if (bw & kHistFlag) l.pb[i] = b;  // history reset (false positive)
