@@ -108,7 +108,10 @@ typedef struct {
     void* cuda_stream;        /* cudaStream_t to run on; NULL = the library's own     */
     int device;               /* CUDA device ordinal                                   */
     /* Optional device allocator (e.g. a framework's caching allocator); both
-     * NULL = cudaMallocAsync / cudaFreeAsync on the context stream. */
+     * NULL = cudaMallocAsync / cudaFreeAsync on the context stream.  Its
+     * blocks must be 256-byte aligned, as cudaMalloc's are (the kernels move
+     * 16- and 32-byte records); a misaligned block fails the call with
+     * DEM_ERR_OOM. */
     void* (*alloc)(size_t bytes, void* user);
     void (*free)(void* ptr, void* user);
     void* alloc_user;

@@ -187,6 +187,10 @@ void* dalloc(dem_ctx* c, size_t bytes, cudaStream_t st = nullptr) {
   void* p = nullptr;
   if (c->P.alloc) {
     p = c->P.alloc(bytes, c->P.alloc_user);
+    if (p && ((uintptr_t)p & 255u)) {  // the kernels' 16- and 32-byte records need it
+      if (c->P.free) c->P.free(p, c->P.alloc_user);
+      p = nullptr;
+    }
   } else if (cudaMallocAsync(&p, bytes, st ? st : c->st) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
