@@ -65,8 +65,9 @@ def ALGO_PAIRS(ncl, ns, n_pairs):
 # margin, none in this workload) and 160 B written (offset, orientation,
 # velocity record, FP32 mirrors 32, cleared accumulators 32; the voxel only
 # when it changes); per sphere its 16-byte pose record written.
-# Pair forces: per listed pair its ids (8 B) and owner record (16 B: both
-# sides' owner and template sphere, written at the rebuild); per active
+# Pair forces: per listed pair its ids (8 B) and its record (20 B: both
+# sides' owner and radius and the pair-material row, written at the
+# rebuild); per active
 # contact the history read + write (48 B); per sphere its pose record (16 B)
 # read once; per clump voxel and offset (32 B), velocity mirrors (32 B) and
 # accumulators read + written (64 B).
@@ -75,7 +76,7 @@ def IMPL_UPDATE(ncl, ns):
 
 
 def IMPL_PAIRS(ncl, ns, n_pairs, n_active):
-    return 24 * n_pairs + 48 * n_active + 16 * ns + 128 * ncl
+    return 28 * n_pairs + 48 * n_active + 16 * ns + 128 * ncl
 
 
 # DRAM bytes (read + write) of one launch in an ncu capture of the same

@@ -126,7 +126,7 @@ struct dem_ctx {
   long long n_entry_bins = 0;    // bins of that rebuild
   // contact lists (current, next) and an audit list
   struct ListBufs {
-    Buf pa, pb, pown, u, row, ws, ww, uw, wrow, dnb;
+    Buf pa, pb, pown, ppm, u, row, ws, ww, uw, wrow, dnb;
     ContactList L{};
   } lists[5];  // 0, 1: current and next; 2: audit; 3: outer list; 4: the next outer list
   int cur = 0;
@@ -579,10 +579,12 @@ int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, 
   if ((long long)NP > L.cap || !LB.pa.p) {
     const long long cap = std::max<long long>((long long)(NP + NP / 4), 1024);
     dfree(c, LB.pa.p, st); dfree(c, LB.pb.p, st); dfree(c, LB.u.p, st); dfree(c, LB.pown.p, st);
-    LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf(); LB.pown = Buf();
+    dfree(c, LB.ppm.p, st);
+    LB.pa = Buf(); LB.pb = Buf(); LB.u = Buf(); LB.pown = Buf(); LB.ppm = Buf();
     const bool own = hist && c->P.precision != DEM_FP64;
     if (!grow(c, LB.pa, 4 * cap, 0, st) || !grow(c, LB.pb, 4 * cap, 0, st) ||
-        (hist && !grow(c, LB.u, 24 * cap, 0, st)) || (own && !grow(c, LB.pown, 16 * cap, 0, st)))
+        (hist && !grow(c, LB.u, 24 * cap, 0, st)) ||
+        (own && (!grow(c, LB.pown, 16 * cap, 0, st) || !grow(c, LB.ppm, 4 * cap, 0, st))))
       return fail(c, DEM_ERR_OOM, "pair list");
     L.cap = cap;
   }
@@ -597,6 +599,7 @@ int size_list(dem_ctx* c, int li, unsigned long long NP, unsigned long long NW, 
   L.pa = ptr<int>(LB.pa);
   L.pb = ptr<uint32_t>(LB.pb);
   L.pown = ptr<int4>(LB.pown);
+  L.ppm = ptr<int>(LB.ppm);
   L.u = ptr<double>(LB.u);
   L.row = ptr<uint32_t>(LB.row);
   L.ws = ptr<int>(LB.ws);
@@ -1575,7 +1578,7 @@ void dem_destroy(dem_ctx* c) {
   }
   dfree(c, c->b_q1.p);
   for (auto& lb : c->lists) {
-    Buf* lbs[] = {&lb.pa, &lb.pb, &lb.pown, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow, &lb.dnb};
+    Buf* lbs[] = {&lb.pa, &lb.pb, &lb.pown, &lb.ppm, &lb.u, &lb.row, &lb.ws, &lb.ww, &lb.uw, &lb.wrow, &lb.dnb};
     for (Buf* b : lbs) dfree(c, b->p);
   }
   cudaStreamSynchronize(c->st);

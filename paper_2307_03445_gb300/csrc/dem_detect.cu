@@ -834,14 +834,17 @@ __global__ void k_sort_rows(long long ns, const uint32_t* __restrict__ row, int*
   for (uint32_t i = r0; i < r1; ++i) pa[i] = (int)a;
 }
 
-// The owner clumps and template spheres of both sides of every pair, so that
-// the force kernel issues all of a pair's pose loads at once.
+// The owner clumps and radii of both sides of every pair and its row of the
+// pair-material table, so that the force kernel issues all of a pair's pose
+// loads at once and reads no per-sphere table.
 __global__ void k_pair_owners(DevState d, ContactList l) {
   const long long n = l.dn[0];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int2 sa = d.sinfo[l.pa[i]], sb = d.sinfo[l.pb[i] & ~kHistFlag];
-    l.pown[i] = make_int4(sa.x, sb.x, sa.y, sb.y);
+    const float2 ra = d.trm[sa.y], rb = d.trm[sb.y];
+    l.pown[i] = make_int4(sa.x, sb.x, __float_as_int(ra.x), __float_as_int(rb.x));
+    l.ppm[i] = __float_as_int(ra.y) * d.nmat + __float_as_int(rb.y);
   }
 }
 
@@ -1096,7 +1099,7 @@ void launch_filter_emit(const DevState& d, const DetectOut& o, const ContactList
 }
 
 void launch_pair_owners(const DevState& d, const ContactList& l, cudaStream_t st) {
-  if (l.n > 0 && l.pown) {
+  if (l.n > 0 && l.pown && l.ppm) {
     k_pair_owners<<<nblk(l.n, 256), 256, 0, st>>>(d, l);
     count_launch();
   }

@@ -159,8 +159,9 @@ struct DetectOut {
 struct ContactList {
   int* pa;                  // sphere a (pairs)
   uint32_t* pb;             // sphere b | kHistFlag
-  int4* pown;               // FP32_VOXEL lists the force kernel reads: per pair {owner of a,
-                            //   owner of b, template sphere of a, of b} (written at the rebuild)
+  int4* pown;               // FP32_VOXEL lists the force kernel reads, written at the rebuild:
+                            //   per pair {owner of a, owner of b, radius of a, of b (float bits)}
+  int* ppm;                 //   and its row of the pair-material table (ma * nmat + mb)
   double* u;                // 3 * capacity (SoA: ux | uy | uz)
   uint32_t* row;            // ns + 1 row pointer by sphere a
   long long n, cap;
@@ -213,7 +214,7 @@ void launch_facet_finish(const DevState& d, const DetectOut& o, long long nf, in
                          cudaStream_t st);
 void launch_hist_walls(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
 void launch_hist_pairs(const ContactList& oldl, ContactList& newl, long long old_ns, cudaStream_t st);
-// The per-pair owner records l.pown of a finished FP32_VOXEL list.
+// The per-pair records l.pown, l.ppm of a finished FP32_VOXEL list.
 void launch_pair_owners(const DevState& d, const ContactList& l, cudaStream_t st);
 // Inner list from an outer list (see dem_detect.cu): the lattice points at
 // margin m into o.det, with the count of spheres past their allowance around

@@ -139,27 +139,25 @@ __device__ __forceinline__ V3<float> arm32(const Side32& S) {
 
 // One side of an FP32_VOXEL sphere pair, as the pair kernel uses it: the
 // owner's voxel, the centre from that voxel's corner (the pose record), the
-// radius, material and owner.  The centre difference of two sides is
+// radius and owner.  The centre difference of two sides is
 // ((voxel_b - voxel_a) << 24) + (rel_b - rel_a), in 2^-44 m.  With the owner
-// and template sphere taken from the list's per-pair record, all of these
-// loads depend on the pair alone and issue together.
+// and radius taken from the list's per-pair record, the two loads of a side
+// depend on the pair alone and issue together.
 struct PairSide32 {
   int vx, vy, vz;
-  int owner, mat;
+  int owner;
   float r;
   long long rel[3];
 };
 
 __device__ __forceinline__ PairSide32 load_pair_side32(const DevState& d, uint32_t s, int owner,
-                                                       int tsph) {
+                                                       float r) {
   PairSide32 S;
   const uint4 rec = d.srec32[s];
   S.owner = owner;
   const int4 v = d.cvox[owner];
   S.vx = v.x; S.vy = v.y; S.vz = v.z;
-  const float2 rm = d.trm[tsph];
-  S.r = rm.x;
-  S.mat = __float_as_int(rm.y);
+  S.r = r;
   unpack_rel(rec, S.rel[0], S.rel[1], S.rel[2]);
   return S;
 }
@@ -189,14 +187,13 @@ __device__ __forceinline__ float2 hist_add(float2 u, float inc) {
 // history update, and the force and moments added to both clumps.
 __device__ __forceinline__ void pair_force32(const DevState& d, ContactList& l, long long i,
                                              uint32_t b, uint32_t bw, const PairSide32& A,
-                                             const PairSide32& B, float fx, float fy, float fz,
-                                             float dist, float dn) {
+                                             const PairSide32& B, int pmi, float fx, float fy,
+                                             float fz, float dist, float dn) {
     const float inv = __fdividef(1.f, dist);
     const V3<float> n = {fx * inv, fy * inv, fz * inv};
     const float4 va = d.mv32[A.owner], wa = d.mw32[A.owner];
     const float4 vb = d.mv32[B.owner], wb = d.mw32[B.owner];
     const float4 offa = d.coff[A.owner], offb = d.coff[B.owner];
-    const int ma = A.mat, mb = B.mat;
     float2* uf = reinterpret_cast<float2*>(l.u);
     float2 u0 = make_float2(0.f, 0.f), u1 = u0, u2 = u0;
     if (bw & kHistFlag) {
@@ -209,7 +206,7 @@ __device__ __forceinline__ void pair_force32(const DevState& d, ContactList& l, 
     const V3<float> cb = arm32(B, offb) - sb * n;
     const V3<float> vA = V3<float>{va.x, va.y, va.z} + cross(V3<float>{wa.x, wa.y, wa.z}, ca);
     const V3<float> vB = V3<float>{vb.x, vb.y, vb.z} + cross(V3<float>{wb.x, wb.y, wb.z}, cb);
-    const PairMat<float> pm = d.pm32[ma * d.nmat + mb];
+    const PairMat<float> pm = d.pm32[pmi];
     const float Rbar = __fdividef(A.r * B.r, A.r + B.r);
     const float mbar = __fdividef(va.w * vb.w, va.w + vb.w);
     const Law<float> law = contact_law<float>(pm, d.hf, n, dn, vB - vA,
@@ -240,23 +237,29 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
   if (halted(d)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long ln = l.dn[0];
-  // software pipeline: the ids and owner record of the next pair are loaded
-  // one iteration ahead, and its two pose records and its b owner's voxel
-  // are prefetched into L2 once those have arrived, so the loads of an
-  // iteration (one round: pose records, voxels, radii) start from L2
+  // software pipeline: the ids and per-pair record of the next pair are
+  // loaded one iteration ahead, so that the loads of an iteration (pose
+  // records and voxels of both sides) issue together at its start.  (L2
+  // prefetches of the next pair's pose records cost more load-unit requests
+  // than the latency they saved.)
   long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int a_n = 0;
   uint32_t bw_n = 0;
   int4 own_n = make_int4(0, 0, 0, 0);
-  if (i0 < ln) { a_n = l.pa[i0]; bw_n = l.pb[i0]; own_n = l.pown[i0]; }
+  int pm_n = 0;
+  if (i0 < ln) { a_n = l.pa[i0]; bw_n = l.pb[i0]; own_n = l.pown[i0]; pm_n = l.ppm[i0]; }
   for (long long i = i0; i < ln; i += stride) {
     const int a = a_n;
     const uint32_t bw = bw_n;
     const uint32_t b = bw & ~kHistFlag;
     const int4 own = own_n;
-    if (i + stride < ln) { a_n = l.pa[i + stride]; bw_n = l.pb[i + stride]; own_n = l.pown[i + stride]; }
-    const PairSide32 A = load_pair_side32(d, (uint32_t)a, own.x, own.z);
-    const PairSide32 B = load_pair_side32(d, b, own.y, own.w);
+    const int pmi = pm_n;
+    if (i + stride < ln) {
+      a_n = l.pa[i + stride]; bw_n = l.pb[i + stride]; own_n = l.pown[i + stride];
+      pm_n = l.ppm[i + stride];
+    }
+    const PairSide32 A = load_pair_side32(d, (uint32_t)a, own.x, __int_as_float(own.z));
+    const PairSide32 B = load_pair_side32(d, b, own.y, __int_as_float(own.w));
     // the centre difference b - a as exact float-float metres; its high
     // parts are the float estimate used for the cheap rejection
     const ff dx = fix_to_ff_near(fix_diff(A.vx, B.vx, A.rel[0], B.rel[0]));
@@ -278,12 +281,6 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
     }
     const bool active = dn > 0.f;
     if (count_active) warp_count(active, d.counters);
-    if (i + stride < ln) {
-      const uint32_t bn = bw_n & ~kHistFlag;
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.srec32 + a_n));
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.srec32 + bn));
-      asm volatile("prefetch.global.L2 [%0];" :: "l"(d.cvox + own_n.y));
-    }
     if (!active) {
       if (bw & kHistFlag) l.pb[i] = b;  // history reset (false positive)
       if (d.det_off) {
@@ -291,7 +288,7 @@ __global__ void __launch_bounds__(256) k_pairs32(DevState d, ContactList l, int 
         d.det_pair32[3 * i] = z; d.det_pair32[3 * i + 1] = z; d.det_pair32[3 * i + 2] = z;
       }
     } else {
-      pair_force32(d, l, i, b, bw, A, B, fx, fy, fz, dist, dn);
+      pair_force32(d, l, i, b, bw, A, B, pmi, fx, fy, fz, dist, dn);
     }
     // the lanes of a warp take the next pair together
     __syncwarp();
