@@ -84,7 +84,8 @@ def IMPL_PAIRS(ncl, ns, n_pairs, n_active):
 # that launch's algorithmic bytes; a launch on a bed of this family is scaled
 # by its algorithmic bytes (both grow with the clumps, spheres and pairs in
 # the same proportions).  None once the kernel changes.
-TRAFFIC = {"k_update32": None, "k_pairs32": None}
+TRAFFIC = {"k_update32": (140.305664e6 + 87.813376e6, 181879360),
+           "k_pairs32": (216.608256e6 + 41.233920e6, 202121440)}
 TRAFFIC_SRC = {k: "ncu dram__bytes_read.sum + dram__bytes_write.sum, 687,504-clump bed, scaled "
                   "by algorithmic bytes (profiles/ncu_pairs_update_bed_2M_spheres.md)"
                for k in TRAFFIC}
