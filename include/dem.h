@@ -111,7 +111,11 @@ typedef struct {
      * NULL = cudaMallocAsync / cudaFreeAsync on the context stream.  Its
      * blocks must be 256-byte aligned, as cudaMalloc's are (the kernels move
      * 16- and 32-byte records); a misaligned block fails the call with
-     * DEM_ERR_OOM. */
+     * DEM_ERR_OOM.  free is called where cudaFreeAsync would be: work queued
+     * on the context stream may still use the block, so the allocator must
+     * not hand it out again before that work is done (a caching allocator
+     * whose blocks belong to the context stream, as PyTorch's do when
+     * allocated on it, satisfies this). */
     void* (*alloc)(size_t bytes, void* user);
     void (*free)(void* ptr, void* user);
     void* alloc_user;

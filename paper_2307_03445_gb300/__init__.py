@@ -69,11 +69,14 @@ class Simulation:
         v_bound * dt * rebuild_interval.
     extra_scenes: further Scene objects sharing templates/materials/dt/g with
         the first one (batched independent systems).
+    allocator: optional (alloc, free) Python callables for the context's
+        device memory: alloc(nbytes) -> device address (256-byte aligned),
+        free(address); None = the library's stream-ordered allocator.
     """
 
     def __init__(self, scene, margin=None, rebuild_interval=10, v_bound=0.5, precision=None,
                  guard=DEM_GUARD_COUNT, device=0, stream=None, bin_size=None, max_contacts=0,
-                 extra_scenes=(), extra_walls=()):
+                 extra_scenes=(), extra_walls=(), allocator=None):
         self.lib = capi.load()
         self.scene = scene
         prec = scene.precision if precision is None else precision
@@ -107,6 +110,11 @@ class Simulation:
         p.guard = int(guard)
         p.cuda_stream = stream
         p.device = int(device)
+        if allocator is not None:
+            a_fn, f_fn = allocator
+            p.alloc = capi.ALLOC_FN(lambda n, user: a_fn(int(n)))
+            p.free = capi.FREE_FN(lambda ptr, user: f_fn(int(ptr)))
+            self._keep += [p.alloc, p.free]  # the callbacks must outlive the context
         ctx = C.c_void_p()
         rc = self.lib.dem_create(C.byref(p), C.byref(ctx))
         if rc != 0:
