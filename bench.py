@@ -116,7 +116,12 @@ def workload_name(n_clumps, n_spheres):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 100 ms.  Started before the last untimed steps
+    (its start-up would otherwise overlap the first milliseconds of the timed
+    region); mark_start() / mark_end() bracket the timed region, and the
+    summary keeps the samples taken inside it (else those within 0.25 s of
+    it, else all)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -124,6 +129,13 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __enter__(self):
         try:
@@ -149,25 +161,38 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    def _samples(self):
+        import datetime
+
+        out = []
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                out.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        return out
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        allx = self._samples()
+        window, pick = "all samples", allx
+        if self.t0 is not None and self.t1 is not None:
+            inside = [s for s in allx if self.t0 <= s[0] <= self.t1]
+            near = [s for s in allx if self.t0 - 0.25 <= s[0] <= self.t1 + 0.25]
+            if inside:
+                window, pick = "timed region", inside
+            elif near:
+                window, pick = "within 0.25 s of the timed region", near
+        if not pick:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = {nm for s in pick for nm, v in zip(names, s[3]) if v.lower() == "active"}
+        return {"sm_mhz": float(np.median([s[1] for s in pick])),
+                "sm_max_mhz": float(max(s[2] for s in pick)), "reasons": sorted(reasons),
+                "samples": len(pick), "window": window}
 
 
 # ---------------------------------------------------------------------------
@@ -542,11 +567,14 @@ def small_config_line(args, dem, workloads, world, rank, local, log):
     if ncl >= 100_000:
         sim.autotune_bins(BIN_FACTORS, reps=1)
         sim.autotune_tiles(steps=6, reps=1)
-        sim.step(args.warmup)
-    s0 = sim.state()
-    sim.reset_stats()
     with ClockSampler(local) as clk:
+        if ncl >= 100_000:
+            sim.step(args.warmup)
+        s0 = sim.state()
+        sim.reset_stats()
+        clk.mark_start()
         ms = _timed_steps(sim, stream, args.steps)
+        clk.mark_end()
     st = sim.stats()
     if world > 1:
         ms = max_over_ranks(ms, torch.device("cuda", local))
@@ -716,20 +744,22 @@ def main():
     log(f"bin autotune: factor {bin_factor} ({bin_ms})")
     tiles = sim.autotune_tiles(steps=6, reps=2)
     log(f"tile autotune: {tiles}")
-    sim.step(args.warmup)
-    sim.reset_stats()
     sim.set_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        sim.step(args.warmup)
+        sim.reset_stats()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
         torch.cuda.nvtx.range_push("timed")  # profilers select the timed launches by this range
         ev0.record(stream)
         sim.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
+        clk.mark_end()
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)

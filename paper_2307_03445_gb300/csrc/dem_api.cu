@@ -1108,8 +1108,9 @@ int take_snapshot(dem_ctx* c) {
   const size_t n = (size_t)c->ncl;
   const bool f64 = c->P.precision == DEM_FP64;
   ContactList& L = curL(c);
-  // position 32 | orientation 32 | velocity record 48 bytes per clump
-  if (!grow(c, c->s_state, 112 * (n + 1)) || !grow(c, c->s_pb, 4 * (size_t)(L.n + 1)) ||
+  // position 32 | orientation 32 | velocity record 48 | certificate reference
+  // 48 bytes per clump
+  if (!grow(c, c->s_state, 160 * (n + 1)) || !grow(c, c->s_pb, 4 * (size_t)(L.n + 1)) ||
       !grow(c, c->s_u, 24 * (size_t)(L.n + 1)) || !grow(c, c->s_ww, 4 * (size_t)(L.nw + 1)) ||
       !grow(c, c->s_uw, 24 * (size_t)(L.nw + 1)))
     return fail(c, DEM_ERR_OOM, "snapshot");
@@ -1122,6 +1123,13 @@ int take_snapshot(dem_ctx* c) {
   }
   cudaMemcpyAsync(s + 32 * n, c->b_cq.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
   cudaMemcpyAsync(s + 64 * n, c->b_cvw.p, sizeof(VelRec) * n, cudaMemcpyDeviceToDevice, c->st);
+  if (f64) {
+    cudaMemcpyAsync(s + 112 * n, c->b_ref_pos.p, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    cudaMemcpyAsync(s + 112 * n, c->b_ref_vox.p, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(s + 128 * n, c->b_ref_off.p, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+  }
+  cudaMemcpyAsync(s + 144 * n, c->b_ref_q.p, 16 * n, cudaMemcpyDeviceToDevice, c->st);
   cudaMemcpyAsync(c->s_pb.p, L.pb, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, c->st);
   for (int k = 0; k < 3; ++k)
     cudaMemcpyAsync((double*)c->s_u.p + k * L.n, L.u + k * L.cap, 8 * (size_t)L.n,
@@ -1147,6 +1155,13 @@ int restore_snapshot(dem_ctx* c) {
   }
   cudaMemcpyAsync(c->b_cq.p, s + 32 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
   cudaMemcpyAsync(c->b_cvw.p, s + 64 * n, sizeof(VelRec) * n, cudaMemcpyDeviceToDevice, c->st);
+  if (f64) {
+    cudaMemcpyAsync(c->b_ref_pos.p, s + 112 * n, 32 * n, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    cudaMemcpyAsync(c->b_ref_vox.p, s + 112 * n, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(c->b_ref_off.p, s + 128 * n, 16 * n, cudaMemcpyDeviceToDevice, c->st);
+  }
+  cudaMemcpyAsync(c->b_ref_q.p, s + 144 * n, 16 * n, cudaMemcpyDeviceToDevice, c->st);
   cudaMemcpyAsync(L.pb, c->s_pb.p, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, c->st);
   for (int k = 0; k < 3; ++k)
     cudaMemcpyAsync(L.u + k * L.cap, (double*)c->s_u.p + k * L.n, 8 * (size_t)L.n,
@@ -1156,9 +1171,10 @@ int restore_snapshot(dem_ctx* c) {
     cudaMemcpyAsync(L.uw + k * L.capw, (double*)c->s_uw.p + k * L.nw, 8 * (size_t)L.nw,
                     cudaMemcpyDeviceToDevice, c->st);
   c->step = c->snap_step;
-  // accumulators are zero after every update; poses, mirrors and walls follow the state
+  // accumulators are zero after every update; poses, mirrors and walls follow
+  // the state; the motion bounds hold for the restored certificate reference
   c->D.cmargin = nullptr;
-  launch_update(c->D, false, c->step, c->margin, false, c->st);
+  launch_update(c->D, false, c->step, c->margin, true, c->st);
   return cuda_check(c, "restore");
 }
 

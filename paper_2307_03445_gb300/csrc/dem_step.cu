@@ -12,6 +12,12 @@
 // The update kernel integrates Eq. (5) for a block of clumps, then, with the
 // new orientation held as a float-float rotation matrix in shared memory,
 // recomputes the pose records of all spheres of those clumps.
+//
+// FP32_VOXEL specifics: the pair kernel takes each pair's owners, radii and
+// pair-material row from the list's per-pair record (written at the
+// rebuild) and keeps the tangential history as float-float; the update
+// kernel keeps a per-clump motion bound since the last rebuild, which decides
+// when the exact displacement certificate has to read that rebuild's state.
 #include <algorithm>
 
 #include "dem_dev.cuh"
@@ -838,8 +844,10 @@ __global__ void __launch_bounds__(B, 896 / B) k_update32(DevState d, float margi
     if (!INTEG) {
       wf_new = {d2f(w.x), d2f(w.y), d2f(w.z)};
       vf_new[0] = d2f(v.x); vf_new[1] = d2f(v.y); vf_new[2] = d2f(v.z);
-      // a state set from outside: its motion since the last rebuild is unknown
-      d.coff[c] = make_float4(off.x, off.y, off.z, __int_as_float(0x7f800000));
+      // a state set from outside: its motion since the last rebuild is
+      // unknown (CERT here: a state restored with its certificate reference,
+      // whose motion bound still holds)
+      if (!CERT) d.coff[c] = make_float4(off.x, off.y, off.z, __int_as_float(0x7f800000));
     }
     const V3<float> ww = mat_mul(Rf, wf_new);
     d.mv32[c] = make_float4(vf_new[0], vf_new[1], vf_new[2], mass);
@@ -1180,7 +1188,12 @@ void launch_force_walls(const DevState& d, ContactList& l, double t, bool count_
 template <int B>
 void launch_update32(const DevState& d, bool integrate, bool cert, float margin, cudaStream_t st) {
   const unsigned g = nblk(d.ncl, B);
-  if (!integrate) k_update32<B, false, false><<<g, B, 0, st>>>(d, margin);
+  // without integration, cert = true keeps the motion bounds (a state restored
+  // together with its certificate reference)
+  if (!integrate) {
+    if (cert) k_update32<B, false, true><<<g, B, 0, st>>>(d, margin);
+    else k_update32<B, false, false><<<g, B, 0, st>>>(d, margin);
+  }
   else if (cert) k_update32<B, true, true><<<g, B, 0, st>>>(d, margin);
   else k_update32<B, true, false><<<g, B, 0, st>>>(d, margin);
   count_launch();
